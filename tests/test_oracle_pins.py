@@ -1,0 +1,470 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+None of these re-types an oracle formula: each checks an identity, a closed
+form, a printed table of the paper or a physical law that a slip in the oracle
+(a dropped term, a wrong sign, a transposed index) would break.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_02459_gb300 import inputs
+
+CS2 = 1.0 / 3.0
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---- lattice and moment matrix (Sec. III.A Eqs. D2Q9, D2Q9MRT) -------------
+
+def test_lattice_isotropy():
+    c, w = oracle.lattice()
+    assert np.isclose(w.sum(), 1.0, atol=1e-15)
+    assert np.allclose(w @ c, 0.0, atol=1e-15)
+    cc = np.einsum("q,qa,qb->ab", w, c, c)
+    assert np.allclose(cc, CS2 * np.eye(2), atol=1e-15)
+    c4 = np.einsum("q,qa,qb,qc,qd->abcd", w, c, c, c, c)
+    d = np.eye(2)
+    iso = CS2 ** 2 * (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+                      + np.einsum("ad,bc->abcd", d, d))
+    assert np.allclose(c4, iso, atol=1e-15)
+    # velocities are the unit axis and diagonal directions, antipodes paired
+    assert set(map(tuple, c.tolist())) == {(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1),
+                                            (1, 1), (-1, 1), (-1, -1), (1, -1)}
+
+
+def test_mrt_matrix_structure():
+    c, w = oracle.lattice()
+    M = oracle.mrt_matrix()
+    Minv = oracle.mrt_inverse()
+    assert np.allclose(M @ Minv, np.eye(9), atol=1e-14)
+    assert np.allclose(Minv @ M, np.eye(9), atol=1e-14)
+    G = M @ M.T
+    assert np.allclose(G, np.diag(np.diag(G)), atol=0)          # rows orthogonal
+    assert np.allclose(np.diag(G), [9, 36, 36, 6, 12, 6, 12, 4, 4])
+    # rows tie to the lattice: density, energy, momentum, stresses
+    c2 = (c ** 2).sum(1)
+    assert np.array_equal(M[0], np.ones(9))
+    assert np.array_equal(M[1], 3 * c2 - 4)
+    assert np.array_equal(M[3], c[:, 0]) and np.array_equal(M[5], c[:, 1])
+    assert np.array_equal(M[7], c[:, 0] ** 2 - c[:, 1] ** 2)
+    assert np.array_equal(M[8], c[:, 0] * c[:, 1])
+
+
+# ---- equilibria and sources (Eqs. feq_CH, geq, Fi, Gi, mG1) ----------------
+
+@pytest.mark.parametrize("seed", range(5))
+def test_feq_moments(seed):
+    rng = np.random.default_rng(seed)
+    phi, mu, ux, uy, eta = rng.uniform(-1, 1), rng.normal() * 1e-3, *rng.normal(size=2) * 0.05, 2.0
+    c, _ = oracle.lattice()
+    fe = oracle.feq(phi, mu, ux, uy, eta)
+    u = np.array([ux, uy])
+    assert np.isclose(fe.sum(), phi, atol=1e-15)
+    assert np.allclose(fe @ c, phi * u, atol=1e-15)
+    assert np.allclose(np.einsum("q,qa,qb->ab", fe, c, c),
+                       eta * mu * CS2 * np.eye(2) + phi * np.outer(u, u), atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_geq_moments(seed):
+    rng = np.random.default_rng(100 + seed)
+    p, ux, uy = rng.normal() * 1e-2, *rng.normal(size=2) * 0.05
+    c, _ = oracle.lattice()
+    ge = oracle.geq(p, ux, uy)
+    u = np.array([ux, uy])
+    assert np.isclose(ge.sum(), p / CS2, atol=1e-15)
+    assert np.allclose(ge @ c, u, atol=1e-15)
+    assert np.allclose(np.einsum("q,qa,qb->ab", ge, c, c), p * np.eye(2) + np.outer(u, u), atol=1e-15)
+    # App. A Eq. (mg0): conserved moments of g_eq are (p/cs2, u_x, u_y)
+    m = oracle.mrt_matrix() @ ge
+    assert np.allclose(m[[0, 3, 5]], [p / CS2, ux, uy], atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_source_moments_match_appendix_form(seed):
+    rng = np.random.default_rng(200 + seed)
+    rho = rng.uniform(1, 1000)
+    F = rng.normal(size=2) * 1e-3
+    u = rng.normal(size=2) * 0.05
+    dp = rng.normal(size=2) * 1e-4
+    G = oracle.src_ns(rho, F[0], F[1], u[0], u[1], dp[0], dp[1])
+    b = F / rho - dp
+    # App. A Eq. (mG1), with (F - grad p)/rho read as F/rho - grad p
+    expect = np.array([0.0, 6 * b @ u, -6 * b @ u, F[0] / rho, -F[0] / rho, F[1] / rho,
+                       -F[1] / rho, 2 * (b[0] * u[0] - b[1] * u[1]), b[1] * u[0] + b[0] * u[1]])
+    assert np.allclose(oracle.mrt_matrix() @ G, expect, atol=1e-16, rtol=1e-12)
+    # CH source: zero mass, first moment phi * a
+    c, _ = oracle.lattice()
+    phi, a = rng.uniform(-1, 1), rng.normal(size=2) * 1e-3
+    Fi = oracle.src_ch(phi, a[0], a[1])
+    assert abs(Fi.sum()) < 1e-18
+    assert np.allclose(Fi @ c, phi * a, atol=1e-18)
+
+
+def test_collision_closed_forms():
+    rng = np.random.default_rng(7)
+    f = rng.uniform(0, 0.2, 9)
+    fe = oracle.feq(0.3, 1e-3, 0.02, -0.01, 2.0)
+    F = oracle.src_ch(0.3, 1e-3, 2e-3)
+    # all rates 1: f* = feq + F/2
+    assert np.allclose(oracle.collide_f(f, fe, F, np.ones(9)), fe + F / 2, atol=1e-15)
+    # all rates 0: f* = f + F
+    assert np.allclose(oracle.collide_f(f, fe, F, np.zeros(9)), f + F, atol=1e-15)
+    # equal rates 1/tau: the single-relaxation-time (BGK) update
+    tau = 0.8
+    srt = f - (f - fe) / tau + (1 - 1 / (2 * tau)) * F
+    assert np.allclose(oracle.collide_f(f, fe, F, np.full(9, 1 / tau)), srt, atol=1e-15)
+    # s_0 = 1: the zeroth moment becomes the equilibrium's (corrected phi)
+    s = np.array([1, 1.2, 1.4, 1 / 0.65, 1.1, 1 / 0.65, 1.3, 1.5, 1.6])
+    assert np.isclose(oracle.collide_f(f, fe, F, s).sum(), fe.sum(), atol=1e-15)
+    # NS collision with equal filtered and unfiltered equilibria reduces to BGK/MRT form
+    g = rng.uniform(0, 0.2, 9)
+    ge = oracle.geq(1e-3, 0.02, 0.01)
+    G = oracle.src_ns(5.0, 1e-4, -2e-4, 0.02, 0.01, 1e-5, 0.0)
+    assert np.allclose(oracle.collide_g(g, ge, ge, G, np.full(9, 1 / tau)),
+                       g - (g - ge) / tau + (1 - 1 / (2 * tau)) * G, atol=1e-15)
+    # rates 1: the non-equilibrium part is discarded whatever the unfiltered state
+    ge2 = oracle.geq(5e-3, -0.03, 0.0)
+    assert np.allclose(oracle.collide_g(g, ge, ge2, G, np.ones(9)), ge + G / 2, atol=1e-15)
+
+
+# ---- streaming --------------------------------------------------------------
+
+def test_stream_periodic_is_shift():
+    rng = np.random.default_rng(3)
+    fs = rng.normal(size=(9, 6, 7))
+    c, _ = oracle.lattice()
+    out = oracle.stream(fs)
+    for q in range(9):
+        assert np.array_equal(out[q], np.roll(fs[q], shift=(c[q, 1], c[q, 0]), axis=(0, 1)))
+
+
+def test_stream_bounce_back_walls():
+    rng = np.random.default_rng(4)
+    fs = rng.normal(size=(9, 5, 6))
+    c, _ = oracle.lattice()
+    out = oracle.stream(fs, px=1, py=0)
+    assert np.isclose(out.sum(), fs.sum(), rtol=1e-15)          # walls conserve mass
+    opp = [int(np.where((c == -c[q]).all(1))[0][0]) for q in range(9)]
+    for q in range(9):
+        if c[q, 1] == 1:   # enters the bottom row from below the wall
+            assert np.array_equal(out[q, 0], fs[opp[q], 0])
+        if c[q, 1] == -1:
+            assert np.array_equal(out[q, -1], fs[opp[q], -1])
+
+
+# ---- stencils (Eqs. dicretized, fourOrder_FDM) ------------------------------
+
+@pytest.mark.parametrize("kx,ky", [(1, 2), (3, 1), (5, 4)])
+def test_isotropic_stencils_on_plane_waves(kx, ky):
+    nx, ny = 24, 20
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    ax, ay = 2 * math.pi * kx / nx, 2 * math.pi * ky / ny
+    f = np.sin(ax * x + ay * y + 0.3)
+    gx, gy = oracle.grad_iso(f)
+    # exact: d_x -> sin(ax)(2 + cos(ay))/3 on e^{i k.x}
+    assert np.allclose(gx, math.sin(ax) * (2 + math.cos(ay)) / 3 * np.cos(ax * x + ay * y + 0.3), atol=1e-13)
+    assert np.allclose(gy, math.sin(ay) * (2 + math.cos(ax)) / 3 * np.cos(ax * x + ay * y + 0.3), atol=1e-13)
+    lap = oracle.lap_iso(f)
+    sym = 6 * (2 / 9 * (math.cos(ax) + math.cos(ay)) + math.cos(ax) * math.cos(ay) / 9 - 5 / 9)
+    assert np.allclose(lap, sym * f, atol=1e-13)
+
+
+@pytest.mark.parametrize("k", [1, 2, 5])
+def test_fd4_stencils_on_plane_waves(k):
+    nx, ny = 30, 18
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    a = 2 * math.pi * k / nx
+    b = 2 * math.pi * 2 / ny
+    f = np.cos(a * x) * np.sin(b * y)
+    gx, gy = oracle.grad_fd4(f)
+    da = (8 * math.sin(a) - math.sin(2 * a)) / 6
+    db = (8 * math.sin(b) - math.sin(2 * b)) / 6
+    assert np.allclose(gx, -da * np.sin(a * x) * np.sin(b * y), atol=1e-13)
+    assert np.allclose(gy, db * np.cos(a * x) * np.cos(b * y), atol=1e-13)
+    lap = oracle.lap_fd4(f)
+    s2 = lambda t: (32 * math.cos(t) - 2 * math.cos(2 * t) - 30) / 12
+    assert np.allclose(lap, (s2(a) + s2(b)) * f, atol=1e-13)
+
+
+def test_fd4_exact_on_quartics():
+    nx, ny = 16, 16
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    f = 0.01 * x ** 4 - 0.2 * x ** 3 * y + x * y ** 2 - 3 * y + 0.5
+    gx, gy = oracle.grad_fd4(f)
+    lap = oracle.lap_fd4(f)
+    s = np.s_[2:-2, 2:-2]                  # nodes whose stencils do not wrap
+    assert np.allclose(gx[s], (0.04 * x ** 3 - 0.6 * x ** 2 * y + y ** 2)[s], atol=1e-10)
+    assert np.allclose(gy[s], (-0.2 * x ** 3 + 2 * x * y - 3)[s], atol=1e-10)
+    assert np.allclose(lap[s], (0.12 * x ** 2 - 1.2 * x * y + 2 * x)[s], atol=1e-10)
+
+
+def test_iso_exact_on_quadratics():
+    nx, ny = 10, 10
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    f = 0.3 * x ** 2 - 0.1 * x * y + 0.7 * y ** 2 + x
+    gx, gy = oracle.grad_iso(f)
+    s = np.s_[1:-1, 1:-1]
+    assert np.allclose(gx[s], (0.6 * x - 0.1 * y + 1)[s], atol=1e-12)
+    assert np.allclose(gy[s], (-0.1 * x + 1.4 * y)[s], atol=1e-12)
+    assert np.allclose(oracle.lap_iso(f)[s], 2.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("parity", [1, -1])
+def test_wall_mirror_stencils_on_wall_harmonics(parity):
+    """Halfway-wall mirror ghosts: cos(m pi (y+1/2)/H) is even and sin(...) odd
+    about both walls (y=-1/2, H-1/2), so stencils with mirrored ghosts must
+    reproduce the plane-wave closed forms on every row, wall rows included."""
+    nx, H, m, kx = 12, 20, 3, 2
+    y, x = np.mgrid[0:H, 0:nx].astype(float)
+    ax, ay = 2 * math.pi * kx / nx, math.pi * m / H
+    wall = (np.cos if parity > 0 else np.sin)(ay * (y + 0.5))
+    dwall = -np.sin(ay * (y + 0.5)) if parity > 0 else np.cos(ay * (y + 0.5))
+    f = np.cos(ax * x) * wall
+    gx, gy = oracle.grad_iso(f, py=0, parity=parity)
+    assert np.allclose(gx, -math.sin(ax) * (2 + math.cos(ay)) / 3 * np.sin(ax * x) * wall, atol=1e-13)
+    assert np.allclose(gy, math.sin(ay) * (2 + math.cos(ax)) / 3 * np.cos(ax * x) * dwall, atol=1e-13)
+    sym = 6 * (2 / 9 * (math.cos(ax) + math.cos(ay)) + math.cos(ax) * math.cos(ay) / 9 - 5 / 9)
+    assert np.allclose(oracle.lap_iso(f, py=0, parity=parity), sym * f, atol=1e-13)
+    gx4, gy4 = oracle.grad_fd4(f, py=0, parity=parity)
+    d1 = lambda t: (8 * math.sin(t) - math.sin(2 * t)) / 6
+    assert np.allclose(gy4, d1(ay) * np.cos(ax * x) * dwall, atol=1e-13)
+    d = oracle.filter_coeffs(11)
+    D = lambda k: d[0] + 2 * sum(d[j] * math.cos(j * k) for j in range(1, 6))
+    out = oracle.filter_field(f, 11, 0.5, py=0, parity=parity)
+    assert np.allclose(out, (1 - 0.5 * (D(ax) + D(ay))) * f, atol=1e-13)
+
+
+# ---- selective filter (Eq. filter, App. B) ----------------------------------
+
+def test_filter_coefficients_match_printed_table():
+    table = np.loadtxt(os.path.join(GOLDEN, "selective_filter_appB.txt"))
+    for col, order in enumerate((5, 7, 9, 11)):
+        assert np.array_equal(oracle.filter_coeffs(order), table[:, col])
+
+
+@pytest.mark.parametrize("order", [5, 7, 9, 11])
+def test_filter_coefficient_identities(order):
+    d = oracle.filter_coeffs(order)
+    m = np.arange(1, 6)
+    assert abs(d[0] + 2 * d[1:].sum()) < 1e-11                       # constants pass
+    assert abs(d[0] + 2 * ((-1.0) ** m * d[1:]).sum() - 1.0) < 1e-11  # 2-dx wave removed at a=1
+
+
+@pytest.mark.parametrize("order", [5, 11])
+def test_filter_transfer_function(order):
+    nx, ny = 32, 24
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    d = oracle.filter_coeffs(order)
+    D = lambda k: d[0] + 2 * sum(d[m] * math.cos(m * k) for m in range(1, 6))
+    for kx, ky in [(1, 1), (4, 3), (16, 12)]:
+        ax, ay = 2 * math.pi * kx / nx, 2 * math.pi * ky / ny
+        f = np.cos(ax * x + ay * y)
+        out = oracle.filter_field(f, order, 0.5)
+        assert np.allclose(out, (1 - 0.5 * (D(ax) + D(ay))) * f, atol=1e-13)
+    cb = (-1.0) ** (x + y)
+    assert np.abs(oracle.filter_field(cb, order, 0.5)).max() < 1e-11
+    c = np.full((ny, nx), 2.5)
+    assert np.allclose(oracle.filter_field(c, order, 0.5, py=0), 2.5, atol=1e-14)
+
+
+# ---- finite-difference correction step (Eqs. step2, TVD-3order) -------------
+
+@pytest.mark.parametrize("c", [-0.3, 0.1, -1.2])
+def test_rk3_linear_growth_factor(c):
+    phibar = np.linspace(-1, 1, 7)
+    out = oracle.rk3(phibar, lambda psi: c * psi)
+    assert np.allclose(out, (1 + c + c * c / 2 + c ** 3 / 6) * phibar, rtol=1e-14, atol=1e-15)
+
+
+def test_fd_rhs_conservative_and_constant():
+    prm = inputs.base_params(sigma=1e-2, lam=0.05)
+    phi, _, _, _ = inputs.random_fields(20, 16, seed=11)
+    for py in (1, 0):
+        prm["periodic_y"] = py
+        L = oracle.fd_rhs(phi, prm)
+        assert abs(L.sum()) < 1e-14 * np.abs(L).sum() + 1e-16
+    prm["periodic_y"] = 1
+    assert np.abs(oracle.fd_rhs(np.full((8, 8), 0.3), prm)).max() < 1e-16
+
+
+def test_fd_rhs_vanishes_on_tanh_profile_at_fourth_order():
+    """J_phi and q vanish on the continuum profile tanh(2r/W) (Eq. equilibrium_profile)."""
+    errs = []
+    for W in (4.0, 8.0):
+        ny = int(16 * W)
+        y = np.arange(ny, dtype=float)
+        prof = np.tanh(2 * (y - ny / 2 + 0.25) / W)
+        phi = np.repeat(prof[:, None], 8, axis=1)
+        prm = inputs.base_params(W=W, sigma=1e-2, lam=0.05, periodic_y=0)
+        errs.append(np.abs(oracle.fd_rhs(phi, prm)).max())
+    assert errs[0] < 2e-3
+    assert errs[1] < errs[0] / 8.0         # fourth-order truncation (ideal 16x)
+
+
+def test_flux_correction_removes_normal_diffusion():
+    """q = -M (grad mu . n) n cancels the normal part of the CH diffusion flux
+    (Sec. II.A): a 1-D non-equilibrium profile then barely evolves, unlike the
+    original CH equation (q off) which diffuses it toward equilibrium."""
+    ny, nx = 48, 4
+    y = np.arange(ny, dtype=float)
+    phi0 = np.repeat(np.tanh(2 * (y - 24) / 8.0)[:, None], nx, 1)   # wider than W = 4
+    z = np.zeros((ny, nx))
+    change = {}
+    for fc in (1, 0):
+        prm = inputs.base_params(lam=0.0, flux_correction=fc, sigma=1e-2, rho_H=1.0,
+                                 rho_L=1.0, periodic_y=0)
+        s = oracle.Sim(prm, phi0, z, z, z)
+        s.step(200)
+        change[fc] = np.abs(s.fields()[0] - phi0).max()
+    assert change[0] > 5e-3
+    assert change[1] < 0.25 * change[0]
+
+
+# ---- whole method: invariants and physical laws -----------------------------
+
+@pytest.mark.parametrize("py", [1, 0])
+def test_volume_conserved_to_roundoff(py):
+    phi, p, ux, uy = inputs.random_fields(24, 20, seed=5)
+    prm = inputs.base_params(rho_H=10.0, periodic_y=py, gy=-1e-5 if py == 0 else 0.0)
+    s = oracle.Sim(prm, phi, p, ux, uy)
+    d0 = s.diagnostics()[0]
+    s.step(60)
+    assert abs(s.diagnostics()[0] - d0) < 1e-12 * np.abs(phi).sum()
+
+
+def test_flat_interface_stays_put():
+    """A flat tanh interface (Eq. equilibrium_profile) at rest: no flow arises,
+    the interface does not move, and the profile only relaxes (by a
+    truncation-sized, saturating amount) to the lattice's own equilibrium."""
+    prm = inputs.base_params(rho_H=100.0, sigma=1e-2, periodic_y=0)
+    phi0 = inputs.flat_interface(8, 40, 20.0, prm["W"])
+    z = np.zeros_like(phi0)
+    s = oracle.Sim(prm, phi0, z, z, z)
+    s.step(50)
+    d50 = np.abs(s.fields()[0] - phi0).max()
+    s.step(100)
+    phi150 = s.fields()[0]
+    s.step(50)
+    phi, p, ux, uy = s.fields()
+    assert max(np.abs(ux).max(), np.abs(uy).max()) < 1e-15
+    assert np.abs(phi - phi0).max() < 2e-2
+    assert np.abs(phi - phi150).max() < 0.25 * d50
+    col = phi[:, 3]
+    k = np.where((col[:-1] > 0) & (col[1:] <= 0))[0][0]
+    y0 = k + col[k] / (col[k] - col[k + 1])
+    assert abs(y0 - 20.0) < 1e-6
+    assert phi.max() < 1 + 1e-3 and phi.min() > -1 - 1e-3
+
+
+@pytest.mark.parametrize("order", [0, 11])
+def test_shear_wave_viscous_decay(order):
+    """Single phase: u_x = U sin(k y) decays at rate nu k^2, nu = cs2 (tau_g - 1/2)
+    (Sec. III.B below Eq. dynamic_vis), times the filter factor 1 - a D(k) per
+    step (Eq. filter) with D from the printed App. B coefficients."""
+    n, nu, a = 32, 0.05, 0.5
+    prm = inputs.base_params(rho_H=3.0, rho_L=1.0, nu_H=nu, nu_L=nu, filter_order=order, filter_a=a)
+    y = np.mgrid[0:n, 0:n][0].astype(float)
+    k = 2 * math.pi / n
+    z = np.zeros((n, n))
+    s = oracle.Sim(prm, np.ones((n, n)), z, 1e-3 * np.sin(k * y), z)
+    T = 150
+    amps = []
+    for _ in range(2):
+        s.step(T)
+        ux = s.fields()[2]
+        amps.append((ux * np.sin(k * y)).sum() / (np.sin(k * y) ** 2).sum())
+    rate = math.log(amps[0] / amps[1]) / T
+    d = np.loadtxt(os.path.join(GOLDEN, "selective_filter_appB.txt"))[:, 3]
+    D = d[0] + 2 * sum(d[m] * math.cos(m * k) for m in range(1, 6)) if order else 0.0
+    expect = nu * k * k - math.log(1 - a * D)
+    assert abs(rate / expect - 1) < 6e-3
+
+
+def test_hydrostatic_pressure_gradient():
+    """Single fluid between walls under gravity: grad p = g (kinematic pressure)."""
+    nx, ny = 4, 24
+    g = -1e-5
+    prm = inputs.base_params(rho_H=5.0, nu_H=0.1, nu_L=0.1, gy=g, periodic_y=0)
+    phi0 = np.ones((ny, nx))
+    z = np.zeros((ny, nx))
+    s = oracle.Sim(prm, phi0, z, z, z)
+    s.step(3000)
+    _, p, ux, uy = s.fields()
+    slope = np.polyfit(np.arange(4, ny - 4), p[4:ny - 4, 0], 1)[0]
+    assert abs(slope / g - 1) < 1e-2
+    assert np.abs(uy).max() < 1e-3 * abs(g) * ny * ny
+
+
+def test_galilean_drop_translation():
+    """A drop in a uniform stream moves with it (Sec. IV.B setup, full coupled model)."""
+    n, R, U = 48, 10.0, 0.02
+    prm = inputs.base_params(rho_H=10.0, sigma=1e-2)
+    phi0 = inputs.drop(n, n, R, n / 2, n / 2, prm["W"])
+    z = np.zeros((n, n))
+    s = oracle.Sim(prm, phi0, z, np.full((n, n), U), z)
+    T = 300
+    s.step(T)
+    phi = s.fields()[0]
+    x = np.arange(n, dtype=float)
+    w0, w1 = (1 + phi0) / 2, (1 + phi) / 2
+    cx0 = (w0.sum(0) * x).sum() / w0.sum()
+    cx1 = (w1.sum(0) * x).sum() / w1.sum()
+    assert abs((cx1 - cx0) / (U * T) - 1) < 0.02
+
+
+@pytest.mark.slow
+def test_laplace_law():
+    """Static drop: pressure jump (rho p) across the interface equals sigma/R (Sec. IV.C)."""
+    n, R, sigma = 48, 12.0, 2e-3
+    prm = inputs.base_params(rho_H=10.0, sigma=sigma)
+    phi0 = inputs.drop(n, n, R, n / 2, n / 2, prm["W"])
+    z = np.zeros((n, n))
+    s = oracle.Sim(prm, phi0, z, z, z)
+    s.step(1200)
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    r = np.hypot(x - n / 2, y - n / 2)
+    jumps = []
+    for _ in range(8):
+        s.step(50)
+        phi, p, _, _ = s.fields()
+        rho = 1 + 9 * (1 + np.clip(phi, -1, 1)) / 2
+        pp = rho * p
+        jumps.append(pp[r < R - 4].mean() - pp[r > R + 6].mean())
+    assert abs(np.mean(jumps) / (sigma / R) - 1) < 0.08
+
+
+@pytest.mark.slow
+def test_layered_channel_viscous_stress():
+    """Two fluids layered between walls driven by a body force along x: the
+    steady profile solves d/dy(mu du/dy) = -rho g_x (pins F_nu, the viscosity
+    interpolation and the walls)."""
+    nx, ny, g = 4, 32, 1e-6
+    prm = inputs.base_params(rho_H=4.0, rho_L=1.0, nu_H=0.1, nu_L=0.2, sigma=1e-3,
+                             gx=g, periodic_y=0)
+    y = np.arange(ny, dtype=float)
+    prof = -np.tanh(2 * (y - 8) / 4) * np.tanh(2 * (y - 24) / 4)   # heavy in the middle band
+    phi0 = np.repeat(prof[:, None], nx, axis=1)
+    z = np.zeros((ny, nx))
+    s = oracle.Sim(prm, phi0, z, z, z)
+    s.step(12000)
+    phi, _, ux, _ = s.fields()
+    ph = np.clip(phi[:, 0], -1, 1)
+    rho = 4.0 * (1 + ph) / 2 + 1.0 * (1 - ph) / 2
+    mu = 0.4 * (1 + ph) / 2 + 0.2 * (1 - ph) / 2
+    # walls at y = -1/2 and ny - 1/2; shear mu u' = g (C - int rho)
+    yf = np.linspace(-0.5, ny - 0.5, 64001)
+    rf, mf = np.interp(yf, y, rho), np.interp(yf, y, mu)
+    dy = yf[1] - yf[0]
+    cum = np.concatenate([[0.0], np.cumsum(0.5 * (rf[1:] + rf[:-1]) * dy)])
+    # the constant makes u vanish on both walls: int (C - cum)/mu dy = 0
+    C = np.trapezoid(cum / mf, yf) / np.trapezoid(1.0 / mf, yf)
+    dudy = g * (C - cum) / mf
+    uf = np.concatenate([[0.0], np.cumsum(0.5 * (dudy[1:] + dudy[:-1]) * dy)])
+    u_ref = np.interp(y, yf, uf)
+    num = ux[:, 0]
+    assert abs(num.max() / u_ref.max() - 1) < 3e-3
+    assert np.abs(num - u_ref).max() < 6e-3 * u_ref.max()
