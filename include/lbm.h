@@ -1,0 +1,183 @@
+/*
+ * lbm.h -- C ABI of the GB300 fractional-step MRT lattice Boltzmann solver.
+ *
+ * The library advances the two-phase model of Zhang, Guo & Li, "A fractional
+ * step lattice Boltzmann model for two phase flows with large density
+ * differences" (arXiv:1812.02459) on one CUDA device:
+ *   - Sec. III.A: MRT lattice Boltzmann equation for the Cahn-Hilliard
+ *     sub-equation (Eqs. distribution_CH, feq_CH, collison, D2Q9MRT, Fi);
+ *   - Sec. III.A: finite-difference TVD-RK3 step for the profile and flux
+ *     correction d_t phi = div(lambda J_phi + q) (Eqs. step2, TVD-3order,
+ *     fourOrder_FDM);
+ *   - Sec. III.B: velocity-based MRT lattice Boltzmann equation for the
+ *     incompressible Navier-Stokes equations with the forcing of
+ *     Eqs. (reformNS), (Gi), (u), solved by Picard sweeps;
+ *   - Sec. III.B: explicit selective filter of (p, u) (Eq. filter, App. B).
+ *
+ * Conventions shared by every call:
+ *   - Host fields are row-major double arrays [ny][nx], x = column i,
+ *     y = row j, lattice units (dx = dt = 1).  Population sets are [9][ny][nx]
+ *     in the direction order c0=(0,0) c1=(1,0) c2=(0,1) c3=(-1,0) c4=(0,-1)
+ *     c5=(1,1) c6=(-1,1) c7=(-1,-1) c8=(1,-1) (Sec. III.A Eq. D2Q9).
+ *   - Axes with periodic_* = 0 carry halfway bounce-back no-slip walls at
+ *     -1/2 and n-1/2; stencils see mirrored ghosts there (phi, mu, p even,
+ *     u odd).
+ *   - The handle owns every device buffer it allocates (cudaMalloc at
+ *     lbm_create, cudaFree at lbm_destroy).  The caller owns every pointer it
+ *     passes; no call keeps or aliases a caller pointer after it returns.
+ *   - Every call returns an lbm_status; no C++ exception crosses the ABI.
+ *     After an error, lbm_last_error() describes it.  CUDA errors from
+ *     earlier asynchronous work surface at the next synchronising call.
+ *   - Work is issued on the CUDA stream given to lbm_create (NULL = the
+ *     legacy default stream).  lbm_step is asynchronous; calls that return
+ *     host data synchronise that stream.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_NDIAG 11
+#define LBM_MIN_EXTENT 12   /* smallest nx, ny: the widest stencil halo */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,        /* invalid argument or parameter */
+    LBM_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+    LBM_ERR_OOM = 3,        /* device allocation failed */
+    LBM_ERR_NONFINITE = 4,  /* a field holds NaN or Inf */
+    LBM_ERR_RANGE = 5,      /* phi left [-1-delta, 1+delta] */
+    LBM_ERR_STATE = 6       /* call not valid for this handle */
+} lbm_status;
+
+typedef enum {
+    LBM_FP64 = 0,           /* populations and arithmetic in double */
+    LBM_FP32 = 1,           /* populations and arithmetic in float */
+    LBM_MIX_BF16 = 2,       /* populations stored as bf16, arithmetic in float */
+    LBM_MIX_FP16 = 3        /* populations stored as fp16, arithmetic in float */
+} lbm_precision;
+
+typedef struct {
+    int nx, ny;             /* nodes per axis, each >= LBM_MIN_EXTENT */
+    int periodic_x;         /* 1 periodic, 0 no-slip walls */
+    int periodic_y;
+    int precision;          /* an lbm_precision */
+} lbm_grid;
+
+typedef struct {
+    double M;               /* CH mobility (Sec. II.A Eq. final_mCHE) */
+    double eta;             /* CH equilibrium parameter; tau_f = 1/2 + M/(eta cs^2) (Eq. mobility) */
+    double W;               /* interface width (Eq. equilibrium_profile) */
+    double sigma;           /* surface tension: kappa = 3 sigma W/8, beta = 3 sigma/(4W) (Sec. II.A) */
+    double lambda;          /* weight of the profile flux J_phi in J_d = lambda J_phi + q (Sec. IV.B) */
+    int flux_correction;    /* 1 includes q = -M (grad mu . n) n, 0 drops it */
+    double rho_H, rho_L;    /* densities at phi = +1 and phi = -1 (Eq. rho) */
+    double nu_H, nu_L;      /* kinematic viscosities; mu = rho nu interpolated linearly (Eq. dynamic_vis) */
+    double s_f[9];          /* CH MRT rates; s_f[3], s_f[5] are replaced by 1/tau_f (Eq. CH_Sf) */
+    double s_g[9];          /* NS MRT rates; s_g[7], s_g[8] are replaced by 1/tau_g(x) (Sec. III.B) */
+    double gx, gy;          /* gravity, F_g = rho g (Sec. II.B) */
+    int filter_order;       /* 0 (off), 5, 7, 9 or 11: explicit selective filter SF-n (App. B) */
+    double filter_a;        /* filter intensity, 0 < a <= 1 (Eq. filter) */
+    int picard_iters;       /* sweeps of u = j + F(u)/(2 rho) per step (Eq. u), >= 1 */
+    double picard_zeta;     /* must be 0: fixed sweep count (residual stop is not offered) */
+    double grad_eps;        /* eps in n = grad phi / sqrt(|grad phi|^2 + eps^2), > 0 */
+    unsigned flags;         /* reserved, must be 0 */
+} lbm_params;
+
+typedef struct lbm_handle lbm_handle;
+
+/*
+ * lbm_create -- allocate a simulation and initialise it from host fields.
+ * phi0, p0, ux0, uy0: host [ny][nx] doubles (order parameter, kinematic
+ * pressure p = p'/rho of Sec. II.B, velocity).  Populations start at their
+ * equilibria: f = f_eq(phi0, mu(phi0), u0) (Eq. feq_CH), g = g_eq(p0, u0)
+ * (Eq. geq).  stream: a cudaStream_t or NULL.  On success *out receives the
+ * handle.  Errors: LBM_ERR_ARG for invalid sizes or parameters (tau_f or
+ * tau_g <= 1/2, a rate outside [0,2], rho <= 0, W <= 0, a outside (0,1], a
+ * filter order other than 0/5/7/9/11, picard_iters < 1, picard_zeta != 0,
+ * flags != 0), LBM_ERR_OOM, LBM_ERR_CUDA.
+ */
+lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params,
+                      const double *phi0, const double *p0,
+                      const double *ux0, const double *uy0,
+                      void *stream, lbm_handle **out);
+
+/*
+ * lbm_step -- advance n >= 0 time steps (the whole Sec. III update each
+ * step: fields and forces, collision and streaming of both lattices, the
+ * RK3 finite-difference correction, the implicit velocity, the filter).
+ * Asynchronous on the handle's stream.
+ */
+lbm_status lbm_step(lbm_handle *h, int n);
+
+/*
+ * lbm_fields -- copy phi, the filtered kinematic pressure p, and the
+ * filtered velocity (ux, uy) into host [ny][nx] double arrays.  A NULL
+ * pointer skips that field.  Synchronises the stream.
+ */
+lbm_status lbm_fields(lbm_handle *h, double *phi, double *p, double *ux, double *uy);
+
+/*
+ * lbm_fields_device -- same fields into caller-owned device buffers of
+ * nx*ny elements; dtype 0 = double, 1 = float.  Asynchronous.
+ */
+lbm_status lbm_fields_device(lbm_handle *h, void *phi, void *p, void *ux, void *uy, int dtype);
+
+/*
+ * lbm_set_fields -- re-initialise an existing handle from host fields, as
+ * lbm_create does (no allocation).  Synchronises the stream.
+ */
+lbm_status lbm_set_fields(lbm_handle *h, const double *phi0, const double *p0,
+                          const double *ux0, const double *uy0);
+
+/*
+ * lbm_diagnostics -- FP64 sums over the nodes (Sec. IV.C volume error,
+ * Sec. IV.E Eqs. quantify-yc, quantify-uc), into host out[LBM_NDIAG]:
+ *   [0] sum phi   [1] #(phi>0)   [2] #(phi<0)   [3] sum_{phi<0} y
+ *   [4] sum_{phi<0} u_y   [5] sum w   [6] sum w y   [7] sum w u_y
+ *       (w = (1-phi)/2, y = row index)   [8] max phi   [9] min phi
+ *   [10] number of non-finite values among phi, p, ux, uy.
+ * Synchronises the stream.
+ */
+lbm_status lbm_diagnostics(lbm_handle *h, double *out);
+
+/*
+ * lbm_check -- LBM_ERR_NONFINITE if any field value is NaN/Inf,
+ * LBM_ERR_RANGE if phi leaves [-1-delta, 1+delta], else LBM_OK.
+ * Synchronises the stream.
+ */
+lbm_status lbm_check(lbm_handle *h, double delta);
+
+/*
+ * lbm_get_state / lbm_set_state -- the full state between steps, as host
+ * doubles: post-stream populations f, g [9][ny][nx]; phi; filtered p, ux,
+ * uy; unfiltered velocity (uhx, uhy) of the last implicit update; filtered
+ * velocity of the previous step (upx, upy).  Reduced-precision population
+ * storage is decoded on get and encoded on set.  Synchronise the stream.
+ */
+lbm_status lbm_get_state(lbm_handle *h, double *f, double *g, double *phi, double *p,
+                         double *ux, double *uy, double *uhx, double *uhy,
+                         double *upx, double *upy);
+lbm_status lbm_set_state(lbm_handle *h, const double *f, const double *g, const double *phi,
+                         const double *p, const double *ux, const double *uy,
+                         const double *uhx, const double *uhy,
+                         const double *upx, const double *upy);
+
+/* lbm_device_bytes -- device memory held by the handle, in bytes. */
+size_t lbm_device_bytes(const lbm_handle *h);
+
+/* lbm_destroy -- free every device buffer of the handle; NULL is a no-op. */
+void lbm_destroy(lbm_handle *h);
+
+/* lbm_last_error -- text of the last error on h (or of the last failed
+ * lbm_create when h is NULL); never NULL. */
+const char *lbm_last_error(const lbm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

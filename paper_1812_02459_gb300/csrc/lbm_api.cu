@@ -1,0 +1,520 @@
+// lbm_api.cu -- host side of the C ABI declared in include/lbm.h.
+//
+// A handle owns one device arena holding every plane of the state and the
+// scratch planes of one step.  A step is a fixed sequence of tile kernels on
+// the handle's stream (see lbm_kernels.cuh):
+//   collide+stream (both lattices) -> RK3 stage x3 -> Picard sweep xK -> filter.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_kernels.cuh"
+
+using namespace lbm;
+
+namespace {
+
+constexpr int CS_TX = 32, CS_TY = 8;     // collide+stream tile
+constexpr int RK_TX = 32, RK_TY = 16;    // RK3 stage tile
+constexpr int PC_TX = 32, PC_TY = 8;     // Picard sweep tile
+constexpr int FL_TX = 32, FL_TY = 8;     // filter tile
+constexpr int DIAG_THREADS = 256;
+constexpr int DIAG_MAX_BLOCKS = 1216;    // 8 x 152 SMs
+
+thread_local std::string g_create_error;
+
+// Explicit centred selective-filter coefficients d_0..d_5 (App. B table).
+void filter_table(int order, double d[6])
+{
+    for (int k = 0; k < 6; ++k) d[k] = 0.0;
+    if (order == 5) {
+        d[0] = 6.0 / 16.0; d[1] = -4.0 / 16.0; d[2] = 1.0 / 16.0;
+    } else if (order == 7) {
+        d[0] = 5.0 / 16.0; d[1] = -15.0 / 64.0; d[2] = 3.0 / 32.0; d[3] = -1.0 / 64.0;
+    } else if (order == 9) {
+        d[0] = 0.243527493120; d[1] = -0.204788880640; d[2] = 0.120007591680;
+        d[3] = -0.045211119360; d[4] = 0.008228661760;
+    } else if (order == 11) {
+        d[0] = 0.215044884112; d[1] = -0.187772883589; d[2] = 0.123755948787;
+        d[3] = -0.059227575576; d[4] = 0.018721609157; d[5] = -0.002999540835;
+    }
+}
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct lbm_handle {
+    lbm_grid grid{};
+    lbm_params prm{};
+    cudaStream_t stream = nullptr;
+    std::string err;
+    long long N = 0;
+    size_t elem = 0, pop_elem = 0;     // bytes of T and of S
+    unsigned char *arena = nullptr;
+    size_t arena_bytes = 0;
+    void *f[2]{}, *g[2]{};
+    int cur = 0;                       // which population buffer holds the state
+    void *phi = nullptr, *pf = nullptr, *ux[2]{}, *uy[2]{};
+    int ucur = 0;                      // ux[ucur] = filtered u^n, ux[1-ucur] = u^{n-1}
+    void *uhx = nullptr, *uhy = nullptr;
+    void *phibar = nullptr, *phat = nullptr, *jx = nullptr, *jy = nullptr;
+    void *s1 = nullptr, *s2 = nullptr, *tk[2][2]{};
+    double *diag_part = nullptr, *diag_out = nullptr;
+    int diag_blocks = 1;
+    KP<double> kpd{};
+    KP<float> kpf{};
+};
+
+namespace {
+
+lbm_status fail(lbm_handle *h, lbm_status st, const std::string &msg)
+{
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+lbm_status cuda_fail(lbm_handle *h, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
+}
+
+#define CK(h, call, what)                                          \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, (what));  \
+    } while (0)
+
+template <typename T> KP<T> &kp_of(lbm_handle *h);
+template <> KP<double> &kp_of<double>(lbm_handle *h) { return h->kpd; }
+template <> KP<float> &kp_of<float>(lbm_handle *h) { return h->kpf; }
+
+template <typename T>
+void build_kp(const lbm_grid &gr, const lbm_params &p, KP<T> &k)
+{
+    k.nx = gr.nx; k.ny = gr.ny; k.px = gr.periodic_x ? 1 : 0; k.py = gr.periodic_y ? 1 : 0;
+    k.N = (long long)gr.nx * gr.ny;
+    k.kappa = (T)(3.0 * p.sigma * p.W / 8.0);          // Sec. II.A, below Eq. (free_energy)
+    k.beta = (T)(3.0 * p.sigma / (4.0 * p.W));
+    k.eta = (T)p.eta; k.M = (T)p.M; k.lambda = (T)p.lambda; k.W = (T)p.W;
+    k.flux_corr = p.flux_correction ? 1 : 0;
+    k.rhoH = (T)p.rho_H; k.rhoL = (T)p.rho_L;
+    k.muH = (T)(p.rho_H * p.nu_H); k.muL = (T)(p.rho_L * p.nu_L);
+    k.drho = (T)((p.rho_H - p.rho_L) / 2.0);
+    const double tau_f = 0.5 + p.M / (p.eta / 3.0);    // Eq. (mobility): M = eta cs^2 (tau_f - 1/2)
+    for (int q = 0; q < 9; ++q) { k.sf[q] = (T)p.s_f[q]; k.sg[q] = (T)p.s_g[q]; }
+    k.sf[3] = k.sf[5] = (T)(1.0 / tau_f);
+    k.gx = (T)p.gx; k.gy = (T)p.gy;
+    k.eps2 = (T)(p.grad_eps * p.grad_eps);
+    double d[6];
+    filter_table(p.filter_order, d);
+    for (int m = 0; m < 6; ++m) k.fd[m] = (T)d[m];
+    k.fa = (T)p.filter_a;
+    k.fR = p.filter_order / 2;
+}
+
+lbm_status validate(const lbm_grid *gr, const lbm_params *p)
+{
+    char buf[256];
+    if (!gr || !p) return fail(nullptr, LBM_ERR_ARG, "grid and params must be non-NULL");
+    if (gr->nx < LBM_MIN_EXTENT || gr->ny < LBM_MIN_EXTENT) {
+        snprintf(buf, sizeof buf, "nx, ny must be >= %d (got %d x %d)", LBM_MIN_EXTENT, gr->nx, gr->ny);
+        return fail(nullptr, LBM_ERR_ARG, buf);
+    }
+    if ((long long)gr->nx * gr->ny > (1LL << 31))
+        return fail(nullptr, LBM_ERR_ARG, "nx*ny must be <= 2^31");
+    if (gr->precision != LBM_FP64 && gr->precision != LBM_FP32)
+        return fail(nullptr, LBM_ERR_ARG, "precision must be LBM_FP64 or LBM_FP32");
+    if (!(p->M > 0) || !(p->eta > 0)) return fail(nullptr, LBM_ERR_ARG, "M and eta must be > 0 (tau_f > 1/2)");
+    if (!(p->W > 0)) return fail(nullptr, LBM_ERR_ARG, "W must be > 0");
+    if (!(p->sigma >= 0) || !(p->lambda >= 0)) return fail(nullptr, LBM_ERR_ARG, "sigma, lambda must be >= 0");
+    if (!(p->rho_H > 0) || !(p->rho_L > 0)) return fail(nullptr, LBM_ERR_ARG, "densities must be > 0");
+    if (!(p->nu_H > 0) || !(p->nu_L > 0)) return fail(nullptr, LBM_ERR_ARG, "viscosities must be > 0 (tau_g > 1/2)");
+    for (int q = 0; q < 9; ++q)
+        if (!(p->s_f[q] >= 0 && p->s_f[q] <= 2) || !(p->s_g[q] >= 0 && p->s_g[q] <= 2))
+            return fail(nullptr, LBM_ERR_ARG, "relaxation rates must lie in [0, 2]");
+    const double tau_f = 0.5 + p->M / (p->eta / 3.0);
+    if (!(1.0 / tau_f <= 2.0)) return fail(nullptr, LBM_ERR_ARG, "1/tau_f must be <= 2");
+    int fo = p->filter_order;
+    if (fo != 0 && fo != 5 && fo != 7 && fo != 9 && fo != 11)
+        return fail(nullptr, LBM_ERR_ARG, "filter_order must be 0, 5, 7, 9 or 11");
+    if (fo && !(p->filter_a > 0 && p->filter_a <= 1)) return fail(nullptr, LBM_ERR_ARG, "filter_a must be in (0, 1]");
+    if (p->picard_iters < 1 || p->picard_iters > 64) return fail(nullptr, LBM_ERR_ARG, "picard_iters must be in [1, 64]");
+    if (p->picard_zeta != 0.0) return fail(nullptr, LBM_ERR_ARG, "picard_zeta must be 0 (fixed sweep count)");
+    if (!(p->grad_eps > 0)) return fail(nullptr, LBM_ERR_ARG, "grad_eps must be > 0");
+    if (p->flags != 0) return fail(nullptr, LBM_ERR_ARG, "flags must be 0");
+    if (!std::isfinite(p->gx) || !std::isfinite(p->gy)) return fail(nullptr, LBM_ERR_ARG, "gravity must be finite");
+    return LBM_OK;
+}
+
+template <typename T> size_t smem_cs() { return sizeof(T) * CSGeom<CS_TX, CS_TY>::NSCALAR; }
+template <typename T> size_t smem_rk() { return sizeof(T) * RKGeom<RK_TX, RK_TY>::NSCALAR; }
+template <typename T> size_t smem_pc() { return sizeof(T) * PCGeom<PC_TX, PC_TY>::NSCALAR; }
+template <typename T, int R> size_t smem_fl() { return sizeof(T) * FLGeom<FL_TX, FL_TY, R>::NSCALAR; }
+
+template <typename T, typename S>
+lbm_status set_smem_limits(lbm_handle *h)
+{
+    CK(h, cudaFuncSetAttribute(k_collide_stream<T, S, CS_TX, CS_TY>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cs<T>()),
+       "cudaFuncSetAttribute(collide_stream)");
+    CK(h, cudaFuncSetAttribute(k_rk_stage<T, RK_TX, RK_TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_rk<T>()),
+       "cudaFuncSetAttribute(rk_stage)");
+    return LBM_OK;
+}
+
+template <typename T, int R>
+void launch_filter_r(lbm_handle *h, const T *pin, const T *uxi, const T *uyi, T *po, T *uxo, T *uyo)
+{
+    const KP<T> &P = kp_of<T>(h);
+    dim3 grid((P.nx + FL_TX - 1) / FL_TX, (P.ny + FL_TY - 1) / FL_TY);
+    k_filter<T, FL_TX, FL_TY, R><<<grid, FL_TX * FL_TY, smem_fl<T, R>(), h->stream>>>(P, pin, uxi, uyi, po, uxo, uyo);
+}
+
+template <typename T, typename S>
+lbm_status step_impl(lbm_handle *h)
+{
+    const KP<T> &P = kp_of<T>(h);
+    cudaStream_t st = h->stream;
+    const int c = h->cur, u = h->ucur;
+    T *phi = (T *)h->phi, *pf = (T *)h->pf;
+    T *uxc = (T *)h->ux[u], *uyc = (T *)h->uy[u], *uxp = (T *)h->ux[1 - u], *uyp = (T *)h->uy[1 - u];
+    T *uhx = (T *)h->uhx, *uhy = (T *)h->uhy;
+    T *phibar = (T *)h->phibar, *phat = (T *)h->phat, *jx = (T *)h->jx, *jy = (T *)h->jy;
+
+    {   // fields, forces, collision of f and g, pull streaming, post-stream moments
+        dim3 grid((P.nx + CS_TX - 1) / CS_TX, (P.ny + CS_TY - 1) / CS_TY);
+        k_collide_stream<T, S, CS_TX, CS_TY><<<grid, CS_TX * CS_TY, smem_cs<T>(), st>>>(
+            P, (const S *)h->f[c], (const S *)h->g[c], (S *)h->f[1 - c], (S *)h->g[1 - c], phi, pf, uxc, uyc,
+            uxp, uyp, uhx, uhy, phibar, phat, jx, jy);
+    }
+    {   // TVD-RK3 finite-difference correction: phi_bar -> phi^{n+1}
+        dim3 grid((P.nx + RK_TX - 1) / RK_TX, (P.ny + RK_TY - 1) / RK_TY);
+        const size_t sm = smem_rk<T>();
+        k_rk_stage<T, RK_TX, RK_TY><<<grid, RK_TX * RK_TY, sm, st>>>(P, phibar, phibar, (T *)h->s1, T(0), T(1));
+        k_rk_stage<T, RK_TX, RK_TY><<<grid, RK_TX * RK_TY, sm, st>>>(P, (T *)h->s1, phibar, (T *)h->s2,
+                                                                     T(0.75), T(0.25));
+        k_rk_stage<T, RK_TX, RK_TY><<<grid, RK_TX * RK_TY, sm, st>>>(P, (T *)h->s2, phibar, phi,
+                                                                     T(1.0 / 3.0), T(2.0 / 3.0));
+    }
+    {   // implicit velocity by Picard sweeps; the last sweep lands in u_hat
+        dim3 grid((P.nx + PC_TX - 1) / PC_TX, (P.ny + PC_TY - 1) / PC_TY);
+        const int K = h->prm.picard_iters;
+        for (int k = 0; k < K; ++k) {
+            const T *ix = k == 0 ? uxc : (const T *)h->tk[(k - 1) & 1][0];
+            const T *iy = k == 0 ? uyc : (const T *)h->tk[(k - 1) & 1][1];
+            T *ox = k == K - 1 ? uhx : (T *)h->tk[k & 1][0];
+            T *oy = k == K - 1 ? uhy : (T *)h->tk[k & 1][1];
+            k_picard<T, PC_TX, PC_TY><<<grid, PC_TX * PC_TY, smem_pc<T>(), st>>>(P, phi, phat, jx, jy, ix, iy, ox, oy);
+        }
+    }
+    // selective filter of (p_hat, u_hat) -> (p_f, u_f^{n+1}); u^{n-1} slot is reused
+    switch (P.fR) {
+    case 2: launch_filter_r<T, 2>(h, phat, uhx, uhy, pf, uxp, uyp); break;
+    case 3: launch_filter_r<T, 3>(h, phat, uhx, uhy, pf, uxp, uyp); break;
+    case 4: launch_filter_r<T, 4>(h, phat, uhx, uhy, pf, uxp, uyp); break;
+    case 5: launch_filter_r<T, 5>(h, phat, uhx, uhy, pf, uxp, uyp); break;
+    default: {
+        const size_t b = sizeof(T) * (size_t)P.N;
+        CK(h, cudaMemcpyAsync(pf, phat, b, cudaMemcpyDeviceToDevice, st), "copy p");
+        CK(h, cudaMemcpyAsync(uxp, uhx, b, cudaMemcpyDeviceToDevice, st), "copy ux");
+        CK(h, cudaMemcpyAsync(uyp, uhy, b, cudaMemcpyDeviceToDevice, st), "copy uy");
+    }
+    }
+    CK(h, cudaGetLastError(), "kernel launch");
+    h->cur ^= 1;
+    h->ucur ^= 1;
+    return LBM_OK;
+}
+
+template <typename T>
+lbm_status upload_field(lbm_handle *h, void *dst, const double *src)
+{
+    const size_t n = (size_t)h->N;
+    if (sizeof(T) == sizeof(double)) {
+        CK(h, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "upload");
+        return LBM_OK;
+    }
+    std::vector<T> tmp(n);
+    for (size_t k = 0; k < n; ++k) tmp[k] = (T)src[k];
+    CK(h, cudaMemcpyAsync(dst, tmp.data(), n * sizeof(T), cudaMemcpyHostToDevice, h->stream), "upload");
+    CK(h, cudaStreamSynchronize(h->stream), "upload sync");
+    return LBM_OK;
+}
+
+template <typename T>
+lbm_status download_field(lbm_handle *h, double *dst, const void *src, size_t count)
+{
+    if (!dst) return LBM_OK;
+    if (sizeof(T) == sizeof(double)) {
+        CK(h, cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "download");
+        CK(h, cudaStreamSynchronize(h->stream), "download sync");
+        return LBM_OK;
+    }
+    std::vector<T> tmp(count);
+    CK(h, cudaMemcpyAsync(tmp.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost, h->stream), "download");
+    CK(h, cudaStreamSynchronize(h->stream), "download sync");
+    for (size_t k = 0; k < count; ++k) dst[k] = (double)tmp[k];
+    return LBM_OK;
+}
+
+template <typename T, typename S>
+lbm_status init_impl(lbm_handle *h, const double *phi0, const double *p0, const double *ux0, const double *uy0)
+{
+    lbm_status st;
+    if ((st = upload_field<T>(h, h->phi, phi0))) return st;
+    if ((st = upload_field<T>(h, h->pf, p0))) return st;
+    if ((st = upload_field<T>(h, h->ux[0], ux0))) return st;
+    if ((st = upload_field<T>(h, h->uy[0], uy0))) return st;
+    const size_t b = sizeof(T) * (size_t)h->N;
+    h->cur = 0;
+    h->ucur = 0;
+    // u^{n-1} = u_hat = u0 at the start
+    CK(h, cudaMemcpyAsync(h->ux[1], h->ux[0], b, cudaMemcpyDeviceToDevice, h->stream), "init copy");
+    CK(h, cudaMemcpyAsync(h->uy[1], h->uy[0], b, cudaMemcpyDeviceToDevice, h->stream), "init copy");
+    CK(h, cudaMemcpyAsync(h->uhx, h->ux[0], b, cudaMemcpyDeviceToDevice, h->stream), "init copy");
+    CK(h, cudaMemcpyAsync(h->uhy, h->uy[0], b, cudaMemcpyDeviceToDevice, h->stream), "init copy");
+    const KP<T> &P = kp_of<T>(h);
+    int blocks = (int)std::min<long long>((P.N + 255) / 256, 4096);
+    k_init<T, S><<<blocks, 256, 0, h->stream>>>(P, (const T *)h->phi, (const T *)h->pf, (const T *)h->ux[0],
+                                                 (const T *)h->uy[0], (S *)h->f[0], (S *)h->g[0]);
+    CK(h, cudaGetLastError(), "init kernel");
+    CK(h, cudaStreamSynchronize(h->stream), "init sync");
+    return LBM_OK;
+}
+
+template <typename T>
+lbm_status diag_impl(lbm_handle *h, double *out)
+{
+    const KP<T> &P = kp_of<T>(h);
+    k_diag_partial<T><<<h->diag_blocks, DIAG_THREADS, 0, h->stream>>>(
+        P.nx, P.N, (const T *)h->phi, (const T *)h->pf, (const T *)h->ux[h->ucur], (const T *)h->uy[h->ucur],
+        h->diag_part);
+    k_diag_final<<<1, 32, 0, h->stream>>>(h->diag_blocks, h->diag_part, h->diag_out);
+    CK(h, cudaGetLastError(), "diagnostics launch");
+    CK(h, cudaMemcpyAsync(out, h->diag_out, sizeof(double) * NDIAG, cudaMemcpyDeviceToHost, h->stream),
+       "diagnostics copy");
+    CK(h, cudaStreamSynchronize(h->stream), "diagnostics sync");
+    return LBM_OK;
+}
+
+template <typename T>
+lbm_status fields_impl(lbm_handle *h, double *phi, double *p, double *ux, double *uy)
+{
+    lbm_status st;
+    const size_t n = (size_t)h->N;
+    if ((st = download_field<T>(h, phi, h->phi, n))) return st;
+    if ((st = download_field<T>(h, p, h->pf, n))) return st;
+    if ((st = download_field<T>(h, ux, h->ux[h->ucur], n))) return st;
+    if ((st = download_field<T>(h, uy, h->uy[h->ucur], n))) return st;
+    return LBM_OK;
+}
+
+template <typename T, typename S>
+lbm_status get_state_impl(lbm_handle *h, double *f, double *g, double *phi, double *p, double *ux, double *uy,
+                          double *uhx, double *uhy, double *upx, double *upy)
+{
+    lbm_status st;
+    const size_t n = (size_t)h->N;
+    if ((st = download_field<S>(h, f, h->f[h->cur], 9 * n))) return st;
+    if ((st = download_field<S>(h, g, h->g[h->cur], 9 * n))) return st;
+    if ((st = fields_impl<T>(h, phi, p, ux, uy))) return st;
+    if ((st = download_field<T>(h, uhx, h->uhx, n))) return st;
+    if ((st = download_field<T>(h, uhy, h->uhy, n))) return st;
+    if ((st = download_field<T>(h, upx, h->ux[1 - h->ucur], n))) return st;
+    if ((st = download_field<T>(h, upy, h->uy[1 - h->ucur], n))) return st;
+    return LBM_OK;
+}
+
+template <typename T, typename S>
+lbm_status set_state_impl(lbm_handle *h, const double *f, const double *g, const double *phi, const double *p,
+                          const double *ux, const double *uy, const double *uhx, const double *uhy,
+                          const double *upx, const double *upy)
+{
+    lbm_status st;
+    const size_t n = (size_t)h->N;
+    h->cur = 0;
+    h->ucur = 0;
+    std::vector<double> slice;
+    for (int q = 0; q < 9; ++q) {
+        if ((st = upload_field<S>(h, (S *)h->f[0] + q * n, f + q * n))) return st;
+        if ((st = upload_field<S>(h, (S *)h->g[0] + q * n, g + q * n))) return st;
+    }
+    if ((st = upload_field<T>(h, h->phi, phi))) return st;
+    if ((st = upload_field<T>(h, h->pf, p))) return st;
+    if ((st = upload_field<T>(h, h->ux[0], ux))) return st;
+    if ((st = upload_field<T>(h, h->uy[0], uy))) return st;
+    if ((st = upload_field<T>(h, h->uhx, uhx))) return st;
+    if ((st = upload_field<T>(h, h->uhy, uhy))) return st;
+    if ((st = upload_field<T>(h, h->ux[1], upx))) return st;
+    if ((st = upload_field<T>(h, h->uy[1], upy))) return st;
+    CK(h, cudaStreamSynchronize(h->stream), "set_state sync");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params, const double *phi0, const double *p0,
+                      const double *ux0, const double *uy0, void *stream, lbm_handle **out)
+{
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out must be non-NULL");
+    *out = nullptr;
+    lbm_status st = validate(grid, params);
+    if (st) return st;
+    if (!phi0 || !p0 || !ux0 || !uy0) return fail(nullptr, LBM_ERR_ARG, "initial fields must be non-NULL");
+    lbm_handle *h = new (std::nothrow) lbm_handle();
+    if (!h) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+    h->grid = *grid;
+    h->prm = *params;
+    h->stream = (cudaStream_t)stream;
+    h->N = (long long)grid->nx * grid->ny;
+    const bool dbl = grid->precision == LBM_FP64;
+    h->elem = dbl ? sizeof(double) : sizeof(float);
+    h->pop_elem = h->elem;
+    if (dbl) build_kp<double>(*grid, *params, h->kpd);
+    else build_kp<float>(*grid, *params, h->kpf);
+
+    // one arena: 2x9 f planes, 2x9 g planes, then the scalar planes, 256-byte aligned each
+    const size_t plane = round_up((size_t)h->N * h->elem, 256);
+    const size_t pplane = round_up((size_t)h->N * 9 * h->pop_elem, 256);
+    const int nscalar = 20;   // phi, pf, ux[2], uy[2], uhx, uhy, phibar, phat, jx, jy, s1, s2, tk[2][2], 2 spare
+    h->diag_blocks = (int)std::min<long long>((h->N + DIAG_THREADS - 1) / DIAG_THREADS, DIAG_MAX_BLOCKS);
+    const size_t diag_bytes = round_up(sizeof(double) * (size_t)(h->diag_blocks + 1) * NDIAG, 256);
+    h->arena_bytes = 4 * pplane + nscalar * plane + diag_bytes;
+    cudaError_t e = cudaMalloc((void **)&h->arena, h->arena_bytes);
+    if (e != cudaSuccess) {
+        std::string m = std::string("cudaMalloc arena: ") + cudaGetErrorString(e);
+        delete h;
+        cudaGetLastError();
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
+    }
+    unsigned char *a = h->arena;
+    h->f[0] = a; a += pplane;
+    h->f[1] = a; a += pplane;
+    h->g[0] = a; a += pplane;
+    h->g[1] = a; a += pplane;
+    void **sc[] = {&h->phi, &h->pf, &h->ux[0], &h->ux[1], &h->uy[0], &h->uy[1], &h->uhx, &h->uhy,
+                   &h->phibar, &h->phat, &h->jx, &h->jy, &h->s1, &h->s2,
+                   &h->tk[0][0], &h->tk[0][1], &h->tk[1][0], &h->tk[1][1]};
+    for (void **pp : sc) { *pp = a; a += plane; }
+    a += 2 * plane;
+    h->diag_part = (double *)a;
+    h->diag_out = h->diag_part + (size_t)h->diag_blocks * NDIAG;
+
+    st = dbl ? set_smem_limits<double, double>(h) : set_smem_limits<float, float>(h);
+    if (!st) st = dbl ? init_impl<double, double>(h, phi0, p0, ux0, uy0) : init_impl<float, float>(h, phi0, p0, ux0, uy0);
+    if (st) {
+        g_create_error = h->err;
+        lbm_destroy(h);
+        return st;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_handle *h, int n)
+{
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
+    if (n < 0) return fail(h, LBM_ERR_ARG, "n must be >= 0");
+    for (int t = 0; t < n; ++t) {
+        lbm_status st = h->grid.precision == LBM_FP64 ? step_impl<double, double>(h) : step_impl<float, float>(h);
+        if (st) return st;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_fields(lbm_handle *h, double *phi, double *p, double *ux, double *uy)
+{
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
+    return h->grid.precision == LBM_FP64 ? fields_impl<double>(h, phi, p, ux, uy) : fields_impl<float>(h, phi, p, ux, uy);
+}
+
+lbm_status lbm_fields_device(lbm_handle *h, void *phi, void *p, void *ux, void *uy, int dtype)
+{
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
+    const bool dbl = h->grid.precision == LBM_FP64;
+    if (dtype != (dbl ? 0 : 1))
+        return fail(h, LBM_ERR_ARG, "dtype must match the handle's arithmetic type (0 double, 1 float)");
+    const size_t b = h->elem * (size_t)h->N;
+    void *dst[4] = {phi, p, ux, uy};
+    const void *src[4] = {h->phi, h->pf, h->ux[h->ucur], h->uy[h->ucur]};
+    for (int k = 0; k < 4; ++k)
+        if (dst[k]) CK(h, cudaMemcpyAsync(dst[k], src[k], b, cudaMemcpyDeviceToDevice, h->stream), "fields_device");
+    return LBM_OK;
+}
+
+lbm_status lbm_set_fields(lbm_handle *h, const double *phi0, const double *p0, const double *ux0, const double *uy0)
+{
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
+    if (!phi0 || !p0 || !ux0 || !uy0) return fail(h, LBM_ERR_ARG, "fields must be non-NULL");
+    return h->grid.precision == LBM_FP64 ? init_impl<double, double>(h, phi0, p0, ux0, uy0)
+                                         : init_impl<float, float>(h, phi0, p0, ux0, uy0);
+}
+
+lbm_status lbm_diagnostics(lbm_handle *h, double *out)
+{
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
+    if (!out) return fail(h, LBM_ERR_ARG, "out must be non-NULL");
+    return h->grid.precision == LBM_FP64 ? diag_impl<double>(h, out) : diag_impl<float>(h, out);
+}
+
+lbm_status lbm_check(lbm_handle *h, double delta)
+{
+    double d[NDIAG];
+    lbm_status st = lbm_diagnostics(h, d);
+    if (st) return st;
+    if (d[10] > 0) return fail(h, LBM_ERR_NONFINITE, "non-finite field value");
+    if (d[8] > 1.0 + delta || d[9] < -1.0 - delta) return fail(h, LBM_ERR_RANGE, "phi outside [-1-delta, 1+delta]");
+    return LBM_OK;
+}
+
+lbm_status lbm_get_state(lbm_handle *h, double *f, double *g, double *phi, double *p, double *ux, double *uy,
+                         double *uhx, double *uhy, double *upx, double *upy)
+{
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
+    return h->grid.precision == LBM_FP64
+               ? get_state_impl<double, double>(h, f, g, phi, p, ux, uy, uhx, uhy, upx, upy)
+               : get_state_impl<float, float>(h, f, g, phi, p, ux, uy, uhx, uhy, upx, upy);
+}
+
+lbm_status lbm_set_state(lbm_handle *h, const double *f, const double *g, const double *phi, const double *p,
+                         const double *ux, const double *uy, const double *uhx, const double *uhy,
+                         const double *upx, const double *upy)
+{
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
+    const double *all[10] = {f, g, phi, p, ux, uy, uhx, uhy, upx, upy};
+    for (const double *q : all)
+        if (!q) return fail(h, LBM_ERR_ARG, "every state array must be non-NULL");
+    return h->grid.precision == LBM_FP64
+               ? set_state_impl<double, double>(h, f, g, phi, p, ux, uy, uhx, uhy, upx, upy)
+               : set_state_impl<float, float>(h, f, g, phi, p, ux, uy, uhx, uhy, upx, upy);
+}
+
+size_t lbm_device_bytes(const lbm_handle *h) { return h ? h->arena_bytes : 0; }
+
+void lbm_destroy(lbm_handle *h)
+{
+    if (!h) return;
+    if (h->arena) cudaFree(h->arena);
+    delete h;
+}
+
+const char *lbm_last_error(const lbm_handle *h)
+{
+    if (h) return h->err.c_str();
+    return g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,751 @@
+// lbm_kernels.cuh -- CUDA kernels of the fractional-step MRT lattice Boltzmann
+// update (Zhang, Guo & Li, arXiv:1812.02459), written for sm_103a.
+//
+// The update is a chain of stencils, so every pass below is a tile kernel:
+// a CTA stages the tile of its inputs plus the halo its stencils need in
+// shared memory (periodic wrap or halfway-wall mirror), computes, and writes
+// its tile once.  Arithmetic type T is double or float; populations are
+// stored in S (T itself, or bf16 / fp16 in the reduced-storage modes).
+//
+// Lattice directions (Sec. III.A Eq. D2Q9):
+//   c0=(0,0) c1=(1,0) c2=(0,1) c3=(-1,0) c4=(0,-1) c5=(1,1) c6=(-1,1) c7=(-1,-1) c8=(1,-1)
+// Moment basis: the rows of Eq. (D2Q9MRT), m = (rho, e, eps, jx, qx, jy, qy, pxx, pxy).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Population storage codecs.
+// ---------------------------------------------------------------------------
+template <typename S, typename T> struct Codec {
+    static __device__ __forceinline__ T load(S v) { return (T)v; }
+    static __device__ __forceinline__ S store(T v) { return (S)v; }
+};
+template <> struct Codec<__nv_bfloat16, float> {
+    static __device__ __forceinline__ float load(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 store(float v) { return __float2bfloat16_rn(v); }
+};
+template <> struct Codec<__half, float> {
+    static __device__ __forceinline__ float load(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half store(float v) { return __float2half_rn(v); }
+};
+
+// ---------------------------------------------------------------------------
+// Model constants handed to every kernel (by value).
+// ---------------------------------------------------------------------------
+template <typename T> struct KP {
+    int nx, ny, px, py;
+    long long N;
+    T kappa, beta;           // free-energy coefficients (Sec. II.A)
+    T eta, M, lambda, W;     // CH equilibrium parameter, mobility, profile weight, width
+    int flux_corr;
+    T rhoH, rhoL, muH, muL;  // densities and dynamic viscosities of the two fluids
+    T drho;                  // (rho_H - rho_L)/2 = d rho / d phi
+    T sf[9], sg[9];          // relaxation rates (sg[7], sg[8] set per node)
+    T gx, gy;
+    T eps2;                  // regularisation of |grad phi|^2
+    T fd[6];                 // filter coefficients d_0..d_5
+    T fa;                    // filter intensity
+    int fR;                  // filter half-width (0 = off)
+};
+
+// Map a coordinate onto [0,n): periodic wrap, or reflection about the
+// halfway walls (-1/2 and n-1/2), which repeats with period 2n; `flip`
+// reports an odd number of reflections (sign change of an odd field).
+__device__ __forceinline__ int map_axis(int k, int n, int periodic, int &flip)
+{
+    if (periodic) {
+        int r = k % n;
+        if (r < 0) r += n;
+        flip = 0;
+        return r;
+    }
+    int p = 2 * n;
+    int m = k % p;
+    if (m < 0) m += p;
+    if (m < n) { flip = 0; return m; }
+    flip = 1;
+    return p - 1 - m;
+}
+
+// Stage a (WS x HS) window of a scalar field whose top-left corner is global
+// (x0, y0) into shared memory s[HS][WS]; odd fields change sign in mirrors.
+template <typename T, int WS, int HS>
+__device__ __forceinline__ void load_tile(T *s, const T *__restrict__ g, int x0, int y0,
+                                          const KP<T> &P, bool odd)
+{
+    for (int t = threadIdx.x; t < WS * HS; t += blockDim.x) {
+        int ly = t / WS, lx = t - ly * WS;
+        int fx, fy;
+        int gx = map_axis(x0 + lx, P.nx, P.px, fx);
+        int gy = map_axis(y0 + ly, P.ny, P.py, fy);
+        T v = __ldg(&g[(long long)gy * P.nx + gx]);
+        s[t] = (odd && (fx ^ fy)) ? -v : v;
+    }
+}
+
+// Isotropic first derivatives and Laplacian on a D2Q9 neighbourhood
+// (Sec. III.B Eq. dicretized): with E,W,N,S the axis neighbours and
+// NE,NW,SW,SE the diagonals,
+//   d_x = (E-W)/3 + (NE-NW-SW+SE)/12,  d_y = (N-S)/3 + (NE+NW-SW-SE)/12,
+//   lap = 2/3 (E+W+N+S) + 1/6 (NE+NW+SW+SE) - 10/3 C.
+template <typename T, int WS>
+__device__ __forceinline__ void iso_grad(const T *s, int i, T &dx, T &dy)
+{
+    const T E = s[i + 1], Wv = s[i - 1], N = s[i + WS], S = s[i - WS];
+    const T NE = s[i + WS + 1], NW = s[i + WS - 1], SW = s[i - WS - 1], SE = s[i - WS + 1];
+    dx = (E - Wv) * T(1.0 / 3.0) + (NE - NW - SW + SE) * T(1.0 / 12.0);
+    dy = (N - S) * T(1.0 / 3.0) + (NE + NW - SW - SE) * T(1.0 / 12.0);
+}
+template <typename T, int WS>
+__device__ __forceinline__ T iso_lap(const T *s, int i)
+{
+    const T ax = s[i + 1] + s[i - 1] + s[i + WS] + s[i - WS];
+    const T dg = s[i + WS + 1] + s[i + WS - 1] + s[i - WS - 1] + s[i - WS + 1];
+    return ax * T(2.0 / 3.0) + dg * T(1.0 / 6.0) - s[i] * T(10.0 / 3.0);
+}
+
+// Fourth-order central differences (Sec. III.A Eq. fourOrder_FDM) and the
+// five-point fourth-order second derivative.
+template <typename T, int STRIDE>
+__device__ __forceinline__ T fd4_d1(const T *s, int i)
+{
+    return (s[i - 2 * STRIDE] - T(8) * s[i - STRIDE] + T(8) * s[i + STRIDE] - s[i + 2 * STRIDE]) *
+           T(1.0 / 12.0);
+}
+template <typename T, int STRIDE>
+__device__ __forceinline__ T fd4_d2(const T *s, int i)
+{
+    return (-s[i - 2 * STRIDE] + T(16) * s[i - STRIDE] - T(30) * s[i] + T(16) * s[i + STRIDE] -
+            s[i + 2 * STRIDE]) *
+           T(1.0 / 12.0);
+}
+
+// Density and kinematic viscosity at a node (Sec. II.B Eq. rho,
+// Sec. III.B Eq. dynamic_vis), with phi clamped to [-1,1] here only.
+template <typename T>
+__device__ __forceinline__ void rho_nu(const KP<T> &P, T phi, T &rho, T &nu)
+{
+    T c = phi < T(-1) ? T(-1) : (phi > T(1) ? T(1) : phi);
+    T hp = (T(1) + c) * T(0.5), hm = (T(1) - c) * T(0.5);
+    rho = P.rhoH * hp + P.rhoL * hm;
+    nu = (P.muH * hp + P.muL * hm) / rho;
+}
+
+// Moment transform m = M f with the rows of Eq. (D2Q9MRT).
+template <typename T>
+__device__ __forceinline__ void to_moments(const T f[9], T m[9])
+{
+    const T a = f[1] + f[2] + f[3] + f[4], d = f[5] + f[6] + f[7] + f[8];
+    m[0] = f[0] + a + d;
+    m[1] = T(-4) * f[0] - a + T(2) * d;
+    m[2] = T(4) * f[0] - T(2) * a + d;
+    const T d58 = f[5] - f[6] - f[7] + f[8];
+    m[3] = f[1] - f[3] + d58;
+    m[4] = T(2) * (f[3] - f[1]) + d58;
+    const T d56 = f[5] + f[6] - f[7] - f[8];
+    m[5] = f[2] - f[4] + d56;
+    m[6] = T(2) * (f[4] - f[2]) + d56;
+    m[7] = f[1] - f[2] + f[3] - f[4];
+    m[8] = f[5] - f[6] + f[7] - f[8];
+}
+
+// Inverse transform f = M^{-1} m; the rows of M are orthogonal with squared
+// norms (9,36,36,6,12,6,12,4,4), so M^{-1} = M^T diag(1/norm^2).
+template <typename T>
+__device__ __forceinline__ void from_moments(const T m[9], T f[9])
+{
+    const T r = m[0] * T(1.0 / 9.0), e = m[1] * T(1.0 / 36.0), ep = m[2] * T(1.0 / 36.0);
+    const T jx = m[3] * T(1.0 / 6.0), qx = m[4] * T(1.0 / 12.0);
+    const T jy = m[5] * T(1.0 / 6.0), qy = m[6] * T(1.0 / 12.0);
+    const T pxx = m[7] * T(0.25), pxy = m[8] * T(0.25);
+    f[0] = r - T(4) * e + T(4) * ep;
+    const T ax = r - e - T(2) * ep;
+    const T sx = jx - T(2) * qx, sy = jy - T(2) * qy;
+    f[1] = ax + sx + pxx;
+    f[2] = ax + sy - pxx;
+    f[3] = ax - sx + pxx;
+    f[4] = ax - sy - pxx;
+    const T dg = r + T(2) * e + ep;
+    const T tx = jx + qx, ty = jy + qy;
+    f[5] = dg + tx + ty + pxy;
+    f[6] = dg - tx + ty - pxy;
+    f[7] = dg - tx - ty + pxy;
+    f[8] = dg + tx - ty - pxy;
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1: fields and forces at t^n, collision of both lattices, pull
+// streaming and the post-stream moments, fused per tile.
+//
+// For every node of the tile plus a one-node ring the CTA evaluates
+//   mu   = 4 beta (phi^3 - phi) - kappa lap phi          (Sec. II.A Eq. chemical)
+//   F    = -p grad rho + kappa div(|grad phi|^2 I - grad phi grad phi)
+//          + nu (grad u + grad u^T).grad rho + J.grad u + rho g,
+//   J    = (d rho/d phi) M grad mu                       (Sec. II.B Eqs. surfaceforce, reformNS)
+//   a    = (u^n - u^{n-1}) + u.grad u                    (source of Eq. Fi)
+// and collides in moment space:
+//   f:  m* = m - S^f (m - m_eq(phi, mu, u)) + (I - S^f/2) M F_i         (Eqs. distribution_CH, feq_CH, Fi)
+//   g:  m* = m_eq(p_f, u_f) + (I - S^g)(m - m_eq(p_hat, u_hat)) + (I - S^g/2) M G_i
+//        with M G_i = (0, 6 b.u, -6 b.u, Fx/rho, -Fx/rho, Fy/rho, -Fy/rho,
+//                      2(bx ux - by uy), by ux + bx uy),  b = F/rho - grad p   (Eq. Gi, App. A)
+// The post-collision populations of tile+ring sit in shared memory, so each
+// tile node pulls f_i(x) = f*_i(x - c_i) (halfway bounce-back at walls),
+// writes it once, and emits phi_bar = sum f (Eq. compute_phi),
+// p_hat = cs^2 sum g (Eq. p) and j = sum c g (first part of Eq. u).
+// ---------------------------------------------------------------------------
+template <int TX, int TY> struct CSGeom {
+    static constexpr int W3 = TX + 6, H3 = TY + 6;   // phi window (ring 3)
+    static constexpr int W2 = TX + 4, H2 = TY + 4;   // p, u windows; mu, grad phi (ring 2)
+    static constexpr int W1 = TX + 2, H1 = TY + 2;   // collision region (ring 1)
+    static constexpr int A3 = W3 * H3, A2 = W2 * H2, A1 = W1 * H1;
+    static constexpr int NSCALAR = A3 + 6 * A2 + 4 * A1 + 18 * A1;
+};
+
+template <typename T, typename S, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
+                 S *__restrict__ fout, S *__restrict__ gout,
+                 const T *__restrict__ phi, const T *__restrict__ pfl,
+                 const T *__restrict__ ux, const T *__restrict__ uy,
+                 const T *__restrict__ upx, const T *__restrict__ upy,
+                 const T *__restrict__ uhx, const T *__restrict__ uhy,
+                 T *__restrict__ phibar, T *__restrict__ phat,
+                 T *__restrict__ jxo, T *__restrict__ jyo)
+{
+    using G = CSGeom<TX, TY>;
+    constexpr int W3 = G::W3, W2 = G::W2, H2 = G::H2, W1 = G::W1, H1 = G::H1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s_phi = reinterpret_cast<T *>(smem_raw);
+    T *s_p = s_phi + G::A3;
+    T *s_ux = s_p + G::A2;
+    T *s_uy = s_ux + G::A2;
+    T *s_mu = s_uy + G::A2;
+    T *s_gx = s_mu + G::A2;
+    T *s_gy = s_gx + G::A2;
+    T *s_upx = s_gy + G::A2;
+    T *s_upy = s_upx + G::A1;
+    T *s_uhx = s_upy + G::A1;
+    T *s_uhy = s_uhx + G::A1;
+    T *s_f = s_uhy + G::A1;      // [9][A1]
+    T *s_g = s_f + 9 * G::A1;    // [9][A1]
+
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const long long N = P.N;
+
+    load_tile<T, G::W3, G::H3>(s_phi, phi, x0 - 3, y0 - 3, P, false);
+    load_tile<T, W2, H2>(s_p, pfl, x0 - 2, y0 - 2, P, false);
+    load_tile<T, W2, H2>(s_ux, ux, x0 - 2, y0 - 2, P, true);
+    load_tile<T, W2, H2>(s_uy, uy, x0 - 2, y0 - 2, P, true);
+    load_tile<T, W1, H1>(s_upx, upx, x0 - 1, y0 - 1, P, true);
+    load_tile<T, W1, H1>(s_upy, upy, x0 - 1, y0 - 1, P, true);
+    load_tile<T, W1, H1>(s_uhx, uhx, x0 - 1, y0 - 1, P, true);
+    load_tile<T, W1, H1>(s_uhy, uhy, x0 - 1, y0 - 1, P, true);
+    __syncthreads();
+
+    // chemical potential and grad phi on tile + ring 2
+    for (int t = threadIdx.x; t < G::A2; t += blockDim.x) {
+        int ly = t / W2, lx = t - ly * W2;
+        int i3 = (ly + 1) * W3 + (lx + 1);
+        T ph = s_phi[i3];
+        s_mu[t] = T(4) * P.beta * (ph * ph * ph - ph) - P.kappa * iso_lap<T, W3>(s_phi, i3);
+        T gx, gy;
+        iso_grad<T, W3>(s_phi, i3, gx, gy);
+        s_gx[t] = gx;
+        s_gy[t] = gy;
+    }
+    __syncthreads();
+
+    // forces and collision on tile + ring 1
+    for (int t = threadIdx.x; t < G::A1; t += blockDim.x) {
+        int ly = t / W1, lx = t - ly * W1;
+        const int X = x0 - 1 + lx, Y = y0 - 1 + ly;
+        const bool ghost = (!P.px && (X < 0 || X >= P.nx)) || (!P.py && (Y < 0 || Y >= P.ny));
+        if (ghost) continue;   // beyond a wall: never pulled (bounce-back instead)
+        int fxm, fym;
+        const long long gidx = (long long)map_axis(Y, P.ny, P.py, fym) * P.nx + map_axis(X, P.nx, P.px, fxm);
+        const int i2 = (ly + 1) * W2 + (lx + 1);
+        const int i3 = (ly + 2) * W3 + (lx + 2);
+
+        const T ph = s_phi[i3];
+        T rho, nu;
+        rho_nu(P, ph, rho, nu);
+        const T mu = s_mu[i2];
+        const T gphx = s_gx[i2], gphy = s_gy[i2];
+        const T grx = P.drho * gphx, gry = P.drho * gphy;
+        T dmx, dmy;
+        iso_grad<T, W2>(s_mu, i2, dmx, dmy);
+        const T Jx = P.drho * P.M * dmx, Jy = P.drho * P.M * dmy;
+        // surface force: kappa div T, T = (gy^2, -gx gy; -gx gy, gx^2) from grad phi
+        T Fsx, Fsy;
+        {
+            const int nb[8] = {i2 + 1, i2 - 1, i2 + W2, i2 - W2, i2 + W2 + 1, i2 + W2 - 1, i2 - W2 - 1, i2 - W2 + 1};
+            T txx[8], txy[8], tyy[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const T a = s_gx[nb[k]], b = s_gy[nb[k]];
+                txx[k] = b * b;
+                txy[k] = -a * b;
+                tyy[k] = a * a;
+            }
+            // order: E, W, N, S, NE, NW, SW, SE
+            const T dxx = (txx[0] - txx[1]) * T(1.0 / 3.0) + (txx[4] - txx[5] - txx[6] + txx[7]) * T(1.0 / 12.0);
+            const T dyxy = (txy[2] - txy[3]) * T(1.0 / 3.0) + (txy[4] + txy[5] - txy[6] - txy[7]) * T(1.0 / 12.0);
+            const T dxxy = (txy[0] - txy[1]) * T(1.0 / 3.0) + (txy[4] - txy[5] - txy[6] + txy[7]) * T(1.0 / 12.0);
+            const T dyyy = (tyy[2] - tyy[3]) * T(1.0 / 3.0) + (tyy[4] + tyy[5] - tyy[6] - tyy[7]) * T(1.0 / 12.0);
+            Fsx = P.kappa * (dxx + dyxy);
+            Fsy = P.kappa * (dxxy + dyyy);
+        }
+        const T pc = s_p[i2];
+        T dpx, dpy, dxux, dyux, dxuy, dyuy;
+        iso_grad<T, W2>(s_p, i2, dpx, dpy);
+        iso_grad<T, W2>(s_ux, i2, dxux, dyux);
+        iso_grad<T, W2>(s_uy, i2, dxuy, dyuy);
+        const T u0 = s_ux[i2], u1 = s_uy[i2];
+        const T Sxx = T(2) * dxux, Sxy = dyux + dxuy, Syy = T(2) * dyuy;
+        const T Fx = -pc * grx + Fsx + nu * (Sxx * grx + Sxy * gry) + (Jx * dxux + Jy * dyux) + rho * P.gx;
+        const T Fy = -pc * gry + Fsy + nu * (Sxy * grx + Syy * gry) + (Jx * dxuy + Jy * dyuy) + rho * P.gy;
+        const T ax = (u0 - s_upx[t]) + u0 * dxux + u1 * dyux;
+        const T ay = (u1 - s_upy[t]) + u0 * dxuy + u1 * dyuy;
+        const T u2 = u0 * u0 + u1 * u1;
+
+        // ---- CH populations
+        {
+            T f[9], m[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) f[q] = Codec<S, T>::load(fin[q * N + gidx]);
+            to_moments(f, m);
+            const T em = P.eta * mu;
+            const T meq[9] = {ph, T(2) * em - T(4) * ph + T(3) * ph * u2, T(4) * ph - T(3) * em - T(3) * ph * u2,
+                              ph * u0, -ph * u0, ph * u1, -ph * u1, ph * (u0 * u0 - u1 * u1), ph * u0 * u1};
+            const T mF[9] = {T(0), T(0), T(0), ph * ax, -ph * ax, ph * ay, -ph * ay, T(0), T(0)};
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                m[k] = m[k] - P.sf[k] * (m[k] - meq[k]) + (T(1) - T(0.5) * P.sf[k]) * mF[k];
+            from_moments(m, f);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) s_f[q * G::A1 + t] = f[q];
+        }
+        // ---- NS populations
+        {
+            T g[9], m[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) g[q] = Codec<S, T>::load(gin[q * N + gidx]);
+            to_moments(g, m);
+            const T ph_ = m[0] * T(1.0 / 3.0);          // p_hat = cs^2 sum g
+            const T h0 = s_uhx[t], h1 = s_uhy[t];
+            const T h2 = h0 * h0 + h1 * h1;
+            const T pf = pc;
+            const T mef[9] = {T(3) * pf, T(-6) * pf + T(3) * u2, T(3) * pf - T(3) * u2, u0, -u0, u1, -u1,
+                              u0 * u0 - u1 * u1, u0 * u1};
+            const T meh[9] = {T(3) * ph_, T(-6) * ph_ + T(3) * h2, T(3) * ph_ - T(3) * h2, h0, -h0, h1, -h1,
+                              h0 * h0 - h1 * h1, h0 * h1};
+            const T ir = T(1) / rho;
+            const T bx = Fx * ir - dpx, by = Fy * ir - dpy;
+            const T bu = bx * u0 + by * u1;
+            const T mG[9] = {T(0), T(6) * bu, T(-6) * bu, Fx * ir, -Fx * ir, Fy * ir, -Fy * ir,
+                             T(2) * (bx * u0 - by * u1), by * u0 + bx * u1};
+            const T s78 = T(1) / (nu * T(3) + T(0.5));  // 1/tau_g, tau_g = nu/cs^2 + 1/2
+            T s[9];
+#pragma unroll
+            for (int k = 0; k < 7; ++k) s[k] = P.sg[k];
+            s[7] = s78;
+            s[8] = s78;
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                m[k] = mef[k] + (T(1) - s[k]) * (m[k] - meh[k]) + (T(1) - T(0.5) * s[k]) * mG[k];
+            from_moments(m, g);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) s_g[q * G::A1 + t] = g[q];
+        }
+    }
+    __syncthreads();
+
+    // pull streaming for the tile and post-stream moments
+    constexpr int cxv[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    constexpr int cyv[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    constexpr int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    for (int t = threadIdx.x; t < TX * TY; t += blockDim.x) {
+        int ly = t / TX, lx = t - ly * TX;
+        const int X = x0 + lx, Y = y0 + ly;
+        if (X >= P.nx || Y >= P.ny) continue;
+        const long long gidx = (long long)Y * P.nx + X;
+        const int c1 = (ly + 1) * W1 + (lx + 1);
+        T sf = T(0), sg = T(0), sgx = T(0), sgy = T(0);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int SX = X - cxv[q], SY = Y - cyv[q];
+            const bool wall = (!P.px && (SX < 0 || SX >= P.nx)) || (!P.py && (SY < 0 || SY >= P.ny));
+            const int src = wall ? (opp[q] * G::A1 + c1) : (q * G::A1 + c1 - cyv[q] * W1 - cxv[q]);
+            const T fv = s_f[src];
+            const T gv = s_g[src];
+            const S fs = Codec<S, T>::store(fv);
+            const S gs = Codec<S, T>::store(gv);
+            fout[q * N + gidx] = fs;
+            gout[q * N + gidx] = gs;
+            // moments of what is stored, so the stored state is self-consistent
+            const T fr = Codec<S, T>::load(fs), gr = Codec<S, T>::load(gs);
+            sf += fr;
+            sg += gr;
+            sgx += T(cxv[q]) * gr;
+            sgy += T(cyv[q]) * gr;
+        }
+        phibar[gidx] = sf;
+        phat[gidx] = sg * T(1.0 / 3.0);
+        jxo[gidx] = sgx;
+        jyo[gidx] = sgy;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2: one stage of the TVD-RK3 correction (Sec. III.A Eq. TVD-3order)
+//   out = a * phi_bar + b * (psi + L(psi)),  L(psi) = div(lambda J_phi + q),
+//   J_phi = (|grad psi| - 2(1 - psi^2)/W) n,  q = -M (grad mu_psi . n) n,
+//   n = grad psi / |grad psi|,  mu_psi = 4 beta (psi^3 - psi) - kappa lap psi,
+// every derivative by fourth-order central differences (Eq. fourOrder_FDM).
+// The composite stencil reaches 6 nodes, so the CTA stages psi with ring 6,
+// mu_psi on ring 4 and J_d on ring 2.
+// ---------------------------------------------------------------------------
+template <int TX, int TY> struct RKGeom {
+    static constexpr int W6 = TX + 12, H6 = TY + 12;
+    static constexpr int W4 = TX + 8, H4 = TY + 8;
+    static constexpr int W2 = TX + 4, H2 = TY + 4;
+    static constexpr int NSCALAR = W6 * H6 + W4 * H4 + 2 * W2 * H2;
+};
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+k_rk_stage(KP<T> P, const T *__restrict__ psi, const T *__restrict__ phibar, T *__restrict__ out,
+           T a, T b)
+{
+    using G = RKGeom<TX, TY>;
+    constexpr int W6 = G::W6, H6 = G::H6, W4 = G::W4, H4 = G::H4, W2 = G::W2, H2 = G::H2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s_psi = reinterpret_cast<T *>(smem_raw);
+    T *s_mu = s_psi + W6 * H6;
+    T *s_jx = s_mu + W4 * H4;
+    T *s_jy = s_jx + W2 * H2;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+
+    load_tile<T, W6, H6>(s_psi, psi, x0 - 6, y0 - 6, P, false);
+    __syncthreads();
+
+    for (int t = threadIdx.x; t < W4 * H4; t += blockDim.x) {
+        int ly = t / W4, lx = t - ly * W4;
+        int i6 = (ly + 2) * W6 + (lx + 2);
+        T v = s_psi[i6];
+        T lap = fd4_d2<T, 1>(s_psi, i6) + fd4_d2<T, W6>(s_psi, i6);
+        s_mu[t] = T(4) * P.beta * (v * v * v - v) - P.kappa * lap;
+    }
+    __syncthreads();
+
+    for (int t = threadIdx.x; t < W2 * H2; t += blockDim.x) {
+        int ly = t / W2, lx = t - ly * W2;
+        int i6 = (ly + 4) * W6 + (lx + 4);
+        int i4 = (ly + 2) * W4 + (lx + 2);
+        T gx = fd4_d1<T, 1>(s_psi, i6), gy = fd4_d1<T, W6>(s_psi, i6);
+        T v = s_psi[i6];
+        T mag = sqrt(gx * gx + gy * gy + P.eps2);
+        T inv = T(1) / mag;
+        T nxv = gx * inv, nyv = gy * inv;
+        T jphi = mag - T(2) * (T(1) - v * v) / P.W;
+        T jx = P.lambda * jphi * nxv, jy = P.lambda * jphi * nyv;
+        if (P.flux_corr) {
+            T mx = fd4_d1<T, 1>(s_mu, i4), my = fd4_d1<T, W4>(s_mu, i4);
+            T dmn = mx * nxv + my * nyv;
+            jx += -P.M * dmn * nxv;
+            jy += -P.M * dmn * nyv;
+        }
+        s_jx[t] = jx;
+        s_jy[t] = jy;
+    }
+    __syncthreads();
+
+    for (int t = threadIdx.x; t < TX * TY; t += blockDim.x) {
+        int ly = t / TX, lx = t - ly * TX;
+        const int X = x0 + lx, Y = y0 + ly;
+        if (X >= P.nx || Y >= P.ny) continue;
+        int i2 = (ly + 2) * W2 + (lx + 2);
+        T L = fd4_d1<T, 1>(s_jx, i2) + fd4_d1<T, W2>(s_jy, i2);
+        T v = s_psi[(ly + 6) * W6 + (lx + 6)];
+        long long gidx = (long long)Y * P.nx + X;
+        T r = b * (v + L);
+        if (a != T(0)) r = a * phibar[gidx] + r;
+        out[gidx] = r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 3: one Picard sweep of the implicit velocity (Sec. III.B Eq. u)
+//   u^{k+1} = j + F(u^k) / (2 rho),
+// F as in pass 1 but with phi^{n+1} and p_hat, the velocity gradients taken
+// from the previous iterate u^k.
+// ---------------------------------------------------------------------------
+template <int TX, int TY> struct PCGeom {
+    static constexpr int W2 = TX + 4, H2 = TY + 4;
+    static constexpr int W1 = TX + 2, H1 = TY + 2;
+    static constexpr int NSCALAR = W2 * H2 + 6 * W1 * H1;
+};
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+k_picard(KP<T> P, const T *__restrict__ phi, const T *__restrict__ phat,
+         const T *__restrict__ jx, const T *__restrict__ jy,
+         const T *__restrict__ ukx, const T *__restrict__ uky,
+         T *__restrict__ uox, T *__restrict__ uoy)
+{
+    using G = PCGeom<TX, TY>;
+    constexpr int W2 = G::W2, H2 = G::H2, W1 = G::W1, H1 = G::H1, A1 = W1 * H1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s_phi = reinterpret_cast<T *>(smem_raw);
+    T *s_p = s_phi + W2 * H2;
+    T *s_ux = s_p + A1;
+    T *s_uy = s_ux + A1;
+    T *s_mu = s_uy + A1;
+    T *s_gx = s_mu + A1;
+    T *s_gy = s_gx + A1;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+
+    load_tile<T, W2, H2>(s_phi, phi, x0 - 2, y0 - 2, P, false);
+    load_tile<T, W1, H1>(s_p, phat, x0 - 1, y0 - 1, P, false);
+    load_tile<T, W1, H1>(s_ux, ukx, x0 - 1, y0 - 1, P, true);
+    load_tile<T, W1, H1>(s_uy, uky, x0 - 1, y0 - 1, P, true);
+    __syncthreads();
+
+    for (int t = threadIdx.x; t < A1; t += blockDim.x) {
+        int ly = t / W1, lx = t - ly * W1;
+        int i2 = (ly + 1) * W2 + (lx + 1);
+        T ph = s_phi[i2];
+        s_mu[t] = T(4) * P.beta * (ph * ph * ph - ph) - P.kappa * iso_lap<T, W2>(s_phi, i2);
+        T gx, gy;
+        iso_grad<T, W2>(s_phi, i2, gx, gy);
+        s_gx[t] = gx;
+        s_gy[t] = gy;
+    }
+    __syncthreads();
+
+    for (int t = threadIdx.x; t < TX * TY; t += blockDim.x) {
+        int ly = t / TX, lx = t - ly * TX;
+        const int X = x0 + lx, Y = y0 + ly;
+        if (X >= P.nx || Y >= P.ny) continue;
+        const long long gidx = (long long)Y * P.nx + X;
+        const int i1 = (ly + 1) * W1 + (lx + 1);
+        const T ph = s_phi[(ly + 2) * W2 + (lx + 2)];
+        T rho, nu;
+        rho_nu(P, ph, rho, nu);
+        const T grx = P.drho * s_gx[i1], gry = P.drho * s_gy[i1];
+        T dmx, dmy;
+        iso_grad<T, W1>(s_mu, i1, dmx, dmy);
+        const T Jx = P.drho * P.M * dmx, Jy = P.drho * P.M * dmy;
+        T Fsx, Fsy;
+        {
+            const int nb[8] = {i1 + 1, i1 - 1, i1 + W1, i1 - W1, i1 + W1 + 1, i1 + W1 - 1, i1 - W1 - 1, i1 - W1 + 1};
+            T txx[8], txy[8], tyy[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const T a = s_gx[nb[k]], b = s_gy[nb[k]];
+                txx[k] = b * b;
+                txy[k] = -a * b;
+                tyy[k] = a * a;
+            }
+            const T dxx = (txx[0] - txx[1]) * T(1.0 / 3.0) + (txx[4] - txx[5] - txx[6] + txx[7]) * T(1.0 / 12.0);
+            const T dyxy = (txy[2] - txy[3]) * T(1.0 / 3.0) + (txy[4] + txy[5] - txy[6] - txy[7]) * T(1.0 / 12.0);
+            const T dxxy = (txy[0] - txy[1]) * T(1.0 / 3.0) + (txy[4] - txy[5] - txy[6] + txy[7]) * T(1.0 / 12.0);
+            const T dyyy = (tyy[2] - tyy[3]) * T(1.0 / 3.0) + (tyy[4] + tyy[5] - tyy[6] - tyy[7]) * T(1.0 / 12.0);
+            Fsx = P.kappa * (dxx + dyxy);
+            Fsy = P.kappa * (dxxy + dyyy);
+        }
+        const T pc = s_p[i1];
+        T dxux, dyux, dxuy, dyuy;
+        iso_grad<T, W1>(s_ux, i1, dxux, dyux);
+        iso_grad<T, W1>(s_uy, i1, dxuy, dyuy);
+        const T Sxx = T(2) * dxux, Sxy = dyux + dxuy, Syy = T(2) * dyuy;
+        const T Fx = -pc * grx + Fsx + nu * (Sxx * grx + Sxy * gry) + (Jx * dxux + Jy * dyux) + rho * P.gx;
+        const T Fy = -pc * gry + Fsy + nu * (Sxy * grx + Syy * gry) + (Jx * dxuy + Jy * dyuy) + rho * P.gy;
+        const T h = T(1) / (T(2) * rho);
+        uox[gidx] = jx[gidx] + Fx * h;
+        uoy[gidx] = jy[gidx] + Fy * h;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 4: explicit selective filter (Sec. III.B Eq. filter, App. B) of
+// chi = (p, ux, uy), every node from the unfiltered field:
+//   chi <- chi - a [ 2 d_0 chi + sum_{m=1..R} d_m (chi_{x+m} + chi_{x-m} + chi_{y+m} + chi_{y-m}) ].
+// ---------------------------------------------------------------------------
+template <int TX, int TY, int R> struct FLGeom {
+    static constexpr int WR = TX + 2 * R, HR = TY + 2 * R;
+    static constexpr int NSCALAR = 3 * WR * HR;
+};
+
+template <typename T, int TX, int TY, int R>
+__global__ void __launch_bounds__(TX * TY)
+k_filter(KP<T> P, const T *__restrict__ pin, const T *__restrict__ uxin, const T *__restrict__ uyin,
+         T *__restrict__ pout, T *__restrict__ uxout, T *__restrict__ uyout)
+{
+    using G = FLGeom<TX, TY, R>;
+    constexpr int WR = G::WR, HR = G::HR, A = WR * HR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s_p = reinterpret_cast<T *>(smem_raw);
+    T *s_ux = s_p + A;
+    T *s_uy = s_ux + A;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    load_tile<T, WR, HR>(s_p, pin, x0 - R, y0 - R, P, false);
+    load_tile<T, WR, HR>(s_ux, uxin, x0 - R, y0 - R, P, true);
+    load_tile<T, WR, HR>(s_uy, uyin, x0 - R, y0 - R, P, true);
+    __syncthreads();
+    for (int t = threadIdx.x; t < TX * TY; t += blockDim.x) {
+        int ly = t / TX, lx = t - ly * TX;
+        const int X = x0 + lx, Y = y0 + ly;
+        if (X >= P.nx || Y >= P.ny) continue;
+        const long long gidx = (long long)Y * P.nx + X;
+        const int c = (ly + R) * WR + (lx + R);
+        T *arr[3] = {s_p, s_ux, s_uy};
+        T res[3];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const T *s = arr[v];
+            T acc = T(2) * P.fd[0] * s[c];
+#pragma unroll
+            for (int m = 1; m <= R; ++m)
+                acc += P.fd[m] * (s[c + m] + s[c - m] + s[c + m * WR] + s[c - m * WR]);
+            res[v] = s[c] - P.fa * acc;
+        }
+        pout[gidx] = res[0];
+        uxout[gidx] = res[1];
+        uyout[gidx] = res[2];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Initialisation: f = f_eq(phi, mu(phi), u) (Eq. feq_CH), g = g_eq(p, u) (Eq. geq),
+// written through the moment form of the equilibria.
+// ---------------------------------------------------------------------------
+template <typename T, typename S>
+__global__ void k_init(KP<T> P, const T *__restrict__ phi, const T *__restrict__ p,
+                       const T *__restrict__ ux, const T *__restrict__ uy,
+                       S *__restrict__ f, S *__restrict__ g)
+{
+    const long long N = P.N;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < N;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int Y = (int)(k / P.nx), X = (int)(k - (long long)Y * P.nx);
+        T nbv[9];
+        constexpr int cxv[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+        constexpr int cyv[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            int fx, fy;
+            int gx = map_axis(X + cxv[q], P.nx, P.px, fx);
+            int gy = map_axis(Y + cyv[q], P.ny, P.py, fy);
+            nbv[q] = phi[(long long)gy * P.nx + gx];
+        }
+        // order in nbv: C, E, N, W, S, NE, NW, SW, SE
+        const T lap = (nbv[1] + nbv[2] + nbv[3] + nbv[4]) * T(2.0 / 3.0) +
+                      (nbv[5] + nbv[6] + nbv[7] + nbv[8]) * T(1.0 / 6.0) - nbv[0] * T(10.0 / 3.0);
+        const T ph = nbv[0];
+        const T mu = T(4) * P.beta * (ph * ph * ph - ph) - P.kappa * lap;
+        const T u0 = ux[k], u1 = uy[k], u2 = u0 * u0 + u1 * u1, pc = p[k];
+        const T em = P.eta * mu;
+        const T mf[9] = {ph, T(2) * em - T(4) * ph + T(3) * ph * u2, T(4) * ph - T(3) * em - T(3) * ph * u2,
+                         ph * u0, -ph * u0, ph * u1, -ph * u1, ph * (u0 * u0 - u1 * u1), ph * u0 * u1};
+        const T mg[9] = {T(3) * pc, T(-6) * pc + T(3) * u2, T(3) * pc - T(3) * u2, u0, -u0, u1, -u1,
+                         u0 * u0 - u1 * u1, u0 * u1};
+        T fv[9], gv[9];
+        from_moments(mf, fv);
+        from_moments(mg, gv);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            f[q * N + k] = Codec<S, T>::store(fv[q]);
+            g[q * N + k] = Codec<S, T>::store(gv[q]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics: per-block FP64 partial sums (Sec. IV.C volume, Sec. IV.E
+// centroid and rise velocity), reduced by warp shuffles; a second kernel
+// folds the block partials in a fixed order (deterministic).
+// ---------------------------------------------------------------------------
+constexpr int NDIAG = 11;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_diag_partial(int nx, long long N, const T *__restrict__ phi, const T *__restrict__ p,
+               const T *__restrict__ ux, const T *__restrict__ uy, double *__restrict__ part)
+{
+    double acc[NDIAG];
+#pragma unroll
+    for (int k = 0; k < NDIAG; ++k) acc[k] = 0.0;
+    acc[8] = -INFINITY;
+    acc[9] = INFINITY;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < N;
+         k += (long long)gridDim.x * blockDim.x) {
+        const double ph = (double)phi[k], v = (double)uy[k];
+        const double y = (double)(k / nx);
+        const double w = (1.0 - ph) * 0.5;
+        acc[0] += ph;
+        if (ph > 0) acc[1] += 1.0;
+        if (ph < 0) { acc[2] += 1.0; acc[3] += y; acc[4] += v; }
+        acc[5] += w;
+        acc[6] += w * y;
+        acc[7] += w * v;
+        acc[8] = fmax(acc[8], ph);
+        acc[9] = fmin(acc[9], ph);
+        acc[10] += (double)(!isfinite(ph)) + (double)(!isfinite((double)p[k])) +
+                   (double)(!isfinite((double)ux[k])) + (double)(!isfinite(v));
+    }
+    __shared__ double red[NDIAG][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NDIAG; ++k) {
+        double v = k == 8 ? warp_max(acc[k]) : (k == 9 ? warp_min(acc[k]) : warp_sum(acc[k]));
+        if (lane == 0) red[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NDIAG) {
+        const int k = threadIdx.x;
+        double v = red[k][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            v = k == 8 ? fmax(v, red[k][w]) : (k == 9 ? fmin(v, red[k][w]) : v + red[k][w]);
+        part[blockIdx.x * NDIAG + k] = v;
+    }
+}
+
+__global__ void k_diag_final(int nblocks, const double *__restrict__ part, double *__restrict__ out)
+{
+    const int k = threadIdx.x;
+    if (k >= NDIAG) return;
+    double v = part[k];
+    for (int b = 1; b < nblocks; ++b) {
+        double x = part[b * NDIAG + k];
+        v = k == 8 ? fmax(v, x) : (k == 9 ? fmin(v, x) : v + x);
+    }
+    out[k] = v;
+}
+
+}  // namespace lbm

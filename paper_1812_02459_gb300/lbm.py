@@ -1,0 +1,206 @@
+"""Python binding of the C ABI in include/lbm.h (argument marshalling only).
+
+Every step of the lattice update runs in the CUDA kernels of ``liblbm.so``;
+this module only converts arguments and raises on error codes.  There is no
+CPU fallback: if the library cannot be loaded, importing a solver fails.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_dp = C.POINTER(C.c_double)
+
+LBM_NDIAG = 11
+LBM_MIN_EXTENT = 12
+PRECISIONS = {"fp64": 0, "fp32": 1, "mix_bf16": 2, "mix_fp16": 3}
+STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_CUDA", 3: "LBM_ERR_OOM",
+          4: "LBM_ERR_NONFINITE", 5: "LBM_ERR_RANGE", 6: "LBM_ERR_STATE"}
+
+
+class LbmGrid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("periodic_x", C.c_int),
+                ("periodic_y", C.c_int), ("precision", C.c_int)]
+
+
+class LbmParams(C.Structure):
+    _fields_ = [
+        ("M", C.c_double), ("eta", C.c_double), ("W", C.c_double), ("sigma", C.c_double),
+        ("lambda_", C.c_double), ("flux_correction", C.c_int),
+        ("rho_H", C.c_double), ("rho_L", C.c_double), ("nu_H", C.c_double), ("nu_L", C.c_double),
+        ("s_f", C.c_double * 9), ("s_g", C.c_double * 9),
+        ("gx", C.c_double), ("gy", C.c_double),
+        ("filter_order", C.c_int), ("filter_a", C.c_double),
+        ("picard_iters", C.c_int), ("picard_zeta", C.c_double),
+        ("grad_eps", C.c_double), ("flags", C.c_uint),
+    ]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+EXPORTS = ("lbm_create", "lbm_step", "lbm_fields", "lbm_fields_device", "lbm_set_fields",
+           "lbm_diagnostics", "lbm_check", "lbm_get_state", "lbm_set_state",
+           "lbm_device_bytes", "lbm_destroy", "lbm_last_error")
+
+_lib = None
+
+
+def load(path=None):
+    """Load liblbm.so (building it first when missing); raise if that fails."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        p = _build.build()
+    L = C.CDLL(p)
+    vp = C.c_void_p
+    L.lbm_create.restype = C.c_int
+    L.lbm_create.argtypes = [C.POINTER(LbmGrid), C.POINTER(LbmParams), _dp, _dp, _dp, _dp, vp,
+                             C.POINTER(vp)]
+    L.lbm_step.restype = C.c_int
+    L.lbm_step.argtypes = [vp, C.c_int]
+    L.lbm_fields.restype = C.c_int
+    L.lbm_fields.argtypes = [vp, _dp, _dp, _dp, _dp]
+    L.lbm_fields_device.restype = C.c_int
+    L.lbm_fields_device.argtypes = [vp, vp, vp, vp, vp, C.c_int]
+    L.lbm_set_fields.restype = C.c_int
+    L.lbm_set_fields.argtypes = [vp, _dp, _dp, _dp, _dp]
+    L.lbm_diagnostics.restype = C.c_int
+    L.lbm_diagnostics.argtypes = [vp, _dp]
+    L.lbm_check.restype = C.c_int
+    L.lbm_check.argtypes = [vp, C.c_double]
+    L.lbm_get_state.restype = C.c_int
+    L.lbm_get_state.argtypes = [vp] + [_dp] * 10
+    L.lbm_set_state.restype = C.c_int
+    L.lbm_set_state.argtypes = [vp] + [_dp] * 10
+    L.lbm_device_bytes.restype = C.c_size_t
+    L.lbm_device_bytes.argtypes = [vp]
+    L.lbm_destroy.restype = None
+    L.lbm_destroy.argtypes = [vp]
+    L.lbm_last_error.restype = C.c_char_p
+    L.lbm_last_error.argtypes = [vp]
+    if path is None:
+        _lib = L
+    return L
+
+
+def make_params(prm):
+    """lbm_params from a plain dict (keys as in inputs.base_params)."""
+    p = LbmParams()
+    p.M = prm["M"]; p.eta = prm["eta"]; p.W = prm["W"]; p.sigma = prm["sigma"]
+    p.lambda_ = prm["lambda"]; p.flux_correction = int(prm.get("flux_correction", 1))
+    p.rho_H = prm["rho_H"]; p.rho_L = prm["rho_L"]; p.nu_H = prm["nu_H"]; p.nu_L = prm["nu_L"]
+    for k in range(9):
+        p.s_f[k] = prm["s_f"][k]
+        p.s_g[k] = prm["s_g"][k]
+    p.gx = prm.get("gx", 0.0); p.gy = prm.get("gy", 0.0)
+    p.filter_order = int(prm.get("filter_order", 11)); p.filter_a = prm.get("filter_a", 0.5)
+    p.picard_iters = int(prm.get("picard_iters", 2)); p.picard_zeta = prm.get("picard_zeta", 0.0)
+    p.grad_eps = prm.get("grad_eps", 1e-6); p.flags = int(prm.get("flags", 0))
+    return p
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def current_stream():
+    """The current torch CUDA stream handle, or 0 (legacy default stream)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0
+
+
+class Sim:
+    """A simulation on the GPU; host fields are float64 numpy arrays shaped [ny, nx]."""
+
+    def __init__(self, prm, phi0, p0, ux0, uy0, precision="fp32", stream=None):
+        self._lib = load()
+        phi0, p0, ux0, uy0 = (_f64(a) for a in (phi0, p0, ux0, uy0))
+        self.ny, self.nx = phi0.shape
+        self.precision = precision
+        g = LbmGrid(self.nx, self.ny, int(prm.get("periodic_x", 1)), int(prm.get("periodic_y", 1)),
+                    PRECISIONS[precision])
+        self.params = make_params(prm)
+        h = C.c_void_p()
+        st = self._lib.lbm_create(C.byref(g), C.byref(self.params), _ptr(phi0), _ptr(p0), _ptr(ux0),
+                                  _ptr(uy0), C.c_void_p(current_stream() if stream is None else stream),
+                                  C.byref(h))
+        if st != 0:
+            raise LbmError(st, self._lib.lbm_last_error(None).decode())
+        self._h = h
+
+    def _ck(self, st):
+        if st != 0:
+            raise LbmError(st, self._lib.lbm_last_error(self._h).decode())
+
+    def step(self, n=1):
+        self._ck(self._lib.lbm_step(self._h, int(n)))
+
+    def fields(self):
+        shp = (self.ny, self.nx)
+        out = [np.empty(shp) for _ in range(4)]
+        self._ck(self._lib.lbm_fields(self._h, *[_ptr(a) for a in out]))
+        return tuple(out)
+
+    def fields_device(self, phi, p, ux, uy):
+        """Copy into caller-owned device tensors (dtype of the handle's arithmetic)."""
+        import torch
+        dt = 0 if phi.dtype == torch.float64 else 1
+        ptrs = [None if t is None else C.c_void_p(t.data_ptr()) for t in (phi, p, ux, uy)]
+        self._ck(self._lib.lbm_fields_device(self._h, *ptrs, dt))
+
+    def set_fields(self, phi0, p0, ux0, uy0):
+        arrs = [_f64(a) for a in (phi0, p0, ux0, uy0)]
+        self._ck(self._lib.lbm_set_fields(self._h, *[_ptr(a) for a in arrs]))
+
+    def diagnostics(self, out=None):
+        o = np.empty(LBM_NDIAG) if out is None else out
+        self._ck(self._lib.lbm_diagnostics(self._h, _ptr(o)))
+        return o
+
+    def check(self, delta=0.05):
+        return self._lib.lbm_check(self._h, C.c_double(delta))
+
+    def state(self):
+        shp = (self.ny, self.nx)
+        f = np.empty((9,) + shp); g = np.empty((9,) + shp)
+        rest = [np.empty(shp) for _ in range(8)]
+        self._ck(self._lib.lbm_get_state(self._h, _ptr(f), _ptr(g), *[_ptr(a) for a in rest]))
+        keys = ("phi", "p", "ux", "uy", "uhx", "uhy", "upx", "upy")
+        d = dict(zip(keys, rest))
+        d["f"], d["g"] = f, g
+        return d
+
+    def set_state(self, f, g, phi, p, ux, uy, uhx, uhy, upx, upy):
+        arrs = [_f64(a) for a in (f, g, phi, p, ux, uy, uhx, uhy, upx, upy)]
+        self._ck(self._lib.lbm_set_state(self._h, *[_ptr(a) for a in arrs]))
+
+    def device_bytes(self):
+        return int(self._lib.lbm_device_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

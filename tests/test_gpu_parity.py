@@ -1,0 +1,168 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerance: max |gpu - oracle| / max |oracle| per field, at most 1e-12 in FP64
+and 1e-5 in FP32 after the stated number of steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_02459_gb300 import inputs, lbm
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def rel_err(a, b):
+    scale = np.abs(b).max()
+    return np.abs(a - b).max() / (scale if scale > 0 else 1.0)
+
+
+def run_both(prm, fields, steps, precision):
+    o = oracle.Sim(prm, *fields)
+    g = lbm.Sim(prm, *fields, precision=precision)
+    o.step(steps)
+    g.step(steps)
+    return o, g
+
+
+def assert_parity(o, g, tol, names=("phi", "p", "ux", "uy")):
+    of, gf = o.fields(), g.fields()
+    errs = {n: rel_err(b, a) for n, a, b in zip(names, of, gf)}
+    for n, e in errs.items():
+        assert e <= tol, f"{n}: {e:.3e} > {tol:.0e} ({errs})"
+    return errs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_static_drop_200_steps(precision):
+    prm, fields = inputs.static_drop(n=64, R=16.0)
+    o, g = run_both(prm, fields, 200, precision)
+    assert_parity(o, g, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ragged_walls_gravity(precision):
+    nx, ny = 45, 37
+    phi, p, ux, uy = inputs.random_fields(nx, ny, seed=1)
+    prm = inputs.base_params(rho_H=20.0, sigma=5e-3, gy=-2e-6, periodic_y=0)
+    o, g = run_both(prm, (phi, p, ux, uy), 60, precision)
+    assert_parity(o, g, TOL[precision])
+
+
+def test_walls_on_both_axes_fp64():
+    nx, ny = 37, 29
+    phi, p, ux, uy = inputs.random_fields(nx, ny, seed=2)
+    prm = inputs.base_params(rho_H=5.0, sigma=2e-3, gx=1e-6, periodic_x=0, periodic_y=0)
+    o, g = run_both(prm, (phi, p, ux, uy), 40, "fp64")
+    assert_parity(o, g, TOL["fp64"])
+
+
+@pytest.mark.parametrize("shape", [(12, 12), (12, 20), (33, 12)])
+def test_minimal_extents_fp64(shape):
+    nx, ny = shape
+    phi, p, ux, uy = inputs.random_fields(nx, ny, seed=3)
+    prm = inputs.base_params(rho_H=3.0, sigma=1e-3, periodic_y=0 if nx == 33 else 1)
+    o, g = run_both(prm, (phi, p, ux, uy), 20, "fp64")
+    assert_parity(o, g, TOL["fp64"])
+
+
+@pytest.mark.parametrize("order,picard", [(0, 1), (5, 2), (7, 3), (9, 2)])
+def test_filter_orders_and_sweeps_fp64(order, picard):
+    nx, ny = 33, 27
+    phi, p, ux, uy = inputs.random_fields(nx, ny, seed=4)
+    prm = inputs.base_params(rho_H=10.0, sigma=2e-3, filter_order=order, picard_iters=picard,
+                             filter_a=0.3, periodic_y=0, gy=-1e-6)
+    o, g = run_both(prm, (phi, p, ux, uy), 30, "fp64")
+    assert_parity(o, g, TOL["fp64"])
+
+
+def test_original_ch_variant_fp64():
+    prm, fields = inputs.static_drop(n=48, R=12.0)
+    prm.update({"lambda": 0.0, "flux_correction": 0})
+    o, g = run_both(prm, fields, 100, "fp64")
+    assert_parity(o, g, TOL["fp64"])
+
+
+def test_state_matches_oracle_and_round_trips_fp64():
+    nx, ny = 40, 24
+    phi, p, ux, uy = inputs.random_fields(nx, ny, seed=6)
+    prm = inputs.base_params(rho_H=8.0, sigma=3e-3, periodic_y=0, gy=-1e-6)
+    o, g = run_both(prm, (phi, p, ux, uy), 25, "fp64")
+    os_, gs = o.state(), g.state()
+    for k in ("f", "g", "uhx", "uhy", "upx", "upy"):
+        assert rel_err(gs[k], os_[k]) <= 1e-12, k
+    # restore the state into a fresh handle and continue: identical to continuing in place
+    h2 = lbm.Sim(prm, phi, p, ux, uy, precision="fp64")
+    h2.set_state(gs["f"], gs["g"], gs["phi"], gs["p"], gs["ux"], gs["uy"], gs["uhx"], gs["uhy"],
+                 gs["upx"], gs["upy"])
+    g.step(5)
+    h2.step(5)
+    for a, b in zip(g.fields(), h2.fields()):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_diagnostics_match_oracle(precision):
+    prm, fields = inputs.rising_bubble(nx=48, ny=96, R=8.0, yc=30.0)
+    o, g = run_both(prm, fields, 40, precision)
+    do, dg = o.diagnostics(), g.diagnostics()
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    assert abs(dg[0] - do[0]) <= tol * np.abs(o.fields()[0]).sum()
+    for k in (5, 6, 8, 9):
+        assert abs(dg[k] - do[k]) <= tol * max(1.0, abs(do[k])) * 10, k
+    assert dg[10] == 0
+    if precision == "fp64":
+        assert dg[1] == do[1] and dg[2] == do[2]
+
+
+def test_zero_steps_and_conservation_fp32():
+    prm, fields = inputs.static_drop(n=40, R=10.0)
+    g = lbm.Sim(prm, *fields, precision="fp32")
+    g.step(0)
+    phi0 = g.fields()[0]
+    assert np.abs(phi0 - fields[0]).max() < 1e-7
+    d0 = g.diagnostics()[0]
+    g.step(300)
+    assert abs(g.diagnostics()[0] - d0) < 1e-4     # fp32 round-off on a sum of ~1600 values
+    assert g.check(1e-2) == 0
+
+
+@pytest.mark.slow
+def test_rising_bubble_256x512_fp32():
+    """The rising-bubble workload (rho ratio 1000, walls) at its full size."""
+    prm, fields = inputs.rising_bubble()
+    o, g = run_both(prm, fields, 40, "fp32")
+    assert_parity(o, g, TOL["fp32"])
+
+
+def test_full_size_capillary_wave_sampled_fp32():
+    """4096^2 capillary wave (the throughput workload), one step in the launch
+    configuration the benchmark times, checked on sampled patches: the oracle
+    advances each 128^2 patch of the initial state on its own (periodic in x,
+    the real wall where the patch touches one) and the central nodes, which no
+    patch edge reaches within one step, must match."""
+    n = 4096
+    prm, fields = inputs.capillary_wave(n=n)
+    g = lbm.Sim(prm, *fields, precision="fp32")
+    g.step(1)
+    gf = g.fields()
+    g.close()
+    P, m = 128, 40
+    for (x0, y0, wall) in [(1000, 1980, False), (4096 - 128, 2000, False), (200, 0, True)]:
+        sub = [a[y0:y0 + P, x0:x0 + P] for a in fields]
+        pp = dict(prm)
+        pp["periodic_x"] = 1
+        pp["periodic_y"] = 0 if wall else 1
+        o = oracle.Sim(pp, *sub)
+        o.step(1)
+        of = o.fields()
+        ys = slice(0, P - m) if wall else slice(m, P - m)
+        for a, b in zip(gf, of):
+            ga = a[y0:y0 + P, x0:x0 + P][ys, m:P - m]
+            ob = b[ys, m:P - m]
+            scale = max(np.abs(b).max(), 1e-30)
+            assert np.abs(ga - ob).max() / scale <= 2e-5
