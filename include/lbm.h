@@ -167,6 +167,20 @@ lbm_status lbm_set_state(lbm_handle *h, const double *f, const double *g, const 
                          const double *uhx, const double *uhy,
                          const double *upx, const double *upy);
 
+/*
+ * Per-kernel device timing (a tracing aid, not part of the method).
+ * lbm_profile(h, 1) clears the totals and starts recording a pair of CUDA
+ * events around every kernel launch that lbm_step issues; lbm_profile(h, 0)
+ * stops.  lbm_profile_read fills ms[k] (total device milliseconds) and
+ * launches[k] for each kernel kind k < LBM_NKERNELS, summed since recording
+ * started; it synchronises the stream.  Kinds: 0 collide+stream,
+ * 1 RK3 stage, 2 Picard sweep, 3 filter.
+ */
+#define LBM_NKERNELS 4
+lbm_status lbm_profile(lbm_handle *h, int on);
+lbm_status lbm_profile_read(lbm_handle *h, double *ms, long long *launches);
+const char *lbm_kernel_name(int kind);
+
 /* lbm_device_bytes -- device memory held by the handle, in bytes. */
 size_t lbm_device_bytes(const lbm_handle *h);
 

@@ -85,7 +85,7 @@ def make_params(nx, ny, prm):
     p.filter_a = prm.get("filter_a", 0.5)
     p.picard_iters = int(prm.get("picard_iters", 2))
     p.picard_zeta = prm.get("picard_zeta", 0.0)
-    p.grad_eps = prm.get("grad_eps", 1e-6)
+    p.grad_eps = prm.get("grad_eps", 1e-4)
     return p
 
 

@@ -21,7 +21,7 @@ using namespace lbm;
 
 namespace {
 
-constexpr int CS_TX = 32, CS_TY = 8;     // collide+stream tile
+constexpr int CS_TX = 30, CS_TY = 14;    // collide+stream tile: its ring-1 region is 32 x 16 = one node per thread
 constexpr int RK_TX = 32, RK_TY = 16;    // RK3 stage tile
 constexpr int PC_TX = 32, PC_TY = 8;     // Picard sweep tile
 constexpr int FL_TX = 32, FL_TY = 8;     // filter tile
@@ -71,6 +71,13 @@ struct lbm_handle {
     int diag_blocks = 1;
     KP<double> kpd{};
     KP<float> kpf{};
+    // per-kernel timing
+    bool prof = false;
+    struct Mark { int kind; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[LBM_NKERNELS]{};
+    long long prof_n[LBM_NKERNELS]{};
 };
 
 namespace {
@@ -173,11 +180,46 @@ lbm_status set_smem_limits(lbm_handle *h)
     return LBM_OK;
 }
 
+cudaEvent_t take_event(lbm_handle *h)
+{
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one kernel launch with events when per-kernel timing is on.
+struct Timed {
+    lbm_handle *h;
+    int kind;
+    cudaEvent_t a = nullptr;
+    Timed(lbm_handle *h_, int k) : h(h_), kind(k)
+    {
+        if (h->prof) {
+            a = take_event(h);
+            cudaEventRecord(a, h->stream);
+        }
+    }
+    ~Timed()
+    {
+        if (h->prof && a) {
+            cudaEvent_t b = take_event(h);
+            cudaEventRecord(b, h->stream);
+            h->marks.push_back({kind, a, b});
+        }
+    }
+};
+
 template <typename T, int R>
 void launch_filter_r(lbm_handle *h, const T *pin, const T *uxi, const T *uyi, T *po, T *uxo, T *uyo)
 {
     const KP<T> &P = kp_of<T>(h);
     dim3 grid((P.nx + FL_TX - 1) / FL_TX, (P.ny + FL_TY - 1) / FL_TY);
+    Timed tm(h, 3);
     k_filter<T, FL_TX, FL_TY, R><<<grid, FL_TX * FL_TY, smem_fl<T, R>(), h->stream>>>(P, pin, uxi, uyi, po, uxo, uyo);
 }
 
@@ -194,18 +236,28 @@ lbm_status step_impl(lbm_handle *h)
 
     {   // fields, forces, collision of f and g, pull streaming, post-stream moments
         dim3 grid((P.nx + CS_TX - 1) / CS_TX, (P.ny + CS_TY - 1) / CS_TY);
-        k_collide_stream<T, S, CS_TX, CS_TY><<<grid, CS_TX * CS_TY, smem_cs<T>(), st>>>(
+        Timed tm(h, 0);
+        k_collide_stream<T, S, CS_TX, CS_TY><<<grid, (CS_TX + 2) * (CS_TY + 2), smem_cs<T>(), st>>>(
             P, (const S *)h->f[c], (const S *)h->g[c], (S *)h->f[1 - c], (S *)h->g[1 - c], phi, pf, uxc, uyc,
             uxp, uyp, uhx, uhy, phibar, phat, jx, jy);
     }
     {   // TVD-RK3 finite-difference correction: phi_bar -> phi^{n+1}
         dim3 grid((P.nx + RK_TX - 1) / RK_TX, (P.ny + RK_TY - 1) / RK_TY);
         const size_t sm = smem_rk<T>();
-        k_rk_stage<T, RK_TX, RK_TY><<<grid, RK_TX * RK_TY, sm, st>>>(P, phibar, phibar, (T *)h->s1, T(0), T(1));
-        k_rk_stage<T, RK_TX, RK_TY><<<grid, RK_TX * RK_TY, sm, st>>>(P, (T *)h->s1, phibar, (T *)h->s2,
-                                                                     T(0.75), T(0.25));
-        k_rk_stage<T, RK_TX, RK_TY><<<grid, RK_TX * RK_TY, sm, st>>>(P, (T *)h->s2, phibar, phi,
-                                                                     T(1.0 / 3.0), T(2.0 / 3.0));
+        {
+            Timed tm(h, 1);
+            k_rk_stage<T, RK_TX, RK_TY><<<grid, RK_TX * RK_TY, sm, st>>>(P, phibar, phibar, (T *)h->s1, T(0), T(1));
+        }
+        {
+            Timed tm(h, 1);
+            k_rk_stage<T, RK_TX, RK_TY><<<grid, RK_TX * RK_TY, sm, st>>>(P, (T *)h->s1, phibar, (T *)h->s2,
+                                                                         T(0.75), T(0.25));
+        }
+        {
+            Timed tm(h, 1);
+            k_rk_stage<T, RK_TX, RK_TY><<<grid, RK_TX * RK_TY, sm, st>>>(P, (T *)h->s2, phibar, phi,
+                                                                         T(1.0 / 3.0), T(2.0 / 3.0));
+        }
     }
     {   // implicit velocity by Picard sweeps; the last sweep lands in u_hat
         dim3 grid((P.nx + PC_TX - 1) / PC_TX, (P.ny + PC_TY - 1) / PC_TY);
@@ -215,6 +267,7 @@ lbm_status step_impl(lbm_handle *h)
             const T *iy = k == 0 ? uyc : (const T *)h->tk[(k - 1) & 1][1];
             T *ox = k == K - 1 ? uhx : (T *)h->tk[k & 1][0];
             T *oy = k == K - 1 ? uhy : (T *)h->tk[k & 1][1];
+            Timed tm(h, 2);
             k_picard<T, PC_TX, PC_TY><<<grid, PC_TX * PC_TY, smem_pc<T>(), st>>>(P, phi, phat, jx, jy, ix, iy, ox, oy);
         }
     }
@@ -234,6 +287,44 @@ lbm_status step_impl(lbm_handle *h)
     CK(h, cudaGetLastError(), "kernel launch");
     h->cur ^= 1;
     h->ucur ^= 1;
+    return LBM_OK;
+}
+
+// The phi_bar and p_hat scratch planes are adjacent in the arena; between
+// steps they serve as an N-double staging area for field transfers.
+double *staging(lbm_handle *h) { return (double *)h->phibar; }
+
+// Host double field -> device plane of T (converted on the device).
+template <typename T>
+lbm_status upload_plane(lbm_handle *h, void *dst, const double *src)
+{
+    const size_t n = (size_t)h->N;
+    if (sizeof(T) == sizeof(double)) {
+        CK(h, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "upload");
+        return LBM_OK;
+    }
+    CK(h, cudaMemcpyAsync(staging(h), src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "upload");
+    k_cast<double, T><<<(int)std::min<long long>((h->N + 255) / 256, 4096), 256, 0, h->stream>>>(
+        staging(h), (T *)dst, h->N);
+    CK(h, cudaGetLastError(), "upload cast");
+    return LBM_OK;
+}
+
+// Device plane of T -> host double field (converted on the device).
+template <typename T>
+lbm_status download_plane(lbm_handle *h, double *dst, const void *src)
+{
+    if (!dst) return LBM_OK;
+    const size_t n = (size_t)h->N;
+    const void *from = src;
+    if (sizeof(T) != sizeof(double)) {
+        k_cast<T, double><<<(int)std::min<long long>((h->N + 255) / 256, 4096), 256, 0, h->stream>>>(
+            (const T *)src, staging(h), h->N);
+        CK(h, cudaGetLastError(), "download cast");
+        from = staging(h);
+    }
+    CK(h, cudaMemcpyAsync(dst, from, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "download");
+    CK(h, cudaStreamSynchronize(h->stream), "download sync");
     return LBM_OK;
 }
 
@@ -272,10 +363,10 @@ template <typename T, typename S>
 lbm_status init_impl(lbm_handle *h, const double *phi0, const double *p0, const double *ux0, const double *uy0)
 {
     lbm_status st;
-    if ((st = upload_field<T>(h, h->phi, phi0))) return st;
-    if ((st = upload_field<T>(h, h->pf, p0))) return st;
-    if ((st = upload_field<T>(h, h->ux[0], ux0))) return st;
-    if ((st = upload_field<T>(h, h->uy[0], uy0))) return st;
+    if ((st = upload_plane<T>(h, h->phi, phi0))) return st;
+    if ((st = upload_plane<T>(h, h->pf, p0))) return st;
+    if ((st = upload_plane<T>(h, h->ux[0], ux0))) return st;
+    if ((st = upload_plane<T>(h, h->uy[0], uy0))) return st;
     const size_t b = sizeof(T) * (size_t)h->N;
     h->cur = 0;
     h->ucur = 0;
@@ -312,11 +403,10 @@ template <typename T>
 lbm_status fields_impl(lbm_handle *h, double *phi, double *p, double *ux, double *uy)
 {
     lbm_status st;
-    const size_t n = (size_t)h->N;
-    if ((st = download_field<T>(h, phi, h->phi, n))) return st;
-    if ((st = download_field<T>(h, p, h->pf, n))) return st;
-    if ((st = download_field<T>(h, ux, h->ux[h->ucur], n))) return st;
-    if ((st = download_field<T>(h, uy, h->uy[h->ucur], n))) return st;
+    if ((st = download_plane<T>(h, phi, h->phi))) return st;
+    if ((st = download_plane<T>(h, p, h->pf))) return st;
+    if ((st = download_plane<T>(h, ux, h->ux[h->ucur]))) return st;
+    if ((st = download_plane<T>(h, uy, h->uy[h->ucur]))) return st;
     return LBM_OK;
 }
 
@@ -502,11 +592,52 @@ lbm_status lbm_set_state(lbm_handle *h, const double *f, const double *g, const 
                : set_state_impl<float, float>(h, f, g, phi, p, ux, uy, uhx, uhy, upx, upy);
 }
 
+lbm_status lbm_profile(lbm_handle *h, int on)
+{
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
+    if (on) {
+        CK(h, cudaStreamSynchronize(h->stream), "profile sync");
+        for (auto &m : h->marks) { h->pool.push_back(m.a); h->pool.push_back(m.b); }
+        h->marks.clear();
+        for (int k = 0; k < LBM_NKERNELS; ++k) { h->prof_ms[k] = 0.0; h->prof_n[k] = 0; }
+    }
+    h->prof = on != 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_handle *h, double *ms, long long *launches)
+{
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
+    CK(h, cudaStreamSynchronize(h->stream), "profile sync");
+    for (auto &m : h->marks) {
+        float t = 0.f;
+        CK(h, cudaEventElapsedTime(&t, m.a, m.b), "cudaEventElapsedTime");
+        h->prof_ms[m.kind] += t;
+        h->prof_n[m.kind] += 1;
+        h->pool.push_back(m.a);
+        h->pool.push_back(m.b);
+    }
+    h->marks.clear();
+    for (int k = 0; k < LBM_NKERNELS; ++k) {
+        if (ms) ms[k] = h->prof_ms[k];
+        if (launches) launches[k] = h->prof_n[k];
+    }
+    return LBM_OK;
+}
+
+const char *lbm_kernel_name(int kind)
+{
+    static const char *names[LBM_NKERNELS] = {"k_collide_stream", "k_rk_stage", "k_picard", "k_filter"};
+    return (kind >= 0 && kind < LBM_NKERNELS) ? names[kind] : "unknown";
+}
+
 size_t lbm_device_bytes(const lbm_handle *h) { return h ? h->arena_bytes : 0; }
 
 void lbm_destroy(lbm_handle *h)
 {
     if (!h) return;
+    for (auto &m : h->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+    for (auto e : h->pool) cudaEventDestroy(e);
     if (h->arena) cudaFree(h->arena);
     delete h;
 }

@@ -59,6 +59,7 @@ template <typename T> struct KP {
 // reports an odd number of reflections (sign change of an odd field).
 __device__ __forceinline__ int map_axis(int k, int n, int periodic, int &flip)
 {
+    if ((unsigned)k < (unsigned)n) { flip = 0; return k; }   // inside: the common case
     if (periodic) {
         int r = k % n;
         if (r < 0) r += n;
@@ -79,6 +80,14 @@ template <typename T, int WS, int HS>
 __device__ __forceinline__ void load_tile(T *s, const T *__restrict__ g, int x0, int y0,
                                           const KP<T> &P, bool odd)
 {
+    if (x0 >= 0 && y0 >= 0 && x0 + WS <= P.nx && y0 + HS <= P.ny) {
+        const T *base = g + (long long)y0 * P.nx + x0;
+        for (int t = threadIdx.x; t < WS * HS; t += blockDim.x) {
+            int ly = t / WS, lx = t - ly * WS;
+            s[t] = __ldg(&base[(long long)ly * P.nx + lx]);
+        }
+        return;
+    }
     for (int t = threadIdx.x; t < WS * HS; t += blockDim.x) {
         int ly = t / WS, lx = t - ly * WS;
         int fx, fy;
@@ -204,11 +213,35 @@ template <int TX, int TY> struct CSGeom {
     static constexpr int W2 = TX + 4, H2 = TY + 4;   // p, u windows; mu, grad phi (ring 2)
     static constexpr int W1 = TX + 2, H1 = TY + 2;   // collision region (ring 1)
     static constexpr int A3 = W3 * H3, A2 = W2 * H2, A1 = W1 * H1;
-    static constexpr int NSCALAR = A3 + 6 * A2 + 4 * A1 + 18 * A1;
+    static constexpr int NSCALAR = A3 + 6 * A2 + 18 * A1;
 };
 
+// Surface force kappa div(T), T = |grad phi|^2 I - grad phi grad phi
+// = (gy^2, -gx gy; -gx gy, gx^2), isotropic divergence from grad phi stored
+// at the eight neighbours of index i of a window of row stride WS.
+template <typename T, int WS>
+__device__ __forceinline__ void surface_force(const T *sgx, const T *sgy, int i, T kappa, T &Fx, T &Fy)
+{
+    const int nb[8] = {i + 1, i - 1, i + WS, i - WS, i + WS + 1, i + WS - 1, i - WS - 1, i - WS + 1};
+    T txx[8], txy[8], tyy[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const T a = sgx[nb[k]], b = sgy[nb[k]];
+        txx[k] = b * b;
+        txy[k] = -a * b;
+        tyy[k] = a * a;
+    }
+    // neighbour order: E, W, N, S, NE, NW, SW, SE
+    const T dxx = (txx[0] - txx[1]) * T(1.0 / 3.0) + (txx[4] - txx[5] - txx[6] + txx[7]) * T(1.0 / 12.0);
+    const T dyxy = (txy[2] - txy[3]) * T(1.0 / 3.0) + (txy[4] + txy[5] - txy[6] - txy[7]) * T(1.0 / 12.0);
+    const T dxxy = (txy[0] - txy[1]) * T(1.0 / 3.0) + (txy[4] - txy[5] - txy[6] + txy[7]) * T(1.0 / 12.0);
+    const T dyyy = (tyy[2] - tyy[3]) * T(1.0 / 3.0) + (tyy[4] + tyy[5] - tyy[6] - tyy[7]) * T(1.0 / 12.0);
+    Fx = kappa * (dxx + dyxy);
+    Fy = kappa * (dxxy + dyyy);
+}
+
 template <typename T, typename S, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
+__global__ void __launch_bounds__((TX + 2) * (TY + 2), 2)
 k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
                  S *__restrict__ fout, S *__restrict__ gout,
                  const T *__restrict__ phi, const T *__restrict__ pfl,
@@ -219,7 +252,7 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
                  T *__restrict__ jxo, T *__restrict__ jyo)
 {
     using G = CSGeom<TX, TY>;
-    constexpr int W3 = G::W3, W2 = G::W2, H2 = G::H2, W1 = G::W1, H1 = G::H1;
+    constexpr int W3 = G::W3, W2 = G::W2, H2 = G::H2, W1 = G::W1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s_phi = reinterpret_cast<T *>(smem_raw);
     T *s_p = s_phi + G::A3;
@@ -228,11 +261,7 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
     T *s_mu = s_uy + G::A2;
     T *s_gx = s_mu + G::A2;
     T *s_gy = s_gx + G::A2;
-    T *s_upx = s_gy + G::A2;
-    T *s_upy = s_upx + G::A1;
-    T *s_uhx = s_upy + G::A1;
-    T *s_uhy = s_uhx + G::A1;
-    T *s_f = s_uhy + G::A1;      // [9][A1]
+    T *s_f = s_gy + G::A2;       // [9][A1]
     T *s_g = s_f + 9 * G::A1;    // [9][A1]
 
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -242,10 +271,6 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
     load_tile<T, W2, H2>(s_p, pfl, x0 - 2, y0 - 2, P, false);
     load_tile<T, W2, H2>(s_ux, ux, x0 - 2, y0 - 2, P, true);
     load_tile<T, W2, H2>(s_uy, uy, x0 - 2, y0 - 2, P, true);
-    load_tile<T, W1, H1>(s_upx, upx, x0 - 1, y0 - 1, P, true);
-    load_tile<T, W1, H1>(s_upy, upy, x0 - 1, y0 - 1, P, true);
-    load_tile<T, W1, H1>(s_uhx, uhx, x0 - 1, y0 - 1, P, true);
-    load_tile<T, W1, H1>(s_uhy, uhy, x0 - 1, y0 - 1, P, true);
     __syncthreads();
 
     // chemical potential and grad phi on tile + ring 2
@@ -261,7 +286,7 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
     }
     __syncthreads();
 
-    // forces and collision on tile + ring 1
+    // forces and collision on tile + ring 1 (one node per thread)
     for (int t = threadIdx.x; t < G::A1; t += blockDim.x) {
         int ly = t / W1, lx = t - ly * W1;
         const int X = x0 - 1 + lx, Y = y0 - 1 + ly;
@@ -276,31 +301,12 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
         T rho, nu;
         rho_nu(P, ph, rho, nu);
         const T mu = s_mu[i2];
-        const T gphx = s_gx[i2], gphy = s_gy[i2];
-        const T grx = P.drho * gphx, gry = P.drho * gphy;
+        const T grx = P.drho * s_gx[i2], gry = P.drho * s_gy[i2];
         T dmx, dmy;
         iso_grad<T, W2>(s_mu, i2, dmx, dmy);
         const T Jx = P.drho * P.M * dmx, Jy = P.drho * P.M * dmy;
-        // surface force: kappa div T, T = (gy^2, -gx gy; -gx gy, gx^2) from grad phi
         T Fsx, Fsy;
-        {
-            const int nb[8] = {i2 + 1, i2 - 1, i2 + W2, i2 - W2, i2 + W2 + 1, i2 + W2 - 1, i2 - W2 - 1, i2 - W2 + 1};
-            T txx[8], txy[8], tyy[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const T a = s_gx[nb[k]], b = s_gy[nb[k]];
-                txx[k] = b * b;
-                txy[k] = -a * b;
-                tyy[k] = a * a;
-            }
-            // order: E, W, N, S, NE, NW, SW, SE
-            const T dxx = (txx[0] - txx[1]) * T(1.0 / 3.0) + (txx[4] - txx[5] - txx[6] + txx[7]) * T(1.0 / 12.0);
-            const T dyxy = (txy[2] - txy[3]) * T(1.0 / 3.0) + (txy[4] + txy[5] - txy[6] - txy[7]) * T(1.0 / 12.0);
-            const T dxxy = (txy[0] - txy[1]) * T(1.0 / 3.0) + (txy[4] - txy[5] - txy[6] + txy[7]) * T(1.0 / 12.0);
-            const T dyyy = (tyy[2] - tyy[3]) * T(1.0 / 3.0) + (tyy[4] + tyy[5] - tyy[6] - tyy[7]) * T(1.0 / 12.0);
-            Fsx = P.kappa * (dxx + dyxy);
-            Fsy = P.kappa * (dxxy + dyyy);
-        }
+        surface_force<T, W2>(s_gx, s_gy, i2, P.kappa, Fsx, Fsy);
         const T pc = s_p[i2];
         T dpx, dpy, dxux, dyux, dxuy, dyuy;
         iso_grad<T, W2>(s_p, i2, dpx, dpy);
@@ -310,8 +316,10 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
         const T Sxx = T(2) * dxux, Sxy = dyux + dxuy, Syy = T(2) * dyuy;
         const T Fx = -pc * grx + Fsx + nu * (Sxx * grx + Sxy * gry) + (Jx * dxux + Jy * dyux) + rho * P.gx;
         const T Fy = -pc * gry + Fsy + nu * (Sxy * grx + Syy * gry) + (Jx * dxuy + Jy * dyuy) + rho * P.gy;
-        const T ax = (u0 - s_upx[t]) + u0 * dxux + u1 * dyux;
-        const T ay = (u1 - s_upy[t]) + u0 * dxuy + u1 * dyuy;
+        // mirrored ring nodes carry the odd sign of u^{n-1} and u_hat too
+        const T sgn = (fxm ^ fym) ? T(-1) : T(1);
+        const T ax = (u0 - sgn * __ldg(&upx[gidx])) + u0 * dxux + u1 * dyux;
+        const T ay = (u1 - sgn * __ldg(&upy[gidx])) + u0 * dxuy + u1 * dyuy;
         const T u2 = u0 * u0 + u1 * u1;
 
         // ---- CH populations
@@ -338,10 +346,9 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
             for (int q = 0; q < 9; ++q) g[q] = Codec<S, T>::load(gin[q * N + gidx]);
             to_moments(g, m);
             const T ph_ = m[0] * T(1.0 / 3.0);          // p_hat = cs^2 sum g
-            const T h0 = s_uhx[t], h1 = s_uhy[t];
+            const T h0 = sgn * __ldg(&uhx[gidx]), h1 = sgn * __ldg(&uhy[gidx]);
             const T h2 = h0 * h0 + h1 * h1;
-            const T pf = pc;
-            const T mef[9] = {T(3) * pf, T(-6) * pf + T(3) * u2, T(3) * pf - T(3) * u2, u0, -u0, u1, -u1,
+            const T mef[9] = {T(3) * pc, T(-6) * pc + T(3) * u2, T(3) * pc - T(3) * u2, u0, -u0, u1, -u1,
                               u0 * u0 - u1 * u1, u0 * u1};
             const T meh[9] = {T(3) * ph_, T(-6) * ph_ + T(3) * h2, T(3) * ph_ - T(3) * h2, h0, -h0, h1, -h1,
                               h0 * h0 - h1 * h1, h0 * h1};
@@ -351,14 +358,11 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
             const T mG[9] = {T(0), T(6) * bu, T(-6) * bu, Fx * ir, -Fx * ir, Fy * ir, -Fy * ir,
                              T(2) * (bx * u0 - by * u1), by * u0 + bx * u1};
             const T s78 = T(1) / (nu * T(3) + T(0.5));  // 1/tau_g, tau_g = nu/cs^2 + 1/2
-            T s[9];
 #pragma unroll
-            for (int k = 0; k < 7; ++k) s[k] = P.sg[k];
-            s[7] = s78;
-            s[8] = s78;
-#pragma unroll
-            for (int k = 0; k < 9; ++k)
-                m[k] = mef[k] + (T(1) - s[k]) * (m[k] - meh[k]) + (T(1) - T(0.5) * s[k]) * mG[k];
+            for (int k = 0; k < 9; ++k) {
+                const T sk = k < 7 ? P.sg[k] : s78;
+                m[k] = mef[k] + (T(1) - sk) * (m[k] - meh[k]) + (T(1) - T(0.5) * sk) * mG[k];
+            }
             from_moments(m, g);
 #pragma unroll
             for (int q = 0; q < 9; ++q) s_g[q * G::A1 + t] = g[q];
@@ -376,16 +380,18 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
         if (X >= P.nx || Y >= P.ny) continue;
         const long long gidx = (long long)Y * P.nx + X;
         const int c1 = (ly + 1) * W1 + (lx + 1);
+        const bool edge = (!P.px && (X == 0 || X == P.nx - 1)) || (!P.py && (Y == 0 || Y == P.ny - 1));
         T sf = T(0), sg = T(0), sgx = T(0), sgy = T(0);
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-            const int SX = X - cxv[q], SY = Y - cyv[q];
-            const bool wall = (!P.px && (SX < 0 || SX >= P.nx)) || (!P.py && (SY < 0 || SY >= P.ny));
-            const int src = wall ? (opp[q] * G::A1 + c1) : (q * G::A1 + c1 - cyv[q] * W1 - cxv[q]);
-            const T fv = s_f[src];
-            const T gv = s_g[src];
-            const S fs = Codec<S, T>::store(fv);
-            const S gs = Codec<S, T>::store(gv);
+            int src = q * G::A1 + c1 - cyv[q] * W1 - cxv[q];
+            if (edge) {
+                const int SX = X - cxv[q], SY = Y - cyv[q];
+                const bool wall = (!P.px && (SX < 0 || SX >= P.nx)) || (!P.py && (SY < 0 || SY >= P.ny));
+                if (wall) src = opp[q] * G::A1 + c1;
+            }
+            const S fs = Codec<S, T>::store(s_f[src]);
+            const S gs = Codec<S, T>::store(s_g[src]);
             fout[q * N + gidx] = fs;
             gout[q * N + gidx] = gs;
             // moments of what is stored, so the stored state is self-consistent
@@ -665,6 +671,15 @@ __global__ void k_init(KP<T> P, const T *__restrict__ phi, const T *__restrict__
             g[q * N + k] = Codec<S, T>::store(gv[q]);
         }
     }
+}
+
+// Element-wise type conversion (host double fields <-> device arithmetic type).
+template <typename A, typename B>
+__global__ void k_cast(const A *__restrict__ in, B *__restrict__ out, long long n)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        out[k] = (B)in[k];
 }
 
 // ---------------------------------------------------------------------------

@@ -25,7 +25,7 @@ def base_params(**kw):
              rho_H=10.0, rho_L=1.0, nu_H=0.1, nu_L=0.1,
              s_f=list(S_F_DEFAULT), s_g=list(S_G_DEFAULT),
              gx=0.0, gy=0.0, filter_order=11, filter_a=0.5,
-             picard_iters=2, picard_zeta=0.0, grad_eps=1e-6,
+             picard_iters=2, picard_zeta=0.0, grad_eps=1e-4,
              periodic_x=1, periodic_y=1)
     p.update(kw)
     p["lambda"] = p.pop("lam")
@@ -77,7 +77,7 @@ def static_drop(n=64, R=16.0):
     return prm, (phi, zeros(n, n), zeros(n, n), zeros(n, n))
 
 
-def bubble_params(R, rho_ratio=1000.0, mu_ratio=100.0, Eo=10.0, Mo=1e-3, nu_H=1.0 / 60, M=0.05):
+def bubble_params(R, rho_ratio=1000.0, mu_ratio=100.0, Eo=10.0, Mo=1e-3, nu_H=1.0 / 300, M=0.05):
     """Rising-bubble parameters from the Eotvos and Morton numbers.
 
     Eo = rho_H g (2R)^2 / sigma, Mo = g mu_H^4 (rho_H - rho_L) / (rho_H^2 sigma^3),

@@ -46,7 +46,9 @@ class LbmError(RuntimeError):
 
 EXPORTS = ("lbm_create", "lbm_step", "lbm_fields", "lbm_fields_device", "lbm_set_fields",
            "lbm_diagnostics", "lbm_check", "lbm_get_state", "lbm_set_state",
+           "lbm_profile", "lbm_profile_read", "lbm_kernel_name",
            "lbm_device_bytes", "lbm_destroy", "lbm_last_error")
+LBM_NKERNELS = 4
 
 _lib = None
 
@@ -80,6 +82,12 @@ def load(path=None):
     L.lbm_get_state.argtypes = [vp] + [_dp] * 10
     L.lbm_set_state.restype = C.c_int
     L.lbm_set_state.argtypes = [vp] + [_dp] * 10
+    L.lbm_profile.restype = C.c_int
+    L.lbm_profile.argtypes = [vp, C.c_int]
+    L.lbm_profile_read.restype = C.c_int
+    L.lbm_profile_read.argtypes = [vp, _dp, C.POINTER(C.c_longlong)]
+    L.lbm_kernel_name.restype = C.c_char_p
+    L.lbm_kernel_name.argtypes = [C.c_int]
     L.lbm_device_bytes.restype = C.c_size_t
     L.lbm_device_bytes.argtypes = [vp]
     L.lbm_destroy.restype = None
@@ -103,7 +111,7 @@ def make_params(prm):
     p.gx = prm.get("gx", 0.0); p.gy = prm.get("gy", 0.0)
     p.filter_order = int(prm.get("filter_order", 11)); p.filter_a = prm.get("filter_a", 0.5)
     p.picard_iters = int(prm.get("picard_iters", 2)); p.picard_zeta = prm.get("picard_zeta", 0.0)
-    p.grad_eps = prm.get("grad_eps", 1e-6); p.flags = int(prm.get("flags", 0))
+    p.grad_eps = prm.get("grad_eps", 1e-4); p.flags = int(prm.get("flags", 0))
     return p
 
 
@@ -190,6 +198,18 @@ class Sim:
     def set_state(self, f, g, phi, p, ux, uy, uhx, uhy, upx, upy):
         arrs = [_f64(a) for a in (f, g, phi, p, ux, uy, uhx, uhy, upx, upy)]
         self._ck(self._lib.lbm_set_state(self._h, *[_ptr(a) for a in arrs]))
+
+    def profile(self, on=True):
+        """Start (clearing totals) or stop per-kernel device timing."""
+        self._ck(self._lib.lbm_profile(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches)} since profiling started."""
+        ms = np.zeros(LBM_NKERNELS)
+        n = (C.c_longlong * LBM_NKERNELS)()
+        self._ck(self._lib.lbm_profile_read(self._h, _ptr(ms), n))
+        return {self._lib.lbm_kernel_name(k).decode(): (float(ms[k]), int(n[k]))
+                for k in range(LBM_NKERNELS)}
 
     def device_bytes(self):
         return int(self._lib.lbm_device_bytes(self._h))
