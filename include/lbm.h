@@ -181,6 +181,38 @@ lbm_status lbm_profile(lbm_handle *h, int on);
 lbm_status lbm_profile_read(lbm_handle *h, double *ms, long long *launches);
 const char *lbm_kernel_name(int kind);
 
+/*
+ * lbm_field_sums_noalloc -- the sums of lbm_diagnostics for fields the
+ * caller holds on the device, computed without allocating device memory.
+ * The paper has no counterpart: this is an operational entry point.  It is
+ * for callers that cannot call cudaMalloc -- a host framework that owns all
+ * device memory through its own pool, a loop that cannot absorb the
+ * device-wide synchronisation of cudaMalloc/cudaFree, a monitor that must
+ * keep working after device memory is exhausted.
+ *   phi, p, ux, uy: device arrays of nx*ny elements, row-major [ny][nx],
+ *     dtype 0 = double, 1 = float (caller-owned, read only).
+ *   out: device array of LBM_NDIAG doubles (caller-owned), written with the
+ *     layout documented at lbm_diagnostics.
+ *   stream: a cudaStream_t or NULL; the call is asynchronous on it.
+ * Scratch: the block partial sums live in one file-scope static device
+ * array sized for LBM_NOALLOC_MAX_NODES nodes (4096 partials x 11 doubles,
+ * 352 KiB), held by every GPU that loads the library until the process
+ * exits.  nx*ny above LBM_NOALLOC_MAX_NODES is rejected with LBM_ERR_ARG.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls share the one array: calls that overlap on the
+ * GPU (different streams, or different host threads without ordering) race
+ * on it.  Nothing accumulates into it -- each call writes every partial it
+ * later reads -- so no clearing is needed between calls.
+ * Errors: LBM_ERR_ARG (NULL pointer, bad sizes or dtype), LBM_ERR_CUDA; the
+ * text is in lbm_noalloc_last_error().  No cudaMalloc, cudaFree or
+ * allocating library call is made.
+ */
+#define LBM_NOALLOC_MAX_NODES 67108864
+lbm_status lbm_field_sums_noalloc(const void *phi, const void *p, const void *ux, const void *uy,
+                                  int nx, int ny, int dtype, double *out, void *stream);
+const char *lbm_noalloc_last_error(void);
+
 /* lbm_device_bytes -- device memory held by the handle, in bytes. */
 size_t lbm_device_bytes(const lbm_handle *h);
 

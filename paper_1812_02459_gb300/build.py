@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "liblbm.so")
-SOURCES = [os.path.join(CSRC, "lbm_api.cu")]
+SOURCES = [os.path.join(CSRC, "lbm_api.cu"), os.path.join(CSRC, "lbm_noalloc.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "lbm_kernels.cuh"), os.path.join(INCLUDE, "lbm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -751,7 +751,7 @@ k_diag_partial(int nx, long long N, const T *__restrict__ phi, const T *__restri
     }
 }
 
-__global__ void k_diag_final(int nblocks, const double *__restrict__ part, double *__restrict__ out)
+static __global__ void k_diag_final(int nblocks, const double *__restrict__ part, double *__restrict__ out)
 {
     const int k = threadIdx.x;
     if (k >= NDIAG) return;

@@ -47,6 +47,7 @@ class LbmError(RuntimeError):
 EXPORTS = ("lbm_create", "lbm_step", "lbm_fields", "lbm_fields_device", "lbm_set_fields",
            "lbm_diagnostics", "lbm_check", "lbm_get_state", "lbm_set_state",
            "lbm_profile", "lbm_profile_read", "lbm_kernel_name",
+           "lbm_field_sums_noalloc", "lbm_noalloc_last_error",
            "lbm_device_bytes", "lbm_destroy", "lbm_last_error")
 LBM_NKERNELS = 4
 
@@ -88,6 +89,10 @@ def load(path=None):
     L.lbm_profile_read.argtypes = [vp, _dp, C.POINTER(C.c_longlong)]
     L.lbm_kernel_name.restype = C.c_char_p
     L.lbm_kernel_name.argtypes = [C.c_int]
+    L.lbm_field_sums_noalloc.restype = C.c_int
+    L.lbm_field_sums_noalloc.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, C.c_int, vp, vp]
+    L.lbm_noalloc_last_error.restype = C.c_char_p
+    L.lbm_noalloc_last_error.argtypes = []
     L.lbm_device_bytes.restype = C.c_size_t
     L.lbm_device_bytes.argtypes = [vp]
     L.lbm_destroy.restype = None
@@ -132,6 +137,22 @@ def current_stream():
     except Exception:
         pass
     return 0
+
+
+LBM_NOALLOC_MAX_NODES = 67108864
+
+
+def field_sums_noalloc(phi, p, ux, uy, out, stream=None):
+    """lbm_field_sums_noalloc on caller-owned device tensors (float32 or float64,
+    shaped [ny, nx]); out is a device float64 tensor of LBM_NDIAG elements."""
+    L = load()
+    ny, nx = phi.shape
+    dt = {"torch.float64": 0, "torch.float32": 1}[str(phi.dtype)]
+    ptr = lambda t: C.c_void_p(t.data_ptr())
+    st = L.lbm_field_sums_noalloc(ptr(phi), ptr(p), ptr(ux), ptr(uy), nx, ny, dt, ptr(out),
+                                  C.c_void_p(current_stream() if stream is None else stream))
+    if st != 0:
+        raise LbmError(st, L.lbm_noalloc_last_error().decode())
 
 
 class Sim:
