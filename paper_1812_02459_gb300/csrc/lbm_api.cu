@@ -23,8 +23,8 @@ namespace {
 
 constexpr int CS_TX = 30, CS_TY = 14;    // collide+stream tile: its ring-1 region is 32 x 16 = one node per thread
 constexpr int RK_TX = 32, RK_TY = 16;    // RK3 stage tile
-constexpr int PC_TX = 32, PC_TY = 8;     // Picard sweep tile
-constexpr int FL_TX = 32, FL_TY = 8;     // filter tile
+constexpr int PC_TX = 32, PC_TY = 16;    // Picard sweep tile
+constexpr int FL_TX = 32, FL_TY = 16;    // filter tile
 constexpr int DIAG_THREADS = 256;
 constexpr int DIAG_MAX_BLOCKS = 1216;    // 8 x 152 SMs
 
@@ -122,6 +122,7 @@ void build_kp(const lbm_grid &gr, const lbm_params &p, KP<T> &k)
     k.sf[3] = k.sf[5] = (T)(1.0 / tau_f);
     k.gx = (T)p.gx; k.gy = (T)p.gy;
     k.eps2 = (T)(p.grad_eps * p.grad_eps);
+    k.two_over_W = (T)(2.0 / p.W);
     double d[6];
     filter_table(p.filter_order, d);
     for (int m = 0; m < 6; ++m) k.fd[m] = (T)d[m];

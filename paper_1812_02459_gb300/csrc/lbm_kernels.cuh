@@ -49,6 +49,7 @@ template <typename T> struct KP {
     T sf[9], sg[9];          // relaxation rates (sg[7], sg[8] set per node)
     T gx, gy;
     T eps2;                  // regularisation of |grad phi|^2
+    T two_over_W;            // 2/W
     T fd[6];                 // filter coefficients d_0..d_5
     T fa;                    // filter intensity
     int fR;                  // filter half-width (0 = off)
@@ -76,25 +77,34 @@ __device__ __forceinline__ int map_axis(int k, int n, int periodic, int &flip)
 
 // Stage a (WS x HS) window of a scalar field whose top-left corner is global
 // (x0, y0) into shared memory s[HS][WS]; odd fields change sign in mirrors.
+// Each warp copies whole rows (lanes along x), so no per-element division
+// and at most one coordinate mapping per element on boundary tiles.
 template <typename T, int WS, int HS>
 __device__ __forceinline__ void load_tile(T *s, const T *__restrict__ g, int x0, int y0,
                                           const KP<T> &P, bool odd)
 {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (x0 >= 0 && y0 >= 0 && x0 + WS <= P.nx && y0 + HS <= P.ny) {
-        const T *base = g + (long long)y0 * P.nx + x0;
-        for (int t = threadIdx.x; t < WS * HS; t += blockDim.x) {
-            int ly = t / WS, lx = t - ly * WS;
-            s[t] = __ldg(&base[(long long)ly * P.nx + lx]);
+        const T *row = g + ((long long)y0 * P.nx + x0) + warp * P.nx;
+        T *srow = s + warp * WS;
+        const int rstep = nw * P.nx;
+        for (int r = warp; r < HS; r += nw, row += rstep, srow += nw * WS) {
+#pragma unroll
+            for (int c = lane; c < WS; c += 32) srow[c] = __ldg(row + c);
         }
         return;
     }
-    for (int t = threadIdx.x; t < WS * HS; t += blockDim.x) {
-        int ly = t / WS, lx = t - ly * WS;
-        int fx, fy;
-        int gx = map_axis(x0 + lx, P.nx, P.px, fx);
-        int gy = map_axis(y0 + ly, P.ny, P.py, fy);
-        T v = __ldg(&g[(long long)gy * P.nx + gx]);
-        s[t] = (odd && (fx ^ fy)) ? -v : v;
+    for (int r = warp; r < HS; r += nw) {
+        int fy;
+        const int gy = map_axis(y0 + r, P.ny, P.py, fy);
+        const T *row = g + (long long)gy * P.nx;
+#pragma unroll
+        for (int c = lane; c < WS; c += 32) {
+            int fx;
+            const int gx = map_axis(x0 + c, P.nx, P.px, fx);
+            const T v = __ldg(row + gx);
+            s[r * WS + c] = (odd && (fx ^ fy)) ? -v : v;
+        }
     }
 }
 
@@ -135,15 +145,24 @@ __device__ __forceinline__ T fd4_d2(const T *s, int i)
            T(1.0 / 12.0);
 }
 
-// Density and kinematic viscosity at a node (Sec. II.B Eq. rho,
-// Sec. III.B Eq. dynamic_vis), with phi clamped to [-1,1] here only.
+// Reciprocal and reciprocal square root: IEEE in FP64 (the parity build);
+// the hardware approximations (<= 2 ulp) in FP32, whose results are compared
+// with the oracle at FP32 tolerances.
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
+
+// Density, its reciprocal and the kinematic viscosity at a node (Sec. II.B
+// Eq. rho, Sec. III.B Eq. dynamic_vis), with phi clamped to [-1,1] here only.
 template <typename T>
-__device__ __forceinline__ void rho_nu(const KP<T> &P, T phi, T &rho, T &nu)
+__device__ __forceinline__ void rho_nu(const KP<T> &P, T phi, T &rho, T &irho, T &nu)
 {
     T c = phi < T(-1) ? T(-1) : (phi > T(1) ? T(1) : phi);
     T hp = (T(1) + c) * T(0.5), hm = (T(1) - c) * T(0.5);
     rho = P.rhoH * hp + P.rhoL * hm;
-    nu = (P.muH * hp + P.muL * hm) / rho;
+    irho = rcp(rho);
+    nu = (P.muH * hp + P.muL * hm) * irho;
 }
 
 // Moment transform m = M f with the rows of Eq. (D2Q9MRT).
@@ -241,7 +260,7 @@ __device__ __forceinline__ void surface_force(const T *sgx, const T *sgy, int i,
 }
 
 template <typename T, typename S, int TX, int TY>
-__global__ void __launch_bounds__((TX + 2) * (TY + 2), 2)
+__global__ void __launch_bounds__((TX + 2) * (TY + 2), sizeof(T) == 4 ? 3 : 2)
 k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
                  S *__restrict__ fout, S *__restrict__ gout,
                  const T *__restrict__ phi, const T *__restrict__ pfl,
@@ -251,6 +270,8 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
                  T *__restrict__ phibar, T *__restrict__ phat,
                  T *__restrict__ jxo, T *__restrict__ jyo)
 {
+    // One thread per node of the collision region (tile + ring 1): the
+    // launch uses exactly A1 threads.
     using G = CSGeom<TX, TY>;
     constexpr int W3 = G::W3, W2 = G::W2, H2 = G::H2, W1 = G::W1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -267,6 +288,31 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const long long N = P.N;
 
+    // this thread's collision node, and its populations requested up front so
+    // that their latency overlaps the staging and the first stencil phase
+    const int t = threadIdx.x;
+    const int ly = t / W1, lx = t - ly * W1;
+    const int X = x0 - 1 + lx, Y = y0 - 1 + ly;
+    const bool ghost = (!P.px && (X < 0 || X >= P.nx)) || (!P.py && (Y < 0 || Y >= P.ny));
+    int fxm, fym;
+    const int gidx = map_axis(Y, P.ny, P.py, fym) * P.nx + map_axis(X, P.nx, P.px, fxm);
+    T f[9], g[9], upx_ = T(0), upy_ = T(0), uhx_ = T(0), uhy_ = T(0);
+    if (!ghost) {
+        const S *fp = fin + gidx;
+        const S *gp = gin + gidx;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            f[q] = Codec<S, T>::load(__ldg(fp));
+            g[q] = Codec<S, T>::load(__ldg(gp));
+            fp += N;
+            gp += N;
+        }
+        upx_ = __ldg(&upx[gidx]);
+        upy_ = __ldg(&upy[gidx]);
+        uhx_ = __ldg(&uhx[gidx]);
+        uhy_ = __ldg(&uhy[gidx]);
+    }
+
     load_tile<T, G::W3, G::H3>(s_phi, phi, x0 - 3, y0 - 3, P, false);
     load_tile<T, W2, H2>(s_p, pfl, x0 - 2, y0 - 2, P, false);
     load_tile<T, W2, H2>(s_ux, ux, x0 - 2, y0 - 2, P, true);
@@ -274,32 +320,26 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
     __syncthreads();
 
     // chemical potential and grad phi on tile + ring 2
-    for (int t = threadIdx.x; t < G::A2; t += blockDim.x) {
-        int ly = t / W2, lx = t - ly * W2;
-        int i3 = (ly + 1) * W3 + (lx + 1);
+    for (int k = threadIdx.x; k < G::A2; k += blockDim.x) {
+        int ky = k / W2, kx = k - ky * W2;
+        int i3 = (ky + 1) * W3 + (kx + 1);
         T ph = s_phi[i3];
-        s_mu[t] = T(4) * P.beta * (ph * ph * ph - ph) - P.kappa * iso_lap<T, W3>(s_phi, i3);
+        s_mu[k] = T(4) * P.beta * (ph * ph * ph - ph) - P.kappa * iso_lap<T, W3>(s_phi, i3);
         T gx, gy;
         iso_grad<T, W3>(s_phi, i3, gx, gy);
-        s_gx[t] = gx;
-        s_gy[t] = gy;
+        s_gx[k] = gx;
+        s_gy[k] = gy;
     }
     __syncthreads();
 
-    // forces and collision on tile + ring 1 (one node per thread)
-    for (int t = threadIdx.x; t < G::A1; t += blockDim.x) {
-        int ly = t / W1, lx = t - ly * W1;
-        const int X = x0 - 1 + lx, Y = y0 - 1 + ly;
-        const bool ghost = (!P.px && (X < 0 || X >= P.nx)) || (!P.py && (Y < 0 || Y >= P.ny));
-        if (ghost) continue;   // beyond a wall: never pulled (bounce-back instead)
-        int fxm, fym;
-        const long long gidx = (long long)map_axis(Y, P.ny, P.py, fym) * P.nx + map_axis(X, P.nx, P.px, fxm);
+    // forces and collision of this thread's node
+    if (!ghost) {   // beyond a wall: never pulled (bounce-back instead)
         const int i2 = (ly + 1) * W2 + (lx + 1);
         const int i3 = (ly + 2) * W3 + (lx + 2);
 
         const T ph = s_phi[i3];
-        T rho, nu;
-        rho_nu(P, ph, rho, nu);
+        T rho, ir, nu;
+        rho_nu(P, ph, rho, ir, nu);
         const T mu = s_mu[i2];
         const T grx = P.drho * s_gx[i2], gry = P.drho * s_gy[i2];
         T dmx, dmy;
@@ -318,15 +358,13 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
         const T Fy = -pc * gry + Fsy + nu * (Sxy * grx + Syy * gry) + (Jx * dxuy + Jy * dyuy) + rho * P.gy;
         // mirrored ring nodes carry the odd sign of u^{n-1} and u_hat too
         const T sgn = (fxm ^ fym) ? T(-1) : T(1);
-        const T ax = (u0 - sgn * __ldg(&upx[gidx])) + u0 * dxux + u1 * dyux;
-        const T ay = (u1 - sgn * __ldg(&upy[gidx])) + u0 * dxuy + u1 * dyuy;
+        const T ax = (u0 - sgn * upx_) + u0 * dxux + u1 * dyux;
+        const T ay = (u1 - sgn * upy_) + u0 * dxuy + u1 * dyuy;
         const T u2 = u0 * u0 + u1 * u1;
 
         // ---- CH populations
         {
-            T f[9], m[9];
-#pragma unroll
-            for (int q = 0; q < 9; ++q) f[q] = Codec<S, T>::load(fin[q * N + gidx]);
+            T m[9];
             to_moments(f, m);
             const T em = P.eta * mu;
             const T meq[9] = {ph, T(2) * em - T(4) * ph + T(3) * ph * u2, T(4) * ph - T(3) * em - T(3) * ph * u2,
@@ -341,23 +379,20 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
         }
         // ---- NS populations
         {
-            T g[9], m[9];
-#pragma unroll
-            for (int q = 0; q < 9; ++q) g[q] = Codec<S, T>::load(gin[q * N + gidx]);
+            T m[9];
             to_moments(g, m);
             const T ph_ = m[0] * T(1.0 / 3.0);          // p_hat = cs^2 sum g
-            const T h0 = sgn * __ldg(&uhx[gidx]), h1 = sgn * __ldg(&uhy[gidx]);
+            const T h0 = sgn * uhx_, h1 = sgn * uhy_;
             const T h2 = h0 * h0 + h1 * h1;
             const T mef[9] = {T(3) * pc, T(-6) * pc + T(3) * u2, T(3) * pc - T(3) * u2, u0, -u0, u1, -u1,
                               u0 * u0 - u1 * u1, u0 * u1};
             const T meh[9] = {T(3) * ph_, T(-6) * ph_ + T(3) * h2, T(3) * ph_ - T(3) * h2, h0, -h0, h1, -h1,
                               h0 * h0 - h1 * h1, h0 * h1};
-            const T ir = T(1) / rho;
             const T bx = Fx * ir - dpx, by = Fy * ir - dpy;
             const T bu = bx * u0 + by * u1;
             const T mG[9] = {T(0), T(6) * bu, T(-6) * bu, Fx * ir, -Fx * ir, Fy * ir, -Fy * ir,
                              T(2) * (bx * u0 - by * u1), by * u0 + bx * u1};
-            const T s78 = T(1) / (nu * T(3) + T(0.5));  // 1/tau_g, tau_g = nu/cs^2 + 1/2
+            const T s78 = rcp(nu * T(3) + T(0.5));   // 1/tau_g, tau_g = nu/cs^2 + 1/2
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
                 const T sk = k < 7 ? P.sg[k] : s78;
@@ -374,26 +409,30 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
     constexpr int cxv[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     constexpr int cyv[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     constexpr int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-    for (int t = threadIdx.x; t < TX * TY; t += blockDim.x) {
-        int ly = t / TX, lx = t - ly * TX;
-        const int X = x0 + lx, Y = y0 + ly;
-        if (X >= P.nx || Y >= P.ny) continue;
-        const long long gidx = (long long)Y * P.nx + X;
-        const int c1 = (ly + 1) * W1 + (lx + 1);
-        const bool edge = (!P.px && (X == 0 || X == P.nx - 1)) || (!P.py && (Y == 0 || Y == P.ny - 1));
+    for (int k = threadIdx.x; k < TX * TY; k += blockDim.x) {
+        const int ky = k / TX, kx = k - ky * TX;
+        const int Xn = x0 + kx, Yn = y0 + ky;
+        if (Xn >= P.nx || Yn >= P.ny) continue;
+        const int nidx = Yn * P.nx + Xn;
+        const int c1 = (ky + 1) * W1 + (kx + 1);
+        const bool edge = (!P.px && (Xn == 0 || Xn == P.nx - 1)) || (!P.py && (Yn == 0 || Yn == P.ny - 1));
         T sf = T(0), sg = T(0), sgx = T(0), sgy = T(0);
+        S *fo = fout + nidx;
+        S *go = gout + nidx;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             int src = q * G::A1 + c1 - cyv[q] * W1 - cxv[q];
             if (edge) {
-                const int SX = X - cxv[q], SY = Y - cyv[q];
+                const int SX = Xn - cxv[q], SY = Yn - cyv[q];
                 const bool wall = (!P.px && (SX < 0 || SX >= P.nx)) || (!P.py && (SY < 0 || SY >= P.ny));
                 if (wall) src = opp[q] * G::A1 + c1;
             }
             const S fs = Codec<S, T>::store(s_f[src]);
             const S gs = Codec<S, T>::store(s_g[src]);
-            fout[q * N + gidx] = fs;
-            gout[q * N + gidx] = gs;
+            *fo = fs;
+            *go = gs;
+            fo += N;
+            go += N;
             // moments of what is stored, so the stored state is self-consistent
             const T fr = Codec<S, T>::load(fs), gr = Codec<S, T>::load(gs);
             sf += fr;
@@ -401,10 +440,10 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
             sgx += T(cxv[q]) * gr;
             sgy += T(cyv[q]) * gr;
         }
-        phibar[gidx] = sf;
-        phat[gidx] = sg * T(1.0 / 3.0);
-        jxo[gidx] = sgx;
-        jyo[gidx] = sgy;
+        phibar[nidx] = sf;
+        phat[nidx] = sg * T(1.0 / 3.0);
+        jxo[nidx] = sgx;
+        jyo[nidx] = sgy;
     }
 }
 
@@ -456,10 +495,11 @@ k_rk_stage(KP<T> P, const T *__restrict__ psi, const T *__restrict__ phibar, T *
         int i4 = (ly + 2) * W4 + (lx + 2);
         T gx = fd4_d1<T, 1>(s_psi, i6), gy = fd4_d1<T, W6>(s_psi, i6);
         T v = s_psi[i6];
-        T mag = sqrt(gx * gx + gy * gy + P.eps2);
-        T inv = T(1) / mag;
+        const T m2 = gx * gx + gy * gy + P.eps2;
+        const T inv = rsq(m2);
+        const T mag = m2 * inv;
         T nxv = gx * inv, nyv = gy * inv;
-        T jphi = mag - T(2) * (T(1) - v * v) / P.W;
+        T jphi = mag - P.two_over_W * (T(1) - v * v);
         T jx = P.lambda * jphi * nxv, jy = P.lambda * jphi * nyv;
         if (P.flux_corr) {
             T mx = fd4_d1<T, 1>(s_mu, i4), my = fd4_d1<T, W4>(s_mu, i4);
@@ -542,8 +582,8 @@ k_picard(KP<T> P, const T *__restrict__ phi, const T *__restrict__ phat,
         const long long gidx = (long long)Y * P.nx + X;
         const int i1 = (ly + 1) * W1 + (lx + 1);
         const T ph = s_phi[(ly + 2) * W2 + (lx + 2)];
-        T rho, nu;
-        rho_nu(P, ph, rho, nu);
+        T rho, ir, nu;
+        rho_nu(P, ph, rho, ir, nu);
         const T grx = P.drho * s_gx[i1], gry = P.drho * s_gy[i1];
         T dmx, dmy;
         iso_grad<T, W1>(s_mu, i1, dmx, dmy);
@@ -573,7 +613,7 @@ k_picard(KP<T> P, const T *__restrict__ phi, const T *__restrict__ phat,
         const T Sxx = T(2) * dxux, Sxy = dyux + dxuy, Syy = T(2) * dyuy;
         const T Fx = -pc * grx + Fsx + nu * (Sxx * grx + Sxy * gry) + (Jx * dxux + Jy * dyux) + rho * P.gx;
         const T Fy = -pc * gry + Fsy + nu * (Sxy * grx + Syy * gry) + (Jx * dxuy + Jy * dyuy) + rho * P.gy;
-        const T h = T(1) / (T(2) * rho);
+        const T h = T(0.5) * ir;
         uox[gidx] = jx[gidx] + Fx * h;
         uoy[gidx] = jy[gidx] + Fy * h;
     }
