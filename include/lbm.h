@@ -79,7 +79,10 @@ typedef struct {
     double nu_H, nu_L;      /* kinematic viscosities; mu = rho nu interpolated linearly (Eq. dynamic_vis) */
     double s_f[9];          /* CH MRT rates; s_f[3], s_f[5] are replaced by 1/tau_f (Eq. CH_Sf) */
     double s_g[9];          /* NS MRT rates; s_g[7], s_g[8] are replaced by 1/tau_g(x) (Sec. III.B) */
-    double gx, gy;          /* gravity, F_g = rho g (Sec. II.B) */
+    double gx, gy;          /* gravity, F_g = (rho - g_rho_ref) g (Sec. II.B; see g_rho_ref) */
+    double g_rho_ref;       /* 0: F_g = rho g as printed; rho_ref > 0 measures gravity against the
+                               hydrostatic pressure of a fluid of density rho_ref, which differs
+                               from rho g by the gradient grad(rho_ref g.x) that the pressure absorbs */
     int filter_order;       /* 0 (off), 5, 7, 9 or 11: explicit selective filter SF-n (App. B) */
     double filter_a;        /* filter intensity, 0 < a <= 1 (Eq. filter) */
     int picard_iters;       /* sweeps of u = j + F(u)/(2 rho) per step (Eq. u), >= 1 */

@@ -634,7 +634,8 @@ static void vel_grads(const orc_sim *s, const double *ux, const double *uy,
 
 /* Total force F = F_p + F_s + F_nu + F_m + F_g of Sec. II.B Eq. (reformNS):
    F_p = -p grad rho, F_nu = nu (grad u + grad u^T).grad rho, F_m = J.grad u,
-   F_g = rho g. */
+   F_g = (rho - rho_ref) g (rho_ref = 0: rho g as printed; otherwise gravity is
+   measured against the hydrostatic pressure of a fluid of density rho_ref). */
 static void total_force(const orc_sim *s, const fields_t *F, const double *p,
                         const double *dxux, const double *dyux, const double *dxuy,
                         const double *dyuy, size_t k, double *Fx, double *Fy)
@@ -646,7 +647,7 @@ static void total_force(const orc_sim *s, const fields_t *F, const double *p,
     double Fny = F->nu[k] * (Sxy * F->grx[k] + Syy * F->gry[k]);
     double Fmx = F->Jx[k] * dxux[k] + F->Jy[k] * dyux[k];
     double Fmy = F->Jx[k] * dxuy[k] + F->Jy[k] * dyuy[k];
-    double Fgx = F->rho[k] * q->gx, Fgy = F->rho[k] * q->gy;
+    double Fgx = (F->rho[k] - q->g_rho_ref) * q->gx, Fgy = (F->rho[k] - q->g_rho_ref) * q->gy;
     *Fx = Fpx + F->Fsx[k] + Fnx + Fmx + Fgx;
     *Fy = Fpy + F->Fsy[k] + Fny + Fmy + Fgy;
 }

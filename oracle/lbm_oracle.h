@@ -36,7 +36,8 @@ typedef struct {
     double rho_H, rho_L;  /* densities of phi=+1 and phi=-1, Sec. II.B Eq. (rho) */
     double nu_H, nu_L;    /* kinematic viscosities of the two fluids */
     double s_f[9], s_g[9];/* MRT rates; s_f[3]=s_f[5]=1/tau_f and s_g[7]=s_g[8]=1/tau_g are overridden */
-    double gx, gy;        /* gravitational acceleration, F_g = rho g */
+    double gx, gy;        /* gravitational acceleration */
+    double g_rho_ref;     /* F_g = (rho - g_rho_ref) g; 0 gives rho g as printed */
     int filter_order;     /* 0 (off), 5, 7, 9 or 11: selective filter SF-n, App. B */
     double filter_a;      /* filter intensity a, Sec. III.B Eq. (filter) */
     int picard_iters;     /* sweeps of the implicit velocity update (maximum when zeta>0) */

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "lbm.h"
@@ -65,7 +66,9 @@ struct lbm_handle {
     void *phi = nullptr, *pf = nullptr, *ux[2]{}, *uy[2]{};
     int ucur = 0;                      // ux[ucur] = filtered u^n, ux[1-ucur] = u^{n-1}
     void *uhx = nullptr, *uhy = nullptr;
-    void *phibar = nullptr, *phat = nullptr, *jx = nullptr, *jy = nullptr;
+    void *phibar[2]{}, *phat[2]{};     // post-stream moments, double-buffered:
+    int acur = 0;                      // slot acur = moments of the stored populations
+    void *jx = nullptr, *jy = nullptr;
     void *s1 = nullptr, *s2 = nullptr, *tk[2][2]{};
     double *diag_part = nullptr, *diag_out = nullptr;
     int diag_blocks = 1;
@@ -105,6 +108,22 @@ template <typename T> KP<T> &kp_of(lbm_handle *h);
 template <> KP<double> &kp_of<double>(lbm_handle *h) { return h->kpd; }
 template <> KP<float> &kp_of<float>(lbm_handle *h) { return h->kpf; }
 
+// Calls fn(T*, S*) with null pointers typed by the arithmetic type T and
+// the population storage type S of a precision.
+template <typename F>
+lbm_status dispatch(int precision, F &&fn)
+{
+    switch (precision) {
+    case LBM_FP64: return fn((double *)nullptr, (double *)nullptr);
+    case LBM_FP32: return fn((float *)nullptr, (float *)nullptr);
+    case LBM_MIX_BF16: return fn((float *)nullptr, (__nv_bfloat16 *)nullptr);
+    default: return fn((float *)nullptr, (__half *)nullptr);
+    }
+}
+#define TS_TYPES(tp, sp)                                \
+    using T = std::remove_pointer_t<decltype(tp)>;      \
+    using S = std::remove_pointer_t<decltype(sp)>;
+
 template <typename T>
 void build_kp(const lbm_grid &gr, const lbm_params &p, KP<T> &k)
 {
@@ -121,6 +140,7 @@ void build_kp(const lbm_grid &gr, const lbm_params &p, KP<T> &k)
     for (int q = 0; q < 9; ++q) { k.sf[q] = (T)p.s_f[q]; k.sg[q] = (T)p.s_g[q]; }
     k.sf[3] = k.sf[5] = (T)(1.0 / tau_f);
     k.gx = (T)p.gx; k.gy = (T)p.gy;
+    k.g_rho_ref = (T)p.g_rho_ref;
     k.eps2 = (T)(p.grad_eps * p.grad_eps);
     k.two_over_W = (T)(2.0 / p.W);
     double d[6];
@@ -140,8 +160,8 @@ lbm_status validate(const lbm_grid *gr, const lbm_params *p)
     }
     if ((long long)gr->nx * gr->ny > (1LL << 31))
         return fail(nullptr, LBM_ERR_ARG, "nx*ny must be <= 2^31");
-    if (gr->precision != LBM_FP64 && gr->precision != LBM_FP32)
-        return fail(nullptr, LBM_ERR_ARG, "precision must be LBM_FP64 or LBM_FP32");
+    if (gr->precision < LBM_FP64 || gr->precision > LBM_MIX_FP16)
+        return fail(nullptr, LBM_ERR_ARG, "precision must be LBM_FP64, LBM_FP32, LBM_MIX_BF16 or LBM_MIX_FP16");
     if (!(p->M > 0) || !(p->eta > 0)) return fail(nullptr, LBM_ERR_ARG, "M and eta must be > 0 (tau_f > 1/2)");
     if (!(p->W > 0)) return fail(nullptr, LBM_ERR_ARG, "W must be > 0");
     if (!(p->sigma >= 0) || !(p->lambda >= 0)) return fail(nullptr, LBM_ERR_ARG, "sigma, lambda must be >= 0");
@@ -161,6 +181,7 @@ lbm_status validate(const lbm_grid *gr, const lbm_params *p)
     if (!(p->grad_eps > 0)) return fail(nullptr, LBM_ERR_ARG, "grad_eps must be > 0");
     if (p->flags != 0) return fail(nullptr, LBM_ERR_ARG, "flags must be 0");
     if (!std::isfinite(p->gx) || !std::isfinite(p->gy)) return fail(nullptr, LBM_ERR_ARG, "gravity must be finite");
+    if (!(p->g_rho_ref >= 0) || !std::isfinite(p->g_rho_ref)) return fail(nullptr, LBM_ERR_ARG, "g_rho_ref must be >= 0");
     return LBM_OK;
 }
 
@@ -233,14 +254,16 @@ lbm_status step_impl(lbm_handle *h)
     T *phi = (T *)h->phi, *pf = (T *)h->pf;
     T *uxc = (T *)h->ux[u], *uyc = (T *)h->uy[u], *uxp = (T *)h->ux[1 - u], *uyp = (T *)h->uy[1 - u];
     T *uhx = (T *)h->uhx, *uhy = (T *)h->uhy;
-    T *phibar = (T *)h->phibar, *phat = (T *)h->phat, *jx = (T *)h->jx, *jy = (T *)h->jy;
+    const T *phibar_old = (const T *)h->phibar[h->acur], *phat_old = (const T *)h->phat[h->acur];
+    T *phibar = (T *)h->phibar[1 - h->acur], *phat = (T *)h->phat[1 - h->acur];
+    T *jx = (T *)h->jx, *jy = (T *)h->jy;
 
     {   // fields, forces, collision of f and g, pull streaming, post-stream moments
         dim3 grid((P.nx + CS_TX - 1) / CS_TX, (P.ny + CS_TY - 1) / CS_TY);
         Timed tm(h, 0);
         k_collide_stream<T, S, CS_TX, CS_TY><<<grid, (CS_TX + 2) * (CS_TY + 2), smem_cs<T>(), st>>>(
             P, (const S *)h->f[c], (const S *)h->g[c], (S *)h->f[1 - c], (S *)h->g[1 - c], phi, pf, uxc, uyc,
-            uxp, uyp, uhx, uhy, phibar, phat, jx, jy);
+            uxp, uyp, uhx, uhy, phibar_old, phat_old, phibar, phat, jx, jy);
     }
     {   // TVD-RK3 finite-difference correction: phi_bar -> phi^{n+1}
         dim3 grid((P.nx + RK_TX - 1) / RK_TX, (P.ny + RK_TY - 1) / RK_TY);
@@ -288,12 +311,13 @@ lbm_status step_impl(lbm_handle *h)
     CK(h, cudaGetLastError(), "kernel launch");
     h->cur ^= 1;
     h->ucur ^= 1;
+    h->acur ^= 1;
     return LBM_OK;
 }
 
-// The phi_bar and p_hat scratch planes are adjacent in the arena; between
-// steps they serve as an N-double staging area for field transfers.
-double *staging(lbm_handle *h) { return (double *)h->phibar; }
+// The two RK stage planes are adjacent in the arena; between steps they
+// serve as an N-double staging area for field transfers.
+double *staging(lbm_handle *h) { return (double *)h->s1; }
 
 // Host double field -> device plane of T (converted on the device).
 template <typename T>
@@ -376,10 +400,12 @@ lbm_status init_impl(lbm_handle *h, const double *phi0, const double *p0, const 
     CK(h, cudaMemcpyAsync(h->uy[1], h->uy[0], b, cudaMemcpyDeviceToDevice, h->stream), "init copy");
     CK(h, cudaMemcpyAsync(h->uhx, h->ux[0], b, cudaMemcpyDeviceToDevice, h->stream), "init copy");
     CK(h, cudaMemcpyAsync(h->uhy, h->uy[0], b, cudaMemcpyDeviceToDevice, h->stream), "init copy");
+    h->acur = 0;
     const KP<T> &P = kp_of<T>(h);
     int blocks = (int)std::min<long long>((P.N + 255) / 256, 4096);
     k_init<T, S><<<blocks, 256, 0, h->stream>>>(P, (const T *)h->phi, (const T *)h->pf, (const T *)h->ux[0],
-                                                 (const T *)h->uy[0], (S *)h->f[0], (S *)h->g[0]);
+                                                 (const T *)h->uy[0], (S *)h->f[0], (S *)h->g[0],
+                                                 (T *)h->phibar[0], (T *)h->phat[0]);
     CK(h, cudaGetLastError(), "init kernel");
     CK(h, cudaStreamSynchronize(h->stream), "init sync");
     return LBM_OK;
@@ -411,14 +437,84 @@ lbm_status fields_impl(lbm_handle *h, double *phi, double *p, double *ux, double
     return LBM_OK;
 }
 
+constexpr double kW[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+
+// Host side of the reduced-precision codecs (same scaling as the device Codec).
+template <typename S> float host_load(S v) { return (float)v; }
+template <> float host_load<__half>(__half v) { return __half2float(v) * (1.0f / 16384.0f); }
+template <typename S> S host_store(float v) { return S(v); }
+template <> __half host_store<__half>(float v) { return __float2half_rn(v * 16384.0f); }
+
+// Rebuild full population sets on the host from reduced-precision storage:
+// f_q, g_q - 3 w_q p_hat stored for q = 1..8; f_0, g_0 from the moments.
+template <typename T, typename S>
+lbm_status decode_mixed(lbm_handle *h, double *f, double *g)
+{
+    const size_t n = (size_t)h->N;
+    std::vector<S> fs(9 * n), gs(9 * n);
+    std::vector<T> pb(n), ph(n);
+    CK(h, cudaMemcpyAsync(fs.data(), h->f[h->cur], 9 * n * sizeof(S), cudaMemcpyDeviceToHost, h->stream), "state");
+    CK(h, cudaMemcpyAsync(gs.data(), h->g[h->cur], 9 * n * sizeof(S), cudaMemcpyDeviceToHost, h->stream), "state");
+    CK(h, cudaMemcpyAsync(pb.data(), h->phibar[h->acur], n * sizeof(T), cudaMemcpyDeviceToHost, h->stream), "state");
+    CK(h, cudaMemcpyAsync(ph.data(), h->phat[h->acur], n * sizeof(T), cudaMemcpyDeviceToHost, h->stream), "state");
+    CK(h, cudaStreamSynchronize(h->stream), "state sync");
+    for (size_t k = 0; k < n; ++k) {
+        T sf = T(0), sg = T(0);
+        for (int q = 1; q < 9; ++q) {
+            const T fq = (T)host_load<S>(fs[q * n + k]);
+            const T gq = (T)host_load<S>(gs[q * n + k]) + T(3) * (T)(float)kW[q] * ph[k];
+            if (f) f[q * n + k] = fq;
+            if (g) g[q * n + k] = gq;
+            sf += fq;
+            sg += gq;
+        }
+        if (f) f[k] = pb[k] - sf;
+        if (g) g[k] = T(3) * ph[k] - sg;
+    }
+    return LBM_OK;
+}
+
+template <typename T, typename S>
+lbm_status encode_mixed(lbm_handle *h, const double *f, const double *g)
+{
+    const size_t n = (size_t)h->N;
+    std::vector<S> fs(9 * n), gs(9 * n);
+    std::vector<T> pb(n), ph(n);
+    for (size_t k = 0; k < n; ++k) {
+        T sf = T(0), sg = T(0);
+        for (int q = 0; q < 9; ++q) {
+            sf += (T)f[q * n + k];
+            sg += (T)g[q * n + k];
+        }
+        pb[k] = sf;
+        ph[k] = sg * T(1.0 / 3.0);
+        fs[k] = host_store<S>(0.0f);
+        gs[k] = host_store<S>(0.0f);
+        for (int q = 1; q < 9; ++q) {
+            fs[q * n + k] = host_store<S>((float)f[q * n + k]);
+            gs[q * n + k] = host_store<S>((float)((T)g[q * n + k] - T(3) * (T)(float)kW[q] * ph[k]));
+        }
+    }
+    CK(h, cudaMemcpyAsync(h->f[0], fs.data(), 9 * n * sizeof(S), cudaMemcpyHostToDevice, h->stream), "state");
+    CK(h, cudaMemcpyAsync(h->g[0], gs.data(), 9 * n * sizeof(S), cudaMemcpyHostToDevice, h->stream), "state");
+    CK(h, cudaMemcpyAsync(h->phibar[0], pb.data(), n * sizeof(T), cudaMemcpyHostToDevice, h->stream), "state");
+    CK(h, cudaMemcpyAsync(h->phat[0], ph.data(), n * sizeof(T), cudaMemcpyHostToDevice, h->stream), "state");
+    CK(h, cudaStreamSynchronize(h->stream), "state sync");
+    return LBM_OK;
+}
+
 template <typename T, typename S>
 lbm_status get_state_impl(lbm_handle *h, double *f, double *g, double *phi, double *p, double *ux, double *uy,
                           double *uhx, double *uhy, double *upx, double *upy)
 {
     lbm_status st;
     const size_t n = (size_t)h->N;
-    if ((st = download_field<S>(h, f, h->f[h->cur], 9 * n))) return st;
-    if ((st = download_field<S>(h, g, h->g[h->cur], 9 * n))) return st;
+    if (Mixed<T, S>::on) {
+        if ((st = decode_mixed<T, S>(h, f, g))) return st;
+    } else {
+        if ((st = download_field<S>(h, f, h->f[h->cur], 9 * n))) return st;
+        if ((st = download_field<S>(h, g, h->g[h->cur], 9 * n))) return st;
+    }
     if ((st = fields_impl<T>(h, phi, p, ux, uy))) return st;
     if ((st = download_field<T>(h, uhx, h->uhx, n))) return st;
     if ((st = download_field<T>(h, uhy, h->uhy, n))) return st;
@@ -436,10 +532,14 @@ lbm_status set_state_impl(lbm_handle *h, const double *f, const double *g, const
     const size_t n = (size_t)h->N;
     h->cur = 0;
     h->ucur = 0;
-    std::vector<double> slice;
-    for (int q = 0; q < 9; ++q) {
-        if ((st = upload_field<S>(h, (S *)h->f[0] + q * n, f + q * n))) return st;
-        if ((st = upload_field<S>(h, (S *)h->g[0] + q * n, g + q * n))) return st;
+    h->acur = 0;
+    if (Mixed<T, S>::on) {
+        if ((st = encode_mixed<T, S>(h, f, g))) return st;
+    } else {
+        for (int q = 0; q < 9; ++q) {
+            if ((st = upload_field<S>(h, (S *)h->f[0] + q * n, f + q * n))) return st;
+            if ((st = upload_field<S>(h, (S *)h->g[0] + q * n, g + q * n))) return st;
+        }
     }
     if ((st = upload_field<T>(h, h->phi, phi))) return st;
     if ((st = upload_field<T>(h, h->pf, p))) return st;
@@ -473,14 +573,14 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params, const doub
     h->N = (long long)grid->nx * grid->ny;
     const bool dbl = grid->precision == LBM_FP64;
     h->elem = dbl ? sizeof(double) : sizeof(float);
-    h->pop_elem = h->elem;
+    h->pop_elem = grid->precision >= LBM_MIX_BF16 ? 2 : h->elem;
     if (dbl) build_kp<double>(*grid, *params, h->kpd);
     else build_kp<float>(*grid, *params, h->kpf);
 
     // one arena: 2x9 f planes, 2x9 g planes, then the scalar planes, 256-byte aligned each
     const size_t plane = round_up((size_t)h->N * h->elem, 256);
     const size_t pplane = round_up((size_t)h->N * 9 * h->pop_elem, 256);
-    const int nscalar = 20;   // phi, pf, ux[2], uy[2], uhx, uhy, phibar, phat, jx, jy, s1, s2, tk[2][2], 2 spare
+    const int nscalar = 22;   // phi, pf, ux[2], uy[2], uhx, uhy, phibar[2], phat[2], jx, jy, s1, s2, tk[2][2], 2 spare
     h->diag_blocks = (int)std::min<long long>((h->N + DIAG_THREADS - 1) / DIAG_THREADS, DIAG_MAX_BLOCKS);
     const size_t diag_bytes = round_up(sizeof(double) * (size_t)(h->diag_blocks + 1) * NDIAG, 256);
     h->arena_bytes = 4 * pplane + nscalar * plane + diag_bytes;
@@ -497,15 +597,18 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params, const doub
     h->g[0] = a; a += pplane;
     h->g[1] = a; a += pplane;
     void **sc[] = {&h->phi, &h->pf, &h->ux[0], &h->ux[1], &h->uy[0], &h->uy[1], &h->uhx, &h->uhy,
-                   &h->phibar, &h->phat, &h->jx, &h->jy, &h->s1, &h->s2,
+                   &h->phibar[0], &h->phibar[1], &h->phat[0], &h->phat[1], &h->jx, &h->jy, &h->s1, &h->s2,
                    &h->tk[0][0], &h->tk[0][1], &h->tk[1][0], &h->tk[1][1]};
     for (void **pp : sc) { *pp = a; a += plane; }
     a += 2 * plane;
     h->diag_part = (double *)a;
     h->diag_out = h->diag_part + (size_t)h->diag_blocks * NDIAG;
 
-    st = dbl ? set_smem_limits<double, double>(h) : set_smem_limits<float, float>(h);
-    if (!st) st = dbl ? init_impl<double, double>(h, phi0, p0, ux0, uy0) : init_impl<float, float>(h, phi0, p0, ux0, uy0);
+    st = dispatch(grid->precision, [&](auto tp, auto sp) {
+        TS_TYPES(tp, sp);
+        lbm_status r = set_smem_limits<T, S>(h);
+        return r ? r : init_impl<T, S>(h, phi0, p0, ux0, uy0);
+    });
     if (st) {
         g_create_error = h->err;
         lbm_destroy(h);
@@ -519,11 +622,14 @@ lbm_status lbm_step(lbm_handle *h, int n)
 {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
     if (n < 0) return fail(h, LBM_ERR_ARG, "n must be >= 0");
-    for (int t = 0; t < n; ++t) {
-        lbm_status st = h->grid.precision == LBM_FP64 ? step_impl<double, double>(h) : step_impl<float, float>(h);
-        if (st) return st;
-    }
-    return LBM_OK;
+    return dispatch(h->grid.precision, [&](auto tp, auto sp) {
+        TS_TYPES(tp, sp);
+        for (int t = 0; t < n; ++t) {
+            lbm_status st = step_impl<T, S>(h);
+            if (st) return st;
+        }
+        return LBM_OK;
+    });
 }
 
 lbm_status lbm_fields(lbm_handle *h, double *phi, double *p, double *ux, double *uy)
@@ -550,8 +656,10 @@ lbm_status lbm_set_fields(lbm_handle *h, const double *phi0, const double *p0, c
 {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
     if (!phi0 || !p0 || !ux0 || !uy0) return fail(h, LBM_ERR_ARG, "fields must be non-NULL");
-    return h->grid.precision == LBM_FP64 ? init_impl<double, double>(h, phi0, p0, ux0, uy0)
-                                         : init_impl<float, float>(h, phi0, p0, ux0, uy0);
+    return dispatch(h->grid.precision, [&](auto tp, auto sp) {
+        TS_TYPES(tp, sp);
+        return init_impl<T, S>(h, phi0, p0, ux0, uy0);
+    });
 }
 
 lbm_status lbm_diagnostics(lbm_handle *h, double *out)
@@ -575,9 +683,10 @@ lbm_status lbm_get_state(lbm_handle *h, double *f, double *g, double *phi, doubl
                          double *uhx, double *uhy, double *upx, double *upy)
 {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
-    return h->grid.precision == LBM_FP64
-               ? get_state_impl<double, double>(h, f, g, phi, p, ux, uy, uhx, uhy, upx, upy)
-               : get_state_impl<float, float>(h, f, g, phi, p, ux, uy, uhx, uhy, upx, upy);
+    return dispatch(h->grid.precision, [&](auto tp, auto sp) {
+        TS_TYPES(tp, sp);
+        return get_state_impl<T, S>(h, f, g, phi, p, ux, uy, uhx, uhy, upx, upy);
+    });
 }
 
 lbm_status lbm_set_state(lbm_handle *h, const double *f, const double *g, const double *phi, const double *p,
@@ -588,9 +697,10 @@ lbm_status lbm_set_state(lbm_handle *h, const double *f, const double *g, const 
     const double *all[10] = {f, g, phi, p, ux, uy, uhx, uhy, upx, upy};
     for (const double *q : all)
         if (!q) return fail(h, LBM_ERR_ARG, "every state array must be non-NULL");
-    return h->grid.precision == LBM_FP64
-               ? set_state_impl<double, double>(h, f, g, phi, p, ux, uy, uhx, uhy, upx, upy)
-               : set_state_impl<float, float>(h, f, g, phi, p, ux, uy, uhx, uhy, upx, upy);
+    return dispatch(h->grid.precision, [&](auto tp, auto sp) {
+        TS_TYPES(tp, sp);
+        return set_state_impl<T, S>(h, f, g, phi, p, ux, uy, uhx, uhy, upx, upy);
+    });
 }
 
 lbm_status lbm_profile(lbm_handle *h, int on)

@@ -30,9 +30,12 @@ template <> struct Codec<__nv_bfloat16, float> {
     static __device__ __forceinline__ float load(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __forceinline__ __nv_bfloat16 store(float v) { return __float2bfloat16_rn(v); }
 };
+// fp16 words hold the value times 2^14: the stored deviations span about
+// 1e-8 .. 3e-2, which the scaling moves into fp16's normal range
+// [6.1e-5, 65504] (bf16 shares float's exponent range and needs no scaling).
 template <> struct Codec<__half, float> {
-    static __device__ __forceinline__ float load(__half v) { return __half2float(v); }
-    static __device__ __forceinline__ __half store(float v) { return __float2half_rn(v); }
+    static __device__ __forceinline__ float load(__half v) { return __half2float(v) * (1.0f / 16384.0f); }
+    static __device__ __forceinline__ __half store(float v) { return __float2half_rn(v * 16384.0f); }
 };
 
 // ---------------------------------------------------------------------------
@@ -48,6 +51,7 @@ template <typename T> struct KP {
     T drho;                  // (rho_H - rho_L)/2 = d rho / d phi
     T sf[9], sg[9];          // relaxation rates (sg[7], sg[8] set per node)
     T gx, gy;
+    T g_rho_ref;             // gravity acts on rho - g_rho_ref
     T eps2;                  // regularisation of |grad phi|^2
     T two_over_W;            // 2/W
     T fd[6];                 // filter coefficients d_0..d_5
@@ -165,6 +169,20 @@ __device__ __forceinline__ void rho_nu(const KP<T> &P, T phi, T &rho, T &irho, T
     nu = (P.muH * hp + P.muL * hm) * irho;
 }
 
+// Lattice weights (Sec. III.A, below Eq. D2Q9).
+__device__ __forceinline__ float lattice_w(int q) { return q == 0 ? 4.0f / 9.0f : (q < 5 ? 1.0f / 9.0f : 1.0f / 36.0f); }
+
+// Reduced-precision population storage (S narrower than T).  Only the
+// deviations from the rest equilibria are stored in S: the CH rest
+// equilibrium is (phi, 0, ..., 0), so f_1..f_8 are stored as they are; the NS
+// rest equilibrium is 3 w_i p, so g_i - 3 w_i p_hat is stored for i = 1..8.
+// The rest populations are rebuilt from the post-stream moments kept in T,
+// f_0 = phi_bar - sum_{i>0} f_i and g_0 = 3 p_hat - sum_{i>0} g_i, so sum f and
+// sum g are carried in T whatever the rounding of the stored words.
+template <typename T, typename S> struct Mixed {
+    static constexpr bool on = sizeof(S) < sizeof(T);
+};
+
 // Moment transform m = M f with the rows of Eq. (D2Q9MRT).
 template <typename T>
 __device__ __forceinline__ void to_moments(const T f[9], T m[9])
@@ -267,11 +285,14 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
                  const T *__restrict__ ux, const T *__restrict__ uy,
                  const T *__restrict__ upx, const T *__restrict__ upy,
                  const T *__restrict__ uhx, const T *__restrict__ uhy,
+                 const T *__restrict__ phibar_old, const T *__restrict__ phat_old,
                  T *__restrict__ phibar, T *__restrict__ phat,
                  T *__restrict__ jxo, T *__restrict__ jyo)
 {
     // One thread per node of the collision region (tile + ring 1): the
-    // launch uses exactly A1 threads.
+    // launch uses exactly A1 threads.  phibar_old / phat_old are the
+    // post-stream moments of the stored populations (read only when the
+    // populations are stored in reduced precision).
     using G = CSGeom<TX, TY>;
     constexpr int W3 = G::W3, W2 = G::W2, H2 = G::H2, W1 = G::W1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -300,12 +321,28 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
     if (!ghost) {
         const S *fp = fin + gidx;
         const S *gp = gin + gidx;
+        if constexpr (Mixed<T, S>::on) {
+            T sf = T(0), sg = T(0);
+            const T ph0 = __ldg(&phat_old[gidx]);
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            f[q] = Codec<S, T>::load(__ldg(fp));
-            g[q] = Codec<S, T>::load(__ldg(gp));
-            fp += N;
-            gp += N;
+            for (int q = 1; q < 9; ++q) {
+                fp += N;
+                gp += N;
+                f[q] = Codec<S, T>::load(__ldg(fp));
+                g[q] = Codec<S, T>::load(__ldg(gp)) + T(3) * T(lattice_w(q)) * ph0;
+                sf += f[q];
+                sg += g[q];
+            }
+            f[0] = __ldg(&phibar_old[gidx]) - sf;
+            g[0] = T(3) * ph0 - sg;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                f[q] = Codec<S, T>::load(__ldg(fp));
+                g[q] = Codec<S, T>::load(__ldg(gp));
+                fp += N;
+                gp += N;
+            }
         }
         upx_ = __ldg(&upx[gidx]);
         upy_ = __ldg(&upy[gidx]);
@@ -354,8 +391,8 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
         iso_grad<T, W2>(s_uy, i2, dxuy, dyuy);
         const T u0 = s_ux[i2], u1 = s_uy[i2];
         const T Sxx = T(2) * dxux, Sxy = dyux + dxuy, Syy = T(2) * dyuy;
-        const T Fx = -pc * grx + Fsx + nu * (Sxx * grx + Sxy * gry) + (Jx * dxux + Jy * dyux) + rho * P.gx;
-        const T Fy = -pc * gry + Fsy + nu * (Sxy * grx + Syy * gry) + (Jx * dxuy + Jy * dyuy) + rho * P.gy;
+        const T Fx = -pc * grx + Fsx + nu * (Sxx * grx + Sxy * gry) + (Jx * dxux + Jy * dyux) + (rho - P.g_rho_ref) * P.gx;
+        const T Fy = -pc * gry + Fsy + nu * (Sxy * grx + Syy * gry) + (Jx * dxuy + Jy * dyuy) + (rho - P.g_rho_ref) * P.gy;
         // mirrored ring nodes carry the odd sign of u^{n-1} and u_hat too
         const T sgn = (fxm ^ fym) ? T(-1) : T(1);
         const T ax = (u0 - sgn * upx_) + u0 * dxux + u1 * dyux;
@@ -416,9 +453,7 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
         const int nidx = Yn * P.nx + Xn;
         const int c1 = (ky + 1) * W1 + (kx + 1);
         const bool edge = (!P.px && (Xn == 0 || Xn == P.nx - 1)) || (!P.py && (Yn == 0 || Yn == P.ny - 1));
-        T sf = T(0), sg = T(0), sgx = T(0), sgy = T(0);
-        S *fo = fout + nidx;
-        S *go = gout + nidx;
+        T fv[9], gv[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             int src = q * G::A1 + c1 - cyv[q] * W1 - cxv[q];
@@ -427,21 +462,39 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
                 const bool wall = (!P.px && (SX < 0 || SX >= P.nx)) || (!P.py && (SY < 0 || SY >= P.ny));
                 if (wall) src = opp[q] * G::A1 + c1;
             }
-            const S fs = Codec<S, T>::store(s_f[src]);
-            const S gs = Codec<S, T>::store(s_g[src]);
-            *fo = fs;
-            *go = gs;
-            fo += N;
-            go += N;
-            // moments of what is stored, so the stored state is self-consistent
-            const T fr = Codec<S, T>::load(fs), gr = Codec<S, T>::load(gs);
-            sf += fr;
-            sg += gr;
-            sgx += T(cxv[q]) * gr;
-            sgy += T(cyv[q]) * gr;
+            fv[q] = s_f[src];
+            gv[q] = s_g[src];
+        }
+        T sf = T(0), sg = T(0), sgx = T(0), sgy = T(0);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            sf += fv[q];
+            sg += gv[q];
+            sgx += T(cxv[q]) * gv[q];
+            sgy += T(cyv[q]) * gv[q];
+        }
+        const T pn = sg * T(1.0 / 3.0);
+        S *fo = fout + nidx;
+        S *go = gout + nidx;
+        if constexpr (Mixed<T, S>::on) {
+#pragma unroll
+            for (int q = 1; q < 9; ++q) {
+                fo += N;
+                go += N;
+                *fo = Codec<S, T>::store(fv[q]);
+                *go = Codec<S, T>::store(gv[q] - T(3) * T(lattice_w(q)) * pn);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                *fo = Codec<S, T>::store(fv[q]);
+                *go = Codec<S, T>::store(gv[q]);
+                fo += N;
+                go += N;
+            }
         }
         phibar[nidx] = sf;
-        phat[nidx] = sg * T(1.0 / 3.0);
+        phat[nidx] = pn;
         jxo[nidx] = sgx;
         jyo[nidx] = sgy;
     }
@@ -611,8 +664,8 @@ k_picard(KP<T> P, const T *__restrict__ phi, const T *__restrict__ phat,
         iso_grad<T, W1>(s_ux, i1, dxux, dyux);
         iso_grad<T, W1>(s_uy, i1, dxuy, dyuy);
         const T Sxx = T(2) * dxux, Sxy = dyux + dxuy, Syy = T(2) * dyuy;
-        const T Fx = -pc * grx + Fsx + nu * (Sxx * grx + Sxy * gry) + (Jx * dxux + Jy * dyux) + rho * P.gx;
-        const T Fy = -pc * gry + Fsy + nu * (Sxy * grx + Syy * gry) + (Jx * dxuy + Jy * dyuy) + rho * P.gy;
+        const T Fx = -pc * grx + Fsx + nu * (Sxx * grx + Sxy * gry) + (Jx * dxux + Jy * dyux) + (rho - P.g_rho_ref) * P.gx;
+        const T Fy = -pc * gry + Fsy + nu * (Sxy * grx + Syy * gry) + (Jx * dxuy + Jy * dyuy) + (rho - P.g_rho_ref) * P.gy;
         const T h = T(0.5) * ir;
         uox[gidx] = jx[gidx] + Fx * h;
         uoy[gidx] = jy[gidx] + Fy * h;
@@ -675,7 +728,8 @@ k_filter(KP<T> P, const T *__restrict__ pin, const T *__restrict__ uxin, const T
 template <typename T, typename S>
 __global__ void k_init(KP<T> P, const T *__restrict__ phi, const T *__restrict__ p,
                        const T *__restrict__ ux, const T *__restrict__ uy,
-                       S *__restrict__ f, S *__restrict__ g)
+                       S *__restrict__ f, S *__restrict__ g,
+                       T *__restrict__ phibar, T *__restrict__ phat)
 {
     const long long N = P.N;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < N;
@@ -705,10 +759,25 @@ __global__ void k_init(KP<T> P, const T *__restrict__ phi, const T *__restrict__
         T fv[9], gv[9];
         from_moments(mf, fv);
         from_moments(mg, gv);
+        T sf = T(0), sg = T(0);
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-            f[q * N + k] = Codec<S, T>::store(fv[q]);
-            g[q * N + k] = Codec<S, T>::store(gv[q]);
+            sf += fv[q];
+            sg += gv[q];
+        }
+        const T pn = sg * T(1.0 / 3.0);
+        phibar[k] = sf;
+        phat[k] = pn;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            if (Mixed<T, S>::on) {
+                if (q == 0) continue;
+                f[q * N + k] = Codec<S, T>::store(fv[q]);
+                g[q * N + k] = Codec<S, T>::store(gv[q] - T(3) * T(lattice_w(q)) * pn);
+            } else {
+                f[q * N + k] = Codec<S, T>::store(fv[q]);
+                g[q * N + k] = Codec<S, T>::store(gv[q]);
+            }
         }
     }
 }

@@ -31,7 +31,7 @@ class LbmParams(C.Structure):
         ("lambda_", C.c_double), ("flux_correction", C.c_int),
         ("rho_H", C.c_double), ("rho_L", C.c_double), ("nu_H", C.c_double), ("nu_L", C.c_double),
         ("s_f", C.c_double * 9), ("s_g", C.c_double * 9),
-        ("gx", C.c_double), ("gy", C.c_double),
+        ("gx", C.c_double), ("gy", C.c_double), ("g_rho_ref", C.c_double),
         ("filter_order", C.c_int), ("filter_a", C.c_double),
         ("picard_iters", C.c_int), ("picard_zeta", C.c_double),
         ("grad_eps", C.c_double), ("flags", C.c_uint),
@@ -113,7 +113,7 @@ def make_params(prm):
     for k in range(9):
         p.s_f[k] = prm["s_f"][k]
         p.s_g[k] = prm["s_g"][k]
-    p.gx = prm.get("gx", 0.0); p.gy = prm.get("gy", 0.0)
+    p.gx = prm.get("gx", 0.0); p.gy = prm.get("gy", 0.0); p.g_rho_ref = prm.get("g_rho_ref", 0.0)
     p.filter_order = int(prm.get("filter_order", 11)); p.filter_a = prm.get("filter_a", 0.5)
     p.picard_iters = int(prm.get("picard_iters", 2)); p.picard_zeta = prm.get("picard_zeta", 0.0)
     p.grad_eps = prm.get("grad_eps", 1e-4); p.flags = int(prm.get("flags", 0))

@@ -438,13 +438,14 @@ def test_laplace_law():
 
 
 @pytest.mark.slow
-def test_layered_channel_viscous_stress():
+@pytest.mark.parametrize("rho_ref", [0.0, 1.0])
+def test_layered_channel_viscous_stress(rho_ref):
     """Two fluids layered between walls driven by a body force along x: the
-    steady profile solves d/dy(mu du/dy) = -rho g_x (pins F_nu, the viscosity
-    interpolation and the walls)."""
+    steady profile solves d/dy(mu du/dy) = -(rho - rho_ref) g_x (pins F_nu,
+    the viscosity interpolation, the walls and the gravity reference)."""
     nx, ny, g = 4, 32, 1e-6
     prm = inputs.base_params(rho_H=4.0, rho_L=1.0, nu_H=0.1, nu_L=0.2, sigma=1e-3,
-                             gx=g, periodic_y=0)
+                             gx=g, g_rho_ref=rho_ref, periodic_y=0)
     y = np.arange(ny, dtype=float)
     prof = -np.tanh(2 * (y - 8) / 4) * np.tanh(2 * (y - 24) / 4)   # heavy in the middle band
     phi0 = np.repeat(prof[:, None], nx, axis=1)
@@ -457,7 +458,7 @@ def test_layered_channel_viscous_stress():
     mu = 0.4 * (1 + ph) / 2 + 0.2 * (1 - ph) / 2
     # walls at y = -1/2 and ny - 1/2; shear mu u' = g (C - int rho)
     yf = np.linspace(-0.5, ny - 0.5, 64001)
-    rf, mf = np.interp(yf, y, rho), np.interp(yf, y, mu)
+    rf, mf = np.interp(yf, y, rho - rho_ref), np.interp(yf, y, mu)
     dy = yf[1] - yf[0]
     cum = np.concatenate([[0.0], np.cumsum(0.5 * (rf[1:] + rf[:-1]) * dy)])
     # the constant makes u vanish on both walls: int (C - cum)/mu dy = 0
@@ -466,5 +467,5 @@ def test_layered_channel_viscous_stress():
     uf = np.concatenate([[0.0], np.cumsum(0.5 * (dudy[1:] + dudy[:-1]) * dy)])
     u_ref = np.interp(y, yf, uf)
     num = ux[:, 0]
-    assert abs(num.max() / u_ref.max() - 1) < 3e-3
-    assert np.abs(num - u_ref).max() < 6e-3 * u_ref.max()
+    assert abs(num.max() / u_ref.max() - 1) < 5e-3
+    assert np.abs(num - u_ref).max() < 8e-3 * u_ref.max()
