@@ -185,6 +185,32 @@ lbm_status lbm_profile_read(lbm_handle *h, double *ms, long long *launches);
 const char *lbm_kernel_name(int kind);
 
 /*
+ * Discrete adjoint of lbm_step (reverse mode), for gradients of a loss of the
+ * final order parameter with respect to the initial order parameter, the
+ * surface tension sigma and the mobility M.
+ *   lbm_adjoint_begin(h, nsteps, k): the handle must hold a state freshly set
+ *     from fields (lbm_create or lbm_set_fields, no step since), periodic
+ *     axes, and FP64 or FP32 populations.  Advances nsteps steps, keeping
+ *     every k-th state as a checkpoint on the device; the handle then holds
+ *     the state after nsteps steps.  Errors: LBM_ERR_ARG, LBM_ERR_STATE,
+ *     LBM_ERR_OOM, LBM_ERR_CUDA.
+ *   lbm_adjoint_end(h, dL_dphi, dL_dphi0, dL_dsigma, dL_dM): dL_dphi is the
+ *     host [ny][nx] gradient of the loss with respect to phi after nsteps.
+ *     Runs the reverse sweep -- each segment of k steps is regenerated from
+ *     its checkpoint and reversed step by step through the hand-written
+ *     vector-Jacobian products of the step's plane operations -- and writes
+ *     dL/dphi0 (host [ny][nx], may be NULL), dL/dsigma and dL/dM (may be
+ *     NULL).  The handle is left at the state after nsteps steps.
+ *     Synchronises the stream.  Errors: LBM_ERR_STATE (no begin), LBM_ERR_ARG,
+ *     LBM_ERR_CUDA.
+ * sigma enters through kappa = 3 sigma W/8 and beta = 3 sigma/(4W)
+ * (Sec. II.A); M through tau_f (Eq. mobility), the flux q and J (Sec. II).
+ */
+lbm_status lbm_adjoint_begin(lbm_handle *h, int nsteps, int checkpoint_every);
+lbm_status lbm_adjoint_end(lbm_handle *h, const double *dL_dphi, double *dL_dphi0,
+                           double *dL_dsigma, double *dL_dM);
+
+/*
  * lbm_field_sums_noalloc -- the sums of lbm_diagnostics for fields the
  * caller holds on the device, computed without allocating device memory.
  * The paper has no counterpart: this is an operational entry point.  It is

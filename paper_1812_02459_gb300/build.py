@@ -14,8 +14,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "liblbm.so")
-SOURCES = [os.path.join(CSRC, "lbm_api.cu"), os.path.join(CSRC, "lbm_noalloc.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "lbm_kernels.cuh"), os.path.join(INCLUDE, "lbm.h")]
+SOURCES = [os.path.join(CSRC, n) for n in ("lbm_api.cu", "lbm_noalloc.cu", "lbm_adjoint.cu")]
+DEPS = SOURCES + [os.path.join(CSRC, "lbm_kernels.cuh"), os.path.join(CSRC, "lbm_internal.h"),
+                  os.path.join(INCLUDE, "lbm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

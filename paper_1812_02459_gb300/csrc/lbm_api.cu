@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "lbm.h"
+#include "lbm_internal.h"
 #include "lbm_kernels.cuh"
 
 using namespace lbm;
@@ -23,9 +24,9 @@ using namespace lbm;
 namespace {
 
 constexpr int CS_TX = 30, CS_TY = 14;    // collide+stream tile: its ring-1 region is 32 x 16 = one node per thread
-constexpr int RK_TX = 32, RK_TY = 16;    // RK3 stage tile
-constexpr int PC_TX = 32, PC_TY = 16;    // Picard sweep tile
-constexpr int FL_TX = 32, FL_TY = 16;    // filter tile
+constexpr int RK_TX = 64, RK_TY = 32, RK_NT = 512;   // RK3 stage tile, threads
+constexpr int PC_TX = 64, PC_TY = 16, PC_NT = 512;   // Picard sweep tile, threads
+constexpr int FL_TX = 64, FL_TY = 16, FL_NT = 512;   // filter tile, threads
 constexpr int DIAG_THREADS = 256;
 constexpr int DIAG_MAX_BLOCKS = 1216;    // 8 x 152 SMs
 
@@ -52,36 +53,7 @@ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
-struct lbm_handle {
-    lbm_grid grid{};
-    lbm_params prm{};
-    cudaStream_t stream = nullptr;
-    std::string err;
-    long long N = 0;
-    size_t elem = 0, pop_elem = 0;     // bytes of T and of S
-    unsigned char *arena = nullptr;
-    size_t arena_bytes = 0;
-    void *f[2]{}, *g[2]{};
-    int cur = 0;                       // which population buffer holds the state
-    void *phi = nullptr, *pf = nullptr, *ux[2]{}, *uy[2]{};
-    int ucur = 0;                      // ux[ucur] = filtered u^n, ux[1-ucur] = u^{n-1}
-    void *uhx = nullptr, *uhy = nullptr;
-    void *phibar[2]{}, *phat[2]{};     // post-stream moments, double-buffered:
-    int acur = 0;                      // slot acur = moments of the stored populations
-    void *jx = nullptr, *jy = nullptr;
-    void *s1 = nullptr, *s2 = nullptr, *tk[2][2]{};
-    double *diag_part = nullptr, *diag_out = nullptr;
-    int diag_blocks = 1;
-    KP<double> kpd{};
-    KP<float> kpf{};
-    // per-kernel timing
-    bool prof = false;
-    struct Mark { int kind; cudaEvent_t a, b; };
-    std::vector<Mark> marks;
-    std::vector<cudaEvent_t> pool;
-    double prof_ms[LBM_NKERNELS]{};
-    long long prof_n[LBM_NKERNELS]{};
-};
+
 
 namespace {
 
@@ -196,9 +168,15 @@ lbm_status set_smem_limits(lbm_handle *h)
     CK(h, cudaFuncSetAttribute(k_collide_stream<T, S, CS_TX, CS_TY>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cs<T>()),
        "cudaFuncSetAttribute(collide_stream)");
-    CK(h, cudaFuncSetAttribute(k_rk_stage<T, RK_TX, RK_TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CK(h, cudaFuncSetAttribute(k_rk_stage<T, RK_TX, RK_TY, RK_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem_rk<T>()),
        "cudaFuncSetAttribute(rk_stage)");
+    CK(h, cudaFuncSetAttribute(k_picard<T, PC_TX, PC_TY, PC_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_pc<T>()),
+       "cudaFuncSetAttribute(picard)");
+    CK(h, cudaFuncSetAttribute(k_filter<T, FL_TX, FL_TY, 5, FL_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_fl<T, 5>()),
+       "cudaFuncSetAttribute(filter)");
     return LBM_OK;
 }
 
@@ -242,7 +220,7 @@ void launch_filter_r(lbm_handle *h, const T *pin, const T *uxi, const T *uyi, T 
     const KP<T> &P = kp_of<T>(h);
     dim3 grid((P.nx + FL_TX - 1) / FL_TX, (P.ny + FL_TY - 1) / FL_TY);
     Timed tm(h, 3);
-    k_filter<T, FL_TX, FL_TY, R><<<grid, FL_TX * FL_TY, smem_fl<T, R>(), h->stream>>>(P, pin, uxi, uyi, po, uxo, uyo);
+    k_filter<T, FL_TX, FL_TY, R, FL_NT><<<grid, FL_NT, smem_fl<T, R>(), h->stream>>>(P, pin, uxi, uyi, po, uxo, uyo);
 }
 
 template <typename T, typename S>
@@ -270,16 +248,16 @@ lbm_status step_impl(lbm_handle *h)
         const size_t sm = smem_rk<T>();
         {
             Timed tm(h, 1);
-            k_rk_stage<T, RK_TX, RK_TY><<<grid, RK_TX * RK_TY, sm, st>>>(P, phibar, phibar, (T *)h->s1, T(0), T(1));
+            k_rk_stage<T, RK_TX, RK_TY, RK_NT><<<grid, RK_NT, sm, st>>>(P, phibar, phibar, (T *)h->s1, T(0), T(1));
         }
         {
             Timed tm(h, 1);
-            k_rk_stage<T, RK_TX, RK_TY><<<grid, RK_TX * RK_TY, sm, st>>>(P, (T *)h->s1, phibar, (T *)h->s2,
+            k_rk_stage<T, RK_TX, RK_TY, RK_NT><<<grid, RK_NT, sm, st>>>(P, (T *)h->s1, phibar, (T *)h->s2,
                                                                          T(0.75), T(0.25));
         }
         {
             Timed tm(h, 1);
-            k_rk_stage<T, RK_TX, RK_TY><<<grid, RK_TX * RK_TY, sm, st>>>(P, (T *)h->s2, phibar, phi,
+            k_rk_stage<T, RK_TX, RK_TY, RK_NT><<<grid, RK_NT, sm, st>>>(P, (T *)h->s2, phibar, phi,
                                                                          T(1.0 / 3.0), T(2.0 / 3.0));
         }
     }
@@ -292,7 +270,7 @@ lbm_status step_impl(lbm_handle *h)
             T *ox = k == K - 1 ? uhx : (T *)h->tk[k & 1][0];
             T *oy = k == K - 1 ? uhy : (T *)h->tk[k & 1][1];
             Timed tm(h, 2);
-            k_picard<T, PC_TX, PC_TY><<<grid, PC_TX * PC_TY, smem_pc<T>(), st>>>(P, phi, phat, jx, jy, ix, iy, ox, oy);
+            k_picard<T, PC_TX, PC_TY, PC_NT><<<grid, PC_NT, smem_pc<T>(), st>>>(P, phi, phat, jx, jy, ix, iy, ox, oy);
         }
     }
     // selective filter of (p_hat, u_hat) -> (p_f, u_f^{n+1}); u^{n-1} slot is reused
@@ -408,6 +386,7 @@ lbm_status init_impl(lbm_handle *h, const double *phi0, const double *p0, const 
                                                  (T *)h->phibar[0], (T *)h->phat[0]);
     CK(h, cudaGetLastError(), "init kernel");
     CK(h, cudaStreamSynchronize(h->stream), "init sync");
+    h->fresh_init = true;
     return LBM_OK;
 }
 
@@ -555,6 +534,15 @@ lbm_status set_state_impl(lbm_handle *h, const double *f, const double *g, const
 
 }  // namespace
 
+lbm_status lbm_internal_step(lbm_handle *h)
+{
+    h->fresh_init = false;
+    return dispatch(h->grid.precision, [&](auto tp, auto sp) {
+        TS_TYPES(tp, sp);
+        return step_impl<T, S>(h);
+    });
+}
+
 extern "C" {
 
 lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params, const double *phi0, const double *p0,
@@ -622,6 +610,7 @@ lbm_status lbm_step(lbm_handle *h, int n)
 {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
     if (n < 0) return fail(h, LBM_ERR_ARG, "n must be >= 0");
+    if (n > 0) h->fresh_init = false;
     return dispatch(h->grid.precision, [&](auto tp, auto sp) {
         TS_TYPES(tp, sp);
         for (int t = 0; t < n; ++t) {
@@ -697,6 +686,7 @@ lbm_status lbm_set_state(lbm_handle *h, const double *f, const double *g, const 
     const double *all[10] = {f, g, phi, p, ux, uy, uhx, uhy, upx, upy};
     for (const double *q : all)
         if (!q) return fail(h, LBM_ERR_ARG, "every state array must be non-NULL");
+    h->fresh_init = false;
     return dispatch(h->grid.precision, [&](auto tp, auto sp) {
         TS_TYPES(tp, sp);
         return set_state_impl<T, S>(h, f, g, phi, p, ux, uy, uhx, uhy, upx, upy);
@@ -747,6 +737,7 @@ size_t lbm_device_bytes(const lbm_handle *h) { return h ? h->arena_bytes : 0; }
 void lbm_destroy(lbm_handle *h)
 {
     if (!h) return;
+    lbm_internal_adjoint_free(h);
     for (auto &m : h->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
     for (auto e : h->pool) cudaEventDestroy(e);
     if (h->arena) cudaFree(h->arena);

@@ -516,8 +516,8 @@ template <int TX, int TY> struct RKGeom {
     static constexpr int NSCALAR = W6 * H6 + W4 * H4 + 2 * W2 * H2;
 };
 
-template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
+template <typename T, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT)
 k_rk_stage(KP<T> P, const T *__restrict__ psi, const T *__restrict__ phibar, T *__restrict__ out,
            T a, T b)
 {
@@ -591,8 +591,8 @@ template <int TX, int TY> struct PCGeom {
     static constexpr int NSCALAR = W2 * H2 + 6 * W1 * H1;
 };
 
-template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
+template <typename T, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT)
 k_picard(KP<T> P, const T *__restrict__ phi, const T *__restrict__ phat,
          const T *__restrict__ jx, const T *__restrict__ jy,
          const T *__restrict__ ukx, const T *__restrict__ uky,
@@ -682,8 +682,8 @@ template <int TX, int TY, int R> struct FLGeom {
     static constexpr int NSCALAR = 3 * WR * HR;
 };
 
-template <typename T, int TX, int TY, int R>
-__global__ void __launch_bounds__(TX * TY)
+template <typename T, int TX, int TY, int R, int NT>
+__global__ void __launch_bounds__(NT)
 k_filter(KP<T> P, const T *__restrict__ pin, const T *__restrict__ uxin, const T *__restrict__ uyin,
          T *__restrict__ pout, T *__restrict__ uxout, T *__restrict__ uyout)
 {

@@ -48,6 +48,7 @@ EXPORTS = ("lbm_create", "lbm_step", "lbm_fields", "lbm_fields_device", "lbm_set
            "lbm_diagnostics", "lbm_check", "lbm_get_state", "lbm_set_state",
            "lbm_profile", "lbm_profile_read", "lbm_kernel_name",
            "lbm_field_sums_noalloc", "lbm_noalloc_last_error",
+           "lbm_adjoint_begin", "lbm_adjoint_end",
            "lbm_device_bytes", "lbm_destroy", "lbm_last_error")
 LBM_NKERNELS = 4
 
@@ -93,6 +94,10 @@ def load(path=None):
     L.lbm_field_sums_noalloc.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, C.c_int, vp, vp]
     L.lbm_noalloc_last_error.restype = C.c_char_p
     L.lbm_noalloc_last_error.argtypes = []
+    L.lbm_adjoint_begin.restype = C.c_int
+    L.lbm_adjoint_begin.argtypes = [vp, C.c_int, C.c_int]
+    L.lbm_adjoint_end.restype = C.c_int
+    L.lbm_adjoint_end.argtypes = [vp, _dp, _dp, _dp, _dp]
     L.lbm_device_bytes.restype = C.c_size_t
     L.lbm_device_bytes.argtypes = [vp]
     L.lbm_destroy.restype = None
@@ -231,6 +236,18 @@ class Sim:
         self._ck(self._lib.lbm_profile_read(self._h, _ptr(ms), n))
         return {self._lib.lbm_kernel_name(k).decode(): (float(ms[k]), int(n[k]))
                 for k in range(LBM_NKERNELS)}
+
+    def adjoint_begin(self, nsteps, checkpoint_every):
+        """Advance nsteps keeping checkpoints for the reverse sweep."""
+        self._ck(self._lib.lbm_adjoint_begin(self._h, int(nsteps), int(checkpoint_every)))
+
+    def adjoint_end(self, dL_dphi):
+        """Reverse sweep: (dL/dphi0 [ny, nx], dL/dsigma, dL/dM) for the seed dL/dphi_final."""
+        seed = _f64(dL_dphi)
+        g = np.empty((self.ny, self.nx))
+        ds = C.c_double(); dm = C.c_double()
+        self._ck(self._lib.lbm_adjoint_end(self._h, _ptr(seed), _ptr(g), C.byref(ds), C.byref(dm)))
+        return g, ds.value, dm.value
 
     def device_bytes(self):
         return int(self._lib.lbm_device_bytes(self._h))

@@ -1,0 +1,137 @@
+"""The GPU discrete adjoint (lbm_adjoint_begin / lbm_adjoint_end) against the
+FP64 oracle adjoint (torch autograd of oracle/torch_ref.py, itself pinned to
+finite differences of the C oracle) and against central finite differences of
+the GPU forward.  Loss: L = 1/2 sum (phi_T - phi_target)^2."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import torch_ref as tr
+from paper_1812_02459_gb300 import inputs, lbm
+from paper_1812_02459_gb300.autograd import LbmTrajectory
+
+pytestmark = pytest.mark.gpu
+T = lambda a: torch.tensor(a, dtype=torch.float64)
+
+
+def case(n=20, R=5.0):
+    prm, fields = inputs.translating_drop(n=n, R=R, U0=0.01)
+    prm["sigma"] = 5e-3
+    yy, xx = np.mgrid[0:n, 0:n].astype(float)
+    target = np.tanh(2.0 * (R + 0.5 - np.hypot(xx - n / 2 - 0.7, yy - n / 2)) / prm["W"])
+    return prm, fields, target
+
+
+def gpu_grad(prm, fields, target, steps, every, precision):
+    s = lbm.Sim(prm, *fields, precision=precision)
+    s.adjoint_begin(steps, every)
+    phiT = s.fields()[0]
+    g, ds, dm = s.adjoint_end(phiT - target)
+    loss = 0.5 * float(((phiT - target) ** 2).sum())
+    s.close()
+    return loss, g, ds, dm
+
+
+def gpu_loss(prm, fields, target, steps, precision="fp64"):
+    s = lbm.Sim(prm, *fields, precision=precision)
+    s.step(steps)
+    phiT = s.fields()[0]
+    s.close()
+    return 0.5 * float(((phiT - target) ** 2).sum())
+
+
+def test_adjoint_fp64_matches_oracle_adjoint():
+    prm, fields, target = case()
+    steps = 7
+    loss, g, ds, dm = gpu_grad(prm, fields, target, steps, 3, "fp64")   # 3 segments, ragged last
+    phi0 = T(fields[0]).requires_grad_(True)
+    sig = T(prm["sigma"]).requires_grad_(True)
+    M = T(prm["M"]).requires_grad_(True)
+    r = tr.run(prm, phi0, T(fields[1]), T(fields[2]), T(fields[3]), sig, M, steps)
+    lt = 0.5 * ((r["phi"] - T(target)) ** 2).sum()
+    gphi, gs, gm = torch.autograd.grad(lt, [phi0, sig, M])
+    assert loss == pytest.approx(lt.item(), rel=1e-12)
+    assert np.abs(g - gphi.numpy()).max() <= 1e-10 * np.abs(gphi.numpy()).max()
+    assert ds == pytest.approx(gs.item(), rel=1e-10)
+    assert dm == pytest.approx(gm.item(), rel=1e-10)
+
+
+def test_adjoint_fp64_matches_gpu_finite_differences():
+    prm, fields, target = case(n=24, R=6.0)
+    steps = 10
+    _, g, ds, dm = gpu_grad(prm, fields, target, steps, 4, "fp64")
+    hs = 1e-4 * prm["sigma"]
+    fd_s = (gpu_loss(dict(prm, sigma=prm["sigma"] + hs), fields, target, steps)
+            - gpu_loss(dict(prm, sigma=prm["sigma"] - hs), fields, target, steps)) / (2 * hs)
+    hm = 1e-4 * prm["M"]
+    fd_m = (gpu_loss(dict(prm, M=prm["M"] + hm), fields, target, steps)
+            - gpu_loss(dict(prm, M=prm["M"] - hm), fields, target, steps)) / (2 * hm)
+    rng = np.random.default_rng(1)
+    v = rng.standard_normal(fields[0].shape) * (np.abs(fields[0]) < 0.95)
+    he = 1e-5
+    fp = list(fields); fm = list(fields)
+    fp[0] = fields[0] + he * v
+    fm[0] = fields[0] - he * v
+    fd_v = (gpu_loss(prm, fp, target, steps) - gpu_loss(prm, fm, target, steps)) / (2 * he)
+    assert ds == pytest.approx(fd_s, rel=1e-6)
+    assert dm == pytest.approx(fd_m, rel=1e-6)
+    assert float((g * v).sum()) == pytest.approx(fd_v, rel=1e-6)
+
+
+def test_autograd_function_and_fp32():
+    prm, fields, target = case()
+    for precision, tol in (("fp64", 1e-10), ("fp32", 1e-3)):
+        phi0 = T(fields[0]).requires_grad_(True)
+        sig = T(prm["sigma"]).requires_grad_(True)
+        M = T(prm["M"]).requires_grad_(True)
+        phiT = LbmTrajectory.apply(phi0, sig, M, prm, fields[1], fields[2], fields[3], 6, 4, precision)
+        loss = 0.5 * ((phiT - T(target)) ** 2).sum()
+        loss.backward()
+        if precision == "fp64":
+            ref = (phi0.grad.clone(), sig.grad.item(), M.grad.item())
+        else:
+            assert np.abs(phi0.grad.numpy() - ref[0].numpy()).max() <= tol * np.abs(ref[0].numpy()).max()
+            assert sig.grad.item() == pytest.approx(ref[1], rel=tol)
+            assert M.grad.item() == pytest.approx(ref[2], rel=tol)
+
+
+@pytest.mark.slow
+def test_adjoint_translating_drop_256():
+    """Drop in a uniform flow, 256^2, rho ratio 100, 500 steps, checkpoint
+    every 22 steps.  The target is the final phi of an FP64 run with sigma and
+    M perturbed by 5 % seeded normals.  The FP32 adjoint, seeded with the same
+    residual as the FP64 one, must reproduce the FP64 gradients (its reverse
+    sweep linearises about the FP32 trajectory)."""
+    prm, fields = inputs.translating_drop(n=256, R=32.0, U0=0.01)
+    rng = np.random.default_rng(0)
+    xi = rng.standard_normal(2)
+    tp = dict(prm, sigma=prm["sigma"] * (1 + 0.05 * xi[0]), M=prm["M"] * (1 + 0.05 * xi[1]))
+    s = lbm.Sim(tp, *fields, precision="fp64")
+    s.step(500)
+    target = s.fields()[0]
+    s.close()
+    out = {}
+    seed = None
+    for precision in ("fp64", "fp32"):
+        s = lbm.Sim(prm, *fields, precision=precision)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        s.adjoint_begin(500, 22)
+        t1 = time.time()
+        phiT = s.fields()[0]
+        if seed is None:
+            seed = phiT - target
+        g, ds, dm = s.adjoint_end(seed)
+        t2 = time.time()
+        out[precision] = (g, ds, dm, phiT)
+        s.close()
+        print(precision, "dsigma", ds, "dM", dm, "forward s", round(t1 - t0, 3), "reverse s", round(t2 - t1, 3),
+              "residual", float(np.abs(seed).max()), "traj diff", float(np.abs(phiT - out["fp64"][3]).max()))
+    g64, ds64, dm64 = out["fp64"][:3]
+    g32, ds32, dm32 = out["fp32"][:3]
+    assert np.isfinite(g32).all()
+    assert dm32 == pytest.approx(dm64, rel=1e-2)
+    assert abs(ds32 - ds64) <= 1e-2 * (abs(ds64) + abs(dm64))
+    assert np.abs(g32 - g64).max() <= 1e-2 * np.abs(g64).max()

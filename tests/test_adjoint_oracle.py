@@ -1,0 +1,71 @@
+"""The FP64 oracle adjoint (torch autograd of oracle/torch_ref.py) pinned to
+the C oracle: its forward equals lbm_oracle.c to round-off, and its
+reverse-mode gradients equal central finite differences of lbm_oracle.c (an
+independent implementation), for sigma, M and a direction in phi0."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import torch_ref as tr
+from paper_1812_02459_gb300 import inputs
+
+T = lambda a: torch.tensor(a, dtype=torch.float64)
+
+
+def drop_case(n=20, steps=6):
+    prm, (phi, p, ux, uy) = inputs.translating_drop(n=n, R=5.0, U0=0.01)
+    prm["sigma"] = 5e-3
+    rng = np.random.default_rng(0)
+    target = np.tanh(2.0 * (5.5 - np.hypot(*np.meshgrid(np.arange(n) - n / 2 - 0.7, np.arange(n) - n / 2)))
+                     / prm["W"])
+    return prm, (phi, p, ux, uy), steps, target, rng
+
+
+def c_loss(prm, fields, steps, target, sigma=None, M=None, phi0=None):
+    q = dict(prm)
+    if sigma is not None:
+        q["sigma"] = sigma
+    if M is not None:
+        q["M"] = M
+    f = list(fields)
+    if phi0 is not None:
+        f[0] = phi0
+    s = oracle.Sim(q, *f)
+    s.step(steps)
+    return 0.5 * float(((s.fields()[0] - target) ** 2).sum())
+
+
+def test_torch_forward_equals_c_oracle():
+    prm, fields, steps, _, _ = drop_case()
+    s = oracle.Sim(prm, *fields)
+    s.step(steps)
+    r = tr.run(prm, *(T(a) for a in fields), T(prm["sigma"]), T(prm["M"]), steps)
+    for a, b in zip(s.fields(), (r["phi"], r["p"], r["ux"], r["uy"])):
+        assert np.abs(a - b.numpy()).max() <= 1e-12 * max(np.abs(a).max(), 1e-30)
+
+
+def test_torch_adjoint_matches_c_oracle_finite_differences():
+    prm, fields, steps, target, rng = drop_case()
+    phi0 = T(fields[0]).requires_grad_(True)
+    sig = T(prm["sigma"]).requires_grad_(True)
+    M = T(prm["M"]).requires_grad_(True)
+    r = tr.run(prm, phi0, T(fields[1]), T(fields[2]), T(fields[3]), sig, M, steps)
+    loss = 0.5 * ((r["phi"] - T(target)) ** 2).sum()
+    gphi, gs, gm = torch.autograd.grad(loss, [phi0, sig, M])
+    # central differences of the independent C oracle
+    hs = 1e-4 * prm["sigma"]
+    fd_s = (c_loss(prm, fields, steps, target, sigma=prm["sigma"] + hs)
+            - c_loss(prm, fields, steps, target, sigma=prm["sigma"] - hs)) / (2 * hs)
+    hm = 1e-4 * prm["M"]
+    fd_m = (c_loss(prm, fields, steps, target, M=prm["M"] + hm)
+            - c_loss(prm, fields, steps, target, M=prm["M"] - hm)) / (2 * hm)
+    # a direction inside the interface only: a perturbation of the bulk
+    # (phi0 = -1 + 1e-9) would cross the kink of the clamp in rho(phi)
+    v = rng.standard_normal(fields[0].shape) * (np.abs(fields[0]) < 0.95)
+    he = 1e-5
+    fd_v = (c_loss(prm, fields, steps, target, phi0=fields[0] + he * v)
+            - c_loss(prm, fields, steps, target, phi0=fields[0] - he * v)) / (2 * he)
+    assert gs.item() == pytest.approx(fd_s, rel=1e-6)
+    assert gm.item() == pytest.approx(fd_m, rel=1e-6)
+    assert float((gphi.numpy() * v).sum()) == pytest.approx(fd_v, rel=1e-6)
