@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--precision", default="fp32", choices=("fp32", "fp64"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the reduced-precision and adjoint side measurements")
     return ap.parse_args()
 
 
@@ -359,6 +361,42 @@ def run_ours(args):
                "h2d_bytes_per_step": round(4 * 8 * N / args.steps),
                "d2h_bytes_per_step": round(lbm.LBM_NDIAG * 8 + 4 * 8 * N / args.steps)}
 
+    # side measurements: the same workload with reduced-precision population
+    # storage, and the adjoint/forward time ratio on the adjoint workload
+    variants = None
+    if not args.no_variants:
+        variants = {}
+        for prec in ("mix_bf16", "mix_fp16"):
+            v = lbm.Sim(prm, *fields, precision=prec, stream=stream.cuda_stream)
+            v.step(max(3, args.warmup // 2))
+            torch.cuda.synchronize(dev)
+            k = max(10, args.steps // 2)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            v.step(k)
+            a1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms_v = a0.elapsed_time(a1) / k
+            variants[prec] = {"MLUPS": round(N / ms_v / 1e3, 1), "ms_per_step": round(ms_v, 4), "steps": k,
+                              "vs_fp32": round((N / ms_v / 1e3) / (N / (ms_max / args.steps) / 1e3), 4)}
+            v.close()
+        an, asteps, aevery = 256, 200, 22
+        aprm, afields = inputs.translating_drop(n=an, R=32.0, U0=0.01)
+        a = lbm.Sim(aprm, *afields, precision="fp32", stream=stream.cuda_stream)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        a.adjoint_begin(asteps, aevery)
+        t1 = time.perf_counter()
+        phiT = a.fields()[0]
+        a.adjoint_end(phiT - afields[0])
+        t2 = time.perf_counter()
+        a.close()
+        variants["adjoint"] = {"workload": f"translating drop {an}x{an}, rho ratio 100, {asteps} steps, "
+                                           f"checkpoint every {aevery}, FP32 forward, FP64 reverse sweep",
+                               "forward_s": round(t1 - t0, 4), "reverse_s": round(t2 - t1, 4),
+                               "adjoint_over_forward": round((t2 - t1) / (t1 - t0), 2)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cn, cs = 512, 20
@@ -387,6 +425,7 @@ def run_ours(args):
                               "achieved_GBps": round(step_bytes / (ms_max / args.steps / 1e3) / 1e9, 1),
                               "frac": round(step_bytes / (ms_max / args.steps / 1e3) / 1e9 / peak, 4)},
             "kernels": kernels,
+            "variants": variants,
             "gpu_launches": gpu_launches,
             "clocks": clk,
             "e2e": e2e,
