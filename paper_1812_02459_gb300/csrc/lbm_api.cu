@@ -101,6 +101,7 @@ void build_kp(const lbm_grid &gr, const lbm_params &p, KP<T> &k)
 {
     k.nx = gr.nx; k.ny = gr.ny; k.px = gr.periodic_x ? 1 : 0; k.py = gr.periodic_y ? 1 : 0;
     k.N = (long long)gr.nx * gr.ny;
+    k.N32 = (unsigned)k.N;
     k.kappa = (T)(3.0 * p.sigma * p.W / 8.0);          // Sec. II.A, below Eq. (free_energy)
     k.beta = (T)(3.0 * p.sigma / (4.0 * p.W));
     k.eta = (T)p.eta; k.M = (T)p.M; k.lambda = (T)p.lambda; k.W = (T)p.W;
@@ -130,8 +131,8 @@ lbm_status validate(const lbm_grid *gr, const lbm_params *p)
         snprintf(buf, sizeof buf, "nx, ny must be >= %d (got %d x %d)", LBM_MIN_EXTENT, gr->nx, gr->ny);
         return fail(nullptr, LBM_ERR_ARG, buf);
     }
-    if ((long long)gr->nx * gr->ny > (1LL << 31))
-        return fail(nullptr, LBM_ERR_ARG, "nx*ny must be <= 2^31");
+    if ((long long)gr->nx * gr->ny > (1LL << 28))
+        return fail(nullptr, LBM_ERR_ARG, "nx*ny must be <= 2^28 (16384^2)");
     if (gr->precision < LBM_FP64 || gr->precision > LBM_MIX_FP16)
         return fail(nullptr, LBM_ERR_ARG, "precision must be LBM_FP64, LBM_FP32, LBM_MIX_BF16 or LBM_MIX_FP16");
     if (!(p->M > 0) || !(p->eta > 0)) return fail(nullptr, LBM_ERR_ARG, "M and eta must be > 0 (tau_f > 1/2)");
@@ -162,10 +163,24 @@ template <typename T> size_t smem_rk() { return sizeof(T) * RKGeom<RK_TX, RK_TY>
 template <typename T> size_t smem_pc() { return sizeof(T) * PCGeom<PC_TX, PC_TY>::NSCALAR; }
 template <typename T, int R> size_t smem_fl() { return sizeof(T) * FLGeom<FL_TX, FL_TY, R>::NSCALAR; }
 
+// The default relaxation rates (s_f = 1 except s_f[3], s_f[5]; s_g[0..3] =
+// s_g[5] = 1) select the collide kernel that skips the rate-1 relaxations.
+bool default_rates(const lbm_params &p)
+{
+    for (int k : {0, 1, 2, 4, 6, 7, 8})
+        if (p.s_f[k] != 1.0) return false;
+    for (int k : {0, 1, 2, 3, 5})
+        if (p.s_g[k] != 1.0) return false;
+    return true;
+}
+
 template <typename T, typename S>
 lbm_status set_smem_limits(lbm_handle *h)
 {
-    CK(h, cudaFuncSetAttribute(k_collide_stream<T, S, CS_TX, CS_TY>,
+    CK(h, cudaFuncSetAttribute(k_collide_stream<T, S, CS_TX, CS_TY, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cs<T>()),
+       "cudaFuncSetAttribute(collide_stream)");
+    CK(h, cudaFuncSetAttribute(k_collide_stream<T, S, CS_TX, CS_TY, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cs<T>()),
        "cudaFuncSetAttribute(collide_stream)");
     CK(h, cudaFuncSetAttribute(k_rk_stage<T, RK_TX, RK_TY, RK_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -239,7 +254,9 @@ lbm_status step_impl(lbm_handle *h)
     {   // fields, forces, collision of f and g, pull streaming, post-stream moments
         dim3 grid((P.nx + CS_TX - 1) / CS_TX, (P.ny + CS_TY - 1) / CS_TY);
         Timed tm(h, 0);
-        k_collide_stream<T, S, CS_TX, CS_TY><<<grid, (CS_TX + 2) * (CS_TY + 2), smem_cs<T>(), st>>>(
+        auto kern = default_rates(h->prm) ? k_collide_stream<T, S, CS_TX, CS_TY, true>
+                                          : k_collide_stream<T, S, CS_TX, CS_TY, false>;
+        kern<<<grid, (CS_TX + 2) * (CS_TY + 2), smem_cs<T>(), st>>>(
             P, (const S *)h->f[c], (const S *)h->g[c], (S *)h->f[1 - c], (S *)h->g[1 - c], phi, pf, uxc, uyc,
             uxp, uyp, uhx, uhy, phibar_old, phat_old, phibar, phat, jx, jy);
     }

@@ -44,6 +44,7 @@ template <> struct Codec<__half, float> {
 template <typename T> struct KP {
     int nx, ny, px, py;
     long long N;
+    unsigned N32;            // N as 32-bit (9 N < 2^32 is enforced on the host)
     T kappa, beta;           // free-energy coefficients (Sec. II.A)
     T eta, M, lambda, W;     // CH equilibrium parameter, mobility, profile weight, width
     int flux_corr;
@@ -250,8 +251,24 @@ template <int TX, int TY> struct CSGeom {
     static constexpr int W2 = TX + 4, H2 = TY + 4;   // p, u windows; mu, grad phi (ring 2)
     static constexpr int W1 = TX + 2, H1 = TY + 2;   // collision region (ring 1)
     static constexpr int A3 = W3 * H3, A2 = W2 * H2, A1 = W1 * H1;
-    static constexpr int NSCALAR = A3 + 6 * A2 + 18 * A1;
+    static constexpr int NSCALAR = A3 + 9 * A2 + 18 * A1;
 };
+
+// Surface force kappa div(T) from the tensor components stored in a window
+// of row stride WS: txx = gy^2, txy = -gx gy, tyy = gx^2 (isotropic divergence).
+template <typename T, int WS>
+__device__ __forceinline__ void surface_force_t(const T *txx, const T *txy, const T *tyy, int i, T kappa,
+                                                T &Fx, T &Fy)
+{
+    T dxx, dxy_x, dxy_y, dyy;
+    iso_grad<T, WS>(txy, i, dxy_x, dxy_y);
+    dxx = (txx[i + 1] - txx[i - 1]) * T(1.0 / 3.0) +
+          (txx[i + WS + 1] - txx[i + WS - 1] - txx[i - WS - 1] + txx[i - WS + 1]) * T(1.0 / 12.0);
+    dyy = (tyy[i + WS] - tyy[i - WS]) * T(1.0 / 3.0) +
+          (tyy[i + WS + 1] + tyy[i + WS - 1] - tyy[i - WS - 1] - tyy[i - WS + 1]) * T(1.0 / 12.0);
+    Fx = kappa * (dxx + dxy_y);
+    Fy = kappa * (dxy_x + dyy);
+}
 
 // Surface force kappa div(T), T = |grad phi|^2 I - grad phi grad phi
 // = (gy^2, -gx gy; -gx gy, gx^2), isotropic divergence from grad phi stored
@@ -277,7 +294,11 @@ __device__ __forceinline__ void surface_force(const T *sgx, const T *sgy, int i,
     Fy = kappa * (dxxy + dyyy);
 }
 
-template <typename T, typename S, int TX, int TY>
+// FAST: the relaxation rates hold their defaults -- s_f = 1 except s_f[3],
+// s_f[5] (= 1/tau_f), s_g[0..3] = s_g[5] = 1 -- so every moment relaxed at
+// rate 1 is set straight to m_eq + m_source/2 and only the moments relaxed at
+// other rates are formed from the incoming populations.
+template <typename T, typename S, int TX, int TY, bool FAST>
 __global__ void __launch_bounds__((TX + 2) * (TY + 2), sizeof(T) == 4 ? 3 : 2)
 k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
                  S *__restrict__ fout, S *__restrict__ gout,
@@ -303,7 +324,10 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
     T *s_mu = s_uy + G::A2;
     T *s_gx = s_mu + G::A2;
     T *s_gy = s_gx + G::A2;
-    T *s_f = s_gy + G::A2;       // [9][A1]
+    T *s_txx = s_gy + G::A2;
+    T *s_txy = s_txx + G::A2;
+    T *s_tyy = s_txy + G::A2;
+    T *s_f = s_tyy + G::A2;      // [9][A1]
     T *s_g = s_f + 9 * G::A1;    // [9][A1]
 
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -319,17 +343,15 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
     const int gidx = map_axis(Y, P.ny, P.py, fym) * P.nx + map_axis(X, P.nx, P.px, fxm);
     T f[9], g[9], upx_ = T(0), upy_ = T(0), uhx_ = T(0), uhy_ = T(0);
     if (!ghost) {
-        const S *fp = fin + gidx;
-        const S *gp = gin + gidx;
+        const unsigned N32 = P.N32;
         if constexpr (Mixed<T, S>::on) {
             T sf = T(0), sg = T(0);
             const T ph0 = __ldg(&phat_old[gidx]);
 #pragma unroll
             for (int q = 1; q < 9; ++q) {
-                fp += N;
-                gp += N;
-                f[q] = Codec<S, T>::load(__ldg(fp));
-                g[q] = Codec<S, T>::load(__ldg(gp)) + T(3) * T(lattice_w(q)) * ph0;
+                const unsigned o = (unsigned)gidx + (unsigned)q * N32;
+                f[q] = Codec<S, T>::load(__ldg(&fin[o]));
+                g[q] = Codec<S, T>::load(__ldg(&gin[o])) + T(3) * T(lattice_w(q)) * ph0;
                 sf += f[q];
                 sg += g[q];
             }
@@ -338,10 +360,9 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
         } else {
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
-                f[q] = Codec<S, T>::load(__ldg(fp));
-                g[q] = Codec<S, T>::load(__ldg(gp));
-                fp += N;
-                gp += N;
+                const unsigned o = (unsigned)gidx + (unsigned)q * N32;
+                f[q] = Codec<S, T>::load(__ldg(&fin[o]));
+                g[q] = Codec<S, T>::load(__ldg(&gin[o]));
             }
         }
         upx_ = __ldg(&upx[gidx]);
@@ -366,6 +387,9 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
         iso_grad<T, W3>(s_phi, i3, gx, gy);
         s_gx[k] = gx;
         s_gy[k] = gy;
+        s_txx[k] = gy * gy;
+        s_txy[k] = -gx * gy;
+        s_tyy[k] = gx * gx;
     }
     __syncthreads();
 
@@ -383,7 +407,7 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
         iso_grad<T, W2>(s_mu, i2, dmx, dmy);
         const T Jx = P.drho * P.M * dmx, Jy = P.drho * P.M * dmy;
         T Fsx, Fsy;
-        surface_force<T, W2>(s_gx, s_gy, i2, P.kappa, Fsx, Fsy);
+        surface_force_t<T, W2>(s_txx, s_txy, s_tyy, i2, P.kappa, Fsx, Fsy);
         const T pc = s_p[i2];
         T dpx, dpy, dxux, dyux, dxuy, dyuy;
         iso_grad<T, W2>(s_p, i2, dpx, dpy);
@@ -402,14 +426,24 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
         // ---- CH populations
         {
             T m[9];
-            to_moments(f, m);
             const T em = P.eta * mu;
             const T meq[9] = {ph, T(2) * em - T(4) * ph + T(3) * ph * u2, T(4) * ph - T(3) * em - T(3) * ph * u2,
                               ph * u0, -ph * u0, ph * u1, -ph * u1, ph * (u0 * u0 - u1 * u1), ph * u0 * u1};
             const T mF[9] = {T(0), T(0), T(0), ph * ax, -ph * ax, ph * ay, -ph * ay, T(0), T(0)};
+            if constexpr (FAST) {
+                const T s = P.sf[3];
+                const T m3 = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+                const T m5 = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
 #pragma unroll
-            for (int k = 0; k < 9; ++k)
-                m[k] = m[k] - P.sf[k] * (m[k] - meq[k]) + (T(1) - T(0.5) * P.sf[k]) * mF[k];
+                for (int k = 0; k < 9; ++k) m[k] = meq[k] + T(0.5) * mF[k];
+                m[3] = m3 - s * (m3 - meq[3]) + (T(1) - T(0.5) * s) * mF[3];
+                m[5] = m5 - s * (m5 - meq[5]) + (T(1) - T(0.5) * s) * mF[5];
+            } else {
+                to_moments(f, m);
+#pragma unroll
+                for (int k = 0; k < 9; ++k)
+                    m[k] = m[k] - P.sf[k] * (m[k] - meq[k]) + (T(1) - T(0.5) * P.sf[k]) * mF[k];
+            }
             from_moments(m, f);
 #pragma unroll
             for (int q = 0; q < 9; ++q) s_f[q * G::A1 + t] = f[q];
@@ -417,23 +451,38 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
         // ---- NS populations
         {
             T m[9];
-            to_moments(g, m);
-            const T ph_ = m[0] * T(1.0 / 3.0);          // p_hat = cs^2 sum g
             const T h0 = sgn * uhx_, h1 = sgn * uhy_;
-            const T h2 = h0 * h0 + h1 * h1;
             const T mef[9] = {T(3) * pc, T(-6) * pc + T(3) * u2, T(3) * pc - T(3) * u2, u0, -u0, u1, -u1,
                               u0 * u0 - u1 * u1, u0 * u1};
-            const T meh[9] = {T(3) * ph_, T(-6) * ph_ + T(3) * h2, T(3) * ph_ - T(3) * h2, h0, -h0, h1, -h1,
-                              h0 * h0 - h1 * h1, h0 * h1};
             const T bx = Fx * ir - dpx, by = Fy * ir - dpy;
             const T bu = bx * u0 + by * u1;
             const T mG[9] = {T(0), T(6) * bu, T(-6) * bu, Fx * ir, -Fx * ir, Fy * ir, -Fy * ir,
                              T(2) * (bx * u0 - by * u1), by * u0 + bx * u1};
             const T s78 = rcp(nu * T(3) + T(0.5));   // 1/tau_g, tau_g = nu/cs^2 + 1/2
+            if constexpr (FAST) {
+                // rate-1 moments (0,1,2,3,5) drop the non-equilibrium part,
+                // so the unfiltered p_hat is not needed
 #pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const T sk = k < 7 ? P.sg[k] : s78;
-                m[k] = mef[k] + (T(1) - sk) * (m[k] - meh[k]) + (T(1) - T(0.5) * sk) * mG[k];
+                for (int k = 0; k < 9; ++k) m[k] = mef[k] + T(0.5) * mG[k];
+                const T d58 = g[5] - g[6] - g[7] + g[8], d56 = g[5] + g[6] - g[7] - g[8];
+                const T m4 = T(2) * (g[3] - g[1]) + d58, m6 = T(2) * (g[4] - g[2]) + d56;
+                const T m7 = g[1] - g[2] + g[3] - g[4], m8 = g[5] - g[6] + g[7] - g[8];
+                const T s4 = P.sg[4], s6 = P.sg[6];
+                m[4] += (T(1) - s4) * (m4 + h0) + (T(0.5) - T(0.5) * s4) * mG[4];
+                m[6] += (T(1) - s6) * (m6 + h1) + (T(0.5) - T(0.5) * s6) * mG[6];
+                m[7] += (T(1) - s78) * (m7 - (h0 * h0 - h1 * h1)) + (T(0.5) - T(0.5) * s78) * mG[7];
+                m[8] += (T(1) - s78) * (m8 - h0 * h1) + (T(0.5) - T(0.5) * s78) * mG[8];
+            } else {
+                to_moments(g, m);
+                const T ph_ = m[0] * T(1.0 / 3.0);          // p_hat = cs^2 sum g
+                const T h2 = h0 * h0 + h1 * h1;
+                const T meh[9] = {T(3) * ph_, T(-6) * ph_ + T(3) * h2, T(3) * ph_ - T(3) * h2, h0, -h0, h1, -h1,
+                                  h0 * h0 - h1 * h1, h0 * h1};
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const T sk = k < 7 ? P.sg[k] : s78;
+                    m[k] = mef[k] + (T(1) - sk) * (m[k] - meh[k]) + (T(1) - T(0.5) * sk) * mG[k];
+                }
             }
             from_moments(m, g);
 #pragma unroll
@@ -474,23 +523,20 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
             sgy += T(cyv[q]) * gv[q];
         }
         const T pn = sg * T(1.0 / 3.0);
-        S *fo = fout + nidx;
-        S *go = gout + nidx;
+        const unsigned N32 = P.N32;
         if constexpr (Mixed<T, S>::on) {
 #pragma unroll
             for (int q = 1; q < 9; ++q) {
-                fo += N;
-                go += N;
-                *fo = Codec<S, T>::store(fv[q]);
-                *go = Codec<S, T>::store(gv[q] - T(3) * T(lattice_w(q)) * pn);
+                const unsigned o = (unsigned)nidx + (unsigned)q * N32;
+                fout[o] = Codec<S, T>::store(fv[q]);
+                gout[o] = Codec<S, T>::store(gv[q] - T(3) * T(lattice_w(q)) * pn);
             }
         } else {
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
-                *fo = Codec<S, T>::store(fv[q]);
-                *go = Codec<S, T>::store(gv[q]);
-                fo += N;
-                go += N;
+                const unsigned o = (unsigned)nidx + (unsigned)q * N32;
+                fout[o] = Codec<S, T>::store(fv[q]);
+                gout[o] = Codec<S, T>::store(gv[q]);
             }
         }
         phibar[nidx] = sf;

@@ -197,3 +197,17 @@ def test_full_size_capillary_wave_sampled_fp32():
             scale = max(np.abs(b).max(), 1e-30)
             tol = TOL["fp32"] if name == "phi" else TOL_FP32_PU
             assert np.abs(ga - ob).max() / scale <= tol, name
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_general_relaxation_rates(precision):
+    """Non-default MRT rates take the general collision path (every moment
+    formed from the populations); the defaults take the rate-1 shortcut."""
+    nx, ny = 40, 30
+    prm = inputs.base_params(rho_H=10.0, sigma=3e-3, periodic_y=0, gy=-1e-6)
+    prm["s_f"] = [1.0, 1.2, 1.1, 1.0, 1.4, 1.0, 1.3, 0.9, 1.1]
+    prm["s_g"] = [1.0, 1.1, 1.2, 0.95, 1.6, 1.05, 1.5, 1.0, 1.0]
+    phi = inputs.drop(nx, ny, 8.0, 20.0, 14.0, prm["W"])
+    z = np.zeros_like(phi)
+    o, g = run_both(prm, (phi, z, z, z), 60, precision)
+    assert_parity(o, g, TOL[precision], tol_pu=pu_tol(precision))

