@@ -235,6 +235,13 @@ void launch_filter_r(lbm_handle *h, const T *pin, const T *uxi, const T *uyi, T 
     const KP<T> &P = kp_of<T>(h);
     dim3 grid((P.nx + FL_TX - 1) / FL_TX, (P.ny + FL_TY - 1) / FL_TY);
     Timed tm(h, 3);
+    if constexpr (std::is_same<T, float>::value) {
+        if (P.nx % 2 == 0) {   // node pairs with paired FP32 arithmetic
+            k_filter_pairs<FL_TX, FL_TY, R, FL_NT><<<grid, FL_NT, sizeof(float) * FL2Geom<FL_TX, FL_TY, R>::NSCALAR,
+                                                    h->stream>>>(P, pin, uxi, uyi, po, uxo, uyo);
+            return;
+        }
+    }
     k_filter<T, FL_TX, FL_TY, R, FL_NT><<<grid, FL_NT, smem_fl<T, R>(), h->stream>>>(P, pin, uxi, uyi, po, uxo, uyo);
 }
 

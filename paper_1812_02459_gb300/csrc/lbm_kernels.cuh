@@ -80,10 +80,28 @@ __device__ __forceinline__ int map_axis(int k, int n, int periodic, int &flip)
     return p - 1 - m;
 }
 
+// Asynchronous global -> shared copy of one element (cp.async); the copies
+// of a tile are all in flight together and complete at tiles_ready().
+template <int B> __device__ __forceinline__ void cp_async(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (B == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+// Wait for this thread's asynchronous copies, then for the whole CTA.
+__device__ __forceinline__ void tiles_ready()
+{
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+}
+
 // Stage a (WS x HS) window of a scalar field whose top-left corner is global
 // (x0, y0) into shared memory s[HS][WS]; odd fields change sign in mirrors.
 // Each warp copies whole rows (lanes along x), so no per-element division
-// and at most one coordinate mapping per element on boundary tiles.
+// and at most one coordinate mapping per element on boundary tiles.  Windows
+// inside the domain are copied asynchronously: call tiles_ready() before use.
 template <typename T, int WS, int HS>
 __device__ __forceinline__ void load_tile(T *s, const T *__restrict__ g, int x0, int y0,
                                           const KP<T> &P, bool odd)
@@ -95,7 +113,7 @@ __device__ __forceinline__ void load_tile(T *s, const T *__restrict__ g, int x0,
         const int rstep = nw * P.nx;
         for (int r = warp; r < HS; r += nw, row += rstep, srow += nw * WS) {
 #pragma unroll
-            for (int c = lane; c < WS; c += 32) srow[c] = __ldg(row + c);
+            for (int c = lane; c < WS; c += 32) cp_async<sizeof(T)>(&srow[c], row + c);
         }
         return;
     }
@@ -375,7 +393,7 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
     load_tile<T, W2, H2>(s_p, pfl, x0 - 2, y0 - 2, P, false);
     load_tile<T, W2, H2>(s_ux, ux, x0 - 2, y0 - 2, P, true);
     load_tile<T, W2, H2>(s_uy, uy, x0 - 2, y0 - 2, P, true);
-    __syncthreads();
+    tiles_ready();
 
     // chemical potential and grad phi on tile + ring 2
     for (int k = threadIdx.x; k < G::A2; k += blockDim.x) {
@@ -577,7 +595,7 @@ k_rk_stage(KP<T> P, const T *__restrict__ psi, const T *__restrict__ phibar, T *
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
 
     load_tile<T, W6, H6>(s_psi, psi, x0 - 6, y0 - 6, P, false);
-    __syncthreads();
+    tiles_ready();
 
     for (int t = threadIdx.x; t < W4 * H4; t += blockDim.x) {
         int ly = t / W4, lx = t - ly * W4;
@@ -660,7 +678,7 @@ k_picard(KP<T> P, const T *__restrict__ phi, const T *__restrict__ phat,
     load_tile<T, W1, H1>(s_p, phat, x0 - 1, y0 - 1, P, false);
     load_tile<T, W1, H1>(s_ux, ukx, x0 - 1, y0 - 1, P, true);
     load_tile<T, W1, H1>(s_uy, uky, x0 - 1, y0 - 1, P, true);
-    __syncthreads();
+    tiles_ready();
 
     for (int t = threadIdx.x; t < A1; t += blockDim.x) {
         int ly = t / W1, lx = t - ly * W1;
@@ -743,7 +761,7 @@ k_filter(KP<T> P, const T *__restrict__ pin, const T *__restrict__ uxin, const T
     load_tile<T, WR, HR>(s_p, pin, x0 - R, y0 - R, P, false);
     load_tile<T, WR, HR>(s_ux, uxin, x0 - R, y0 - R, P, true);
     load_tile<T, WR, HR>(s_uy, uyin, x0 - R, y0 - R, P, true);
-    __syncthreads();
+    tiles_ready();
     for (int t = threadIdx.x; t < TX * TY; t += blockDim.x) {
         int ly = t / TX, lx = t - ly * TX;
         const int X = x0 + lx, Y = y0 + ly;
@@ -764,6 +782,83 @@ k_filter(KP<T> P, const T *__restrict__ pin, const T *__restrict__ uxin, const T
         pout[gidx] = res[0];
         uxout[gidx] = res[1];
         uyout[gidx] = res[2];
+    }
+}
+
+// Paired FP32 arithmetic: two horizontally adjacent nodes per thread, so that
+// the additions and multiply-adds issue as FADD2 / FFMA2 on float2 operands.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Filter pass for FP32 on grids of even width: each thread filters the node
+// pair (x, x+1), x even; every shared-memory read is an aligned float2.
+// The staged windows start at x0 - RP with RP = R rounded up to even.
+template <int TX, int TY, int R> struct FL2Geom {
+    static constexpr int RP = (R + 1) & ~1;
+    static constexpr int WR = TX + 2 * RP, HR = TY + 2 * R;
+    static constexpr int NSCALAR = 3 * WR * HR;
+};
+
+template <int TX, int TY, int R, int NT>
+__global__ void __launch_bounds__(NT)
+k_filter_pairs(KP<float> P, const float *__restrict__ pin, const float *__restrict__ uxin,
+               const float *__restrict__ uyin, float *__restrict__ pout, float *__restrict__ uxout,
+               float *__restrict__ uyout)
+{
+    using G = FL2Geom<TX, TY, R>;
+    constexpr int RP = G::RP, WR = G::WR, HR = G::HR, A = WR * HR;
+    static_assert(TX % 2 == 0 && WR % 2 == 0, "pairs need even widths");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *s_p = reinterpret_cast<float *>(smem_raw);
+    float *s_ux = s_p + A;
+    float *s_uy = s_ux + A;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    load_tile<float, WR, HR>(s_p, pin, x0 - RP, y0 - R, P, false);
+    load_tile<float, WR, HR>(s_ux, uxin, x0 - RP, y0 - R, P, true);
+    load_tile<float, WR, HR>(s_uy, uyin, x0 - RP, y0 - R, P, true);
+    tiles_ready();
+    const float2 a2 = f2(P.fa);
+    for (int t = threadIdx.x; t < (TX / 2) * TY; t += blockDim.x) {
+        const int ly = t / (TX / 2), lx = 2 * (t - ly * (TX / 2));
+        const int X = x0 + lx, Y = y0 + ly;
+        if (X >= P.nx || Y >= P.ny) continue;
+        const int c = (ly + R) * WR + (lx + RP);   // even
+        const float *arr[3] = {s_p, s_ux, s_uy};
+        float2 res[3];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const float *sv = arr[v];
+            // row window x - RP .. x + 1 + RP as aligned pairs
+            float2 w[RP + 1];
+#pragma unroll
+            for (int k = 0; k < RP + 1; ++k)
+                w[k] = *reinterpret_cast<const float2 *>(&sv[c - RP + 2 * k]);
+            // w[k] = (x - RP + 2k, x - RP + 2k + 1); node x sits at pair RP/2, lane .x
+            const float2 ctr = w[RP / 2];
+            float2 acc = mul2(f2(2.0f * P.fd[0]), ctr);
+#pragma unroll
+            for (int m = 1; m <= R; ++m) {
+                // x + m and x - m for the lanes (x, x+1)
+                const int e0 = RP + m, e1 = RP + m + 1;   // offsets from x - RP
+                const int w0 = RP - m, w1 = RP - m + 1;
+                const float ex0 = (e0 & 1) ? w[e0 >> 1].y : w[e0 >> 1].x;
+                const float ex1 = (e1 & 1) ? w[e1 >> 1].y : w[e1 >> 1].x;
+                const float wx0 = (w0 & 1) ? w[w0 >> 1].y : w[w0 >> 1].x;
+                const float wx1 = (w1 & 1) ? w[w1 >> 1].y : w[w1 >> 1].x;
+                const float2 up = *reinterpret_cast<const float2 *>(&sv[c + m * WR]);
+                const float2 dn = *reinterpret_cast<const float2 *>(&sv[c - m * WR]);
+                float2 sum = add2(make_float2(ex0, ex1), make_float2(wx0, wx1));
+                sum = add2(sum, add2(up, dn));
+                acc = fma2(f2(P.fd[m]), sum, acc);
+            }
+            res[v] = fma2(make_float2(-a2.x, -a2.y), acc, ctr);
+        }
+        const int gidx = Y * P.nx + X;
+        *reinterpret_cast<float2 *>(&pout[gidx]) = res[0];
+        *reinterpret_cast<float2 *>(&uxout[gidx]) = res[1];
+        *reinterpret_cast<float2 *>(&uyout[gidx]) = res[2];
     }
 }
 
