@@ -150,8 +150,9 @@ lbm_status lbm_diagnostics(lbm_handle *h, double *out);
 
 /*
  * lbm_check -- LBM_ERR_NONFINITE if any field value is NaN/Inf,
- * LBM_ERR_RANGE if phi leaves [-1-delta, 1+delta], else LBM_OK.
- * Synchronises the stream.
+ * LBM_ERR_RANGE if phi leaves [-1-delta, 1+delta], LBM_ERR_CUDA if a kernel
+ * of an earlier step gave up a bounded wait for a tile copy (its tile was
+ * then not updated), else LBM_OK.  Synchronises the stream.
  */
 lbm_status lbm_check(lbm_handle *h, double delta);
 

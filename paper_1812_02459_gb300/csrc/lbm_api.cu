@@ -4,9 +4,12 @@
 // scratch planes of one step.  A step is a fixed sequence of tile kernels on
 // the handle's stream (see lbm_kernels.cuh):
 //   collide+stream (both lattices) -> RK3 stage x3 -> Picard sweep xK -> filter.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -25,8 +28,16 @@ namespace {
 
 constexpr int CS_TX = 30, CS_TY = 14;    // collide+stream tile: its ring-1 region is 32 x 16 = one node per thread
 constexpr int RK_TX = 64, RK_TY = 32, RK_NT = 512;   // RK3 stage tile, threads
+constexpr int RS_NT = 256, RS_VR1 = 8, RS_VR2 = 6, RS_VR3 = 4;   // FP32 strips: threads, rows per strip
+constexpr int PS_TX = 128, PS_TY = 16, PS_NT = 256, PS_VR1 = 6, PS_VR2 = 4;   // FP32 Picard strips
 constexpr int PC_TX = 64, PC_TY = 16, PC_NT = 512;   // Picard sweep tile, threads
 constexpr int FL_TX = 64, FL_TY = 16, FL_NT = 512;   // filter tile, threads
+constexpr int FS_TX = 64, FS_TY = 64, FS_VR = 8;     // FP32 filter: tile, rows per thread
+// TMA-staged FP32 kernels (nx a multiple of 4): tiles, threads, rows per
+// strip, resident CTAs per SM the registers are sized for
+constexpr int RT_NT = 256, RT_MINB = 4;
+constexpr int PT_TX = 128, PT_TY = 16, PT_NT = 256, PT_VR1 = 6, PT_VR2 = 4, PT_MINB = 3;
+constexpr int FT_TX = 64, FT_TY = 32, FT_VR = 4, FT_MINB = 4;
 constexpr int DIAG_THREADS = 256;
 constexpr int DIAG_MAX_BLOCKS = 1216;    // 8 x 152 SMs
 
@@ -174,6 +185,69 @@ bool default_rates(const lbm_params &p)
     return true;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no
+// link-time dependence on the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// The tensor map of an FP32 plane of the handle for bw x bh windows.
+lbm_status tmap(lbm_handle *h, const void *plane, int bw, int bh, CUtensorMap *out)
+{
+    for (const auto &e : h->tmaps)
+        if (e.ptr == plane && e.bw == bw && e.bh == bh) {
+            *out = e.map;
+            return LBM_OK;
+        }
+    auto fn = encode_tiled();
+    if (!fn) return fail(h, LBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    lbm_handle::TmaEntry e{plane, bw, bh, {}};
+    const cuuint64_t dims[2] = {(cuuint64_t)h->grid.nx, (cuuint64_t)h->grid.ny};
+    const cuuint64_t strides[1] = {(cuuint64_t)h->grid.nx * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(&e.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(plane), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, LBM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    h->tmaps.push_back(e);
+    *out = e.map;
+    return LBM_OK;
+}
+
+// Dynamic shared memory of a TMA-staged kernel above the 48 KB default.
+template <typename K> lbm_status setup_tma_kernel(lbm_handle *h, K kern, size_t bytes)
+{
+    CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
+       "cudaFuncSetAttribute(tma kernel)");
+    return LBM_OK;
+}
+
+template <int R> lbm_status setup_filter_tma(lbm_handle *h)
+{
+    return setup_tma_kernel(h, k_filter_tma<FT_TX, FT_TY, R, FT_VR, FT_MINB>, FLTGeom<FT_TX, FT_TY, R, FT_VR>::Tile::BYTES);
+}
+
+template <int R> lbm_status set_strip_smem(lbm_handle *h)
+{
+    CK(h, cudaFuncSetAttribute(k_filter_strips<FS_TX, FS_TY, R, FS_VR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(sizeof(float) * FLSGeom<FS_TX, FS_TY, R, FS_VR>::NSCALAR)),
+       "cudaFuncSetAttribute(filter_strips)");
+    return LBM_OK;
+}
+
 template <typename T, typename S>
 lbm_status set_smem_limits(lbm_handle *h)
 {
@@ -192,6 +266,37 @@ lbm_status set_smem_limits(lbm_handle *h)
     CK(h, cudaFuncSetAttribute(k_filter<T, FL_TX, FL_TY, 5, FL_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem_fl<T, 5>()),
        "cudaFuncSetAttribute(filter)");
+    if constexpr (std::is_same<T, float>::value) {
+        CK(h, cudaFuncSetAttribute(k_rk_strips<RK_TX, RK_TY, RS_NT, RS_VR1, RS_VR2, RS_VR3>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rk<float>()),
+           "cudaFuncSetAttribute(rk_strips)");
+        CK(h, cudaFuncSetAttribute(k_picard_strips<PS_TX, PS_TY, PS_NT, PS_VR1, PS_VR2>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(float) * PSGeom<PS_TX, PS_TY>::NSCALAR)),
+           "cudaFuncSetAttribute(picard_strips)");
+        lbm_status st = set_strip_smem<2>(h);
+        if (st == LBM_OK) st = set_strip_smem<3>(h);
+        if (st == LBM_OK) st = set_strip_smem<4>(h);
+        if (st == LBM_OK) st = set_strip_smem<5>(h);
+        if (st != LBM_OK) return st;
+        if (h->tma) {
+            st = setup_tma_kernel(h, k_rk_tma<RK_TX, RK_TY, RT_NT, RS_VR1, RS_VR2, RS_VR3, RT_MINB>,
+                                  RKTGeom<RK_TX, RK_TY>::Tile::BYTES);
+            if (st == LBM_OK)
+                st = setup_tma_kernel(h, k_picard_tma<PT_TX, PT_TY, PT_NT, PT_VR1, PT_VR2, PT_MINB>,
+                                      PCTGeom<PT_TX, PT_TY>::Tile::BYTES);
+            if (st == LBM_OK) {
+                switch (h->kpf.fR) {
+                case 2: st = setup_filter_tma<2>(h); break;
+                case 3: st = setup_filter_tma<3>(h); break;
+                case 4: st = setup_filter_tma<4>(h); break;
+                case 5: st = setup_filter_tma<5>(h); break;
+                default: break;
+                }
+            }
+            if (st != LBM_OK) return st;
+        }
+    }
     return LBM_OK;
 }
 
@@ -230,19 +335,35 @@ struct Timed {
 };
 
 template <typename T, int R>
-void launch_filter_r(lbm_handle *h, const T *pin, const T *uxi, const T *uyi, T *po, T *uxo, T *uyo)
+lbm_status launch_filter_r(lbm_handle *h, const T *pin, const T *uxi, const T *uyi, T *po, T *uxo, T *uyo)
 {
     const KP<T> &P = kp_of<T>(h);
     dim3 grid((P.nx + FL_TX - 1) / FL_TX, (P.ny + FL_TY - 1) / FL_TY);
     Timed tm(h, 3);
     if constexpr (std::is_same<T, float>::value) {
-        if (P.nx % 2 == 0) {   // node pairs with paired FP32 arithmetic
-            k_filter_pairs<FL_TX, FL_TY, R, FL_NT><<<grid, FL_NT, sizeof(float) * FL2Geom<FL_TX, FL_TY, R>::NSCALAR,
-                                                    h->stream>>>(P, pin, uxi, uyi, po, uxo, uyo);
-            return;
+        if (h->tma) {   // TMA-staged windows, one CTA per tile
+            using GT = FLTGeom<FT_TX, FT_TY, R, FT_VR>;
+            TmaMaps maps{};
+            const void *planes[3] = {pin, uxi, uyi};
+            for (int f = 0; f < 3; ++f) {
+                lbm_status r = tmap(h, planes[f], GT::BW, GT::BH, &maps.m[f]);
+                if (r) return r;
+            }
+            const int ntiles = ((P.nx + FT_TX - 1) / FT_TX) * ((P.ny + FT_TY - 1) / FT_TY);
+            k_filter_tma<FT_TX, FT_TY, R, FT_VR, FT_MINB><<<ntiles, GT::NT, GT::Tile::BYTES, h->stream>>>(
+                maps, P, pin, uxi, uyi, po, uxo, uyo, h->dev_err);
+            return LBM_OK;
+        }
+        if (P.nx % 2 == 0) {   // 2 x 8 node blocks, register reuse, paired FP32 arithmetic
+            using GS = FLSGeom<FS_TX, FS_TY, R, FS_VR>;
+            dim3 gs((P.nx + FS_TX - 1) / FS_TX, (P.ny + FS_TY - 1) / FS_TY);
+            k_filter_strips<FS_TX, FS_TY, R, FS_VR><<<gs, GS::NT, sizeof(float) * GS::NSCALAR, h->stream>>>(
+                P, pin, uxi, uyi, po, uxo, uyo);
+            return LBM_OK;
         }
     }
     k_filter<T, FL_TX, FL_TY, R, FL_NT><<<grid, FL_NT, smem_fl<T, R>(), h->stream>>>(P, pin, uxi, uyi, po, uxo, uyo);
+    return LBM_OK;
 }
 
 template <typename T, typename S>
@@ -270,19 +391,30 @@ lbm_status step_impl(lbm_handle *h)
     {   // TVD-RK3 finite-difference correction: phi_bar -> phi^{n+1}
         dim3 grid((P.nx + RK_TX - 1) / RK_TX, (P.ny + RK_TY - 1) / RK_TY);
         const size_t sm = smem_rk<T>();
-        {
+        const T *src[3] = {phibar, (const T *)h->s1, (const T *)h->s2};
+        T *dst[3] = {(T *)h->s1, (T *)h->s2, phi};
+        const T ca[3] = {T(0), T(0.75), T(1.0 / 3.0)}, cb[3] = {T(1), T(0.25), T(2.0 / 3.0)};
+        for (int k = 0; k < 3; ++k) {
             Timed tm(h, 1);
-            k_rk_stage<T, RK_TX, RK_TY, RK_NT><<<grid, RK_NT, sm, st>>>(P, phibar, phibar, (T *)h->s1, T(0), T(1));
-        }
-        {
-            Timed tm(h, 1);
-            k_rk_stage<T, RK_TX, RK_TY, RK_NT><<<grid, RK_NT, sm, st>>>(P, (T *)h->s1, phibar, (T *)h->s2,
-                                                                         T(0.75), T(0.25));
-        }
-        {
-            Timed tm(h, 1);
-            k_rk_stage<T, RK_TX, RK_TY, RK_NT><<<grid, RK_NT, sm, st>>>(P, (T *)h->s2, phibar, phi,
-                                                                         T(1.0 / 3.0), T(2.0 / 3.0));
+            bool done = false;
+            if constexpr (std::is_same<T, float>::value) {
+                if (h->tma) {   // TMA-staged windows, one CTA per tile
+                    using GT = RKTGeom<RK_TX, RK_TY>;
+                    TmaMaps maps{};
+                    lbm_status r = tmap(h, src[k], GT::BW, GT::BH, &maps.m[0]);
+                    if (r) return r;
+                    k_rk_tma<RK_TX, RK_TY, RT_NT, RS_VR1, RS_VR2, RS_VR3, RT_MINB>
+                        <<<grid.x * grid.y, RT_NT, GT::Tile::BYTES, st>>>(maps, P, src[k], phibar, dst[k], ca[k],
+                                                                         cb[k], h->dev_err);
+                    done = true;
+                } else if (P.nx % 2 == 0) {   // column-pair strips, paired FP32 arithmetic
+                    k_rk_strips<RK_TX, RK_TY, RS_NT, RS_VR1, RS_VR2, RS_VR3><<<grid, RS_NT, sm, st>>>(
+                        P, src[k], phibar, dst[k], ca[k], cb[k]);
+                    done = true;
+                }
+            }
+            if (!done)
+                k_rk_stage<T, RK_TX, RK_TY, RK_NT><<<grid, RK_NT, sm, st>>>(P, src[k], phibar, dst[k], ca[k], cb[k]);
         }
     }
     {   // implicit velocity by Picard sweeps; the last sweep lands in u_hat
@@ -294,15 +426,54 @@ lbm_status step_impl(lbm_handle *h)
             T *ox = k == K - 1 ? uhx : (T *)h->tk[k & 1][0];
             T *oy = k == K - 1 ? uhy : (T *)h->tk[k & 1][1];
             Timed tm(h, 2);
+            if constexpr (std::is_same<T, float>::value) {
+                if (h->tma) {   // TMA-staged windows, one CTA per tile
+                    using GT = PCTGeom<PT_TX, PT_TY>;
+                    TmaMaps maps{};
+                    const void *planes[4] = {phi, phat, ix, iy};
+                    for (int f = 0; f < 4; ++f) {
+                        lbm_status r = tmap(h, planes[f], GT::BW, GT::BH, &maps.m[f]);
+                        if (r) return r;
+                    }
+                    const int ntiles = ((P.nx + PT_TX - 1) / PT_TX) * ((P.ny + PT_TY - 1) / PT_TY);
+                    k_picard_tma<PT_TX, PT_TY, PT_NT, PT_VR1, PT_VR2, PT_MINB>
+                        <<<ntiles, PT_NT, GT::Tile::BYTES, st>>>(maps, P, phi, phat, jx, jy, ix, iy, ox, oy,
+                                                                 h->dev_err);
+                    continue;
+                }
+                if (P.nx % 2 == 0) {   // column-pair strips, paired FP32 arithmetic
+                    dim3 gs((P.nx + PS_TX - 1) / PS_TX, (P.ny + PS_TY - 1) / PS_TY);
+                    k_picard_strips<PS_TX, PS_TY, PS_NT, PS_VR1, PS_VR2>
+                        <<<gs, PS_NT, sizeof(float) * PSGeom<PS_TX, PS_TY>::NSCALAR, st>>>(P, phi, phat, jx, jy, ix, iy,
+                                                                                         ox, oy);
+                    continue;
+                }
+            }
             k_picard<T, PC_TX, PC_TY, PC_NT><<<grid, PC_NT, smem_pc<T>(), st>>>(P, phi, phat, jx, jy, ix, iy, ox, oy);
         }
     }
     // selective filter of (p_hat, u_hat) -> (p_f, u_f^{n+1}); u^{n-1} slot is reused
     switch (P.fR) {
-    case 2: launch_filter_r<T, 2>(h, phat, uhx, uhy, pf, uxp, uyp); break;
-    case 3: launch_filter_r<T, 3>(h, phat, uhx, uhy, pf, uxp, uyp); break;
-    case 4: launch_filter_r<T, 4>(h, phat, uhx, uhy, pf, uxp, uyp); break;
-    case 5: launch_filter_r<T, 5>(h, phat, uhx, uhy, pf, uxp, uyp); break;
+    case 2: {
+        lbm_status r = launch_filter_r<T, 2>(h, phat, uhx, uhy, pf, uxp, uyp);
+        if (r) return r;
+        break;
+    }
+    case 3: {
+        lbm_status r = launch_filter_r<T, 3>(h, phat, uhx, uhy, pf, uxp, uyp);
+        if (r) return r;
+        break;
+    }
+    case 4: {
+        lbm_status r = launch_filter_r<T, 4>(h, phat, uhx, uhy, pf, uxp, uyp);
+        if (r) return r;
+        break;
+    }
+    case 5: {
+        lbm_status r = launch_filter_r<T, 5>(h, phat, uhx, uhy, pf, uxp, uyp);
+        if (r) return r;
+        break;
+    }
     default: {
         const size_t b = sizeof(T) * (size_t)P.N;
         CK(h, cudaMemcpyAsync(pf, phat, b, cudaMemcpyDeviceToDevice, st), "copy p");
@@ -595,7 +766,7 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params, const doub
     const int nscalar = 22;   // phi, pf, ux[2], uy[2], uhx, uhy, phibar[2], phat[2], jx, jy, s1, s2, tk[2][2], 2 spare
     h->diag_blocks = (int)std::min<long long>((h->N + DIAG_THREADS - 1) / DIAG_THREADS, DIAG_MAX_BLOCKS);
     const size_t diag_bytes = round_up(sizeof(double) * (size_t)(h->diag_blocks + 1) * NDIAG, 256);
-    h->arena_bytes = 4 * pplane + nscalar * plane + diag_bytes;
+    h->arena_bytes = 4 * pplane + nscalar * plane + diag_bytes + 256;   // + the device error word
     cudaError_t e = cudaMalloc((void **)&h->arena, h->arena_bytes);
     if (e != cudaSuccess) {
         std::string m = std::string("cudaMalloc arena: ") + cudaGetErrorString(e);
@@ -615,6 +786,16 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params, const doub
     a += 2 * plane;
     h->diag_part = (double *)a;
     h->diag_out = h->diag_part + (size_t)h->diag_blocks * NDIAG;
+    h->dev_err = (unsigned *)(h->arena + h->arena_bytes - 256);
+    h->tma = grid->precision != LBM_FP64 && grid->nx % 4 == 0;
+    e = cudaMemsetAsync(h->dev_err, 0, sizeof(unsigned), h->stream);
+    if (e != cudaSuccess) {
+        std::string m = std::string("cudaMemsetAsync: ") + cudaGetErrorString(e);
+        cudaFree(h->arena);
+        delete h;
+        cudaGetLastError();
+        return fail(nullptr, LBM_ERR_CUDA, m);
+    }
 
     st = dispatch(grid->precision, [&](auto tp, auto sp) {
         TS_TYPES(tp, sp);
@@ -687,6 +868,9 @@ lbm_status lbm_check(lbm_handle *h, double delta)
     double d[NDIAG];
     lbm_status st = lbm_diagnostics(h, d);
     if (st) return st;
+    unsigned derr = 0;
+    CK(h, cudaMemcpy(&derr, h->dev_err, sizeof derr, cudaMemcpyDeviceToHost), "read device error word");
+    if (derr) return fail(h, LBM_ERR_CUDA, "a bounded wait for a TMA tile copy gave up; the step is incomplete");
     if (d[10] > 0) return fail(h, LBM_ERR_NONFINITE, "non-finite field value");
     if (d[8] > 1.0 + delta || d[9] < -1.0 - delta) return fail(h, LBM_ERR_RANGE, "phi outside [-1-delta, 1+delta]");
     return LBM_OK;

@@ -45,6 +45,16 @@ struct lbm_handle {
     // (lbm_create / lbm_set_fields, no step since): the adjoint needs it
     bool fresh_init = false;
     lbm_adjoint *adj = nullptr;
+    // TMA tile staging (FP32 arithmetic, nx a multiple of 4): tensor maps
+    // by (plane, window) and the device word that bounded waits report to
+    struct TmaEntry {
+        const void *ptr;
+        int bw, bh;
+        CUtensorMap map;
+    };
+    bool tma = false;
+    std::vector<TmaEntry> tmaps;
+    unsigned *dev_err = nullptr;
 };
 
 // Issue one step on the handle's stream (lbm_api.cu).

@@ -14,6 +14,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -97,6 +98,27 @@ __device__ __forceinline__ void tiles_ready()
     __syncthreads();
 }
 
+// Stage a window whose coordinates may leave the domain: each element is
+// mapped through the periodic wrap or the wall mirror (synchronous copies).
+template <typename T, int WS, int HS>
+__device__ __forceinline__ void load_tile_mapped(T *s, const T *__restrict__ g, int x0, int y0, const KP<T> &P,
+                                                 bool odd)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = warp; r < HS; r += nw) {
+        int fy;
+        const int gy = map_axis(y0 + r, P.ny, P.py, fy);
+        const T *row = g + (long long)gy * P.nx;
+#pragma unroll
+        for (int c = lane; c < WS; c += 32) {
+            int fx;
+            const int gx = map_axis(x0 + c, P.nx, P.px, fx);
+            const T v = __ldg(row + gx);
+            s[r * WS + c] = (odd && (fx ^ fy)) ? -v : v;
+        }
+    }
+}
+
 // Stage a (WS x HS) window of a scalar field whose top-left corner is global
 // (x0, y0) into shared memory s[HS][WS]; odd fields change sign in mirrors.
 // Each warp copies whole rows (lanes along x), so no per-element division
@@ -117,18 +139,7 @@ __device__ __forceinline__ void load_tile(T *s, const T *__restrict__ g, int x0,
         }
         return;
     }
-    for (int r = warp; r < HS; r += nw) {
-        int fy;
-        const int gy = map_axis(y0 + r, P.ny, P.py, fy);
-        const T *row = g + (long long)gy * P.nx;
-#pragma unroll
-        for (int c = lane; c < WS; c += 32) {
-            int fx;
-            const int gx = map_axis(x0 + c, P.nx, P.px, fx);
-            const T v = __ldg(row + gx);
-            s[r * WS + c] = (odd && (fx ^ fy)) ? -v : v;
-        }
-    }
+    load_tile_mapped<T, WS, HS>(s, g, x0, y0, P, odd);
 }
 
 // Isotropic first derivatives and Laplacian on a D2Q9 neighbourhood
@@ -860,6 +871,603 @@ k_filter_pairs(KP<float> P, const float *__restrict__ pin, const float *__restri
         *reinterpret_cast<float2 *>(&uxout[gidx]) = res[1];
         *reinterpret_cast<float2 *>(&uyout[gidx]) = res[2];
     }
+}
+
+// Filtered values of one field at the column pair (X, X+1) over VR rows from
+// ly0, the window s of row stride WR holding the field from column X - RP.
+template <int WR, int R, int VR>
+__device__ __forceinline__ void filter_strip(const KP<float> &P, const float *sv, int lx, int ly0, int y0, int X,
+                                             float *__restrict__ out)
+{
+    constexpr int RP = (R + 1) & ~1;
+    const float2 na = f2(-P.fa);
+    float2 col[VR + 2 * R];   // rows ly0 - R .. ly0 + VR - 1 + R of columns (X, X+1)
+#pragma unroll
+    for (int k = 0; k < VR + 2 * R; ++k)
+        col[k] = *reinterpret_cast<const float2 *>(&sv[(ly0 + k) * WR + lx + RP]);
+#pragma unroll
+    for (int i = 0; i < VR; ++i) {
+        const int Y = y0 + ly0 + i;
+        if (Y >= P.ny) break;
+        const int c = (ly0 + R + i) * WR + lx + RP;
+        float2 w[RP + 1];
+#pragma unroll
+        for (int k = 0; k < RP + 1; ++k) w[k] = *reinterpret_cast<const float2 *>(&sv[c - RP + 2 * k]);
+        const float2 ctr = col[R + i];
+        float2 acc = mul2(f2(2.0f * P.fd[0]), ctr);
+#pragma unroll
+        for (int m = 1; m <= R; ++m) {
+            const int e0 = RP + m, e1 = RP + m + 1, w0 = RP - m, w1 = RP - m + 1;
+            const float ex0 = (e0 & 1) ? w[e0 >> 1].y : w[e0 >> 1].x;
+            const float ex1 = (e1 & 1) ? w[e1 >> 1].y : w[e1 >> 1].x;
+            const float wx0 = (w0 & 1) ? w[w0 >> 1].y : w[w0 >> 1].x;
+            const float wx1 = (w1 & 1) ? w[w1 >> 1].y : w[w1 >> 1].x;
+            float2 sum = add2(make_float2(ex0, ex1), make_float2(wx0, wx1));
+            sum = add2(sum, add2(col[R + i + m], col[R + i - m]));
+            acc = fma2(f2(P.fd[m]), sum, acc);
+        }
+        *reinterpret_cast<float2 *>(&out[(long long)Y * P.nx + X]) = fma2(na, acc, ctr);
+    }
+}
+
+// Filter pass for FP32 on grids of even width, with register reuse: each
+// thread filters a 2-column x VR-row block.  The y-taps of the whole block
+// come from one column of VR + 2R aligned float2 reads held in registers; the
+// x-taps of each row from RP + 1 aligned float2 reads.
+// The three filtered fields of a TX x TY tile, thread t on the column pair
+// 2 (t mod TX/2) over VR rows; the windows hold the fields from
+// (x0 - RP, y0 - R) with row stride SW.
+template <int TX, int TY, int R, int VR, int SW>
+__device__ __forceinline__ void filter_strips_body(const KP<float> &P, const float *s_p, const float *s_ux,
+                                                   const float *s_uy, int x0, int y0, float *__restrict__ pout,
+                                                   float *__restrict__ uxout, float *__restrict__ uyout)
+{
+    const int t = threadIdx.x;
+    const int lx = 2 * (t % (TX / 2)), ly0 = (t / (TX / 2)) * VR;
+    const int X = x0 + lx;
+    if (X >= P.nx) return;
+    filter_strip<SW, R, VR>(P, s_p, lx, ly0, y0, X, pout);
+    filter_strip<SW, R, VR>(P, s_ux, lx, ly0, y0, X, uxout);
+    filter_strip<SW, R, VR>(P, s_uy, lx, ly0, y0, X, uyout);
+}
+
+template <int TX, int TY, int R, int VR> struct FLSGeom {
+    static constexpr int RP = (R + 1) & ~1;
+    static constexpr int WR = TX + 2 * RP, HR = TY + 2 * R;
+    static constexpr int NT = (TX / 2) * (TY / VR);
+    static constexpr int NSCALAR = 3 * WR * HR;
+};
+
+template <int TX, int TY, int R, int VR>
+__global__ void __launch_bounds__((TX / 2) * (TY / VR), 3)
+k_filter_strips(KP<float> P, const float *__restrict__ pin, const float *__restrict__ uxin,
+                const float *__restrict__ uyin, float *__restrict__ pout, float *__restrict__ uxout,
+                float *__restrict__ uyout)
+{
+    using G = FLSGeom<TX, TY, R, VR>;
+    constexpr int RP = G::RP, WR = G::WR, HR = G::HR, A = WR * HR;
+    static_assert(TX % 2 == 0 && WR % 2 == 0 && TY % VR == 0, "pairs need even widths");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *s_p = reinterpret_cast<float *>(smem_raw);
+    float *s_ux = s_p + A;
+    float *s_uy = s_ux + A;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    load_tile<float, WR, HR>(s_p, pin, x0 - RP, y0 - R, P, false);
+    load_tile<float, WR, HR>(s_ux, uxin, x0 - RP, y0 - R, P, true);
+    load_tile<float, WR, HR>(s_uy, uyin, x0 - RP, y0 - R, P, true);
+    tiles_ready();
+    filter_strips_body<TX, TY, R, VR, WR>(P, s_p, s_ux, s_uy, x0, y0, pout, uxout, uyout);
+}
+
+// Fourth-order differences (Sec. III.A Eq. fourOrder_FDM) of the node pair
+// (x, x+1), x even, from the aligned pairs l = (x-2, x-1), c = (x, x+1),
+// r = (x+2, x+3) of a row, or from five rows of pairs (y-derivatives).
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return fma2(f2(-1.0f), b, a); }
+__device__ __forceinline__ float2 pd1(float2 m2, float2 m1, float2 p1, float2 p2)
+{
+    return fma2(f2(2.0f / 3.0f), sub2(p1, m1), mul2(f2(1.0f / 12.0f), sub2(m2, p2)));
+}
+__device__ __forceinline__ float2 pd2(float2 m2, float2 m1, float2 c, float2 p1, float2 p2)
+{
+    return fma2(f2(4.0f / 3.0f), add2(m1, p1), fma2(f2(-2.5f), c, mul2(f2(-1.0f / 12.0f), add2(m2, p2))));
+}
+__device__ __forceinline__ float2 pd1x(float2 l, float2 c, float2 r)
+{
+    return pd1(l, make_float2(l.y, c.x), make_float2(c.y, r.x), r);
+}
+__device__ __forceinline__ float2 pd2x(float2 l, float2 c, float2 r)
+{
+    return pd2(l, make_float2(l.y, c.x), c, make_float2(c.y, r.x), r);
+}
+__device__ __forceinline__ float2 lds2(const float *s, int i) { return *reinterpret_cast<const float2 *>(s + i); }
+__device__ __forceinline__ void sts2(float *s, int i, float2 v) { *reinterpret_cast<float2 *>(s + i) = v; }
+
+// Pass 2 for FP32 on grids of even width, same tile and result as
+// k_rk_stage: each thread covers a column pair over VR1 / VR2 / VR3 rows of
+// the mu / J / divergence regions, holding the y-neighbours in registers.
+// s_psi holds psi from (x0 - 6, y0 - 6) with row stride SW.
+template <int TX, int TY, int NT, int VR1, int VR2, int VR3, int SW>
+__device__ __forceinline__ void rk_strips_body(const KP<float> &P, const float *s_psi, float *s_mu, float *s_jx,
+                                               float *s_jy, int x0, int y0, const float *__restrict__ phibar,
+                                               float *__restrict__ out, float a, float b)
+{
+    using G = RKGeom<TX, TY>;
+    constexpr int W4 = G::W4, H4 = G::H4, W2 = G::W2, H2 = G::H2;
+    static_assert(TX % 2 == 0 && SW % 2 == 0 && H4 % VR1 == 0 && H2 % VR2 == 0 && TY % VR3 == 0,
+                  "strips must tile the regions");
+
+    if (P.flux_corr) {   // mu on the (TX+8) x (TY+8) region, psi offset 2
+        constexpr int NP = W4 / 2, NI = NP * (H4 / VR1);
+        const float2 fb = f2(4.0f * P.beta), nk = f2(-P.kappa);
+        for (int it = threadIdx.x; it < NI; it += NT) {
+            const int lx = 2 * (it % NP), r0 = (it / NP) * VR1;
+            const int xc = lx + 2;
+            float2 w[VR1 + 4];
+#pragma unroll
+            for (int k = 0; k < VR1 + 4; ++k) w[k] = lds2(s_psi, (r0 + k) * SW + xc);
+#pragma unroll
+            for (int i = 0; i < VR1; ++i) {
+                const int row = (r0 + 2 + i) * SW + xc;
+                const float2 c = w[i + 2];
+                const float2 lap = add2(pd2x(lds2(s_psi, row - 2), c, lds2(s_psi, row + 2)),
+                                        pd2(w[i], w[i + 1], c, w[i + 3], w[i + 4]));
+                const float2 c3 = mul2(mul2(c, c), c);
+                sts2(s_mu, (r0 + i) * W4 + lx, fma2(fb, sub2(c3, c), mul2(nk, lap)));
+            }
+        }
+        __syncthreads();
+    }
+
+    {   // J = lambda J_phi n + q on the (TX+4) x (TY+4) region, psi offset 4, mu offset 2
+        constexpr int NP = W2 / 2, NI = NP * (H2 / VR2);
+        const float2 lam = f2(P.lambda), tw = f2(P.two_over_W), e2 = f2(P.eps2), nm = f2(-P.M);
+        for (int it = threadIdx.x; it < NI; it += NT) {
+            const int lx = 2 * (it % NP), r0 = (it / NP) * VR2;
+            const int xc = lx + 4;
+            float2 w[VR2 + 4];
+#pragma unroll
+            for (int k = 0; k < VR2 + 4; ++k) w[k] = lds2(s_psi, (r0 + 2 + k) * SW + xc);
+            float2 wm[VR2 + 4];
+            if (P.flux_corr) {
+#pragma unroll
+                for (int k = 0; k < VR2 + 4; ++k) wm[k] = lds2(s_mu, (r0 + k) * W4 + lx + 2);
+            }
+#pragma unroll
+            for (int i = 0; i < VR2; ++i) {
+                const int row = (r0 + 4 + i) * SW + xc;
+                const float2 v = w[i + 2];
+                const float2 gx = pd1x(lds2(s_psi, row - 2), v, lds2(s_psi, row + 2));
+                const float2 gy = pd1(w[i], w[i + 1], w[i + 3], w[i + 4]);
+                const float2 m2 = fma2(gx, gx, fma2(gy, gy, e2));
+                const float2 inv = make_float2(rsqrtf(m2.x), rsqrtf(m2.y));
+                const float2 nx = mul2(gx, inv), ny = mul2(gy, inv);
+                // |grad psi| - (2/W)(1 - psi^2)
+                const float2 jphi = fma2(tw, fma2(v, v, f2(-1.0f)), mul2(m2, inv));
+                const float2 lj = mul2(lam, jphi);
+                float2 jx = mul2(lj, nx), jy = mul2(lj, ny);
+                if (P.flux_corr) {
+                    const int mrow = (r0 + 2 + i) * W4 + lx + 2;
+                    const float2 mx = pd1x(lds2(s_mu, mrow - 2), wm[i + 2], lds2(s_mu, mrow + 2));
+                    const float2 my = pd1(wm[i], wm[i + 1], wm[i + 3], wm[i + 4]);
+                    const float2 t = mul2(nm, fma2(mx, nx, mul2(my, ny)));
+                    jx = fma2(t, nx, jx);
+                    jy = fma2(t, ny, jy);
+                }
+                sts2(s_jx, (r0 + i) * W2 + lx, jx);
+                sts2(s_jy, (r0 + i) * W2 + lx, jy);
+            }
+        }
+    }
+    __syncthreads();
+
+    {   // psi + div J on the tile, J offset 2, psi offset 6
+        constexpr int NP = TX / 2, NI = NP * (TY / VR3);
+        const float2 bb = f2(b), aa = f2(a);
+        for (int it = threadIdx.x; it < NI; it += NT) {
+            const int lx = 2 * (it % NP), r0 = (it / NP) * VR3;
+            const int X = x0 + lx;
+            if (X >= P.nx) continue;
+            float2 w[VR3 + 4];
+#pragma unroll
+            for (int k = 0; k < VR3 + 4; ++k) w[k] = lds2(s_jy, (r0 + k) * W2 + lx + 2);
+#pragma unroll
+            for (int i = 0; i < VR3; ++i) {
+                const int Y = y0 + r0 + i;
+                if (Y >= P.ny) break;
+                const int jrow = (r0 + 2 + i) * W2 + lx + 2;
+                const float2 L = add2(pd1x(lds2(s_jx, jrow - 2), lds2(s_jx, jrow), lds2(s_jx, jrow + 2)),
+                                      pd1(w[i], w[i + 1], w[i + 3], w[i + 4]));
+                const float2 v = lds2(s_psi, (r0 + 6 + i) * SW + lx + 6);
+                const long long gidx = (long long)Y * P.nx + X;
+                float2 r = mul2(bb, add2(v, L));
+                if (a != 0.0f) r = fma2(aa, *reinterpret_cast<const float2 *>(&phibar[gidx]), r);
+                *reinterpret_cast<float2 *>(&out[gidx]) = r;
+            }
+        }
+    }
+}
+
+template <int TX, int TY, int NT, int VR1, int VR2, int VR3>
+__global__ void __launch_bounds__(NT, 3)
+k_rk_strips(KP<float> P, const float *__restrict__ psi, const float *__restrict__ phibar, float *__restrict__ out,
+            float a, float b)
+{
+    using G = RKGeom<TX, TY>;
+    constexpr int W6 = G::W6, H6 = G::H6, W4 = G::W4, H4 = G::H4, W2 = G::W2, H2 = G::H2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *s_psi = reinterpret_cast<float *>(smem_raw);
+    float *s_mu = s_psi + W6 * H6;
+    float *s_jx = s_mu + W4 * H4;
+    float *s_jy = s_jx + W2 * H2;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    load_tile<float, W6, H6>(s_psi, psi, x0 - 6, y0 - 6, P, false);
+    tiles_ready();
+    rk_strips_body<TX, TY, NT, VR1, VR2, VR3, W6>(P, s_psi, s_mu, s_jx, s_jy, x0, y0, phibar, out, a, b);
+}
+
+// Pass 3 for FP32 on grids of even width, same result as k_picard: each
+// thread covers a column pair over VR2 rows.  Of each row of a 3 x 3
+// neighbourhood only D = E - W and U = C/3 + (E + W)/12 are kept, from which
+// the isotropic derivatives of Sec. III.B Eq. dicretized follow as
+//   d_x = D_0 / 3 + (D_+ + D_-) / 12,   d_y = U_+ - U_-.
+template <int TX, int TY> struct PSGeom {
+    static constexpr int WP = TX + 8, HP = TY + 4;   // phi, origin (x0 - 4, y0 - 2)
+    static constexpr int WA = TX + 4, HA = TY + 2;   // p, u, mu, grad phi, origin (x0 - 2, y0 - 1)
+    static constexpr int NSCALAR = WP * HP + 6 * WA * HA;
+};
+
+__device__ __forceinline__ void iso_row(float2 l, float2 c, float2 r, float2 &D, float2 &U)
+{
+    const float2 Wv = make_float2(l.y, c.x), E = make_float2(c.y, r.x);
+    D = sub2(E, Wv);
+    U = fma2(f2(1.0f / 3.0f), c, mul2(f2(1.0f / 12.0f), add2(E, Wv)));
+}
+__device__ __forceinline__ float2 iso_dx(float2 Ds, float2 Dc, float2 Dn)
+{
+    return fma2(f2(1.0f / 3.0f), Dc, mul2(f2(1.0f / 12.0f), add2(Dn, Ds)));
+}
+
+struct PicardRow {
+    float2 Dm, Um;              // mu
+    float2 Dxx, Dxy, Uxy, Uyy;  // T = (gy^2, -gx gy; -gx gy, gx^2)
+    float2 Dux, Uux, Duy, Uuy;  // u^k
+};
+
+// s_phi holds phi from (x0 - 4, y0 - 2) with row stride SP; s_p, s_ux, s_uy
+// hold p_hat, u^k from (x0 - 2, y0 - 1) with row stride SA; s_mu, s_gx, s_gy
+// are (TX + 4) x (TY + 2) work arrays.
+template <int TX, int TY, int NT, int VR1, int VR2, int SP, int SA>
+__device__ __forceinline__ void picard_strips_body(const KP<float> &P, const float *s_phi, const float *s_p,
+                                                   const float *s_ux, const float *s_uy, float *s_mu, float *s_gx,
+                                                   float *s_gy, int x0, int y0, const float *__restrict__ jx,
+                                                   const float *__restrict__ jy, float *__restrict__ uox,
+                                                   float *__restrict__ uoy)
+{
+    using G = PSGeom<TX, TY>;
+    constexpr int WA = G::WA, HA = G::HA;
+    static_assert(TX % 2 == 0 && SP % 2 == 0 && SA % 2 == 0 && HA % VR1 == 0 && TY % VR2 == 0,
+                  "strips must tile the regions");
+    {   // mu and grad phi on the (TX+4) x (TY+2) region
+        constexpr int NP = WA / 2, NI = NP * (HA / VR1);
+        const float2 fb = f2(4.0f * P.beta), nk = f2(-P.kappa);
+        for (int it = threadIdx.x; it < NI; it += NT) {
+            const int lx = 2 * (it % NP), r0 = (it / NP) * VR1;
+            float2 C[VR1 + 2], D[VR1 + 2], S[VR1 + 2];
+#pragma unroll
+            for (int k = 0; k < VR1 + 2; ++k) {
+                const int row = (r0 + k) * SP + lx + 2;
+                const float2 l = lds2(s_phi, row - 2), c = lds2(s_phi, row), r = lds2(s_phi, row + 2);
+                const float2 Wv = make_float2(l.y, c.x), E = make_float2(c.y, r.x);
+                C[k] = c;
+                D[k] = sub2(E, Wv);
+                S[k] = add2(E, Wv);
+            }
+#pragma unroll
+            for (int i = 0; i < VR1; ++i) {
+                const float2 gx = iso_dx(D[i], D[i + 1], D[i + 2]);
+                const float2 gy = fma2(f2(1.0f / 3.0f), sub2(C[i + 2], C[i]), mul2(f2(1.0f / 12.0f), sub2(S[i + 2], S[i])));
+                const float2 lap = fma2(f2(2.0f / 3.0f), add2(S[i + 1], add2(C[i + 2], C[i])),
+                                        fma2(f2(1.0f / 6.0f), add2(S[i + 2], S[i]), mul2(f2(-10.0f / 3.0f), C[i + 1])));
+                const float2 ph = C[i + 1];
+                const float2 mu = fma2(fb, sub2(mul2(mul2(ph, ph), ph), ph), mul2(nk, lap));
+                const int o = (r0 + i) * WA + lx;
+                sts2(s_mu, o, mu);
+                sts2(s_gx, o, gx);
+                sts2(s_gy, o, gy);
+            }
+        }
+    }
+    __syncthreads();
+
+    {   // u^{k+1} = j + F(u^k) / (2 rho) on the tile
+        constexpr int NP = TX / 2, NI = NP * (TY / VR2);
+        const float2 dr = f2(P.drho), drm = f2(P.drho * P.M), kap = f2(P.kappa);
+        for (int it = threadIdx.x; it < NI; it += NT) {
+            const int lx = 2 * (it % NP), r0 = (it / NP) * VR2;
+            const int X = x0 + lx;
+            if (X >= P.nx) continue;
+            PicardRow rw[VR2 + 2];
+#pragma unroll
+            for (int k = 0; k < VR2 + 2; ++k) {
+                const int a = (r0 + k) * WA + lx + 2, au = (r0 + k) * SA + lx + 2;
+                iso_row(lds2(s_mu, a - 2), lds2(s_mu, a), lds2(s_mu, a + 2), rw[k].Dm, rw[k].Um);
+                const float2 gxl = lds2(s_gx, a - 2), gxc = lds2(s_gx, a), gxr = lds2(s_gx, a + 2);
+                const float2 gyl = lds2(s_gy, a - 2), gyc = lds2(s_gy, a), gyr = lds2(s_gy, a + 2);
+                float2 dummy;
+                iso_row(mul2(gyl, gyl), mul2(gyc, gyc), mul2(gyr, gyr), rw[k].Dxx, dummy);
+                const float2 m1 = f2(-1.0f);
+                iso_row(mul2(m1, mul2(gxl, gyl)), mul2(m1, mul2(gxc, gyc)), mul2(m1, mul2(gxr, gyr)), rw[k].Dxy,
+                        rw[k].Uxy);
+                iso_row(mul2(gxl, gxl), mul2(gxc, gxc), mul2(gxr, gxr), dummy, rw[k].Uyy);
+                iso_row(lds2(s_ux, au - 2), lds2(s_ux, au), lds2(s_ux, au + 2), rw[k].Dux, rw[k].Uux);
+                iso_row(lds2(s_uy, au - 2), lds2(s_uy, au), lds2(s_uy, au + 2), rw[k].Duy, rw[k].Uuy);
+                if (k < 2) continue;
+                // output row i = k - 2 from rows k - 2 (south), k - 1 (centre), k (north)
+                const int i = k - 2;
+                const int Y = y0 + r0 + i;
+                if (Y >= P.ny) break;
+                const PicardRow &sR = rw[k - 2], &cR = rw[k - 1], &nR = rw[k];
+                const float2 dmx = iso_dx(sR.Dm, cR.Dm, nR.Dm), dmy = sub2(nR.Um, sR.Um);
+                const float2 Fsx = mul2(kap, add2(iso_dx(sR.Dxx, cR.Dxx, nR.Dxx), sub2(nR.Uxy, sR.Uxy)));
+                const float2 Fsy = mul2(kap, add2(iso_dx(sR.Dxy, cR.Dxy, nR.Dxy), sub2(nR.Uyy, sR.Uyy)));
+                const float2 dxux = iso_dx(sR.Dux, cR.Dux, nR.Dux), dyux = sub2(nR.Uux, sR.Uux);
+                const float2 dxuy = iso_dx(sR.Duy, cR.Duy, nR.Duy), dyuy = sub2(nR.Uuy, sR.Uuy);
+                const int ac = (r0 + i + 1) * WA + lx + 2;
+                const float2 grx = mul2(dr, lds2(s_gx, ac)), gry = mul2(dr, lds2(s_gy, ac));
+                const float2 Jx = mul2(drm, dmx), Jy = mul2(drm, dmy);
+                const float2 pc = lds2(s_p, (r0 + i + 1) * SA + lx + 2);
+                const float2 ph = lds2(s_phi, (r0 + i + 2) * SP + lx + 4);
+                float2 rho, ir, nu;
+                rho_nu(P, ph.x, rho.x, ir.x, nu.x);
+                rho_nu(P, ph.y, rho.y, ir.y, nu.y);
+                const float2 Sxx = add2(dxux, dxux), Sxy = add2(dyux, dxuy), Syy = add2(dyuy, dyuy);
+                const float2 rg = sub2(rho, f2(P.g_rho_ref));
+                float2 Fx = fma2(rg, f2(P.gx), fma2(Jx, dxux, mul2(Jy, dyux)));
+                float2 Fy = fma2(rg, f2(P.gy), fma2(Jx, dxuy, mul2(Jy, dyuy)));
+                Fx = fma2(nu, fma2(Sxx, grx, mul2(Sxy, gry)), add2(Fx, fma2(mul2(m1, pc), grx, Fsx)));
+                Fy = fma2(nu, fma2(Sxy, grx, mul2(Syy, gry)), add2(Fy, fma2(mul2(m1, pc), gry, Fsy)));
+                const float2 hh = mul2(f2(0.5f), ir);
+                const long long gidx = (long long)Y * P.nx + X;
+                const float2 jxv = *reinterpret_cast<const float2 *>(&jx[gidx]);
+                const float2 jyv = *reinterpret_cast<const float2 *>(&jy[gidx]);
+                *reinterpret_cast<float2 *>(&uox[gidx]) = fma2(Fx, hh, jxv);
+                *reinterpret_cast<float2 *>(&uoy[gidx]) = fma2(Fy, hh, jyv);
+            }
+        }
+    }
+}
+
+template <int TX, int TY, int NT, int VR1, int VR2>
+__global__ void __launch_bounds__(NT, 3)
+k_picard_strips(KP<float> P, const float *__restrict__ phi, const float *__restrict__ phat,
+                const float *__restrict__ jx, const float *__restrict__ jy,
+                const float *__restrict__ ukx, const float *__restrict__ uky,
+                float *__restrict__ uox, float *__restrict__ uoy)
+{
+    using G = PSGeom<TX, TY>;
+    constexpr int WP = G::WP, HP = G::HP, WA = G::WA, HA = G::HA, AA = WA * HA;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *s_phi = reinterpret_cast<float *>(smem_raw);
+    float *s_p = s_phi + WP * HP;
+    float *s_ux = s_p + AA;
+    float *s_uy = s_ux + AA;
+    float *s_mu = s_uy + AA;
+    float *s_gx = s_mu + AA;
+    float *s_gy = s_gx + AA;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    load_tile<float, WP, HP>(s_phi, phi, x0 - 4, y0 - 2, P, false);
+    load_tile<float, WA, HA>(s_p, phat, x0 - 2, y0 - 1, P, false);
+    load_tile<float, WA, HA>(s_ux, ukx, x0 - 2, y0 - 1, P, true);
+    load_tile<float, WA, HA>(s_uy, uky, x0 - 2, y0 - 1, P, true);
+    tiles_ready();
+    picard_strips_body<TX, TY, NT, VR1, VR2, WP, WA>(P, s_phi, s_p, s_ux, s_uy, s_mu, s_gx, s_gy, x0, y0, jx, jy,
+                                                     uox, uoy);
+}
+
+// ---------------------------------------------------------------------------
+// TMA tile staging (FP32, grid width a multiple of 4 so rows are 16-byte
+// aligned).  One CTA per tile: thread 0 issues one cp.async.bulk.tensor per
+// input field for the tile's window, completing on an mbarrier; a window
+// that crosses the domain edge (periodic wrap or wall mirror) is staged by
+// the threads instead.  The wait is bounded: when it gives up, bit 0 of
+// *err is set and the CTA leaves without computing.
+// ---------------------------------------------------------------------------
+struct TmaMaps {
+    CUtensorMap m[4];
+};
+
+constexpr unsigned TMA_WAIT_POLLS = 1u << 20;   // about a second of polling at most
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(smem_u32(b)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *b, unsigned parity)
+{
+    for (unsigned i = 0; i < TMA_WAIT_POLLS; ++i)
+        if (mbar_try_wait(b, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(float *dst, const CUtensorMap *map, int x, int y,
+                                            unsigned long long *b)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(dst)),
+                 "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(b))
+                 : "memory");
+}
+
+// Shared memory of a TMA-staged tile: the mbarrier and a flag in the first
+// 128 bytes, then NF field windows of BW x BH floats, each starting on a
+// 128-byte boundary, then EXTRA work floats.
+template <int NF, int BW, int BH, int EXTRA> struct TmaTile {
+    static constexpr int FS = (BW * BH + 31) / 32 * 32;
+    static constexpr size_t BYTES = 128 + sizeof(float) * (NF * FS + EXTRA) + 128;   // + base alignment
+
+    unsigned long long *bar;
+    int *flag;
+    float *win;
+    float *work;
+
+    // Carve the dynamic shared memory and initialise the barrier.
+    __device__ __forceinline__ explicit TmaTile(unsigned char *raw)
+    {
+        unsigned char *base = raw + ((128u - (smem_u32(raw) & 127u)) & 127u);
+        bar = reinterpret_cast<unsigned long long *>(base);
+        flag = reinterpret_cast<int *>(base + 16);
+        win = reinterpret_cast<float *>(base + 128);
+        work = win + NF * FS;
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+    }
+
+    // Stage the windows at global (gx, gy) of the NF fields and make them
+    // readable by every thread; false (for the whole CTA) when the TMA wait
+    // gave up, after recording it in *err.
+    __device__ __forceinline__ bool load(const KP<float> &P, const TmaMaps &tm, const float *const *src,
+                                         unsigned oddmask, int gx, int gy, unsigned *err)
+    {
+        const bool inner = gx >= 0 && gy >= 0 && gx + BW <= P.nx && gy + BH <= P.ny;
+        if (!inner) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                load_tile_mapped<float, BW, BH>(win + f * FS, src[f], gx, gy, P, (oddmask >> f) & 1u);
+            __syncthreads();
+            return true;
+        }
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(bar, (unsigned)(NF * BW * BH * sizeof(float)));
+#pragma unroll
+            for (int f = 0; f < NF; ++f) tma_load_2d(win + f * FS, &tm.m[f], gx, gy, bar);
+            *flag = mbar_wait_bounded(bar, 0) ? 1 : 0;
+            if (!*flag) atomicOr(err, 1u);
+        }
+        __syncthreads();
+        const bool ok = *flag != 0;
+        if (ok) mbar_try_wait(bar, 0);   // completed phase: acquires the TMA writes
+        return ok;
+    }
+};
+
+__device__ __forceinline__ void tile_origin(int TX, int TY, int &x0, int &y0, const KP<float> &P)
+{
+    const int ntx = (P.nx + TX - 1) / TX;
+    const int ty = (int)blockIdx.x / ntx;
+    x0 = ((int)blockIdx.x - ty * ntx) * TX;
+    y0 = ty * TY;
+}
+
+// Filter pass with TMA staging, one CTA per TX x TY tile: windows
+// (TX + 16) x (TY + 2R) from (x0 - 8, y0 - R) of p_hat, u_hat_x, u_hat_y.
+template <int TX, int TY, int R, int VR> struct FLTGeom {
+    static constexpr int BW = TX + 16, BH = TY + 2 * R, NT = (TX / 2) * (TY / VR);
+    using Tile = TmaTile<3, BW, BH, 0>;
+};
+
+template <int TX, int TY, int R, int VR, int MINB>
+__global__ void __launch_bounds__((TX / 2) * (TY / VR), MINB)
+k_filter_tma(const __grid_constant__ TmaMaps tm, KP<float> P, const float *__restrict__ pin,
+             const float *__restrict__ uxin, const float *__restrict__ uyin, float *__restrict__ pout,
+             float *__restrict__ uxout, float *__restrict__ uyout, unsigned *err)
+{
+    using G = FLTGeom<TX, TY, R, VR>;
+    constexpr int BW = G::BW, FS = G::Tile::FS, RP = (R + 1) & ~1, OFF = 8 - RP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename G::Tile tile(smem_raw);
+    const float *src[3] = {pin, uxin, uyin};
+    int x0, y0;
+    tile_origin(TX, TY, x0, y0, P);
+    if (!tile.load(P, tm, src, 6u, x0 - 8, y0 - R, err)) return;
+    const float *sp = tile.win + OFF;
+    filter_strips_body<TX, TY, R, VR, BW>(P, sp, sp + FS, sp + 2 * FS, x0, y0, pout, uxout, uyout);
+}
+
+// RK3 stage with TMA staging, one CTA per TX x TY tile: window
+// (TX + 16) x (TY + 12) of psi from (x0 - 8, y0 - 6); mu and J in the work
+// area.
+template <int TX, int TY> struct RKTGeom {
+    using G = RKGeom<TX, TY>;
+    static constexpr int BW = TX + 16, BH = TY + 12;
+    static constexpr int EXTRA = G::W4 * G::H4 + 2 * G::W2 * G::H2;
+    using Tile = TmaTile<1, BW, BH, EXTRA>;
+};
+
+template <int TX, int TY, int NT, int VR1, int VR2, int VR3, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+k_rk_tma(const __grid_constant__ TmaMaps tm, KP<float> P, const float *__restrict__ psi,
+         const float *__restrict__ phibar, float *__restrict__ out, float a, float b, unsigned *err)
+{
+    using T = RKTGeom<TX, TY>;
+    using G = RKGeom<TX, TY>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename T::Tile tile(smem_raw);
+    float *s_mu = tile.work;
+    float *s_jx = s_mu + G::W4 * G::H4;
+    float *s_jy = s_jx + G::W2 * G::H2;
+    const float *src[1] = {psi};
+    int x0, y0;
+    tile_origin(TX, TY, x0, y0, P);
+    if (!tile.load(P, tm, src, 0u, x0 - 8, y0 - 6, err)) return;
+    rk_strips_body<TX, TY, NT, VR1, VR2, VR3, T::BW>(P, tile.win + 2, s_mu, s_jx, s_jy, x0, y0, phibar, out, a, b);
+}
+
+// Picard sweep with TMA staging, one CTA per TX x TY tile: windows
+// (TX + 8) x (TY + 4) from (x0 - 4, y0 - 2) of phi, p_hat, u^k_x, u^k_y;
+// mu and grad phi in the work area.
+template <int TX, int TY> struct PCTGeom {
+    using G = PSGeom<TX, TY>;
+    static constexpr int BW = TX + 8, BH = TY + 4;
+    static constexpr int EXTRA = 3 * G::WA * G::HA;
+    using Tile = TmaTile<4, BW, BH, EXTRA>;
+};
+
+template <int TX, int TY, int NT, int VR1, int VR2, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+k_picard_tma(const __grid_constant__ TmaMaps tm, KP<float> P, const float *__restrict__ phi,
+             const float *__restrict__ phat, const float *__restrict__ jx, const float *__restrict__ jy,
+             const float *__restrict__ ukx, const float *__restrict__ uky, float *__restrict__ uox,
+             float *__restrict__ uoy, unsigned *err)
+{
+    using T = PCTGeom<TX, TY>;
+    using G = PSGeom<TX, TY>;
+    constexpr int BW = T::BW, FS = T::Tile::FS, AA = G::WA * G::HA;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename T::Tile tile(smem_raw);
+    float *s_mu = tile.work;
+    float *s_gx = s_mu + AA;
+    float *s_gy = s_gx + AA;
+    const float *src[4] = {phi, phat, ukx, uky};
+    int x0, y0;
+    tile_origin(TX, TY, x0, y0, P);
+    if (!tile.load(P, tm, src, 12u, x0 - 4, y0 - 2, err)) return;
+    const float *st = tile.win;
+    // p_hat and u^k from (x0 - 2, y0 - 1): one row and two columns into their windows
+    picard_strips_body<TX, TY, NT, VR1, VR2, BW, BW>(P, st, st + FS + BW + 2, st + 2 * FS + BW + 2,
+                                                     st + 3 * FS + BW + 2, s_mu, s_gx, s_gy, x0, y0, jx, jy, uox,
+                                                     uoy);
 }
 
 // ---------------------------------------------------------------------------

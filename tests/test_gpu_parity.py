@@ -82,6 +82,55 @@ def test_ragged_walls_gravity_fp32():
     assert_parity(o, g, TOL["fp32"], tol_pu=TOL_FP32_PU)
 
 
+@pytest.mark.parametrize("nx,ny,px,py", [(46, 37, 1, 0), (46, 38, 0, 0), (12, 12, 1, 1), (130, 18, 0, 1),
+                                         (200, 70, 1, 1), (300, 70, 0, 1), (392, 136, 1, 0)])
+def test_even_width_fp32(nx, ny, px, py):
+    """Even grid widths run the FP32 column-pair kernels: tiles ragged in both
+    axes, small grids whose halos wrap or mirror more than once, every
+    combination of walls.  Widths that are multiples of 4 go through the
+    TMA-pipelined kernels; from nx = 260 every one of them has tiles whose
+    windows lie inside the grid (tensor copies) beside edge tiles (mapped
+    copies)."""
+    prm = inputs.base_params(rho_H=20.0, sigma=5e-3, gy=-2e-6 if py == 0 else 0.0, periodic_x=px, periodic_y=py)
+    R = max(min(nx, ny) / 4.0, 3.0)
+    phi = inputs.drop(nx, ny, R, nx / 2 + 0.3, ny / 2 - 0.2, prm["W"])
+    z = np.zeros_like(phi)
+    o, g = run_both(prm, (phi, z, z, z), 60, "fp32")
+    assert_parity(o, g, TOL["fp32"], tol_pu=TOL_FP32_PU)
+
+
+@pytest.mark.parametrize("order,picard,flux", [(0, 2, 1), (5, 1, 1), (7, 3, 1), (9, 2, 1), (11, 2, 0)])
+def test_even_width_filter_orders_sweeps_fp32(order, picard, flux):
+    """Every filter radius, Picard sweep count and the variant without the
+    flux correction q through the FP32 column-pair kernels, with walls on
+    both axes."""
+    nx, ny = 46, 37
+    prm = inputs.base_params(rho_H=20.0, sigma=5e-3, gy=-2e-6, filter_order=order, picard_iters=picard,
+                             filter_a=0.3, flux_correction=flux, periodic_x=0, periodic_y=0)
+    phi = inputs.drop(nx, ny, 9.0, 22.0, 19.0, prm["W"])
+    z = np.zeros_like(phi)
+    o, g = run_both(prm, (phi, z, z, z), 60, "fp32")
+    assert_parity(o, g, TOL["fp32"], tol_pu=TOL_FP32_PU)
+
+
+@pytest.mark.parametrize("n", [48, 49])
+def test_translating_drop_fp32(n):
+    """A drop carried by a uniform flow U0 along x: nonzero u exercises the
+    velocity gradients of the Picard sweep and the filter of u.  Here u_y and
+    p are spurious residuals ~5e-4 U0, so their error is measured against
+    the flow's own scales instead of their maxima: |du| / U0 and |dp| /
+    (rho_H U0^2) at most 1e-5 (measured ~3e-7; even widths run the
+    column-pair kernels, odd widths the one-node-per-thread kernels)."""
+    U0 = 0.02
+    prm, fields = inputs.translating_drop(n=n, R=10.0, U0=U0)
+    o, g = run_both(prm, fields, 100, "fp32")
+    of, gf = o.fields(), g.fields()
+    assert rel_err(gf[0], of[0]) <= TOL["fp32"]
+    assert np.abs(gf[1] - of[1]).max() / (prm["rho_H"] * U0 ** 2) <= 1e-5
+    for k in (2, 3):
+        assert np.abs(gf[k] - of[k]).max() / U0 <= 1e-5
+
+
 def test_walls_on_both_axes_fp64():
     nx, ny = 37, 29
     phi, p, ux, uy = inputs.random_fields(nx, ny, seed=2)
