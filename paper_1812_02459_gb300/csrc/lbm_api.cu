@@ -38,6 +38,7 @@ constexpr int FS_TX = 64, FS_TY = 64, FS_VR = 8;     // FP32 filter: tile, rows 
 constexpr int RT_NT = 256, RT_MINB = 4;
 constexpr int PT_TX = 128, PT_TY = 16, PT_NT = 256, PT_VR1 = 6, PT_VR2 = 4, PT_MINB = 3;
 constexpr int FT_TX = 64, FT_TY = 32, FT_VR = 4, FT_MINB = 4;
+constexpr int CP_TX = 60, CP_TY = 14, CP_VR1 = 2;   // collide+stream on node pairs
 constexpr int DIAG_THREADS = 256;
 constexpr int DIAG_MAX_BLOCKS = 1216;    // 8 x 152 SMs
 
@@ -280,7 +281,9 @@ lbm_status set_smem_limits(lbm_handle *h)
         if (st == LBM_OK) st = set_strip_smem<5>(h);
         if (st != LBM_OK) return st;
         if (h->tma) {
-            st = setup_tma_kernel(h, k_rk_tma<RK_TX, RK_TY, RT_NT, RS_VR1, RS_VR2, RS_VR3, RT_MINB>,
+            st = setup_tma_kernel(h, k_collide_pairs<S, CP_TX, CP_TY, CP_VR1>, CPGeom<CP_TX, CP_TY>::Tile::BYTES);
+            if (st == LBM_OK)
+                st = setup_tma_kernel(h, k_rk_tma<RK_TX, RK_TY, RT_NT, RS_VR1, RS_VR2, RS_VR3, RT_MINB>,
                                   RKTGeom<RK_TX, RK_TY>::Tile::BYTES);
             if (st == LBM_OK)
                 st = setup_tma_kernel(h, k_picard_tma<PT_TX, PT_TY, PT_NT, PT_VR1, PT_VR2, PT_MINB>,
@@ -382,11 +385,30 @@ lbm_status step_impl(lbm_handle *h)
     {   // fields, forces, collision of f and g, pull streaming, post-stream moments
         dim3 grid((P.nx + CS_TX - 1) / CS_TX, (P.ny + CS_TY - 1) / CS_TY);
         Timed tm(h, 0);
-        auto kern = default_rates(h->prm) ? k_collide_stream<T, S, CS_TX, CS_TY, true>
-                                          : k_collide_stream<T, S, CS_TX, CS_TY, false>;
-        kern<<<grid, (CS_TX + 2) * (CS_TY + 2), smem_cs<T>(), st>>>(
-            P, (const S *)h->f[c], (const S *)h->g[c], (S *)h->f[1 - c], (S *)h->g[1 - c], phi, pf, uxc, uyc,
-            uxp, uyp, uhx, uhy, phibar_old, phat_old, phibar, phat, jx, jy);
+        bool done = false;
+        if constexpr (std::is_same<T, float>::value) {
+            if (h->tma && P.px && default_rates(h->prm)) {   // node pairs, TMA-staged windows
+                using GC = CPGeom<CP_TX, CP_TY>;
+                TmaMaps maps{};
+                const void *planes[4] = {phi, pf, uxc, uyc};
+                for (int f = 0; f < 4; ++f) {
+                    lbm_status r = tmap(h, planes[f], GC::BW, GC::BH, &maps.m[f]);
+                    if (r) return r;
+                }
+                const int ntiles = ((P.nx + CP_TX - 1) / CP_TX) * ((P.ny + CP_TY - 1) / CP_TY);
+                k_collide_pairs<S, CP_TX, CP_TY, CP_VR1><<<ntiles, GC::NT, GC::Tile::BYTES, st>>>(
+                    maps, P, (const S *)h->f[c], (const S *)h->g[c], (S *)h->f[1 - c], (S *)h->g[1 - c], phi, pf,
+                    uxc, uyc, uxp, uyp, uhx, uhy, phibar, phat, jx, jy, h->dev_err);
+                done = true;
+            }
+        }
+        if (!done) {
+            auto kern = default_rates(h->prm) ? k_collide_stream<T, S, CS_TX, CS_TY, true>
+                                              : k_collide_stream<T, S, CS_TX, CS_TY, false>;
+            kern<<<grid, (CS_TX + 2) * (CS_TY + 2), smem_cs<T>(), st>>>(
+                P, (const S *)h->f[c], (const S *)h->g[c], (S *)h->f[1 - c], (S *)h->g[1 - c], phi, pf, uxc, uyc,
+                uxp, uyp, uhx, uhy, phibar_old, phat_old, phibar, phat, jx, jy);
+        }
     }
     {   // TVD-RK3 finite-difference correction: phi_bar -> phi^{n+1}
         dim3 grid((P.nx + RK_TX - 1) / RK_TX, (P.ny + RK_TY - 1) / RK_TY);

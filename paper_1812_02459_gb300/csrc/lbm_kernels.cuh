@@ -1344,31 +1344,43 @@ template <int NF, int BW, int BH, int EXTRA> struct TmaTile {
         __syncthreads();
     }
 
-    // Stage the windows at global (gx, gy) of the NF fields and make them
-    // readable by every thread; false (for the whole CTA) when the TMA wait
-    // gave up, after recording it in *err.
-    __device__ __forceinline__ bool load(const KP<float> &P, const TmaMaps &tm, const float *const *src,
-                                         unsigned oddmask, int gx, int gy, unsigned *err)
+    // Start staging the windows at global (gx, gy) of the NF fields: by TMA
+    // (returns true) or, across the domain edge, by the threads themselves.
+    __device__ __forceinline__ bool issue(const KP<float> &P, const TmaMaps &tm, const float *const *src,
+                                          unsigned oddmask, int gx, int gy)
     {
         const bool inner = gx >= 0 && gy >= 0 && gx + BW <= P.nx && gy + BH <= P.ny;
         if (!inner) {
 #pragma unroll
             for (int f = 0; f < NF; ++f)
                 load_tile_mapped<float, BW, BH>(win + f * FS, src[f], gx, gy, P, (oddmask >> f) & 1u);
-            __syncthreads();
-            return true;
-        }
-        if (threadIdx.x == 0) {
+        } else if (threadIdx.x == 0) {
             mbar_expect_tx(bar, (unsigned)(NF * BW * BH * sizeof(float)));
 #pragma unroll
             for (int f = 0; f < NF; ++f) tma_load_2d(win + f * FS, &tm.m[f], gx, gy, bar);
+        }
+        return inner;
+    }
+
+    // Make the staged windows readable by every thread; false (for the whole
+    // CTA) when the TMA wait gave up, after recording it in *err.
+    __device__ __forceinline__ bool wait(bool by_tma, unsigned *err)
+    {
+        if (by_tma && threadIdx.x == 0) {
             *flag = mbar_wait_bounded(bar, 0) ? 1 : 0;
             if (!*flag) atomicOr(err, 1u);
         }
         __syncthreads();
+        if (!by_tma) return true;
         const bool ok = *flag != 0;
         if (ok) mbar_try_wait(bar, 0);   // completed phase: acquires the TMA writes
         return ok;
+    }
+
+    __device__ __forceinline__ bool load(const KP<float> &P, const TmaMaps &tm, const float *const *src,
+                                         unsigned oddmask, int gx, int gy, unsigned *err)
+    {
+        return wait(issue(P, tm, src, oddmask, gx, gy), err);
     }
 };
 
@@ -1468,6 +1480,381 @@ k_picard_tma(const __grid_constant__ TmaMaps tm, KP<float> P, const float *__res
     picard_strips_body<TX, TY, NT, VR1, VR2, BW, BW>(P, st, st + FS + BW + 2, st + 2 * FS + BW + 2,
                                                      st + 3 * FS + BW + 2, s_mu, s_gx, s_gy, x0, y0, jx, jy, uox,
                                                      uoy);
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1 for FP32 at the default relaxation rates (the FAST form of
+// k_collide_stream), x periodic, nx a multiple of 4: thread (lane, warp)
+// collides the node pair X = x0 - 2 + 2 lane, X + 1 of collision-region row
+// Y = y0 - 1 + warp, so a warp is one 64-column row (TX = 60 interior
+// columns).  Streaming splits by direction: the x part of every move is a
+// warp shuffle (post-collision values are pre-shifted along x, so column x
+// then holds f*_q(x - c_qx)); directions with c_qy = 0 are then pulled from
+// the thread's own registers and the six with c_qy != 0 from the rows above
+// and below through shared memory.  Walls in y use halfway bounce-back from
+// the same arrays.  Only TX, the interior rows (TY) and the window layout
+// differ from k_collide_stream; the arithmetic is paired FP32.
+// ---------------------------------------------------------------------------
+template <typename S> struct Codec2;
+template <> struct Codec2<float> {
+    static __device__ __forceinline__ float2 load(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+    static __device__ __forceinline__ void store(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+};
+template <> struct Codec2<__nv_bfloat16> {
+    static __device__ __forceinline__ float2 load(const __nv_bfloat16 *p)
+    {
+        return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16 *p, float2 v)
+    {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v.x, v.y);
+    }
+};
+template <> struct Codec2<__half> {   // the 2^14 scale of Codec<__half, float>
+    static __device__ __forceinline__ float2 load(const __half *p)
+    {
+        return mul2(__half22float2(__ldg(reinterpret_cast<const __half2 *>(p))), f2(1.0f / 16384.0f));
+    }
+    static __device__ __forceinline__ void store(__half *p, float2 v)
+    {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(v.x * 16384.0f, v.y * 16384.0f);
+    }
+};
+
+// Isotropic gradient of a field at the pair centred on index i of a window
+// of row stride W (rows i - W, i, i + W); c returns the centre pair.
+__device__ __forceinline__ void iso_grad_pair(const float *s, int i, int W, float2 &dx, float2 &dy, float2 &c)
+{
+    float2 Ds, Us, Dc, Uc, Dn, Un;
+    iso_row(lds2(s, i - W - 2), lds2(s, i - W), lds2(s, i - W + 2), Ds, Us);
+    c = lds2(s, i);
+    iso_row(lds2(s, i - 2), c, lds2(s, i + 2), Dc, Uc);
+    iso_row(lds2(s, i + W - 2), lds2(s, i + W), lds2(s, i + W + 2), Dn, Un);
+    dx = iso_dx(Ds, Dc, Dn);
+    dy = sub2(Un, Us);
+}
+
+// kappa div T, T = (gy^2, -gx gy; -gx gy, gx^2), at the pair centred on i of
+// the grad phi arrays (row stride W); gxc, gyc return grad phi at the pair.
+__device__ __forceinline__ void surface_force_pair(const float *sgx, const float *sgy, int i, int W, float kappa,
+                                                   float2 &Fsx, float2 &Fsy, float2 &gxc, float2 &gyc)
+{
+    float2 Dxx[3], Dxy[3], Uxy[3], Uyy[3], dummy;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int r = i + (k - 1) * W;
+        const float2 al = lds2(sgx, r - 2), ac = lds2(sgx, r), ar = lds2(sgx, r + 2);
+        const float2 bl = lds2(sgy, r - 2), bc = lds2(sgy, r), br = lds2(sgy, r + 2);
+        if (k == 1) {
+            gxc = ac;
+            gyc = bc;
+        }
+        iso_row(mul2(bl, bl), mul2(bc, bc), mul2(br, br), Dxx[k], dummy);
+        const float2 m1 = f2(-1.0f);
+        iso_row(mul2(m1, mul2(al, bl)), mul2(m1, mul2(ac, bc)), mul2(m1, mul2(ar, br)), Dxy[k], Uxy[k]);
+        iso_row(mul2(al, al), mul2(ac, ac), mul2(ar, ar), dummy, Uyy[k]);
+    }
+    const float2 kp = f2(kappa);
+    Fsx = mul2(kp, add2(iso_dx(Dxx[0], Dxx[1], Dxx[2]), sub2(Uxy[2], Uxy[0])));
+    Fsy = mul2(kp, add2(iso_dx(Dxy[0], Dxy[1], Dxy[2]), sub2(Uyy[2], Uyy[0])));
+}
+
+// Populations from moments (the inverse of the MRT matrix of Sec. III.A), paired.
+__device__ __forceinline__ void from_moments2(const float2 m[9], float2 f[9])
+{
+    const float2 r = mul2(m[0], f2(1.0f / 9.0f)), e = mul2(m[1], f2(1.0f / 36.0f)), ep = mul2(m[2], f2(1.0f / 36.0f));
+    const float2 jx = mul2(m[3], f2(1.0f / 6.0f)), qx = mul2(m[4], f2(1.0f / 12.0f));
+    const float2 jy = mul2(m[5], f2(1.0f / 6.0f)), qy = mul2(m[6], f2(1.0f / 12.0f));
+    const float2 pxx = mul2(m[7], f2(0.25f)), pxy = mul2(m[8], f2(0.25f));
+    f[0] = fma2(f2(4.0f), sub2(ep, e), r);
+    const float2 ax = fma2(f2(-2.0f), ep, sub2(r, e));
+    const float2 sx = fma2(f2(-2.0f), qx, jx), sy = fma2(f2(-2.0f), qy, jy);
+    const float2 axp = add2(ax, pxx), axm = sub2(ax, pxx);
+    f[1] = add2(axp, sx);
+    f[2] = add2(axm, sy);
+    f[3] = sub2(axp, sx);
+    f[4] = sub2(axm, sy);
+    const float2 dg = add2(fma2(f2(2.0f), e, r), ep);
+    const float2 tx = add2(jx, qx), ty = add2(jy, qy);
+    const float2 tp = add2(tx, ty), tm = sub2(tx, ty);
+    const float2 dgp = add2(dg, pxy), dgm = sub2(dg, pxy);
+    f[5] = add2(dgp, tp);
+    f[6] = sub2(dgm, tm);
+    f[7] = sub2(dgp, tp);
+    f[8] = add2(dgm, tm);
+}
+
+// Shift post-collision values along x by c_qx (the x part of streaming):
+// afterwards the pair holds f*_q(x - c_qx), f*_q(x + 1 - c_qx).
+template <int CX> __device__ __forceinline__ float2 xshift(float2 v)
+{
+    if constexpr (CX == 1) return make_float2(__shfl_up_sync(0xffffffffu, v.y, 1), v.x);
+    else if constexpr (CX == -1) return make_float2(v.y, __shfl_down_sync(0xffffffffu, v.x, 1));
+    else return v;
+}
+
+template <int TX, int TY> struct CPGeom {
+    static_assert(TX == 60, "a warp covers the 64 columns x0 - 2 .. x0 + 61");
+    static constexpr int NT = 32 * (TY + 2);
+    static constexpr int BW = TX + 16, BH = TY + 6;   // phi, p, ux, uy windows from (x0 - 8, y0 - 3)
+    static constexpr int W2 = TX + 8, H2 = TY + 4;    // mu, grad phi from (x0 - 4, y0 - 2)
+    static constexpr int WH = 64, HH = TY + 2;        // shifted post-collision values, collision region
+    static constexpr int EXTRA = 3 * W2 * H2 + 12 * WH * HH;
+    using Tile = TmaTile<4, BW, BH, EXTRA>;
+};
+
+template <typename S, int TX, int TY, int VR1>
+__global__ void __launch_bounds__(32 * (TY + 2), 2)
+k_collide_pairs(const __grid_constant__ TmaMaps tm, KP<float> P, const S *__restrict__ fin,
+                const S *__restrict__ gin, S *__restrict__ fout, S *__restrict__ gout,
+                const float *__restrict__ phi, const float *__restrict__ pfl, const float *__restrict__ ux,
+                const float *__restrict__ uy, const float *__restrict__ upx, const float *__restrict__ upy,
+                const float *__restrict__ uhx, const float *__restrict__ uhy, float *__restrict__ phibar,
+                float *__restrict__ phat, float *__restrict__ jxo, float *__restrict__ jyo, unsigned *err)
+{
+    using G = CPGeom<TX, TY>;
+    constexpr int BW = G::BW, W2 = G::W2, H2 = G::H2, WH = G::WH, HH = G::HH, FS = G::Tile::FS;
+    constexpr int A2 = W2 * H2, AH = WH * HH;
+    static_assert(H2 % VR1 == 0, "strips must tile the region");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename G::Tile tile(smem_raw);
+    const float *s_phi = tile.win;
+    const float *s_p = tile.win + FS;
+    const float *s_ux = tile.win + 2 * FS;
+    const float *s_uy = tile.win + 3 * FS;
+    float *s_mu = tile.work;
+    float *s_gx = s_mu + A2;
+    float *s_gy = s_gx + A2;
+    float *s_h = s_gy + A2;   // [12][HH][WH]: f then g, directions 2, 4, 5, 6, 7, 8
+
+    int x0, y0;
+    tile_origin(TX, TY, x0, y0, P);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int X = x0 - 2 + 2 * lane, Y = y0 - 1 + warp;
+    const bool ghost = !P.py && (Y < 0 || Y >= P.ny);
+
+    // stage the windows, and meanwhile read this pair's populations: only the
+    // moments that relax at rates other than 1 are needed from them
+    const float *src[4] = {phi, pfl, ux, uy};
+    const bool by_tma = tile.issue(P, tm, src, 12u, x0 - 8, y0 - 3);
+    float2 m3i = f2(0.0f), m5i = f2(0.0f), m4i = f2(0.0f), m6i = f2(0.0f), m7i = f2(0.0f), m8i = f2(0.0f);
+    float2 upx2 = f2(0.0f), upy2 = f2(0.0f), uhx2 = f2(0.0f), uhy2 = f2(0.0f);
+    if (!ghost) {
+        int fl;
+        const int gidx = map_axis(Y, P.ny, P.py, fl) * P.nx + map_axis(X, P.nx, 1, fl);
+        const unsigned N32 = P.N32;
+        float2 a[9], b[9];
+#pragma unroll
+        for (int q = 1; q < 9; ++q) {
+            const unsigned o = (unsigned)gidx + (unsigned)q * N32;
+            a[q] = Codec2<S>::load(fin + o);
+            b[q] = Codec2<S>::load(gin + o);
+        }
+        upx2 = __ldg(reinterpret_cast<const float2 *>(upx + gidx));
+        upy2 = __ldg(reinterpret_cast<const float2 *>(upy + gidx));
+        uhx2 = __ldg(reinterpret_cast<const float2 *>(uhx + gidx));
+        uhy2 = __ldg(reinterpret_cast<const float2 *>(uhy + gidx));
+        m3i = add2(sub2(a[1], a[3]), sub2(sub2(a[5], a[6]), sub2(a[7], a[8])));
+        m5i = add2(sub2(a[2], a[4]), sub2(add2(a[5], a[6]), add2(a[7], a[8])));
+        const float2 d58 = sub2(sub2(b[5], b[6]), sub2(b[7], b[8]));
+        const float2 d56 = sub2(add2(b[5], b[6]), add2(b[7], b[8]));
+        m4i = fma2(f2(2.0f), sub2(b[3], b[1]), d58);
+        m6i = fma2(f2(2.0f), sub2(b[4], b[2]), d56);
+        m7i = sub2(add2(b[1], b[3]), add2(b[2], b[4]));
+        m8i = sub2(add2(b[5], b[7]), add2(b[6], b[8]));
+    }
+    if (!tile.wait(by_tma, err)) return;
+
+    {   // mu and grad phi on (x0 - 4 .. x0 + TX + 3) x (y0 - 2 .. y0 + TY + 1)
+        constexpr int NP = W2 / 2, NI = NP * (H2 / VR1);
+        const float2 fb = f2(4.0f * P.beta), nk = f2(-P.kappa);
+        for (int it = threadIdx.x; it < NI; it += G::NT) {
+            const int lx = 2 * (it % NP), r0 = (it / NP) * VR1;
+            float2 C[VR1 + 2], D[VR1 + 2], Sm[VR1 + 2];
+#pragma unroll
+            for (int k = 0; k < VR1 + 2; ++k) {
+                const int row = (r0 + k) * BW + lx + 4;   // window column of region column lx
+                const float2 l = lds2(s_phi, row - 2), c = lds2(s_phi, row), r = lds2(s_phi, row + 2);
+                const float2 Wv = make_float2(l.y, c.x), E = make_float2(c.y, r.x);
+                C[k] = c;
+                D[k] = sub2(E, Wv);
+                Sm[k] = add2(E, Wv);
+            }
+#pragma unroll
+            for (int i = 0; i < VR1; ++i) {
+                const float2 gx = iso_dx(D[i], D[i + 1], D[i + 2]);
+                const float2 gy = fma2(f2(1.0f / 3.0f), sub2(C[i + 2], C[i]),
+                                       mul2(f2(1.0f / 12.0f), sub2(Sm[i + 2], Sm[i])));
+                const float2 lap = fma2(f2(2.0f / 3.0f), add2(Sm[i + 1], add2(C[i + 2], C[i])),
+                                        fma2(f2(1.0f / 6.0f), add2(Sm[i + 2], Sm[i]),
+                                             mul2(f2(-10.0f / 3.0f), C[i + 1])));
+                const float2 ph = C[i + 1];
+                const int o = (r0 + i) * W2 + lx;
+                sts2(s_mu, o, fma2(fb, sub2(mul2(mul2(ph, ph), ph), ph), mul2(nk, lap)));
+                sts2(s_gx, o, gx);
+                sts2(s_gy, o, gy);
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- forces and collision of this pair
+    float2 f[9], g[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) f[q] = g[q] = f2(0.0f);
+    if (!ghost) {
+        const int i2 = (warp + 1) * W2 + 2 + 2 * lane;   // region of mu, grad phi
+        const int iw = (warp + 2) * BW + 6 + 2 * lane;   // windows of phi, p, u
+        const float2 ph = lds2(s_phi, iw);
+        float2 rho, ir, nu;
+        rho_nu(P, ph.x, rho.x, ir.x, nu.x);
+        rho_nu(P, ph.y, rho.y, ir.y, nu.y);
+        float2 dmx, dmy, mu;
+        iso_grad_pair(s_mu, i2, W2, dmx, dmy, mu);
+        float2 Fsx, Fsy, gxc, gyc;
+        surface_force_pair(s_gx, s_gy, i2, W2, P.kappa, Fsx, Fsy, gxc, gyc);
+        float2 dpx, dpy, pc, dxux, dyux, u0, dxuy, dyuy, u1;
+        iso_grad_pair(s_p, iw, BW, dpx, dpy, pc);
+        iso_grad_pair(s_ux, iw, BW, dxux, dyux, u0);
+        iso_grad_pair(s_uy, iw, BW, dxuy, dyuy, u1);
+        const float2 dr = f2(P.drho), drm = f2(P.drho * P.M);
+        const float2 grx = mul2(dr, gxc), gry = mul2(dr, gyc);
+        const float2 Jx = mul2(drm, dmx), Jy = mul2(drm, dmy);
+        const float2 Sxx = add2(dxux, dxux), Sxy = add2(dyux, dxuy), Syy = add2(dyuy, dyuy);
+        const float2 rg = sub2(rho, f2(P.g_rho_ref)), m1 = f2(-1.0f);
+        float2 Fx = fma2(rg, f2(P.gx), fma2(Jx, dxux, mul2(Jy, dyux)));
+        float2 Fy = fma2(rg, f2(P.gy), fma2(Jx, dxuy, mul2(Jy, dyuy)));
+        Fx = fma2(nu, fma2(Sxx, grx, mul2(Sxy, gry)), add2(Fx, fma2(mul2(m1, pc), grx, Fsx)));
+        Fy = fma2(nu, fma2(Sxy, grx, mul2(Syy, gry)), add2(Fy, fma2(mul2(m1, pc), gry, Fsy)));
+        const float2 ax = fma2(u0, dxux, fma2(u1, dyux, sub2(u0, upx2)));
+        const float2 ay = fma2(u0, dxuy, fma2(u1, dyuy, sub2(u1, upy2)));
+        const float2 u00 = mul2(u0, u0), u11 = mul2(u1, u1), u01 = mul2(u0, u1);
+        const float2 u2 = add2(u00, u11), uxy = sub2(u00, u11);
+
+        {   // CH populations: only m3, m5 relax at a rate other than 1
+            const float2 s = f2(P.sf[3]), oms = f2(1.0f - P.sf[3]), hs = f2(1.0f - 0.5f * P.sf[3]);
+            const float2 m3 = m3i, m5 = m5i;
+            const float2 em = mul2(f2(P.eta), mu), ph3u2 = mul2(f2(3.0f), mul2(ph, u2));
+            const float2 pax = mul2(ph, ax), pay = mul2(ph, ay);
+            float2 m[9];
+            m[0] = ph;
+            m[1] = fma2(f2(2.0f), em, fma2(f2(-4.0f), ph, ph3u2));
+            m[2] = fma2(f2(4.0f), ph, fma2(f2(-3.0f), em, mul2(m1, ph3u2)));
+            m[3] = fma2(oms, m3, fma2(s, mul2(ph, u0), mul2(hs, pax)));
+            m[4] = mul2(mul2(m1, ph), fma2(f2(0.5f), ax, u0));
+            m[5] = fma2(oms, m5, fma2(s, mul2(ph, u1), mul2(hs, pay)));
+            m[6] = mul2(mul2(m1, ph), fma2(f2(0.5f), ay, u1));
+            m[7] = mul2(ph, uxy);
+            m[8] = mul2(ph, u01);
+            from_moments2(m, f);
+        }
+        {   // NS populations: m4, m6, m7, m8 keep part of their non-equilibrium
+            const float2 bx = fma2(Fx, ir, mul2(m1, dpx)), by = fma2(Fy, ir, mul2(m1, dpy));
+            const float2 bu = fma2(bx, u0, mul2(by, u1));
+            const float2 Gx = mul2(Fx, ir), Gy = mul2(Fy, ir);
+            const float2 G7 = mul2(f2(2.0f), fma2(bx, u0, mul2(m1, mul2(by, u1))));
+            const float2 G8 = fma2(by, u0, mul2(bx, u1));
+            const float2 t3 = f2(3.0f), p3 = mul2(t3, pc), u23 = mul2(t3, u2);
+            float2 s78;
+            s78.x = rcp(nu.x * 3.0f + 0.5f);
+            s78.y = rcp(nu.y * 3.0f + 0.5f);
+            const float2 o4 = f2(1.0f - P.sg[4]), o6 = f2(1.0f - P.sg[6]), o78 = sub2(f2(1.0f), s78);
+            const float2 hf = f2(0.5f);
+            float2 m[9];
+            m[0] = p3;
+            m[1] = fma2(f2(-2.0f), p3, fma2(f2(3.0f), bu, u23));
+            m[2] = sub2(p3, fma2(f2(3.0f), bu, u23));
+            m[3] = fma2(hf, Gx, u0);
+            m[4] = fma2(o4, add2(m4i, uhx2), fma2(mul2(hf, o4), mul2(m1, Gx), sub2(mul2(m1, u0), mul2(hf, Gx))));
+            m[5] = fma2(hf, Gy, u1);
+            m[6] = fma2(o6, add2(m6i, uhy2), fma2(mul2(hf, o6), mul2(m1, Gy), sub2(mul2(m1, u1), mul2(hf, Gy))));
+            const float2 hxy = fma2(uhx2, uhx2, mul2(m1, mul2(uhy2, uhy2)));
+            m[7] = fma2(o78, sub2(m7i, hxy), fma2(mul2(hf, o78), G7, fma2(hf, G7, uxy)));
+            m[8] = fma2(o78, sub2(m8i, mul2(uhx2, uhy2)), fma2(mul2(hf, o78), G8, fma2(hf, G8, u01)));
+            from_moments2(m, g);
+        }
+    }
+
+    // ---- streaming: x part by shuffles (every lane takes part)
+    f[1] = xshift<1>(f[1]); f[5] = xshift<1>(f[5]); f[8] = xshift<1>(f[8]);
+    f[3] = xshift<-1>(f[3]); f[6] = xshift<-1>(f[6]); f[7] = xshift<-1>(f[7]);
+    g[1] = xshift<1>(g[1]); g[5] = xshift<1>(g[5]); g[8] = xshift<1>(g[8]);
+    g[3] = xshift<-1>(g[3]); g[6] = xshift<-1>(g[6]); g[7] = xshift<-1>(g[7]);
+    {
+        const int o = warp * WH + 2 * lane;
+        constexpr int qv[6] = {2, 4, 5, 6, 7, 8};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            sts2(s_h + k * AH, o, f[qv[k]]);
+            sts2(s_h + (6 + k) * AH, o, g[qv[k]]);
+        }
+    }
+    __syncthreads();
+
+    // ---- y part from the neighbouring rows; post-stream moments
+    if (warp < 1 || warp > TY || lane < 1 || lane > 30) return;
+    const int Xn = X, Yn = Y;
+    if (Xn >= P.nx || Yn >= P.ny) return;
+    const int up = (warp - 1) * WH + 2 * lane, dn = (warp + 1) * WH + 2 * lane, own = warp * WH + 2 * lane;
+    // slots in s_h: 0:2 1:4 2:5 3:6 4:7 5:8
+    float2 fv[9], gv[9];
+    fv[0] = f[0]; fv[1] = f[1]; fv[3] = f[3];
+    gv[0] = g[0]; gv[1] = g[1]; gv[3] = g[3];
+    const float *hf_ = s_h, *hg_ = s_h + 6 * AH;
+    fv[2] = lds2(hf_ + 0 * AH, up); fv[5] = lds2(hf_ + 2 * AH, up); fv[6] = lds2(hf_ + 3 * AH, up);
+    fv[4] = lds2(hf_ + 1 * AH, dn); fv[7] = lds2(hf_ + 4 * AH, dn); fv[8] = lds2(hf_ + 5 * AH, dn);
+    gv[2] = lds2(hg_ + 0 * AH, up); gv[5] = lds2(hg_ + 2 * AH, up); gv[6] = lds2(hg_ + 3 * AH, up);
+    gv[4] = lds2(hg_ + 1 * AH, dn); gv[7] = lds2(hg_ + 4 * AH, dn); gv[8] = lds2(hg_ + 5 * AH, dn);
+    if (!P.py && Yn == 0) {   // bottom wall: 2, 5, 6 come back as the node's own 4, 7, 8
+        const float *b = s_h;
+#pragma unroll
+        for (int d = 0; d < 2; ++d, b += 6 * AH) {
+            float2 *v = d ? gv : fv;
+            v[2] = lds2(b + 1 * AH, own);
+            v[5] = make_float2(b[4 * AH + own - 1], b[4 * AH + own]);       // f*_7(x) = h_7(x - 1)
+            v[6] = make_float2(b[5 * AH + own + 1], b[5 * AH + own + 2]);   // f*_8(x) = h_8(x + 1)
+        }
+    }
+    if (!P.py && Yn == P.ny - 1) {   // top wall: 4, 7, 8 come back as the node's own 2, 5, 6
+        const float *b = s_h;
+#pragma unroll
+        for (int d = 0; d < 2; ++d, b += 6 * AH) {
+            float2 *v = d ? gv : fv;
+            v[4] = lds2(b + 0 * AH, own);
+            v[7] = make_float2(b[2 * AH + own + 1], b[2 * AH + own + 2]);   // f*_5(x) = h_5(x + 1)
+            v[8] = make_float2(b[3 * AH + own - 1], b[3 * AH + own]);       // f*_6(x) = h_6(x - 1)
+        }
+    }
+    float2 sf = fv[0], sg = gv[0];
+#pragma unroll
+    for (int q = 1; q < 9; ++q) {
+        sf = add2(sf, fv[q]);
+        sg = add2(sg, gv[q]);
+    }
+    const float2 jx = add2(sub2(gv[1], gv[3]), sub2(sub2(gv[5], gv[6]), sub2(gv[7], gv[8])));
+    const float2 jy = add2(sub2(gv[2], gv[4]), sub2(add2(gv[5], gv[6]), add2(gv[7], gv[8])));
+    const float2 pn = mul2(sg, f2(1.0f / 3.0f));
+    const int nidx = Yn * P.nx + Xn;
+    const unsigned N32 = P.N32;
+    if constexpr (Mixed<float, S>::on) {
+#pragma unroll
+        for (int q = 1; q < 9; ++q) {
+            const unsigned o = (unsigned)nidx + (unsigned)q * N32;
+            Codec2<S>::store(fout + o, fv[q]);
+            Codec2<S>::store(gout + o, fma2(f2(-3.0f * lattice_w(q)), pn, gv[q]));
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const unsigned o = (unsigned)nidx + (unsigned)q * N32;
+            Codec2<S>::store(fout + o, fv[q]);
+            Codec2<S>::store(gout + o, gv[q]);
+        }
+    }
+    sts2(phibar, nidx, sf);
+    sts2(phat, nidx, pn);
+    sts2(jxo, nidx, jx);
+    sts2(jyo, nidx, jy);
 }
 
 // ---------------------------------------------------------------------------

@@ -2,11 +2,12 @@
 
 Only the deviations from the rest equilibria are stored in 16 bits; the
 post-stream moments phi_bar = sum f and p_hat = cs^2 sum g stay in FP32, so
-the volume is conserved exactly as in the FP32 path.  The benchmark spec reports
-these errors against the FP64 oracle rather than gating them, except the
-bubble centroid, which must stay within 0.5 % (of the bubble diameter) of the
-FP32 run.  The bounds below are set from the measured errors with margin:
-phi as FP32 (1e-5 after 200 steps), p and u 2e-3 of their maxima.
+the volume is conserved exactly as in the FP32 path.  The errors against the
+FP64 oracle are reported, and bounded with margin above their measured
+values: phi as FP32 (1e-5 after 200 steps at density ratio 10, 5e-5 at
+ratio 1000), p and u 2e-3 of their maxima at ratio 10 (at ratio 1000 see
+the capillary-wave test).  The rising-bubble centroid must
+stay within 0.5 % of the bubble diameter of the FP32 run.
 """
 import numpy as np
 import pytest
@@ -37,6 +38,26 @@ def test_static_drop_against_oracle(precision):
     assert max(errs["p"], errs["ux"], errs["uy"]) <= 2e-3
     # the FP32 moments carry the volume: drift as in FP32 storage of phi
     assert abs(g.diagnostics()[0] - d0) <= 200 * fields[0].size * 2.0 ** -24
+
+
+@pytest.mark.parametrize("precision", MIXED)
+@pytest.mark.parametrize("n", [64, 66])
+def test_capillary_wave_walls_against_oracle(precision, n):
+    """Walls in y and density ratio 1000 (the benchmark workload, small).
+    Here p is a residual of the large density contrast: after 100 steps its
+    error is 7.4e-3 of max|p| with bf16 storage (8-bit significand), 1.2e-3
+    with fp16 and 0.6e-3 .. 0.9e-3 in FP32, the same whether the grid width
+    takes the node-pair kernels (64) or not (66); u stays within 1.4e-3."""
+    prm, fields = inputs.capillary_wave(n=n)
+    o = oracle.Sim(prm, *fields)
+    g = lbm.Sim(prm, *fields, precision=precision)
+    o.step(100)
+    g.step(100)
+    errs = {k: rel_err(a, b) for k, a, b in zip(("phi", "p", "ux", "uy"), g.fields(), o.fields())}
+    print(precision, n, errs)
+    assert errs["phi"] <= 5e-5
+    assert errs["p"] <= (1.5e-2 if precision == "mix_bf16" else 3e-3)
+    assert max(errs["ux"], errs["uy"]) <= 3e-3
 
 
 @pytest.mark.parametrize("precision", MIXED)
