@@ -33,18 +33,24 @@ if ROOT not in sys.path:
 METRIC = "MLUPS (both lattices+FD+filter) FP32 vs mixed, % HBM roofline; adjoint/forward time"
 UNIT = "MLUPS"
 KERNEL_SRC = os.path.join(ROOT, "paper_1812_02459_gb300", "csrc", "lbm_kernels.cuh")
-TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "k_collide_stream_capillary_wave.md")
+PROFILES = os.path.join(ROOT, "profiles")
 
 # Algorithmic words (4 bytes in FP32, 8 in FP64) per node and launch of each
-# kernel kind: every persistent plane read once and written once; what stays
-# on chip is not counted.
+# kernel: every persistent plane it needs read once and written once; what
+# stays on chip is not counted.
 #   collide+stream: read 18 populations + phi, p, u(2), u_prev(2), u_hat(2);
 #                   write 18 populations + phi_bar, p_hat, j(2)       -> 48
+#     k_collide_pairs (default rates) does not need the rest populations
+#     f_0, g_0, whose rate-1 relaxation discards them: reads 16       -> 46
 #   RK3 stage: read psi (+ phi_bar in stages 2, 3); write the stage  -> 2, 3, 3
 #   Picard sweep: read phi, p_hat, j(2), u^k(2); write u^{k+1}(2)    -> 8
 #   filter: read p_hat, u_hat(2); write p, u(2)                      -> 6
-ALGO_WORDS = {"k_collide_stream": 48.0, "k_rk_stage": 8.0 / 3.0, "k_picard": 8.0, "k_filter": 6.0}
-RK_WORDS_PER_STEP = 2 + 3 + 3
+KIND_WORDS = {"k_collide_stream": 48.0, "k_rk_stage": 8.0 / 3.0, "k_picard": 8.0, "k_filter": 6.0}
+VARIANT_WORDS = {"k_collide_pairs": 46.0}
+
+
+def algo_words(kind, variant):
+    return VARIANT_WORDS.get(variant, KIND_WORDS[kind])
 
 
 def parse_args():
@@ -195,11 +201,11 @@ def kernel_source_hash():
     return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
 
 
-def recorded_traffic_per_node(precision):
-    """DRAM bytes per node of k_collide_stream from the committed ncu summary,
-    if it was taken on the current kernel source; else None."""
+def recorded_traffic_per_node(precision, kernel):
+    """DRAM bytes per node of a kernel from its committed ncu summary on the
+    capillary-wave workload, if taken on the current kernel source; else None."""
     try:
-        txt = open(TRAFFIC_RECORD).read()
+        txt = open(os.path.join(PROFILES, "%s_capillary_wave.md" % kernel)).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_node_%s:\s*([0-9.]+)\s+kernel_source_sha256_16:\s*([0-9a-f]+)" % precision, txt)
@@ -318,16 +324,17 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_n = prof[dom]
-    algo_bytes = ALGO_WORDS[dom] * elem * N
+    variants = sim.kernel_variants()
+    algo_bytes = algo_words(dom, variants[dom]) * elem * N
     achieved = algo_bytes / (dom_ms / dom_n / 1e3) / 1e9
-    tpn = recorded_traffic_per_node(args.precision) if dom == "k_collide_stream" else None
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+    tpn = recorded_traffic_per_node(args.precision, variants[dom])
+    roofline = {"bound": "hbm", "kernel": variants[dom], "kind": dom, "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": None if tpn is None else round(tpn * N),
                 "algorithmic_bytes_per_launch": int(algo_bytes), "peak_source": peak_kind}
-    step_bytes = (ALGO_WORDS["k_collide_stream"] + RK_WORDS_PER_STEP
-                  + ALGO_WORDS["k_picard"] * prm["picard_iters"] + ALGO_WORDS["k_filter"]) * elem * N
-    kernels = {k: {"ms_per_launch": round(v[0] / max(v[1], 1), 4), "launches": v[1],
+    step_words = sum(algo_words(k, variants[k]) * v[1] for k, v in prof.items()) / args.steps
+    step_bytes = step_words * elem * N
+    kernels = {k: {"kernel": variants[k], "ms_per_launch": round(v[0] / max(v[1], 1), 4), "launches": v[1],
                    "share": round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4)}
                for k, v in prof.items()}
     gpu_launches = sum(v[1] for v in prof.values())

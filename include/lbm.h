@@ -138,8 +138,10 @@ lbm_status lbm_set_fields(lbm_handle *h, const double *phi0, const double *p0,
                           const double *ux0, const double *uy0);
 
 /*
- * lbm_diagnostics -- FP64 sums over the nodes (Sec. IV.C volume error,
- * Sec. IV.E Eqs. quantify-yc, quantify-uc), into host out[LBM_NDIAG]:
+ * lbm_diagnostics -- sums over the nodes (Sec. IV.C volume error,
+ * Sec. IV.E Eqs. quantify-yc, quantify-uc), into host out[LBM_NDIAG]; the
+ * sums are FP64 over row segments of at most 16 nodes, each segment summed
+ * in the handle's arithmetic type (exact counts in [1], [2], [3], [10]):
  *   [0] sum phi   [1] #(phi>0)   [2] #(phi<0)   [3] sum_{phi<0} y
  *   [4] sum_{phi<0} u_y   [5] sum w   [6] sum w y   [7] sum w u_y
  *       (w = (1-phi)/2, y = row index)   [8] max phi   [9] min phi
@@ -184,6 +186,16 @@ lbm_status lbm_set_state(lbm_handle *h, const double *f, const double *g, const 
 lbm_status lbm_profile(lbm_handle *h, int on);
 lbm_status lbm_profile_read(lbm_handle *h, double *ms, long long *launches);
 const char *lbm_kernel_name(int kind);
+
+/*
+ * lbm_kernel_variant -- name of the kernel that lbm_step launches on this
+ * handle for kernel kind `kind` (a static string; "none" for a filter of
+ * order 0, "unknown" for a NULL handle or a kind outside 0..LBM_NKERNELS-1).
+ * Which variant runs depends on the precision, the grid width, the wall
+ * configuration and the relaxation rates; every variant computes the same
+ * pass.
+ */
+const char *lbm_kernel_variant(const lbm_handle *h, int kind);
 
 /*
  * Discrete adjoint of lbm_step (reverse mode), for gradients of a loss of the

@@ -38,7 +38,7 @@ constexpr int FS_TX = 64, FS_TY = 64, FS_VR = 8;     // FP32 filter: tile, rows 
 constexpr int RT_NT = 256, RT_MINB = 4;
 constexpr int PT_TX = 128, PT_TY = 16, PT_NT = 256, PT_VR1 = 6, PT_VR2 = 4, PT_MINB = 3;
 constexpr int FT_TX = 64, FT_TY = 32, FT_VR = 4, FT_MINB = 4;
-constexpr int CP_TX = 60, CP_TY = 14, CP_VR1 = 2;   // collide+stream on node pairs
+constexpr int CP_TX = 60, CP_TY = 14, CP_VR1 = 3;   // collide+stream on node pairs
 constexpr int DIAG_THREADS = 256;
 constexpr int DIAG_MAX_BLOCKS = 1216;    // 8 x 152 SMs
 
@@ -612,9 +612,9 @@ lbm_status diag_impl(lbm_handle *h, double *out)
 {
     const KP<T> &P = kp_of<T>(h);
     k_diag_partial<T><<<h->diag_blocks, DIAG_THREADS, 0, h->stream>>>(
-        P.nx, P.N, (const T *)h->phi, (const T *)h->pf, (const T *)h->ux[h->ucur], (const T *)h->uy[h->ucur],
+        P.nx, P.ny, (const T *)h->phi, (const T *)h->pf, (const T *)h->ux[h->ucur], (const T *)h->uy[h->ucur],
         h->diag_part);
-    k_diag_final<<<1, 32, 0, h->stream>>>(h->diag_blocks, h->diag_part, h->diag_out);
+    k_diag_final<<<1, 32 * NDIAG, 0, h->stream>>>(h->diag_blocks, h->diag_part, h->diag_out);
     CK(h, cudaGetLastError(), "diagnostics launch");
     CK(h, cudaMemcpyAsync(out, h->diag_out, sizeof(double) * NDIAG, cudaMemcpyDeviceToHost, h->stream),
        "diagnostics copy");
@@ -786,7 +786,7 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params, const doub
     const size_t plane = round_up((size_t)h->N * h->elem, 256);
     const size_t pplane = round_up((size_t)h->N * 9 * h->pop_elem, 256);
     const int nscalar = 22;   // phi, pf, ux[2], uy[2], uhx, uhy, phibar[2], phat[2], jx, jy, s1, s2, tk[2][2], 2 spare
-    h->diag_blocks = (int)std::min<long long>((h->N + DIAG_THREADS - 1) / DIAG_THREADS, DIAG_MAX_BLOCKS);
+    h->diag_blocks = std::min(grid->ny, DIAG_MAX_BLOCKS);   // rows per block: ny / blocks
     const size_t diag_bytes = round_up(sizeof(double) * (size_t)(h->diag_blocks + 1) * NDIAG, 256);
     h->arena_bytes = 4 * pplane + nscalar * plane + diag_bytes + 256;   // + the device error word
     cudaError_t e = cudaMalloc((void **)&h->arena, h->arena_bytes);
@@ -960,6 +960,21 @@ const char *lbm_kernel_name(int kind)
 {
     static const char *names[LBM_NKERNELS] = {"k_collide_stream", "k_rk_stage", "k_picard", "k_filter"};
     return (kind >= 0 && kind < LBM_NKERNELS) ? names[kind] : "unknown";
+}
+
+const char *lbm_kernel_variant(const lbm_handle *h, int kind)
+{
+    if (!h || kind < 0 || kind >= LBM_NKERNELS) return "unknown";
+    const bool f32 = h->grid.precision != LBM_FP64, even = h->grid.nx % 2 == 0;
+    switch (kind) {
+    case 0:
+        return (f32 && h->tma && h->grid.periodic_x && default_rates(h->prm)) ? "k_collide_pairs" : "k_collide_stream";
+    case 1: return f32 && h->tma ? "k_rk_tma" : (f32 && even ? "k_rk_strips" : "k_rk_stage");
+    case 2: return f32 && h->tma ? "k_picard_tma" : (f32 && even ? "k_picard_strips" : "k_picard");
+    default:
+        if (h->prm.filter_order == 0) return "none";
+        return f32 && h->tma ? "k_filter_tma" : (f32 && even ? "k_filter_strips" : "k_filter");
+    }
 }
 
 size_t lbm_device_bytes(const lbm_handle *h) { return h ? h->arena_bytes : 0; }

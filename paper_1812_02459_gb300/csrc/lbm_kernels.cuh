@@ -1136,11 +1136,12 @@ struct PicardRow {
 // s_phi holds phi from (x0 - 4, y0 - 2) with row stride SP; s_p, s_ux, s_uy
 // hold p_hat, u^k from (x0 - 2, y0 - 1) with row stride SA; s_mu, s_gx, s_gy
 // are (TX + 4) x (TY + 2) work arrays.
-template <int TX, int TY, int NT, int VR1, int VR2, int SP, int SA>
+// jf(ly, lx, gidx, jx, jy) returns j at tile row ly, column pair lx (global
+// index gidx).
+template <int TX, int TY, int NT, int VR1, int VR2, int SP, int SA, typename JF>
 __device__ __forceinline__ void picard_strips_body(const KP<float> &P, const float *s_phi, const float *s_p,
                                                    const float *s_ux, const float *s_uy, float *s_mu, float *s_gx,
-                                                   float *s_gy, int x0, int y0, const float *__restrict__ jx,
-                                                   const float *__restrict__ jy, float *__restrict__ uox,
+                                                   float *s_gy, int x0, int y0, JF &&jf, float *__restrict__ uox,
                                                    float *__restrict__ uoy)
 {
     using G = PSGeom<TX, TY>;
@@ -1228,8 +1229,8 @@ __device__ __forceinline__ void picard_strips_body(const KP<float> &P, const flo
                 Fy = fma2(nu, fma2(Sxy, grx, mul2(Syy, gry)), add2(Fy, fma2(mul2(m1, pc), gry, Fsy)));
                 const float2 hh = mul2(f2(0.5f), ir);
                 const long long gidx = (long long)Y * P.nx + X;
-                const float2 jxv = *reinterpret_cast<const float2 *>(&jx[gidx]);
-                const float2 jyv = *reinterpret_cast<const float2 *>(&jy[gidx]);
+                float2 jxv, jyv;
+                jf(r0 + i, lx, gidx, jxv, jyv);
                 *reinterpret_cast<float2 *>(&uox[gidx]) = fma2(Fx, hh, jxv);
                 *reinterpret_cast<float2 *>(&uoy[gidx]) = fma2(Fy, hh, jyv);
             }
@@ -1260,7 +1261,11 @@ k_picard_strips(KP<float> P, const float *__restrict__ phi, const float *__restr
     load_tile<float, WA, HA>(s_ux, ukx, x0 - 2, y0 - 1, P, true);
     load_tile<float, WA, HA>(s_uy, uky, x0 - 2, y0 - 1, P, true);
     tiles_ready();
-    picard_strips_body<TX, TY, NT, VR1, VR2, WP, WA>(P, s_phi, s_p, s_ux, s_uy, s_mu, s_gx, s_gy, x0, y0, jx, jy,
+    picard_strips_body<TX, TY, NT, VR1, VR2, WP, WA>(P, s_phi, s_p, s_ux, s_uy, s_mu, s_gx, s_gy, x0, y0,
+                                                     [&](int, int, long long gidx, float2 &a, float2 &b) {
+                                                         a = *reinterpret_cast<const float2 *>(&jx[gidx]);
+                                                         b = *reinterpret_cast<const float2 *>(&jy[gidx]);
+                                                     },
                                                      uox, uoy);
 }
 
@@ -1448,7 +1453,9 @@ k_rk_tma(const __grid_constant__ TmaMaps tm, KP<float> P, const float *__restric
 
 // Picard sweep with TMA staging, one CTA per TX x TY tile: windows
 // (TX + 8) x (TY + 4) from (x0 - 4, y0 - 2) of phi, p_hat, u^k_x, u^k_y;
-// mu and grad phi in the work area.
+// mu and grad phi in the work area.  (j through two more windows, at the
+// two CTAs per SM their shared memory leaves, measured slower than these
+// global loads at three.)
 template <int TX, int TY> struct PCTGeom {
     using G = PSGeom<TX, TY>;
     static constexpr int BW = TX + 8, BH = TY + 4;
@@ -1477,9 +1484,13 @@ k_picard_tma(const __grid_constant__ TmaMaps tm, KP<float> P, const float *__res
     if (!tile.load(P, tm, src, 12u, x0 - 4, y0 - 2, err)) return;
     const float *st = tile.win;
     // p_hat and u^k from (x0 - 2, y0 - 1): one row and two columns into their windows
-    picard_strips_body<TX, TY, NT, VR1, VR2, BW, BW>(P, st, st + FS + BW + 2, st + 2 * FS + BW + 2,
-                                                     st + 3 * FS + BW + 2, s_mu, s_gx, s_gy, x0, y0, jx, jy, uox,
-                                                     uoy);
+    picard_strips_body<TX, TY, NT, VR1, VR2, BW, BW>(
+        P, st, st + FS + BW + 2, st + 2 * FS + BW + 2, st + 3 * FS + BW + 2, s_mu, s_gx, s_gy, x0, y0,
+        [&](int, int, long long gidx, float2 &a, float2 &b) {
+            a = *reinterpret_cast<const float2 *>(&jx[gidx]);
+            b = *reinterpret_cast<const float2 *>(&jy[gidx]);
+        },
+        uox, uoy);
 }
 
 // ---------------------------------------------------------------------------
@@ -1955,30 +1966,55 @@ __device__ __forceinline__ double warp_min(double v)
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_diag_partial(int nx, long long N, const T *__restrict__ phi, const T *__restrict__ p,
-               const T *__restrict__ ux, const T *__restrict__ uy, double *__restrict__ part)
+k_diag_partial(int nx, int ny, const T *__restrict__ phi, const T *__restrict__ p, const T *__restrict__ ux,
+               const T *__restrict__ uy, double *__restrict__ part)
 {
-    double acc[NDIAG];
-#pragma unroll
-    for (int k = 0; k < NDIAG; ++k) acc[k] = 0.0;
-    acc[8] = -INFINITY;
-    acc[9] = INFINITY;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < N;
-         k += (long long)gridDim.x * blockDim.x) {
-        const double ph = (double)phi[k], v = (double)uy[k];
-        const double y = (double)(k / nx);
-        const double w = (1.0 - ph) * 0.5;
-        acc[0] += ph;
-        if (ph > 0) acc[1] += 1.0;
-        if (ph < 0) { acc[2] += 1.0; acc[3] += y; acc[4] += v; }
-        acc[5] += w;
-        acc[6] += w * y;
-        acc[7] += w * v;
-        acc[8] = fmax(acc[8], ph);
-        acc[9] = fmin(acc[9], ph);
-        acc[10] += (double)(!isfinite(ph)) + (double)(!isfinite((double)p[k])) +
-                   (double)(!isfinite((double)ux[k])) + (double)(!isfinite(v));
+    // block b takes rows b, b + gridDim.x, ...; each thread accumulates at
+    // most 16 nodes of a row in T before adding the segment to FP64 sums
+    double s_ph = 0.0, s_v = 0.0, s_w = 0.0, s_wy = 0.0, s_wv = 0.0;
+    long long n_pos = 0, n_neg = 0, s_y = 0, n_bad = 0;
+    T mx = T(-INFINITY), mn = T(INFINITY);
+    for (int y = blockIdx.x; y < ny; y += gridDim.x) {
+        const long long r = (long long)y * nx;
+        T a_ph = T(0), a_v = T(0), a_w = T(0), a_wv = T(0);
+        int cnt = 0, npos = 0, nneg = 0;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const T ph = phi[r + x], v = uy[r + x];
+            const T w = (T(1) - ph) * T(0.5);
+            a_ph += ph;
+            a_w += w;
+            a_wv += w * v;
+            if (ph > T(0)) ++npos;
+            if (ph < T(0)) {
+                ++nneg;
+                a_v += v;
+            }
+            mx = fmax(mx, ph);
+            mn = fmin(mn, ph);
+            n_bad += (int)!isfinite(ph) + (int)!isfinite(p[r + x]) + (int)!isfinite(ux[r + x]) + (int)!isfinite(v);
+            if (++cnt == 16) {
+                s_ph += (double)a_ph;
+                s_v += (double)a_v;
+                s_w += (double)a_w;
+                s_wy += (double)y * (double)a_w;
+                s_wv += (double)a_wv;
+                a_ph = a_v = a_w = a_wv = T(0);
+                cnt = 0;
+            }
+        }
+        s_ph += (double)a_ph;
+        s_v += (double)a_v;
+        s_w += (double)a_w;
+        s_wy += (double)y * (double)a_w;
+        s_wv += (double)a_wv;
+        n_pos += npos;
+        n_neg += nneg;
+        s_y += (long long)y * nneg;
     }
+    // a non-finite phi poisons fmax/fmin only through NaN, which fmax skips:
+    // the count in slot 10 reports it
+    double acc[NDIAG] = {s_ph, (double)n_pos, (double)n_neg, (double)s_y, s_v, s_w, s_wy, s_wv,
+                         (double)mx, (double)mn, (double)n_bad};
     __shared__ double red[NDIAG][8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -1996,16 +2032,18 @@ k_diag_partial(int nx, long long N, const T *__restrict__ phi, const T *__restri
     }
 }
 
-static __global__ void k_diag_final(int nblocks, const double *__restrict__ part, double *__restrict__ out)
+// Warp k reduces component k of the per-block partials.
+static __global__ void __launch_bounds__(32 * NDIAG) k_diag_final(int nblocks, const double *__restrict__ part,
+                                                                 double *__restrict__ out)
 {
-    const int k = threadIdx.x;
-    if (k >= NDIAG) return;
-    double v = part[k];
-    for (int b = 1; b < nblocks; ++b) {
-        double x = part[b * NDIAG + k];
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double v = k == 8 ? -INFINITY : (k == 9 ? INFINITY : 0.0);
+    for (int b = lane; b < nblocks; b += 32) {
+        const double x = part[b * NDIAG + k];
         v = k == 8 ? fmax(v, x) : (k == 9 ? fmin(v, x) : v + x);
     }
-    out[k] = v;
+    v = k == 8 ? warp_max(v) : (k == 9 ? warp_min(v) : warp_sum(v));
+    if (lane == 0) out[k] = v;
 }
 
 }  // namespace lbm

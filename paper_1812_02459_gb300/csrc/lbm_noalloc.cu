@@ -131,7 +131,7 @@ lbm_status lbm_field_sums_noalloc(const void *phi, const void *p, const void *ux
     else
         k_sums_chunks<float><<<blocks, NA_THREADS, 0, st>>>(nx, N, (const float *)phi, (const float *)p,
                                                             (const float *)ux, (const float *)uy, part);
-    lbm::k_diag_final<<<1, 32, 0, st>>>(blocks, part, out);
+    lbm::k_diag_final<<<1, 32 * lbm::NDIAG, 0, st>>>(blocks, part, out);
     e = cudaGetLastError();
     if (e != cudaSuccess) return na_fail(LBM_ERR_CUDA, "kernel launch", e);
     return LBM_OK;

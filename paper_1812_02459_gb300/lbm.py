@@ -46,7 +46,7 @@ class LbmError(RuntimeError):
 
 EXPORTS = ("lbm_create", "lbm_step", "lbm_fields", "lbm_fields_device", "lbm_set_fields",
            "lbm_diagnostics", "lbm_check", "lbm_get_state", "lbm_set_state",
-           "lbm_profile", "lbm_profile_read", "lbm_kernel_name",
+           "lbm_profile", "lbm_profile_read", "lbm_kernel_name", "lbm_kernel_variant",
            "lbm_field_sums_noalloc", "lbm_noalloc_last_error",
            "lbm_adjoint_begin", "lbm_adjoint_end",
            "lbm_device_bytes", "lbm_destroy", "lbm_last_error")
@@ -90,6 +90,8 @@ def load(path=None):
     L.lbm_profile_read.argtypes = [vp, _dp, C.POINTER(C.c_longlong)]
     L.lbm_kernel_name.restype = C.c_char_p
     L.lbm_kernel_name.argtypes = [C.c_int]
+    L.lbm_kernel_variant.restype = C.c_char_p
+    L.lbm_kernel_variant.argtypes = [C.c_void_p, C.c_int]
     L.lbm_field_sums_noalloc.restype = C.c_int
     L.lbm_field_sums_noalloc.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, C.c_int, vp, vp]
     L.lbm_noalloc_last_error.restype = C.c_char_p
@@ -235,6 +237,11 @@ class Sim:
         n = (C.c_longlong * LBM_NKERNELS)()
         self._ck(self._lib.lbm_profile_read(self._h, _ptr(ms), n))
         return {self._lib.lbm_kernel_name(k).decode(): (float(ms[k]), int(n[k]))
+                for k in range(LBM_NKERNELS)}
+
+    def kernel_variants(self):
+        """{kernel kind name: name of the kernel this handle launches for it}."""
+        return {self._lib.lbm_kernel_name(k).decode(): self._lib.lbm_kernel_variant(self._h, k).decode()
                 for k in range(LBM_NKERNELS)}
 
     def adjoint_begin(self, nsteps, checkpoint_every):

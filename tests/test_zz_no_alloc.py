@@ -16,10 +16,6 @@ from paper_1812_02459_gb300 import inputs, lbm
 pytestmark = pytest.mark.gpu
 
 
-def _close(a, b, scale):
-    return abs(a - b) <= 1e-12 * scale
-
-
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_noalloc_sums_match_diagnostics_twice(precision):
     import torch
@@ -37,8 +33,12 @@ def test_noalloc_sums_match_diagnostics_twice(precision):
         lbm.field_sums_noalloc(*bufs, out)
         got = out.cpu().numpy()
         n = shp[0] * shp[1]
-        for k in (0, 3, 4, 5, 6, 7):           # FP64 sums of n terms: 1e-12 of n + |sum|
-            assert _close(got[k], ref[k], n + abs(ref[k])), (k, got[k], ref[k])
+        # FP64 sums of n terms agree to 1e-12 of n + |sum|; an FP32 handle's
+        # diagnostics add row segments of at most 16 terms in FP32 first,
+        # which is off by at most 15 roundings (2^-24) of each |term| <= 1
+        rel = 1e-12 if precision == "fp64" else 15 * 2.0 ** -24
+        for k in (0, 3, 4, 5, 6, 7):
+            assert abs(got[k] - ref[k]) <= rel * (n + abs(ref[k])), (k, got[k], ref[k])
         for k in (1, 2, 8, 9, 10):             # counts and extrema are exact
             assert got[k] == ref[k], (k, got[k], ref[k])
     sim.close()
