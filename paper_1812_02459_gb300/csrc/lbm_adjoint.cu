@@ -8,7 +8,9 @@
 // shifts) and scalings by the differentiable parameters kappa, beta, M and
 // 1/tau_f -- each executed by a small kernel and recorded.  Each operation
 // has a hand-written vector-Jacobian product; the reverse sweep applies them
-// in reverse order.  Across steps, sqrt(N)-style checkpointing keeps every
+// in reverse order.  The operations are executed in groups: the pointwise
+// operations between two layers of stencils run as one kernel that applies
+// them node by node, so a step costs a few dozen launches in each direction.  Across steps, sqrt(N)-style checkpointing keeps every
 // k-th state, regenerates a segment with the fused forward kernels and
 // reverses it step by step.  Periodic axes, FP64 or FP32 populations; the
 // reverse sweep itself always runs in FP64.
@@ -16,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <initializer_list>
 #include <string>
@@ -51,170 +54,285 @@ struct Op {
     int st = -1;
 };
 
-template <typename T> struct PP { const T *p[MAXIN]; T c[MAXIN]; };
-template <typename T> struct AP { T *p[MAXIN]; T c[MAXIN]; };
-template <typename T> struct KSt { int n; int dx[MAXST], dy[MAXST]; T w[MAXST]; };
-
 int blocks_for(long long N) { return (int)std::min<long long>((N + NTH - 1) / NTH, 4096); }
 
 #define GRID_LOOP(k, N) for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < (N); \
                              k += (long long)gridDim.x * blockDim.x)
 
-template <typename T> __global__ void kk_lin(T *out, PP<T> in, int n, T c0, long long N)
+// ---------------------------------------------------------------------------
+// Execution of a recorded tape.  A plane's level counts the stencils on the
+// longest path from the leaves to it.  The forward pass runs the pointwise
+// operations of level 0, then for each level the stencils producing it and
+// the pointwise operations of that level; every group is one kernel, and a
+// pointwise group applies its operations node by node in tape order.  The
+// reverse pass runs the groups backwards, a pointwise group in reverse tape
+// order per node.  The first contribution to each adjoint plane (in that
+// order) stores instead of adding, so no adjoint plane needs clearing.
+// ---------------------------------------------------------------------------
+template <typename T> struct DOp {   // one pointwise operation, both directions
+    int k, nin, param;
+    unsigned assign;                 // bit i: the contribution to ain[i] stores
+    T *out;
+    const T *in[MAXIN];
+    T c[MAXIN];
+    T c0;                            // OP_LIN constant; OP_SCALEP parameter value
+    const T *aout;                   // null: no adjoint flows through this operation
+    T *ain[MAXIN];
+};
+template <typename T> struct DSt {   // one stencil operation
+    int st;
+    unsigned assign;
+    T *out;
+    const T *in;
+    const T *aout;
+    T *ain;
+};
+struct DStencil {
+    int n;
+    int dx[MAXST], dy[MAXST];
+    double w[MAXST];
+};
+constexpr int MAXLEAF = 32;
+template <typename T> struct Leaves {   // dst[i] = src[i] (floats or T), += with add, 0 with zero
+    int n;
+    T *dst[MAXLEAF];
+    const void *src[MAXLEAF];
+    unsigned f32, add, zero;
+};
+
+template <typename T> __device__ __forceinline__ void put(T *p, long long k, T v, bool assign)
 {
-    GRID_LOOP(k, N) {
-        T acc = c0;
-        for (int i = 0; i < n; ++i) acc += in.c[i] * in.p[i][k];
-        out[k] = acc;
-    }
+    if (assign) p[k] = v;
+    else p[k] += v;
 }
-template <typename T> __global__ void kk_lin_vjp(AP<T> ain, int n, const T *aout, long long N)
+
+template <typename T> __global__ void __launch_bounds__(NTH) kk_leaves(Leaves<T> L, long long N)
 {
     GRID_LOOP(k, N) {
-        const T a = aout[k];
-        for (int i = 0; i < n; ++i) ain.p[i][k] += ain.c[i] * a;
-    }
-}
-template <typename T> __global__ void kk_binary(int kind, T *out, const T *a, const T *b, long long N)
-{
-    GRID_LOOP(k, N) {
-        const T x = a[k];
-        T r;
-        switch (kind) {
-        case OP_MUL: r = x * b[k]; break;
-        case OP_DIV: r = x / b[k]; break;
-        case OP_POW3: r = x * x * x; break;
-        case OP_SQRT: r = sqrt(x); break;
-        case OP_CLAMP1: r = x < T(-1) ? T(-1) : (x > T(1) ? T(1) : x); break;
-        default: r = T(1) / x; break;   // OP_RECIP
+        for (int i = 0; i < L.n; ++i) {
+            T v = T(0);
+            if (!((L.zero >> i) & 1u))
+                v = ((L.f32 >> i) & 1u) ? (T)((const float *)L.src[i])[k] : ((const T *)L.src[i])[k];
+            put(L.dst[i], k, v, !((L.add >> i) & 1u));
         }
-        out[k] = r;
     }
 }
+
+template <typename T> __global__ void __launch_bounds__(NTH) kk_pw_fwd(const DOp<T> *__restrict__ ops, int nops, long long N)
+{
+    GRID_LOOP(k, N) {
+        for (int o = 0; o < nops; ++o) {
+            const DOp<T> &op = ops[o];
+            T r;
+            if (op.k == OP_LIN) {
+                r = op.c0;
+                for (int i = 0; i < op.nin; ++i) r += op.c[i] * op.in[i][k];
+            } else if (op.k == OP_SCALEP) {
+                r = op.c0 * op.in[0][k];
+            } else {
+                const T x = op.in[0][k];
+                switch (op.k) {
+                case OP_MUL: r = x * op.in[1][k]; break;
+                case OP_DIV: r = x / op.in[1][k]; break;
+                case OP_POW3: r = x * x * x; break;
+                case OP_SQRT: r = sqrt(x); break;
+                case OP_CLAMP1: r = x < T(-1) ? T(-1) : (x > T(1) ? T(1) : x); break;
+                default: r = T(1) / x; break;   // OP_RECIP
+                }
+            }
+            op.out[k] = r;
+        }
+    }
+}
+
 template <typename T>
-__global__ void kk_binary_vjp(int kind, T *aa, T *ab, const T *a, const T *b, const T *out, const T *aout, long long N)
+__global__ void __launch_bounds__(NTH) kk_pw_rev(const DOp<T> *__restrict__ ops, int nops, double *pgrad, long long N)
 {
+    double pacc[NPARAM] = {};
     GRID_LOOP(k, N) {
-        const T g = aout[k], x = a[k];
-        switch (kind) {
-        case OP_MUL: aa[k] += b[k] * g; ab[k] += x * g; break;
-        case OP_DIV: { const T y = b[k]; aa[k] += g / y; ab[k] -= g * x / (y * y); break; }
-        case OP_POW3: aa[k] += T(3) * x * x * g; break;
-        case OP_SQRT: aa[k] += g / (T(2) * out[k]); break;
-        case OP_CLAMP1: if (x >= T(-1) && x <= T(1)) aa[k] += g; break;
-        default: aa[k] -= g / (x * x); break;   // OP_RECIP
+        for (int o = nops - 1; o >= 0; --o) {
+            const DOp<T> &op = ops[o];
+            if (!op.aout) continue;
+            const T g = op.aout[k];
+            const unsigned as = op.assign;
+            if (op.k == OP_LIN) {
+                for (int i = 0; i < op.nin; ++i) put(op.ain[i], k, op.c[i] * g, (as >> i) & 1u);
+            } else if (op.k == OP_SCALEP) {
+                put(op.ain[0], k, op.c0 * g, as & 1u);
+                const double d = (double)op.in[0][k] * (double)g;
+#pragma unroll
+                for (int q = 0; q < NPARAM; ++q) pacc[q] += q == op.param ? d : 0.0;
+            } else {
+                const T x = op.in[0][k];
+                switch (op.k) {
+                case OP_MUL: {
+                    const T y = op.in[1][k];
+                    put(op.ain[0], k, y * g, as & 1u);
+                    put(op.ain[1], k, x * g, (as >> 1) & 1u);
+                    break;
+                }
+                case OP_DIV: {
+                    const T y = op.in[1][k];
+                    put(op.ain[0], k, g / y, as & 1u);
+                    put(op.ain[1], k, -(g * x / (y * y)), (as >> 1) & 1u);
+                    break;
+                }
+                case OP_POW3: put(op.ain[0], k, T(3) * x * x * g, as & 1u); break;
+                case OP_SQRT: put(op.ain[0], k, g / (T(2) * op.out[k]), as & 1u); break;
+                case OP_CLAMP1: put(op.ain[0], k, (x >= T(-1) && x <= T(1)) ? g : T(0), as & 1u); break;
+                default: put(op.ain[0], k, -(g / (x * x)), as & 1u); break;   // OP_RECIP
+                }
+            }
         }
     }
+    __shared__ double red[NPARAM][NTH / 32];
+#pragma unroll
+    for (int q = 0; q < NPARAM; ++q) {
+        double v = pacc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NPARAM) {
+        double t = 0.0;
+        for (int w = 0; w < NTH / 32; ++w) t += red[threadIdx.x][w];
+        if (t != 0.0) atomicAdd(pgrad + threadIdx.x, t);
+    }
 }
+
+// sum_i w_i src(x + sg dx_i, y + sg dy_i) over the n <= NB taps of S, every
+// tap requested before the first is used (offsets |d| <= 5 < nx, ny).
+template <typename T, int NB>
+__device__ __forceinline__ T taps(const DStencil &S, const T *src, int x, int y, int sg, int nx, int ny)
+{
+    const int n = S.n;
+    T v[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        if (i < n) {
+            int xx = x + sg * S.dx[i], yy = y + sg * S.dy[i];
+            xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+            yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+            v[i] = src[(long long)yy * nx + xx];
+        }
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+        if (i < n) acc += (T)S.w[i] * v[i];
+    return acc;
+}
+
 // out(x, y) = sum_k w_k in(x + dx_k, y + dy_k) on a periodic grid; the
-// transposed stencil adds sum_k w_k aout(x - dx_k, y - dy_k).
+// transpose adds sum_k w_k aout(x - dx_k, y - dy_k) into ain.
 template <typename T>
-__global__ void kk_stencil(T *out, const T *in, KSt<T> S, int nx, int ny, int transpose, long long N)
+__global__ void __launch_bounds__(NTH) kk_st(const DSt<T> *__restrict__ ops, int nops, const DStencil *__restrict__ tab,
+                                             int nx, int ny, int transpose, long long N)
 {
     GRID_LOOP(k, N) {
         const int y = (int)(k / nx), x = (int)(k - (long long)y * nx);
-        T acc = T(0);
-        for (int i = 0; i < S.n; ++i) {
-            int xx = transpose ? x - S.dx[i] : x + S.dx[i];
-            int yy = transpose ? y - S.dy[i] : y + S.dy[i];
-            xx %= nx; if (xx < 0) xx += nx;
-            yy %= ny; if (yy < 0) yy += ny;
-            acc += S.w[i] * in[(long long)yy * nx + xx];
+        for (int o = 0; o < nops; ++o) {
+            const DSt<T> &op = ops[o];
+            if (transpose && !op.aout) continue;
+            const DStencil &S = tab[op.st];
+            const T *src = transpose ? op.aout : op.in;
+            const int sg = transpose ? -1 : 1;
+            const T acc = S.n <= 1 ? taps<T, 1>(S, src, x, y, sg, nx, ny)
+                        : (S.n <= 9 ? taps<T, 9>(S, src, x, y, sg, nx, ny) : taps<T, MAXST>(S, src, x, y, sg, nx, ny));
+            if (transpose) put(op.ain, k, acc, op.assign & 1u);
+            else op.out[k] = acc;
         }
-        if (transpose) out[k] += acc;
-        else out[k] = acc;
-    }
-}
-template <typename U, typename T> __global__ void kk_cast(T *out, const U *in, long long N)
-{
-    GRID_LOOP(k, N) out[k] = (T)in[k];
-}
-template <typename T> __global__ void kk_scale(T *out, const T *in, T s, long long N)
-{
-    GRID_LOOP(k, N) out[k] = s * in[k];
-}
-template <typename T> __global__ void kk_axpy(T *out, const T *in, T s, long long N)
-{
-    GRID_LOOP(k, N) out[k] += s * in[k];
-}
-// grad[p] += sum_k in[k] * aout[k] (FP64 accumulation)
-template <typename T> __global__ void kk_dot(double *acc, const T *a, const T *b, long long N)
-{
-    double s = 0.0;
-    GRID_LOOP(k, N) s += (double)a[k] * (double)b[k];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    __shared__ double red[NTH / 32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < NTH / 32; ++w) t += red[w];
-        atomicAdd(acc, t);
     }
 }
 
 // ---------------------------------------------------------------------------
-// The tape engine.
+// The tape engine.  Planes are kept per plane id across steps (the recorder
+// creates the same planes in the same order every step), so the schedule
+// and the device form of the tape are built once and reused while the
+// recorded tape stays the same.
 // ---------------------------------------------------------------------------
 template <typename T> struct Engine {
     int nx = 0, ny = 0;
     long long N = 0;
     cudaStream_t st = nullptr;
     cudaError_t err = cudaSuccess;
-    std::vector<T *> val, adj;
-    std::vector<T *> pool;
+    std::vector<T *> val, adj;        // by plane id, persistent
+    int nval = 0;
     std::vector<Op> tape;
     std::vector<Stencil> stencils;
     double pval[NPARAM]{};
     double *d_pgrad = nullptr;
     int nb = 1;
+    std::vector<std::pair<int, const void *>> leaves;   // plane, source (this step)
+    std::vector<char> leaf_f32;
+    std::vector<std::pair<int, const T *>> seeds;       // plane, adjoint source
+    std::vector<char> flowed;                           // planes given an adjoint by run()
+    // schedule and device form
+    struct Group { bool stencil; int off, n; };
+    std::vector<Group> groups;
+    std::vector<DOp<T>> hops;
+    std::vector<DSt<T>> hsts;
+    DOp<T> *d_ops = nullptr;
+    DSt<T> *d_sts = nullptr;
+    size_t cap_ops = 0, cap_sts = 0;
+    DStencil *d_tab = nullptr;
+    std::vector<Op> tape_prev;
+    std::vector<std::pair<int, const T *>> seeds_prev;
+    std::vector<char> seed_add;
 
     void check(cudaError_t e) { if (e != cudaSuccess && err == cudaSuccess) err = e; }
 
-    T *take()
+    T *alloc_plane()
     {
-        if (!pool.empty()) { T *p = pool.back(); pool.pop_back(); return p; }
         T *p = nullptr;
         check(cudaMalloc((void **)&p, sizeof(T) * (size_t)N));
         return p;
     }
     void reset()
     {
-        for (T *p : val) if (p) pool.push_back(p);
-        for (T *p : adj) if (p) pool.push_back(p);
-        val.clear();
-        adj.clear();
+        nval = 0;
         tape.clear();
+        leaves.clear();
+        leaf_f32.clear();
+        seeds.clear();
     }
     void release_all()
     {
-        reset();
-        for (T *p : pool) cudaFree(p);
-        pool.clear();
+        for (T *p : val) if (p) cudaFree(p);
+        for (T *p : adj) if (p) cudaFree(p);
+        val.clear();
+        adj.clear();
+        nval = 0;
         if (d_pgrad) cudaFree(d_pgrad);
+        if (d_ops) cudaFree(d_ops);
+        if (d_sts) cudaFree(d_sts);
+        if (d_tab) cudaFree(d_tab);
         d_pgrad = nullptr;
+        d_ops = nullptr;
+        d_sts = nullptr;
+        d_tab = nullptr;
+        cap_ops = cap_sts = 0;
+        tape_prev.clear();
     }
     int newplane()
     {
-        val.push_back(take());
-        adj.push_back(nullptr);
-        return (int)val.size() - 1;
-    }
-    T *A(int id)   // adjoint plane, zeroed on first use
-    {
-        if (!adj[id]) {
-            adj[id] = take();
-            check(cudaMemsetAsync(adj[id], 0, sizeof(T) * (size_t)N, st));
+        if (nval == (int)val.size()) {
+            val.push_back(alloc_plane());
+            adj.push_back(nullptr);
         }
+        return nval++;
+    }
+    T *A(int id)
+    {
+        if (!adj[id]) adj[id] = alloc_plane();
         return adj[id];
     }
     template <typename U> int leaf(const U *src)
     {
+        static_assert(sizeof(U) == sizeof(T) || sizeof(U) == sizeof(float), "leaf type");
         int id = newplane();
-        if (sizeof(U) == sizeof(T))
-            check(cudaMemcpyAsync(val[id], src, sizeof(T) * (size_t)N, cudaMemcpyDeviceToDevice, st));
-        else
-            kk_cast<U, T><<<nb, NTH, 0, st>>>(val[id], src, N);
+        leaves.push_back({id, (const void *)src});
+        leaf_f32.push_back(sizeof(U) == sizeof(float) && sizeof(T) != sizeof(float));
         return id;
     }
     int lin(std::initializer_list<std::pair<int, double>> terms, double c0 = 0.0)
@@ -239,73 +357,208 @@ template <typename T> struct Engine {
     int div(int a, int b) { return binary(OP_DIV, a, b); }
     int sten(int a, int s) { Op o; o.k = OP_STENCIL; o.in[0] = a; o.nin = 1; o.st = s; return emit(o); }
     int scalep(int a, int p) { Op o; o.k = OP_SCALEP; o.in[0] = a; o.nin = 1; o.param = p; return emit(o); }
-
-    KSt<T> kst(int s) const
-    {
-        KSt<T> K;
-        K.n = stencils[s].n;
-        for (int i = 0; i < K.n; ++i) { K.dx[i] = stencils[s].dx[i]; K.dy[i] = stencils[s].dy[i]; K.w[i] = (T)stencils[s].w[i]; }
-        return K;
-    }
-
     int emit(Op o)
     {
         o.out = newplane();
-        T *out = val[o.out];
-        switch (o.k) {
-        case OP_LIN: {
-            PP<T> pp{};
-            for (int i = 0; i < o.nin; ++i) { pp.p[i] = val[o.in[i]]; pp.c[i] = (T)o.c[i]; }
-            kk_lin<T><<<nb, NTH, 0, st>>>(out, pp, o.nin, (T)o.c0, N);
-            break;
-        }
-        case OP_STENCIL:
-            kk_stencil<T><<<nb, NTH, 0, st>>>(out, val[o.in[0]], kst(o.st), nx, ny, 0, N);
-            break;
-        case OP_SCALEP:
-            kk_scale<T><<<nb, NTH, 0, st>>>(out, val[o.in[0]], (T)pval[o.param], N);
-            break;
-        default:
-            kk_binary<T><<<nb, NTH, 0, st>>>((int)o.k, out, val[o.in[0]], o.nin > 1 ? val[o.in[1]] : nullptr, N);
-        }
-        check(cudaGetLastError());
         tape.push_back(o);
         return o.out;
     }
+    void seed(int id, const T *src) { seeds.push_back({id, src}); }
 
-    void reverse()
+    static bool same_tape(const std::vector<Op> &a, const std::vector<Op> &b)
     {
-        for (int t = (int)tape.size() - 1; t >= 0; --t) {
-            const Op &o = tape[t];
-            if (!adj[o.out]) continue;   // nothing flows back through this operation
-            const T *g = adj[o.out];
-            switch (o.k) {
-            case OP_LIN: {
-                AP<T> ap{};
-                for (int i = 0; i < o.nin; ++i) { ap.p[i] = A(o.in[i]); ap.c[i] = (T)o.c[i]; }
-                kk_lin_vjp<T><<<nb, NTH, 0, st>>>(ap, o.nin, g, N);
-                break;
-            }
-            case OP_STENCIL:
-                kk_stencil<T><<<nb, NTH, 0, st>>>(A(o.in[0]), g, kst(o.st), nx, ny, 1, N);
-                break;
-            case OP_SCALEP:
-                kk_axpy<T><<<nb, NTH, 0, st>>>(A(o.in[0]), g, (T)pval[o.param], N);
-                kk_dot<T><<<std::min(nb, 1024), NTH, 0, st>>>(d_pgrad + o.param, val[o.in[0]], g, N);
-                break;
-            default: {
-                T *aa = A(o.in[0]);
-                T *ab = o.nin > 1 ? A(o.in[1]) : nullptr;
-                kk_binary_vjp<T><<<nb, NTH, 0, st>>>((int)o.k, aa, ab, val[o.in[0]],
-                                                     o.nin > 1 ? val[o.in[1]] : nullptr, val[o.out], g, N);
-            }
-            }
-            check(cudaGetLastError());
+        if (a.size() != b.size()) return false;
+        for (size_t i = 0; i < a.size(); ++i) {
+            const Op &x = a[i], &y = b[i];
+            if (x.k != y.k || x.out != y.out || x.nin != y.nin || x.c0 != y.c0 || x.param != y.param || x.st != y.st)
+                return false;
+            for (int j = 0; j < x.nin; ++j)
+                if (x.in[j] != y.in[j] || x.c[j] != y.c[j]) return false;
         }
+        return true;
     }
-    void seed(int id, const T *src)   // adj[id] += src
+
+    // Forward and reverse sweep of the recorded tape, the adjoints of the
+    // seeded planes starting from the seeds.
+    void run()
     {
-        kk_axpy<T><<<nb, NTH, 0, st>>>(A(id), src, T(1), N);
+        if (!(same_tape(tape, tape_prev) && seeds == seeds_prev)) schedule();
+        if (err == cudaSuccess) launch();
+    }
+
+    void schedule()
+    {
+        const int nops = (int)tape.size();
+        std::vector<int> lev(nval, 0);
+        int L = 0;
+        for (const Op &o : tape) {
+            int l = 0;
+            for (int i = 0; i < o.nin; ++i) l = std::max(l, lev[o.in[i]]);
+            if (o.k == OP_STENCIL) ++l;
+            lev[o.out] = l;
+            L = std::max(L, l);
+        }
+        // forward order: P_0, S_1, P_1, ..., S_L, P_L (tape order inside a group)
+        std::vector<std::vector<int>> pw(L + 1), sn(L + 1);
+        for (int t = 0; t < nops; ++t) (tape[t].k == OP_STENCIL ? sn : pw)[lev[tape[t].out]].push_back(t);
+        std::vector<std::pair<bool, const std::vector<int> *>> fwd;
+        for (int l = 0; l <= L; ++l) {
+            if (!sn[l].empty()) fwd.push_back({true, &sn[l]});
+            if (!pw[l].empty()) fwd.push_back({false, &pw[l]});
+        }
+        // adjoint flow and first contributions, in reverse execution order
+        std::vector<char> flow(nval, 0), init(nval, 0);
+        seed_add.assign(seeds.size(), 0);
+        for (size_t i = 0; i < seeds.size(); ++i) {
+            seed_add[i] = init[seeds[i].first];
+            flow[seeds[i].first] = 1;
+            init[seeds[i].first] = 1;
+        }
+        std::vector<unsigned> assign(nops, 0u);
+        std::vector<char> live(nops, 0);
+        for (int g = (int)fwd.size() - 1; g >= 0; --g) {
+            const std::vector<int> &ids = *fwd[g].second;
+            const bool stn = fwd[g].first;
+            for (int j = (int)ids.size() - 1; j >= 0; --j) {
+                // a stencil group visits its operations in tape order per node,
+                // a pointwise group in reverse tape order
+                const int t = stn ? ids[ids.size() - 1 - j] : ids[j];
+                const Op &o = tape[t];
+                if (!flow[o.out]) continue;
+                live[t] = 1;
+                for (int i = 0; i < o.nin; ++i) {
+                    const int p = o.in[i];
+                    flow[p] = 1;
+                    if (!init[p]) { assign[t] |= 1u << i; init[p] = 1; }
+                }
+            }
+        }
+        for (int p = 0; p < nval; ++p) if (flow[p]) A(p);
+        flowed = flow;
+        hops.clear();
+        hsts.clear();
+        groups.clear();
+        for (auto &gr : fwd) {
+            Group G{gr.first, gr.first ? (int)hsts.size() : (int)hops.size(), 0};
+            for (int t : *gr.second) {
+                const Op &o = tape[t];
+                if (gr.first) {
+                    DSt<T> d{};
+                    d.st = o.st;
+                    d.assign = assign[t];
+                    d.out = val[o.out];
+                    d.in = val[o.in[0]];
+                    d.aout = live[t] ? adj[o.out] : nullptr;
+                    d.ain = live[t] ? adj[o.in[0]] : nullptr;
+                    hsts.push_back(d);
+                } else {
+                    DOp<T> d{};
+                    d.k = o.k;
+                    d.nin = o.nin;
+                    d.param = o.param;
+                    d.assign = assign[t];
+                    d.out = val[o.out];
+                    for (int i = 0; i < o.nin; ++i) {
+                        d.in[i] = val[o.in[i]];
+                        d.c[i] = (T)o.c[i];
+                        d.ain[i] = live[t] ? adj[o.in[i]] : nullptr;
+                    }
+                    d.c0 = o.k == OP_SCALEP ? (T)pval[o.param] : (T)o.c0;
+                    d.aout = live[t] ? adj[o.out] : nullptr;
+                    hops.push_back(d);
+                }
+                ++G.n;
+            }
+            groups.push_back(G);
+        }
+        upload();
+        tape_prev = tape;
+        seeds_prev = seeds;
+    }
+
+    void upload()
+    {
+        if (!d_tab) {
+            std::vector<DStencil> tab(stencils.size());
+            for (size_t i = 0; i < stencils.size(); ++i) {
+                tab[i].n = stencils[i].n;
+                for (int j = 0; j < stencils[i].n; ++j) {
+                    tab[i].dx[j] = stencils[i].dx[j];
+                    tab[i].dy[j] = stencils[i].dy[j];
+                    tab[i].w[j] = stencils[i].w[j];
+                }
+            }
+            check(cudaMalloc((void **)&d_tab, sizeof(DStencil) * tab.size()));
+            if (err == cudaSuccess)
+                check(cudaMemcpy(d_tab, tab.data(), sizeof(DStencil) * tab.size(), cudaMemcpyHostToDevice));
+        }
+        if (hops.size() > cap_ops) {
+            if (d_ops) cudaFree(d_ops);
+            cap_ops = hops.size();
+            check(cudaMalloc((void **)&d_ops, sizeof(DOp<T>) * cap_ops));
+        }
+        if (hsts.size() > cap_sts) {
+            if (d_sts) cudaFree(d_sts);
+            cap_sts = hsts.size();
+            check(cudaMalloc((void **)&d_sts, sizeof(DSt<T>) * cap_sts));
+        }
+        // the previous step's kernels may still read the old tape
+        check(cudaStreamSynchronize(st));
+        if (err == cudaSuccess && !hops.empty())
+            check(cudaMemcpy(d_ops, hops.data(), sizeof(DOp<T>) * hops.size(), cudaMemcpyHostToDevice));
+        if (err == cudaSuccess && !hsts.empty())
+            check(cudaMemcpy(d_sts, hsts.data(), sizeof(DSt<T>) * hsts.size(), cudaMemcpyHostToDevice));
+    }
+
+    // The kernels of one forward and reverse sweep of the scheduled tape.
+    void launch()
+    {
+        for (size_t b = 0; b < leaves.size(); b += MAXLEAF) {   // state planes into the tape, as T
+            Leaves<T> Lv{};
+            Lv.n = (int)std::min<size_t>(MAXLEAF, leaves.size() - b);
+            for (int i = 0; i < Lv.n; ++i) {
+                Lv.dst[i] = val[leaves[b + i].first];
+                Lv.src[i] = leaves[b + i].second;
+                if (leaf_f32[b + i]) Lv.f32 |= 1u << i;
+            }
+            kk_leaves<T><<<nb, NTH, 0, st>>>(Lv, N);
+        }
+        for (const Group &G : groups) {
+            if (G.stencil) kk_st<T><<<nb, NTH, 0, st>>>(d_sts + G.off, G.n, d_tab, nx, ny, 0, N);
+            else kk_pw_fwd<T><<<nb, NTH, 0, st>>>(d_ops + G.off, G.n, N);
+        }
+        for (size_t b = 0; b < seeds.size(); b += MAXLEAF) {
+            Leaves<T> Lv{};
+            Lv.n = (int)std::min<size_t>(MAXLEAF, seeds.size() - b);
+            for (int i = 0; i < Lv.n; ++i) {
+                Lv.dst[i] = adj[seeds[b + i].first];
+                Lv.src[i] = seeds[b + i].second;
+                if (seed_add[b + i]) Lv.add |= 1u << i;
+            }
+            kk_leaves<T><<<nb, NTH, 0, st>>>(Lv, N);
+        }
+        for (int g = (int)groups.size() - 1; g >= 0; --g) {
+            const Group &G = groups[g];
+            if (G.stencil) kk_st<T><<<nb, NTH, 0, st>>>(d_sts + G.off, G.n, d_tab, nx, ny, 1, N);
+            else kk_pw_rev<T><<<nb, NTH, 0, st>>>(d_ops + G.off, G.n, d_pgrad, N);
+        }
+        check(cudaGetLastError());
+    }
+
+    // dst[i] = adjoint of plane ids[i] (zero where none flowed).
+    void collect(const int *ids, T *const *dst, int n)
+    {
+        for (int b = 0; b < n; b += MAXLEAF) {
+            Leaves<T> Lv{};
+            Lv.n = std::min(MAXLEAF, n - b);
+            for (int i = 0; i < Lv.n; ++i) {
+                const bool f = ids[b + i] < (int)flowed.size() && flowed[ids[b + i]];
+                Lv.dst[i] = dst[b + i];
+                Lv.src[i] = f ? adj[ids[b + i]] : nullptr;
+                if (!f) Lv.zero |= 1u << i;
+            }
+            kk_leaves<T><<<nb, NTH, 0, st>>>(Lv, N);
+        }
         check(cudaGetLastError());
     }
 };
@@ -707,12 +960,14 @@ template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, 
             for (int i = 0; i < NSTATE; ++i) *slot(in, i) = E->leaf(sj + i * n);
             StateIds out = R.step(in);
             for (int i = 0; i < NSTATE; ++i) E->seed(*slot(out, i), lam + i * n);
-            E->reverse();
+            E->run();
+            int ids[NSTATE];
+            D *dst[NSTATE];
             for (int i = 0; i < NSTATE; ++i) {
-                int id = *slot(in, i);
-                if (E->adj[id]) cudaMemcpyAsync(lam + i * n, E->adj[id], pd, cudaMemcpyDeviceToDevice, h->stream);
-                else cudaMemsetAsync(lam + i * n, 0, pd, h->stream);
+                ids[i] = *slot(in, i);
+                dst[i] = lam + i * n;
             }
+            E->collect(ids, dst, NSTATE);
             if (E->err != cudaSuccess) return afail(h, LBM_ERR_CUDA, std::string("adjoint: ") + cudaGetErrorString(E->err));
         }
     }
@@ -722,9 +977,9 @@ template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, 
     int phi0 = E->leaf(i4), p0 = E->leaf(i4 + n), ux0 = E->leaf(i4 + 2 * n), uy0 = E->leaf(i4 + 3 * n);
     StateIds s0 = R.init(phi0, p0, ux0, uy0);
     for (int i = 0; i < NSTATE; ++i) E->seed(*slot(s0, i), lam + i * n);
-    E->reverse();
+    E->run();
     std::vector<D> g(n, D(0));
-    if (E->adj[phi0]) cudaMemcpyAsync(g.data(), E->adj[phi0], pd, cudaMemcpyDeviceToHost, h->stream);
+    if (E->flowed[phi0]) cudaMemcpyAsync(g.data(), E->adj[phi0], pd, cudaMemcpyDeviceToHost, h->stream);
     double pg[NPARAM];
     cudaMemcpyAsync(pg, E->d_pgrad, sizeof(pg), cudaMemcpyDeviceToHost, h->stream);
     cudaError_t e = cudaStreamSynchronize(h->stream);
