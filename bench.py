@@ -400,7 +400,7 @@ def run_ours(args):
         t2 = time.perf_counter()
         a.close()
         variants["adjoint"] = {"workload": f"translating drop {an}x{an}, rho ratio 100, {asteps} steps, "
-                                           f"checkpoint every {aevery}, FP32 forward, FP64 reverse sweep",
+                                           f"checkpoint every {aevery}, FP32 forward and reverse sweep",
                                "forward_s": round(t1 - t0, 4), "reverse_s": round(t2 - t1, 4),
                                "adjoint_over_forward": round((t2 - t1) / (t1 - t0), 2)}
 

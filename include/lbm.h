@@ -211,9 +211,11 @@ const char *lbm_kernel_variant(const lbm_handle *h, int kind);
  *     host [ny][nx] gradient of the loss with respect to phi after nsteps.
  *     Runs the reverse sweep -- each segment of k steps is regenerated from
  *     its checkpoint and reversed step by step through the hand-written
- *     vector-Jacobian products of the step's plane operations -- and writes
- *     dL/dphi0 (host [ny][nx], may be NULL), dL/dsigma and dL/dM (may be
- *     NULL).  The handle is left at the state after nsteps steps.
+ *     vector-Jacobian products of the step's plane operations, in the
+ *     handle's arithmetic type (FP64 or FP32; the sigma and M gradients are
+ *     summed in FP64) -- and writes dL/dphi0 (host [ny][nx], may be NULL),
+ *     dL/dsigma and dL/dM (may be NULL).  The handle is left at the state
+ *     after nsteps steps.
  *     Synchronises the stream.  Errors: LBM_ERR_STATE (no begin), LBM_ERR_ARG,
  *     LBM_ERR_CUDA.
  * sigma enters through kappa = 3 sigma W/8 and beta = 3 sigma/(4W)

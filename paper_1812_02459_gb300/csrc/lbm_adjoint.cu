@@ -13,7 +13,8 @@
 // them node by node, so a step costs a few dozen launches in each direction.  Across steps, sqrt(N)-style checkpointing keeps every
 // k-th state, regenerates a segment with the fused forward kernels and
 // reverses it step by step.  Periodic axes, FP64 or FP32 populations; the
-// reverse sweep itself always runs in FP64.
+// reverse sweep runs in the handle's arithmetic type, with the parameter
+// gradients summed in FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -69,15 +70,25 @@ int blocks_for(long long N) { return (int)std::min<long long>((N + NTH - 1) / NT
 // order per node.  The first contribution to each adjoint plane (in that
 // order) stores instead of adding, so no adjoint plane needs clearing.
 // ---------------------------------------------------------------------------
-template <typename T> struct DOp {   // one pointwise operation, both directions
-    int k, nin, param;
-    unsigned assign;                 // bit i: the contribution to ain[i] stores
-    T *out;
-    const T *in[MAXIN];
+// One operation of a pointwise group, as the group kernels run it.  Values
+// made and used inside the group live in per-thread slots of shared memory
+// (allocated by their lifetimes); values needed by other groups or by the
+// reverse sweep also go to their global planes.  In the reverse sweep the
+// adjoints of values made inside the group accumulate in slots, and only
+// the adjoints of inputs from outside the group go to global planes.
+template <typename T> struct VOp {
+    int k, nin, param, live;
+    unsigned fint;          // bit i: input i is read from forward slot fslot[i]
+    unsigned rint;          // bit i: the adjoint of input i goes to reverse slot rslot[i]
+    unsigned rassign;       // bit i: that contribution (slot or global) stores instead of adding
+    short fslot[MAXIN], rslot[MAXIN];
+    short fout, rout;       // forward slot of the output; reverse slot with its in-group adjoint (-1: none)
+    T *out;                 // global plane of the output (null: not needed outside the group)
+    const T *in[MAXIN];     // global planes of the inputs' values
     T c[MAXIN];
-    T c0;                            // OP_LIN constant; OP_SCALEP parameter value
-    const T *aout;                   // null: no adjoint flows through this operation
-    T *ain[MAXIN];
+    T c0;                   // OP_LIN constant; OP_SCALEP parameter value
+    const T *aout;          // global adjoint of the output (null: none reaches it from outside)
+    T *ain[MAXIN];          // global adjoints of the inputs from outside the group
 };
 template <typename T> struct DSt {   // one stencil operation
     int st;
@@ -118,74 +129,148 @@ template <typename T> __global__ void __launch_bounds__(NTH) kk_leaves(Leaves<T>
     }
 }
 
-template <typename T> __global__ void __launch_bounds__(NTH) kk_pw_fwd(const DOp<T> *__restrict__ ops, int nops, long long N)
+constexpr int NTV = 128;   // threads of a pointwise-group kernel
+
+// slot q of this thread
+template <typename T> __device__ __forceinline__ T &slot_ref(T *sl, int q) { return sl[q * NTV + threadIdx.x]; }
+
+// Copy n bytes of records (8-byte aligned) into shared memory; every thread
+// of the block takes part and the block waits for the copy.
+__device__ __forceinline__ void stage_records(void *dst, const void *src, size_t bytes)
 {
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(dst);
+    const unsigned long long *s = reinterpret_cast<const unsigned long long *>(src);
+    for (size_t i = threadIdx.x; i < bytes / 8; i += blockDim.x) d[i] = s[i];
+    __syncthreads();
+}
+
+// Ask for the global inputs of a later operation at node k ahead of use.
+// Only planes that no kernel writes while this one runs are requested: the
+// forward values from outside the group and, in the reverse sweep, the
+// adjoints reaching the group from outside.
+constexpr int VM_AHEAD = 4;
+__device__ __forceinline__ void prefetch_l1(const void *p)
+{
+    asm volatile("prefetch.global.L1 [%0];\n" ::"l"(p));
+}
+template <typename T> __device__ __forceinline__ void prefetch_fwd(const VOp<T> &op, long long k)
+{
+    for (int i = 0; i < op.nin; ++i)
+        if (!((op.fint >> i) & 1u)) prefetch_l1(op.in[i] + k);
+}
+template <typename T> __device__ __forceinline__ void prefetch_rev(const VOp<T> &op, long long k)
+{
+    if (!op.live) return;
+    if (op.aout) prefetch_l1(op.aout + k);
+    if (op.k != OP_LIN && op.k != OP_SQRT) prefetch_l1(op.in[0] + k);
+    if (op.k == OP_MUL || op.k == OP_DIV) prefetch_l1(op.in[1] + k);
+    if (op.k == OP_SQRT) prefetch_l1(op.out + k);
+}
+
+// Shared memory of a pointwise-group kernel: the group's operation records,
+// then the value or adjoint slots, NTV per slot.
+template <typename T> __host__ __device__ constexpr size_t vm_ops_bytes(int nops)
+{
+    return (sizeof(VOp<T>) * (size_t)nops + 15) / 16 * 16;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTV) kk_vm_fwd(const VOp<T> *__restrict__ gops, int nops, long long N)
+{
+    extern __shared__ __align__(16) unsigned char vm_raw[];
+    VOp<T> *ops = reinterpret_cast<VOp<T> *>(vm_raw);
+    T *sl = reinterpret_cast<T *>(vm_raw + vm_ops_bytes<T>(nops));
+    stage_records(ops, gops, sizeof(VOp<T>) * (size_t)nops);
     GRID_LOOP(k, N) {
+        for (int o = 0; o < VM_AHEAD && o < nops; ++o) prefetch_fwd(ops[o], k);
         for (int o = 0; o < nops; ++o) {
-            const DOp<T> &op = ops[o];
+            if (o + VM_AHEAD < nops) prefetch_fwd(ops[o + VM_AHEAD], k);
+            const VOp<T> &op = ops[o];
+            const int nin = op.nin;
+            T x[MAXIN];
+#pragma unroll
+            for (int i = 0; i < MAXIN; ++i)   // every input requested before the first is used
+                if (i < nin) x[i] = ((op.fint >> i) & 1u) ? slot_ref(sl, op.fslot[i]) : op.in[i][k];
             T r;
-            if (op.k == OP_LIN) {
+            switch (op.k) {
+            case OP_LIN:
                 r = op.c0;
-                for (int i = 0; i < op.nin; ++i) r += op.c[i] * op.in[i][k];
-            } else if (op.k == OP_SCALEP) {
-                r = op.c0 * op.in[0][k];
-            } else {
-                const T x = op.in[0][k];
-                switch (op.k) {
-                case OP_MUL: r = x * op.in[1][k]; break;
-                case OP_DIV: r = x / op.in[1][k]; break;
-                case OP_POW3: r = x * x * x; break;
-                case OP_SQRT: r = sqrt(x); break;
-                case OP_CLAMP1: r = x < T(-1) ? T(-1) : (x > T(1) ? T(1) : x); break;
-                default: r = T(1) / x; break;   // OP_RECIP
-                }
+#pragma unroll
+                for (int i = 0; i < MAXIN; ++i)
+                    if (i < nin) r += op.c[i] * x[i];
+                break;
+            case OP_SCALEP: r = op.c0 * x[0]; break;
+            case OP_MUL: r = x[0] * x[1]; break;
+            case OP_DIV: r = x[0] / x[1]; break;
+            case OP_POW3: r = x[0] * x[0] * x[0]; break;
+            case OP_SQRT: r = sqrt(x[0]); break;
+            case OP_CLAMP1: r = x[0] < T(-1) ? T(-1) : (x[0] > T(1) ? T(1) : x[0]); break;
+            default: r = T(1) / x[0]; break;   // OP_RECIP
             }
-            op.out[k] = r;
+            if (op.fout >= 0) slot_ref(sl, op.fout) = r;
+            if (op.out) op.out[k] = r;
         }
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NTH) kk_pw_rev(const DOp<T> *__restrict__ ops, int nops, double *pgrad, long long N)
+__global__ void __launch_bounds__(NTV) kk_vm_rev(const VOp<T> *__restrict__ gops, int nops, double *pgrad, long long N)
 {
+    extern __shared__ __align__(16) unsigned char vm_raw[];
+    VOp<T> *ops = reinterpret_cast<VOp<T> *>(vm_raw);
+    T *sl = reinterpret_cast<T *>(vm_raw + vm_ops_bytes<T>(nops));
+    stage_records(ops, gops, sizeof(VOp<T>) * (size_t)nops);
     double pacc[NPARAM] = {};
     GRID_LOOP(k, N) {
+        for (int o = nops - 1; o >= 0 && o >= nops - VM_AHEAD; --o) prefetch_rev(ops[o], k);
         for (int o = nops - 1; o >= 0; --o) {
-            const DOp<T> &op = ops[o];
-            if (!op.aout) continue;
-            const T g = op.aout[k];
-            const unsigned as = op.assign;
-            if (op.k == OP_LIN) {
-                for (int i = 0; i < op.nin; ++i) put(op.ain[i], k, op.c[i] * g, (as >> i) & 1u);
-            } else if (op.k == OP_SCALEP) {
-                put(op.ain[0], k, op.c0 * g, as & 1u);
-                const double d = (double)op.in[0][k] * (double)g;
+            if (o - VM_AHEAD >= 0) prefetch_rev(ops[o - VM_AHEAD], k);
+            const VOp<T> &op = ops[o];
+            if (!op.live) continue;
+            // forward values the product needs, requested first
+            T x = T(0), y = T(0), z = T(0);
+            const int kind = op.k;
+            if (kind != OP_LIN && kind != OP_SQRT) x = op.in[0][k];
+            if (kind == OP_MUL || kind == OP_DIV) y = op.in[1][k];
+            if (kind == OP_SQRT) z = op.out[k];
+            T g = op.aout ? op.aout[k] : T(0);
+            if (op.rout >= 0) g += slot_ref(sl, op.rout);
+            T ci[MAXIN];
+            int nc = 1;
+            switch (kind) {
+            case OP_LIN:
+                nc = op.nin;
+#pragma unroll
+                for (int i = 0; i < MAXIN; ++i) ci[i] = op.c[i] * g;
+                break;
+            case OP_SCALEP: {
+                ci[0] = op.c0 * g;
+                const double d = (double)x * (double)g;
 #pragma unroll
                 for (int q = 0; q < NPARAM; ++q) pacc[q] += q == op.param ? d : 0.0;
-            } else {
-                const T x = op.in[0][k];
-                switch (op.k) {
-                case OP_MUL: {
-                    const T y = op.in[1][k];
-                    put(op.ain[0], k, y * g, as & 1u);
-                    put(op.ain[1], k, x * g, (as >> 1) & 1u);
-                    break;
-                }
-                case OP_DIV: {
-                    const T y = op.in[1][k];
-                    put(op.ain[0], k, g / y, as & 1u);
-                    put(op.ain[1], k, -(g * x / (y * y)), (as >> 1) & 1u);
-                    break;
-                }
-                case OP_POW3: put(op.ain[0], k, T(3) * x * x * g, as & 1u); break;
-                case OP_SQRT: put(op.ain[0], k, g / (T(2) * op.out[k]), as & 1u); break;
-                case OP_CLAMP1: put(op.ain[0], k, (x >= T(-1) && x <= T(1)) ? g : T(0), as & 1u); break;
-                default: put(op.ain[0], k, -(g / (x * x)), as & 1u); break;   // OP_RECIP
+                break;
+            }
+            case OP_MUL: ci[0] = y * g; ci[1] = x * g; nc = 2; break;
+            case OP_DIV: ci[0] = g / y; ci[1] = -(g * x / (y * y)); nc = 2; break;
+            case OP_POW3: ci[0] = T(3) * x * x * g; break;
+            case OP_SQRT: ci[0] = g / (T(2) * z); break;
+            case OP_CLAMP1: ci[0] = (x >= T(-1) && x <= T(1)) ? g : T(0); break;
+            default: ci[0] = -(g / (x * x)); break;   // OP_RECIP
+            }
+#pragma unroll
+            for (int i = 0; i < MAXIN; ++i) {
+                if (i >= nc) break;
+                const bool as = (op.rassign >> i) & 1u;
+                if ((op.rint >> i) & 1u) {
+                    T &q = slot_ref(sl, op.rslot[i]);
+                    q = as ? ci[i] : q + ci[i];
+                } else {
+                    put(op.ain[i], k, ci[i], as);
                 }
             }
         }
     }
-    __shared__ double red[NPARAM][NTH / 32];
+    __shared__ double red[NPARAM][NTV / 32];
 #pragma unroll
     for (int q = 0; q < NPARAM; ++q) {
         double v = pacc[q];
@@ -195,7 +280,7 @@ __global__ void __launch_bounds__(NTH) kk_pw_rev(const DOp<T> *__restrict__ ops,
     __syncthreads();
     if (threadIdx.x < NPARAM) {
         double t = 0.0;
-        for (int w = 0; w < NTH / 32; ++w) t += red[threadIdx.x][w];
+        for (int w = 0; w < NTV / 32; ++w) t += red[threadIdx.x][w];
         if (t != 0.0) atomicAdd(pgrad + threadIdx.x, t);
     }
 }
@@ -226,9 +311,14 @@ __device__ __forceinline__ T taps(const DStencil &S, const T *src, int x, int y,
 // out(x, y) = sum_k w_k in(x + dx_k, y + dy_k) on a periodic grid; the
 // transpose adds sum_k w_k aout(x - dx_k, y - dy_k) into ain.
 template <typename T>
-__global__ void __launch_bounds__(NTH) kk_st(const DSt<T> *__restrict__ ops, int nops, const DStencil *__restrict__ tab,
-                                             int nx, int ny, int transpose, long long N)
+__global__ void __launch_bounds__(NTH) kk_st(const DSt<T> *__restrict__ gops, int nops, const DStencil *__restrict__ gtab,
+                                             int ntab, int nx, int ny, int transpose, long long N)
 {
+    extern __shared__ __align__(16) unsigned char st_raw[];
+    DStencil *tab = reinterpret_cast<DStencil *>(st_raw);
+    DSt<T> *ops = reinterpret_cast<DSt<T> *>(st_raw + sizeof(DStencil) * (size_t)ntab);
+    stage_records(tab, gtab, sizeof(DStencil) * (size_t)ntab);
+    stage_records(ops, gops, sizeof(DSt<T>) * (size_t)nops);
     GRID_LOOP(k, N) {
         const int y = (int)(k / nx), x = (int)(k - (long long)y * nx);
         for (int o = 0; o < nops; ++o) {
@@ -268,11 +358,17 @@ template <typename T> struct Engine {
     std::vector<std::pair<int, const T *>> seeds;       // plane, adjoint source
     std::vector<char> flowed;                           // planes given an adjoint by run()
     // schedule and device form
-    struct Group { bool stencil; int off, n; };
+    struct Group { bool stencil; int off, n, fslots, rslots; };
     std::vector<Group> groups;
-    std::vector<DOp<T>> hops;
+    std::vector<VOp<T>> hops;
     std::vector<DSt<T>> hsts;
-    DOp<T> *d_ops = nullptr;
+    VOp<T> *d_ops = nullptr;
+    int nbv = 1;                      // blocks of a pointwise-group kernel
+    int smem_set = 0, smem_st_set = 0;   // dynamic shared memory the group kernels are set up for
+    int ntab = 0;                        // stencils in the device table
+
+    size_t vm_bytes(int nops, int slots) const { return vm_ops_bytes<T>(nops) + sizeof(T) * NTV * (size_t)slots; }
+    size_t st_bytes(int nops) const { return sizeof(DStencil) * (size_t)ntab + sizeof(DSt<T>) * (size_t)nops; }
     DSt<T> *d_sts = nullptr;
     size_t cap_ops = 0, cap_sts = 0;
     DStencil *d_tab = nullptr;
@@ -389,6 +485,7 @@ template <typename T> struct Engine {
     void schedule()
     {
         const int nops = (int)tape.size();
+        ntab = (int)stencils.size();
         std::vector<int> lev(nval, 0);
         int L = 0;
         for (const Op &o : tape) {
@@ -406,71 +503,172 @@ template <typename T> struct Engine {
             if (!sn[l].empty()) fwd.push_back({true, &sn[l]});
             if (!pw[l].empty()) fwd.push_back({false, &pw[l]});
         }
-        // adjoint flow and first contributions, in reverse execution order
-        std::vector<char> flow(nval, 0), init(nval, 0);
+        const int ng = (int)fwd.size();
+        // the pointwise group making each plane; uses outside it; values the
+        // reverse sweep reads (operands of the nonlinear products)
+        std::vector<int> pgroup(nval, -1);
+        for (int g = 0; g < ng; ++g)
+            if (!fwd[g].first) for (int t : *fwd[g].second) pgroup[tape[t].out] = g;
+        std::vector<char> used_out(nval, 0), needs_val(nval, 0);
+        for (int g = 0; g < ng; ++g)
+            for (int t : *fwd[g].second) {
+                const Op &o = tape[t];
+                for (int i = 0; i < o.nin; ++i)
+                    if (fwd[g].first || pgroup[o.in[i]] != g) used_out[o.in[i]] = 1;
+                if (o.k == OP_MUL || o.k == OP_DIV) needs_val[o.in[0]] = needs_val[o.in[1]] = 1;
+                if (o.k == OP_POW3 || o.k == OP_CLAMP1 || o.k == OP_RECIP || o.k == OP_SCALEP) needs_val[o.in[0]] = 1;
+                if (o.k == OP_SQRT) needs_val[o.out] = 1;
+            }
+        // reverse sweep, simulated in its execution order: which operations
+        // carry an adjoint, which planes receive a global adjoint (gw), which
+        // contributions store, and the reverse slots of each pointwise group
+        std::vector<char> gw(nval, 0), init(nval, 0);
         seed_add.assign(seeds.size(), 0);
         for (size_t i = 0; i < seeds.size(); ++i) {
             seed_add[i] = init[seeds[i].first];
-            flow[seeds[i].first] = 1;
-            init[seeds[i].first] = 1;
+            gw[seeds[i].first] = init[seeds[i].first] = 1;
         }
-        std::vector<unsigned> assign(nops, 0u);
-        std::vector<char> live(nops, 0);
-        for (int g = (int)fwd.size() - 1; g >= 0; --g) {
+        std::vector<VOp<T>> vop(nops);
+        std::vector<DSt<T>> sop(nops);
+        std::vector<int> rslots(ng, 0), fslots(ng, 0);
+        std::vector<int> rslotof(nval, -1);
+        for (int g = ng - 1; g >= 0; --g) {
             const std::vector<int> &ids = *fwd[g].second;
-            const bool stn = fwd[g].first;
+            if (fwd[g].first) {   // stencils: tape order per node, global adjoints
+                for (int t : ids) {
+                    const Op &o = tape[t];
+                    DSt<T> &d = sop[t];
+                    d = DSt<T>{};
+                    if (!gw[o.out]) continue;
+                    const int p = o.in[0];
+                    d.aout = (const T *)(uintptr_t)1;   // live; pointers filled below
+                    gw[p] = 1;
+                    if (!init[p]) { d.assign = 1u; init[p] = 1; }
+                }
+                continue;
+            }
+            std::vector<int> freel;
+            int top = 0;
+            auto alloc = [&]() { if (!freel.empty()) { int q = freel.back(); freel.pop_back(); return q; } return top++; };
             for (int j = (int)ids.size() - 1; j >= 0; --j) {
-                // a stencil group visits its operations in tape order per node,
-                // a pointwise group in reverse tape order
-                const int t = stn ? ids[ids.size() - 1 - j] : ids[j];
+                const int t = ids[j];
                 const Op &o = tape[t];
-                if (!flow[o.out]) continue;
-                live[t] = 1;
-                for (int i = 0; i < o.nin; ++i) {
+                VOp<T> &d = vop[t];
+                d = VOp<T>{};
+                d.rout = -1;
+                const bool inner = rslotof[o.out] >= 0;
+                if (!gw[o.out] && !inner) continue;
+                d.live = 1;
+                if (inner) {
+                    d.rout = (short)rslotof[o.out];
+                    freel.push_back(rslotof[o.out]);
+                    rslotof[o.out] = -1;
+                }
+                const int nc = (o.k == OP_LIN) ? o.nin : (o.k == OP_MUL || o.k == OP_DIV) ? 2 : 1;
+                for (int i = 0; i < nc; ++i) {
                     const int p = o.in[i];
-                    flow[p] = 1;
-                    if (!init[p]) { assign[t] |= 1u << i; init[p] = 1; }
+                    if (pgroup[p] == g) {
+                        d.rint |= 1u << i;
+                        if (rslotof[p] < 0) { rslotof[p] = alloc(); d.rassign |= 1u << i; }
+                        d.rslot[i] = (short)rslotof[p];
+                    } else {
+                        gw[p] = 1;
+                        if (!init[p]) { d.rassign |= 1u << i; init[p] = 1; }
+                    }
                 }
             }
+            rslots[g] = top;
         }
-        for (int p = 0; p < nval; ++p) if (flow[p]) A(p);
-        flowed = flow;
+        for (int p = 0; p < nval; ++p) if (gw[p]) A(p);
+        flowed = gw;
+        // forward slots, device form, groups
         hops.clear();
         hsts.clear();
         groups.clear();
-        for (auto &gr : fwd) {
-            Group G{gr.first, gr.first ? (int)hsts.size() : (int)hops.size(), 0};
-            for (int t : *gr.second) {
-                const Op &o = tape[t];
-                if (gr.first) {
-                    DSt<T> d{};
+        std::vector<int> fslotof(nval, -1), lastuse(nval, -1);
+        int maxslots = 0;
+        for (int g = 0; g < ng; ++g) {
+            const std::vector<int> &ids = *fwd[g].second;
+            Group G{fwd[g].first, fwd[g].first ? (int)hsts.size() : (int)hops.size(), (int)ids.size(), 0, rslots[g]};
+            if (fwd[g].first) {
+                for (int t : ids) {
+                    const Op &o = tape[t];
+                    DSt<T> d = sop[t];
+                    const bool live = d.aout != nullptr;
                     d.st = o.st;
-                    d.assign = assign[t];
                     d.out = val[o.out];
                     d.in = val[o.in[0]];
-                    d.aout = live[t] ? adj[o.out] : nullptr;
-                    d.ain = live[t] ? adj[o.in[0]] : nullptr;
+                    d.aout = live ? adj[o.out] : nullptr;
+                    d.ain = live ? adj[o.in[0]] : nullptr;
                     hsts.push_back(d);
-                } else {
-                    DOp<T> d{};
-                    d.k = o.k;
-                    d.nin = o.nin;
-                    d.param = o.param;
-                    d.assign = assign[t];
-                    d.out = val[o.out];
-                    for (int i = 0; i < o.nin; ++i) {
-                        d.in[i] = val[o.in[i]];
-                        d.c[i] = (T)o.c[i];
-                        d.ain[i] = live[t] ? adj[o.in[i]] : nullptr;
-                    }
-                    d.c0 = o.k == OP_SCALEP ? (T)pval[o.param] : (T)o.c0;
-                    d.aout = live[t] ? adj[o.out] : nullptr;
-                    hops.push_back(d);
                 }
-                ++G.n;
+                groups.push_back(G);
+                continue;
             }
+            for (size_t j = 0; j < ids.size(); ++j) {
+                const Op &o = tape[ids[j]];
+                for (int i = 0; i < o.nin; ++i)
+                    if (pgroup[o.in[i]] == g) lastuse[o.in[i]] = (int)j;
+            }
+            std::vector<int> freel;
+            int top = 0;
+            for (size_t j = 0; j < ids.size(); ++j) {
+                const int t = ids[j];
+                const Op &o = tape[t];
+                VOp<T> d = vop[t];
+                d.k = o.k;
+                d.nin = o.nin;
+                d.param = o.param;
+                for (int i = 0; i < o.nin; ++i) {
+                    const int p = o.in[i];
+                    d.in[i] = val[p];
+                    d.c[i] = (T)o.c[i];
+                    if (pgroup[p] == g) {
+                        d.fint |= 1u << i;
+                        d.fslot[i] = (short)fslotof[p];
+                    }
+                    if (d.live && !((d.rint >> i) & 1u) && i < ((o.k == OP_LIN) ? o.nin : (o.k == OP_MUL || o.k == OP_DIV) ? 2 : 1))
+                        d.ain[i] = adj[p];
+                }
+                for (int i = 0; i < o.nin; ++i) {   // inputs read for the last time free their slots
+                    const int p = o.in[i];
+                    if (pgroup[p] == g && lastuse[p] == (int)j && fslotof[p] >= 0) {
+                        freel.push_back(fslotof[p]);
+                        fslotof[p] = -1;
+                    }
+                }
+                d.fout = -1;
+                if (lastuse[o.out] > (int)j) {
+                    int q;
+                    if (!freel.empty()) { q = freel.back(); freel.pop_back(); } else q = top++;
+                    fslotof[o.out] = q;
+                    d.fout = (short)q;
+                }
+                d.out = (used_out[o.out] || needs_val[o.out]) ? val[o.out] : nullptr;
+                d.c0 = o.k == OP_SCALEP ? (T)pval[o.param] : (T)o.c0;
+                d.aout = (d.live && gw[o.out]) ? adj[o.out] : nullptr;
+                hops.push_back(d);
+            }
+            G.fslots = top;
+            maxslots = std::max(maxslots, std::max(top, rslots[g]));
             groups.push_back(G);
         }
+        (void)maxslots;
+        int smem = 0, smem_st = 0;
+        for (const Group &G : groups) {
+            if (G.stencil) smem_st = std::max(smem_st, (int)st_bytes(G.n));
+            else smem = std::max(smem, (int)std::max(vm_bytes(G.n, G.fslots), vm_bytes(G.n, G.rslots)));
+        }
+        if (smem > smem_set) {
+            check(cudaFuncSetAttribute(kk_vm_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            check(cudaFuncSetAttribute(kk_vm_rev<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            smem_set = smem;
+        }
+        if (smem_st > smem_st_set) {
+            check(cudaFuncSetAttribute(kk_st<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_st));
+            smem_st_set = smem_st;
+        }
+        nbv = (int)std::min<long long>((N + NTV - 1) / NTV, 8192);
         upload();
         tape_prev = tape;
         seeds_prev = seeds;
@@ -488,6 +686,7 @@ template <typename T> struct Engine {
                     tab[i].w[j] = stencils[i].w[j];
                 }
             }
+            ntab = (int)tab.size();
             check(cudaMalloc((void **)&d_tab, sizeof(DStencil) * tab.size()));
             if (err == cudaSuccess)
                 check(cudaMemcpy(d_tab, tab.data(), sizeof(DStencil) * tab.size(), cudaMemcpyHostToDevice));
@@ -495,7 +694,7 @@ template <typename T> struct Engine {
         if (hops.size() > cap_ops) {
             if (d_ops) cudaFree(d_ops);
             cap_ops = hops.size();
-            check(cudaMalloc((void **)&d_ops, sizeof(DOp<T>) * cap_ops));
+            check(cudaMalloc((void **)&d_ops, sizeof(VOp<T>) * cap_ops));
         }
         if (hsts.size() > cap_sts) {
             if (d_sts) cudaFree(d_sts);
@@ -505,7 +704,7 @@ template <typename T> struct Engine {
         // the previous step's kernels may still read the old tape
         check(cudaStreamSynchronize(st));
         if (err == cudaSuccess && !hops.empty())
-            check(cudaMemcpy(d_ops, hops.data(), sizeof(DOp<T>) * hops.size(), cudaMemcpyHostToDevice));
+            check(cudaMemcpy(d_ops, hops.data(), sizeof(VOp<T>) * hops.size(), cudaMemcpyHostToDevice));
         if (err == cudaSuccess && !hsts.empty())
             check(cudaMemcpy(d_sts, hsts.data(), sizeof(DSt<T>) * hsts.size(), cudaMemcpyHostToDevice));
     }
@@ -524,8 +723,10 @@ template <typename T> struct Engine {
             kk_leaves<T><<<nb, NTH, 0, st>>>(Lv, N);
         }
         for (const Group &G : groups) {
-            if (G.stencil) kk_st<T><<<nb, NTH, 0, st>>>(d_sts + G.off, G.n, d_tab, nx, ny, 0, N);
-            else kk_pw_fwd<T><<<nb, NTH, 0, st>>>(d_ops + G.off, G.n, N);
+            if (G.stencil)
+                kk_st<T><<<nb, NTH, st_bytes(G.n), st>>>(d_sts + G.off, G.n, d_tab, ntab, nx, ny, 0, N);
+            else
+                kk_vm_fwd<T><<<nbv, NTV, vm_bytes(G.n, G.fslots), st>>>(d_ops + G.off, G.n, N);
         }
         for (size_t b = 0; b < seeds.size(); b += MAXLEAF) {
             Leaves<T> Lv{};
@@ -539,8 +740,10 @@ template <typename T> struct Engine {
         }
         for (int g = (int)groups.size() - 1; g >= 0; --g) {
             const Group &G = groups[g];
-            if (G.stencil) kk_st<T><<<nb, NTH, 0, st>>>(d_sts + G.off, G.n, d_tab, nx, ny, 1, N);
-            else kk_pw_rev<T><<<nb, NTH, 0, st>>>(d_ops + G.off, G.n, d_pgrad, N);
+            if (G.stencil)
+                kk_st<T><<<nb, NTH, st_bytes(G.n), st>>>(d_sts + G.off, G.n, d_tab, ntab, nx, ny, 1, N);
+            else
+                kk_vm_rev<T><<<nbv, NTV, vm_bytes(G.n, G.rslots), st>>>(d_ops + G.off, G.n, d_pgrad, N);
         }
         check(cudaGetLastError());
     }
@@ -867,7 +1070,8 @@ struct lbm_adjoint {
     void *init4 = nullptr;         // phi0, p0, ux0, uy0
     void *final_state = nullptr;   // state after nsteps
     void *lam = nullptr;           // adjoint state, NSTATE planes
-    void *eng = nullptr;           // Engine<T>
+    void *eng = nullptr;           // Engine<T> of the handle's arithmetic type
+    bool eng64 = false;            // eng is an Engine<double>
     bool ready = false;
 };
 
@@ -908,18 +1112,18 @@ cudaError_t copy_state_in(lbm_handle *h, const void *src)
     return cudaSuccess;
 }
 
-// The reverse sweep runs in FP64 whatever the handle's precision: the states
-// regenerated by the forward kernels (type T) enter the tape converted to
-// double, and the adjoint state is kept in double.
+// The reverse sweep runs in the handle's arithmetic type T (the adjoint
+// state too); only the parameter gradients are summed in FP64.
 template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, double *dphi0, double *dsigma, double *dM)
 {
-    using D = double;
+    using D = T;
     lbm_adjoint *A = h->adj;
     const size_t n = (size_t)h->N, pb = sizeof(T) * n, pd = sizeof(D) * n;
     Engine<D> *E = (Engine<D> *)A->eng;
     if (!E) {
         E = new Engine<D>();
         A->eng = E;
+        A->eng64 = sizeof(D) == sizeof(double);
     }
     E->nx = h->grid.nx; E->ny = h->grid.ny; E->N = h->N; E->st = h->stream; E->nb = blocks_for(h->N);
     E->err = cudaSuccess;
@@ -937,7 +1141,8 @@ template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, 
     // seed: dL/dphi at the final step, every other component zero
     D *lam = (D *)A->lam;
     cudaMemsetAsync(lam, 0, pd * NSTATE, h->stream);
-    cudaMemcpyAsync(lam + 18 * n, seed, pd, cudaMemcpyHostToDevice, h->stream);
+    std::vector<D> seed_t(seed, seed + n);
+    cudaMemcpyAsync(lam + 18 * n, seed_t.data(), pd, cudaMemcpyHostToDevice, h->stream);
     cudaStreamSynchronize(h->stream);
     Recorder<D> R(*E, P);
     const int nseg = (A->nsteps + A->every - 1) / A->every;
@@ -1006,8 +1211,12 @@ void lbm_internal_adjoint_free(lbm_handle *h)
     cudaFree(A->init4);
     cudaFree(A->final_state);
     cudaFree(A->lam);
-    if (A->eng) {
+    if (A->eng && A->eng64) {
         auto *E = (Engine<double> *)A->eng;
+        E->release_all();
+        delete E;
+    } else if (A->eng) {
+        auto *E = (Engine<float> *)A->eng;
         E->release_all();
         delete E;
     }
