@@ -8,9 +8,10 @@
 // shifts) and scalings by the differentiable parameters kappa, beta, M and
 // 1/tau_f -- each executed by a small kernel and recorded.  Each operation
 // has a hand-written vector-Jacobian product; the reverse sweep applies them
-// in reverse order.  The operations are executed in groups: the pointwise
-// operations between two layers of stencils run as one kernel that applies
-// them node by node, so a step costs a few dozen launches in each direction.  Across steps, sqrt(N)-style checkpointing keeps every
+// in reverse order.  The operations are executed a level at a time: the
+// stencils and pointwise operations between two layers of stencils run as
+// one kernel that applies them node by node, so a step costs one launch per
+// level in each direction.  Across steps, sqrt(N)-style checkpointing keeps every
 // k-th state, regenerates a segment with the fused forward kernels and
 // reverses it step by step.  Periodic axes, FP64 or FP32 populations; the
 // reverse sweep runs in the handle's arithmetic type, with the parameter
@@ -55,48 +56,39 @@ struct Op {
     int st = -1;
 };
 
+
+// ---------------------------------------------------------------------------
+// Execution of a recorded tape.  A plane's level counts the stencils on the
+// longest path from the leaves to it.  Forward, one kernel per level: a
+// thread takes a node, gathers the level's stencils from the (complete)
+// planes of lower levels, then applies the level's pointwise operations in
+// tape order.  Reverse, one kernel per level from the top: a thread takes a
+// node, gathers the transposes of the next level's stencils from their
+// (complete) output adjoints, then applies the vector-Jacobian products of
+// the level's pointwise operations in reverse tape order.  Values made and
+// used inside a kernel live in per-thread shared-memory slots, allocated by
+// lifetime, and so do the adjoints accumulated inside a reverse kernel;
+// other planes go through global memory.  The first contribution to each
+// adjoint stores instead of adding, so nothing needs clearing.
+// ---------------------------------------------------------------------------
 int blocks_for(long long N) { return (int)std::min<long long>((N + NTH - 1) / NTH, 4096); }
 
 #define GRID_LOOP(k, N) for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < (N); \
                              k += (long long)gridDim.x * blockDim.x)
 
-// ---------------------------------------------------------------------------
-// Execution of a recorded tape.  A plane's level counts the stencils on the
-// longest path from the leaves to it.  The forward pass runs the pointwise
-// operations of level 0, then for each level the stencils producing it and
-// the pointwise operations of that level; every group is one kernel, and a
-// pointwise group applies its operations node by node in tape order.  The
-// reverse pass runs the groups backwards, a pointwise group in reverse tape
-// order per node.  The first contribution to each adjoint plane (in that
-// order) stores instead of adding, so no adjoint plane needs clearing.
-// ---------------------------------------------------------------------------
-// One operation of a pointwise group, as the group kernels run it.  Values
-// made and used inside the group live in per-thread slots of shared memory
-// (allocated by their lifetimes); values needed by other groups or by the
-// reverse sweep also go to their global planes.  In the reverse sweep the
-// adjoints of values made inside the group accumulate in slots, and only
-// the adjoints of inputs from outside the group go to global planes.
-template <typename T> struct VOp {
-    int k, nin, param, live;
+template <typename T> struct VOp {   // one operation as the level kernels run it
+    int k, nin, param, live, st;
     unsigned fint;          // bit i: input i is read from forward slot fslot[i]
     unsigned rint;          // bit i: the adjoint of input i goes to reverse slot rslot[i]
     unsigned rassign;       // bit i: that contribution (slot or global) stores instead of adding
     short fslot[MAXIN], rslot[MAXIN];
-    short fout, rout;       // forward slot of the output; reverse slot with its in-group adjoint (-1: none)
-    T *out;                 // global plane of the output (null: not needed outside the group)
+    short fout, rout;       // forward slot of the output; reverse slot with its in-kernel adjoint (-1: none)
+    T *out;                 // global plane of the output (null: not needed outside its kernel)
     const T *in[MAXIN];     // global planes of the inputs' values
     T c[MAXIN];
     T c0;                   // OP_LIN constant; OP_SCALEP parameter value
     const T *aout;          // global adjoint of the output (null: none reaches it from outside)
-    T *ain[MAXIN];          // global adjoints of the inputs from outside the group
-};
-template <typename T> struct DSt {   // one stencil operation
-    int st;
-    unsigned assign;
-    T *out;
-    const T *in;
-    const T *aout;
-    T *ain;
+    T *ain[MAXIN];          // global adjoints of the inputs from outside the kernel
 };
 struct DStencil {
     int n;
@@ -129,13 +121,10 @@ template <typename T> __global__ void __launch_bounds__(NTH) kk_leaves(Leaves<T>
     }
 }
 
-constexpr int NTV = 128;   // threads of a pointwise-group kernel
+constexpr int NTV = 128;   // threads of a level kernel
 
-// slot q of this thread
-template <typename T> __device__ __forceinline__ T &slot_ref(T *sl, int q) { return sl[q * NTV + threadIdx.x]; }
-
-// Copy n bytes of records (8-byte aligned) into shared memory; every thread
-// of the block takes part and the block waits for the copy.
+// Copy records (8-byte aligned) into shared memory; every thread of the
+// block takes part and the block waits for the copy.
 __device__ __forceinline__ void stage_records(void *dst, const void *src, size_t bytes)
 {
     unsigned long long *d = reinterpret_cast<unsigned long long *>(dst);
@@ -144,68 +133,87 @@ __device__ __forceinline__ void stage_records(void *dst, const void *src, size_t
     __syncthreads();
 }
 
-// Ask for the global inputs of a later operation at node k ahead of use.
-// Only planes that no kernel writes while this one runs are requested: the
-// forward values from outside the group and, in the reverse sweep, the
-// adjoints reaching the group from outside.
-constexpr int VM_AHEAD = 4;
-__device__ __forceinline__ void prefetch_l1(const void *p)
-{
-    asm volatile("prefetch.global.L1 [%0];\n" ::"l"(p));
-}
-template <typename T> __device__ __forceinline__ void prefetch_fwd(const VOp<T> &op, long long k)
-{
-    for (int i = 0; i < op.nin; ++i)
-        if (!((op.fint >> i) & 1u)) prefetch_l1(op.in[i] + k);
-}
-template <typename T> __device__ __forceinline__ void prefetch_rev(const VOp<T> &op, long long k)
-{
-    if (!op.live) return;
-    if (op.aout) prefetch_l1(op.aout + k);
-    if (op.k != OP_LIN && op.k != OP_SQRT) prefetch_l1(op.in[0] + k);
-    if (op.k == OP_MUL || op.k == OP_DIV) prefetch_l1(op.in[1] + k);
-    if (op.k == OP_SQRT) prefetch_l1(op.out + k);
-}
+// Shared memory of a level kernel: the stencil table, the kernel's
+// operation records, then the slots (NTV values per slot).
+template <typename T> struct VmLayout {
+    static __host__ __device__ size_t tab_bytes(int ntab) { return (sizeof(DStencil) * (size_t)ntab + 15) / 16 * 16; }
+    static __host__ __device__ size_t ops_bytes(int nops) { return (sizeof(VOp<T>) * (size_t)nops + 15) / 16 * 16; }
+    static __host__ __device__ size_t bytes(int ntab, int nops, int slots)
+    {
+        return tab_bytes(ntab) + ops_bytes(nops) + sizeof(T) * NTV * (size_t)slots;
+    }
+};
 
-// Shared memory of a pointwise-group kernel: the group's operation records,
-// then the value or adjoint slots, NTV per slot.
-template <typename T> __host__ __device__ constexpr size_t vm_ops_bytes(int nops)
+template <typename T> __device__ __forceinline__ T &slot_ref(T *sl, int q) { return sl[q * NTV + threadIdx.x]; }
+
+// sum_i w_i src(x + sg dx_i, y + sg dy_i) over the n <= NB taps of S on the
+// periodic grid, every tap requested before the first is used (|d| <= 5).
+template <typename T, int NB>
+__device__ __forceinline__ T taps(const DStencil &S, const T *src, int x, int y, int sg, int nx, int ny)
 {
-    return (sizeof(VOp<T>) * (size_t)nops + 15) / 16 * 16;
+    const int n = S.n;
+    T v[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        if (i < n) {
+            int xx = x + sg * S.dx[i], yy = y + sg * S.dy[i];
+            xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+            yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+            v[i] = src[(long long)yy * nx + xx];
+        }
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+        if (i < n) acc += (T)S.w[i] * v[i];
+    return acc;
+}
+template <typename T>
+__device__ __forceinline__ T gather(const DStencil &S, const T *src, int x, int y, int sg, int nx, int ny)
+{
+    return S.n <= 1 ? taps<T, 1>(S, src, x, y, sg, nx, ny)
+                    : (S.n <= 9 ? taps<T, 9>(S, src, x, y, sg, nx, ny) : taps<T, MAXST>(S, src, x, y, sg, nx, ny));
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NTV) kk_vm_fwd(const VOp<T> *__restrict__ gops, int nops, long long N)
+__global__ void __launch_bounds__(NTV) kk_vm_fwd(const DStencil *__restrict__ gtab, int ntab,
+                                                const VOp<T> *__restrict__ gops, int nops, int nx, int ny, long long N)
 {
     extern __shared__ __align__(16) unsigned char vm_raw[];
-    VOp<T> *ops = reinterpret_cast<VOp<T> *>(vm_raw);
-    T *sl = reinterpret_cast<T *>(vm_raw + vm_ops_bytes<T>(nops));
+    using Ly = VmLayout<T>;
+    DStencil *tab = reinterpret_cast<DStencil *>(vm_raw);
+    VOp<T> *ops = reinterpret_cast<VOp<T> *>(vm_raw + Ly::tab_bytes(ntab));
+    T *sl = reinterpret_cast<T *>(vm_raw + Ly::tab_bytes(ntab) + Ly::ops_bytes(nops));
+    stage_records(tab, gtab, sizeof(DStencil) * (size_t)ntab);
     stage_records(ops, gops, sizeof(VOp<T>) * (size_t)nops);
     GRID_LOOP(k, N) {
-        for (int o = 0; o < VM_AHEAD && o < nops; ++o) prefetch_fwd(ops[o], k);
+        const int y = (int)(k / nx), x = (int)(k - (long long)y * nx);
         for (int o = 0; o < nops; ++o) {
-            if (o + VM_AHEAD < nops) prefetch_fwd(ops[o + VM_AHEAD], k);
             const VOp<T> &op = ops[o];
-            const int nin = op.nin;
-            T x[MAXIN];
-#pragma unroll
-            for (int i = 0; i < MAXIN; ++i)   // every input requested before the first is used
-                if (i < nin) x[i] = ((op.fint >> i) & 1u) ? slot_ref(sl, op.fslot[i]) : op.in[i][k];
             T r;
-            switch (op.k) {
-            case OP_LIN:
-                r = op.c0;
+            if (op.k == OP_STENCIL) {
+                r = gather(tab[op.st], op.in[0], x, y, 1, nx, ny);
+            } else {
+                const int nin = op.nin;
+                T v[MAXIN];
 #pragma unroll
-                for (int i = 0; i < MAXIN; ++i)
-                    if (i < nin) r += op.c[i] * x[i];
-                break;
-            case OP_SCALEP: r = op.c0 * x[0]; break;
-            case OP_MUL: r = x[0] * x[1]; break;
-            case OP_DIV: r = x[0] / x[1]; break;
-            case OP_POW3: r = x[0] * x[0] * x[0]; break;
-            case OP_SQRT: r = sqrt(x[0]); break;
-            case OP_CLAMP1: r = x[0] < T(-1) ? T(-1) : (x[0] > T(1) ? T(1) : x[0]); break;
-            default: r = T(1) / x[0]; break;   // OP_RECIP
+                for (int i = 0; i < MAXIN; ++i)   // every input requested before the first is used
+                    if (i < nin) v[i] = ((op.fint >> i) & 1u) ? slot_ref(sl, op.fslot[i]) : op.in[i][k];
+                switch (op.k) {
+                case OP_LIN:
+                    r = op.c0;
+#pragma unroll
+                    for (int i = 0; i < MAXIN; ++i)
+                        if (i < nin) r += op.c[i] * v[i];
+                    break;
+                case OP_SCALEP: r = op.c0 * v[0]; break;
+                case OP_MUL: r = v[0] * v[1]; break;
+                case OP_DIV: r = v[0] / v[1]; break;
+                case OP_POW3: r = v[0] * v[0] * v[0]; break;
+                case OP_SQRT: r = sqrt(v[0]); break;
+                case OP_CLAMP1: r = v[0] < T(-1) ? T(-1) : (v[0] > T(1) ? T(1) : v[0]); break;
+                default: r = T(1) / v[0]; break;   // OP_RECIP
+                }
             }
             if (op.fout >= 0) slot_ref(sl, op.fout) = r;
             if (op.out) op.out[k] = r;
@@ -214,48 +222,55 @@ __global__ void __launch_bounds__(NTV) kk_vm_fwd(const VOp<T> *__restrict__ gops
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NTV) kk_vm_rev(const VOp<T> *__restrict__ gops, int nops, double *pgrad, long long N)
+__global__ void __launch_bounds__(NTV) kk_vm_rev(const DStencil *__restrict__ gtab, int ntab,
+                                                const VOp<T> *__restrict__ gops, int nops, double *pgrad, int nx, int ny,
+                                                long long N)
 {
     extern __shared__ __align__(16) unsigned char vm_raw[];
-    VOp<T> *ops = reinterpret_cast<VOp<T> *>(vm_raw);
-    T *sl = reinterpret_cast<T *>(vm_raw + vm_ops_bytes<T>(nops));
+    using Ly = VmLayout<T>;
+    DStencil *tab = reinterpret_cast<DStencil *>(vm_raw);
+    VOp<T> *ops = reinterpret_cast<VOp<T> *>(vm_raw + Ly::tab_bytes(ntab));
+    T *sl = reinterpret_cast<T *>(vm_raw + Ly::tab_bytes(ntab) + Ly::ops_bytes(nops));
+    stage_records(tab, gtab, sizeof(DStencil) * (size_t)ntab);
     stage_records(ops, gops, sizeof(VOp<T>) * (size_t)nops);
     double pacc[NPARAM] = {};
     GRID_LOOP(k, N) {
-        for (int o = nops - 1; o >= 0 && o >= nops - VM_AHEAD; --o) prefetch_rev(ops[o], k);
+        const int y = (int)(k / nx), x = (int)(k - (long long)y * nx);
         for (int o = nops - 1; o >= 0; --o) {
-            if (o - VM_AHEAD >= 0) prefetch_rev(ops[o - VM_AHEAD], k);
             const VOp<T> &op = ops[o];
             if (!op.live) continue;
-            // forward values the product needs, requested first
-            T x = T(0), y = T(0), z = T(0);
             const int kind = op.k;
-            if (kind != OP_LIN && kind != OP_SQRT) x = op.in[0][k];
-            if (kind == OP_MUL || kind == OP_DIV) y = op.in[1][k];
-            if (kind == OP_SQRT) z = op.out[k];
-            T g = op.aout ? op.aout[k] : T(0);
-            if (op.rout >= 0) g += slot_ref(sl, op.rout);
             T ci[MAXIN];
             int nc = 1;
-            switch (kind) {
-            case OP_LIN:
-                nc = op.nin;
+            if (kind == OP_STENCIL) {   // transpose: gathered from the output adjoint around the node
+                ci[0] = gather(tab[op.st], op.aout, x, y, -1, nx, ny);
+            } else {
+                T a = T(0), b = T(0), z = T(0);   // forward values the product needs, requested first
+                if (kind != OP_LIN && kind != OP_SQRT) a = op.in[0][k];
+                if (kind == OP_MUL || kind == OP_DIV) b = op.in[1][k];
+                if (kind == OP_SQRT) z = op.out[k];
+                T g = op.aout ? op.aout[k] : T(0);
+                if (op.rout >= 0) g += slot_ref(sl, op.rout);
+                switch (kind) {
+                case OP_LIN:
+                    nc = op.nin;
 #pragma unroll
-                for (int i = 0; i < MAXIN; ++i) ci[i] = op.c[i] * g;
-                break;
-            case OP_SCALEP: {
-                ci[0] = op.c0 * g;
-                const double d = (double)x * (double)g;
+                    for (int i = 0; i < MAXIN; ++i) ci[i] = op.c[i] * g;
+                    break;
+                case OP_SCALEP: {
+                    ci[0] = op.c0 * g;
+                    const double d = (double)a * (double)g;
 #pragma unroll
-                for (int q = 0; q < NPARAM; ++q) pacc[q] += q == op.param ? d : 0.0;
-                break;
-            }
-            case OP_MUL: ci[0] = y * g; ci[1] = x * g; nc = 2; break;
-            case OP_DIV: ci[0] = g / y; ci[1] = -(g * x / (y * y)); nc = 2; break;
-            case OP_POW3: ci[0] = T(3) * x * x * g; break;
-            case OP_SQRT: ci[0] = g / (T(2) * z); break;
-            case OP_CLAMP1: ci[0] = (x >= T(-1) && x <= T(1)) ? g : T(0); break;
-            default: ci[0] = -(g / (x * x)); break;   // OP_RECIP
+                    for (int q = 0; q < NPARAM; ++q) pacc[q] += q == op.param ? d : 0.0;
+                    break;
+                }
+                case OP_MUL: ci[0] = b * g; ci[1] = a * g; nc = 2; break;
+                case OP_DIV: ci[0] = g / b; ci[1] = -(g * a / (b * b)); nc = 2; break;
+                case OP_POW3: ci[0] = T(3) * a * a * g; break;
+                case OP_SQRT: ci[0] = g / (T(2) * z); break;
+                case OP_CLAMP1: ci[0] = (a >= T(-1) && a <= T(1)) ? g : T(0); break;
+                default: ci[0] = -(g / (a * a)); break;   // OP_RECIP
+                }
             }
 #pragma unroll
             for (int i = 0; i < MAXIN; ++i) {
@@ -285,56 +300,6 @@ __global__ void __launch_bounds__(NTV) kk_vm_rev(const VOp<T> *__restrict__ gops
     }
 }
 
-// sum_i w_i src(x + sg dx_i, y + sg dy_i) over the n <= NB taps of S, every
-// tap requested before the first is used (offsets |d| <= 5 < nx, ny).
-template <typename T, int NB>
-__device__ __forceinline__ T taps(const DStencil &S, const T *src, int x, int y, int sg, int nx, int ny)
-{
-    const int n = S.n;
-    T v[NB];
-#pragma unroll
-    for (int i = 0; i < NB; ++i) {
-        if (i < n) {
-            int xx = x + sg * S.dx[i], yy = y + sg * S.dy[i];
-            xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
-            yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
-            v[i] = src[(long long)yy * nx + xx];
-        }
-    }
-    T acc = T(0);
-#pragma unroll
-    for (int i = 0; i < NB; ++i)
-        if (i < n) acc += (T)S.w[i] * v[i];
-    return acc;
-}
-
-// out(x, y) = sum_k w_k in(x + dx_k, y + dy_k) on a periodic grid; the
-// transpose adds sum_k w_k aout(x - dx_k, y - dy_k) into ain.
-template <typename T>
-__global__ void __launch_bounds__(NTH) kk_st(const DSt<T> *__restrict__ gops, int nops, const DStencil *__restrict__ gtab,
-                                             int ntab, int nx, int ny, int transpose, long long N)
-{
-    extern __shared__ __align__(16) unsigned char st_raw[];
-    DStencil *tab = reinterpret_cast<DStencil *>(st_raw);
-    DSt<T> *ops = reinterpret_cast<DSt<T> *>(st_raw + sizeof(DStencil) * (size_t)ntab);
-    stage_records(tab, gtab, sizeof(DStencil) * (size_t)ntab);
-    stage_records(ops, gops, sizeof(DSt<T>) * (size_t)nops);
-    GRID_LOOP(k, N) {
-        const int y = (int)(k / nx), x = (int)(k - (long long)y * nx);
-        for (int o = 0; o < nops; ++o) {
-            const DSt<T> &op = ops[o];
-            if (transpose && !op.aout) continue;
-            const DStencil &S = tab[op.st];
-            const T *src = transpose ? op.aout : op.in;
-            const int sg = transpose ? -1 : 1;
-            const T acc = S.n <= 1 ? taps<T, 1>(S, src, x, y, sg, nx, ny)
-                        : (S.n <= 9 ? taps<T, 9>(S, src, x, y, sg, nx, ny) : taps<T, MAXST>(S, src, x, y, sg, nx, ny));
-            if (transpose) put(op.ain, k, acc, op.assign & 1u);
-            else op.out[k] = acc;
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
 // The tape engine.  Planes are kept per plane id across steps (the recorder
 // creates the same planes in the same order every step), so the schedule
@@ -356,22 +321,16 @@ template <typename T> struct Engine {
     std::vector<std::pair<int, const void *>> leaves;   // plane, source (this step)
     std::vector<char> leaf_f32;
     std::vector<std::pair<int, const T *>> seeds;       // plane, adjoint source
-    std::vector<char> flowed;                           // planes given an adjoint by run()
+    std::vector<char> flowed;                           // planes given a global adjoint by run()
     // schedule and device form
-    struct Group { bool stencil; int off, n, fslots, rslots; };
-    std::vector<Group> groups;
-    std::vector<VOp<T>> hops;
-    std::vector<DSt<T>> hsts;
-    VOp<T> *d_ops = nullptr;
-    int nbv = 1;                      // blocks of a pointwise-group kernel
-    int smem_set = 0, smem_st_set = 0;   // dynamic shared memory the group kernels are set up for
-    int ntab = 0;                        // stencils in the device table
-
-    size_t vm_bytes(int nops, int slots) const { return vm_ops_bytes<T>(nops) + sizeof(T) * NTV * (size_t)slots; }
-    size_t st_bytes(int nops) const { return sizeof(DStencil) * (size_t)ntab + sizeof(DSt<T>) * (size_t)nops; }
-    DSt<T> *d_sts = nullptr;
-    size_t cap_ops = 0, cap_sts = 0;
+    struct Group { int off, n, slots; };
+    std::vector<Group> fgroups, rgroups;                // launch order
+    std::vector<VOp<T>> hfwd, hrev;
+    VOp<T> *d_fwd = nullptr, *d_rev = nullptr;
+    size_t cap_fwd = 0, cap_rev = 0;
     DStencil *d_tab = nullptr;
+    int ntab = 0, nbv = 1;
+    int smem_set = 0;
     std::vector<Op> tape_prev;
     std::vector<std::pair<int, const T *>> seeds_prev;
     std::vector<char> seed_add;
@@ -399,15 +358,12 @@ template <typename T> struct Engine {
         val.clear();
         adj.clear();
         nval = 0;
-        if (d_pgrad) cudaFree(d_pgrad);
-        if (d_ops) cudaFree(d_ops);
-        if (d_sts) cudaFree(d_sts);
-        if (d_tab) cudaFree(d_tab);
+        void *bufs[4] = {d_pgrad, d_fwd, d_rev, d_tab};
+        for (void *b : bufs) if (b) cudaFree(b);
         d_pgrad = nullptr;
-        d_ops = nullptr;
-        d_sts = nullptr;
+        d_fwd = d_rev = nullptr;
         d_tab = nullptr;
-        cap_ops = cap_sts = 0;
+        cap_fwd = cap_rev = 0;
         tape_prev.clear();
     }
     int newplane()
@@ -482,80 +438,73 @@ template <typename T> struct Engine {
         if (err == cudaSuccess) launch();
     }
 
+    static int ncontrib(const Op &o)   // inputs an operation's product reaches
+    {
+        return o.k == OP_LIN ? o.nin : (o.k == OP_MUL || o.k == OP_DIV) ? 2 : 1;
+    }
+
     void schedule()
     {
         const int nops = (int)tape.size();
         ntab = (int)stencils.size();
-        std::vector<int> lev(nval, 0);
+        std::vector<int> lev(nval, -1), made(nval, -1);   // level of a plane (-1: leaf); op making it
         int L = 0;
-        for (const Op &o : tape) {
+        for (int t = 0; t < nops; ++t) {
+            const Op &o = tape[t];
             int l = 0;
-            for (int i = 0; i < o.nin; ++i) l = std::max(l, lev[o.in[i]]);
+            for (int i = 0; i < o.nin; ++i) l = std::max(l, std::max(lev[o.in[i]], 0));
             if (o.k == OP_STENCIL) ++l;
             lev[o.out] = l;
+            made[o.out] = t;
             L = std::max(L, l);
         }
-        // forward order: P_0, S_1, P_1, ..., S_L, P_L (tape order inside a group)
-        std::vector<std::vector<int>> pw(L + 1), sn(L + 1);
-        for (int t = 0; t < nops; ++t) (tape[t].k == OP_STENCIL ? sn : pw)[lev[tape[t].out]].push_back(t);
-        std::vector<std::pair<bool, const std::vector<int> *>> fwd;
-        for (int l = 0; l <= L; ++l) {
-            if (!sn[l].empty()) fwd.push_back({true, &sn[l]});
-            if (!pw[l].empty()) fwd.push_back({false, &pw[l]});
-        }
-        const int ng = (int)fwd.size();
-        // the pointwise group making each plane; uses outside it; values the
-        // reverse sweep reads (operands of the nonlinear products)
-        std::vector<int> pgroup(nval, -1);
-        for (int g = 0; g < ng; ++g)
-            if (!fwd[g].first) for (int t : *fwd[g].second) pgroup[tape[t].out] = g;
+        // kernel lists: forward F_l = stencils of level l, then pointwise ops
+        // of level l (tape order); reverse R_l = pointwise ops of level l, then
+        // stencils of level l + 1 (walked from the end)
+        std::vector<std::vector<int>> F(L + 1), R(L + 1);
+        for (int t = 0; t < nops; ++t)
+            if (tape[t].k == OP_STENCIL) F[lev[tape[t].out]].push_back(t);
+        for (int t = 0; t < nops; ++t)
+            if (tape[t].k != OP_STENCIL) F[lev[tape[t].out]].push_back(t);
+        for (int t = 0; t < nops; ++t)
+            if (tape[t].k != OP_STENCIL) R[lev[tape[t].out]].push_back(t);
+        for (int t = 0; t < nops; ++t)
+            if (tape[t].k == OP_STENCIL) R[lev[tape[t].out] - 1].push_back(t);
+        // a value is inside forward kernel l when made there; inside reverse
+        // kernel l when made by a pointwise op of level l (stencil outputs
+        // keep global adjoints: their transposes gather them around a node)
+        auto fin_kernel = [&](int p) { return made[p] >= 0 ? lev[p] : -1; };
+        auto rin_kernel = [&](int p) { return (made[p] >= 0 && tape[made[p]].k != OP_STENCIL) ? lev[p] : -1; };
         std::vector<char> used_out(nval, 0), needs_val(nval, 0);
-        for (int g = 0; g < ng; ++g)
-            for (int t : *fwd[g].second) {
-                const Op &o = tape[t];
-                for (int i = 0; i < o.nin; ++i)
-                    if (fwd[g].first || pgroup[o.in[i]] != g) used_out[o.in[i]] = 1;
-                if (o.k == OP_MUL || o.k == OP_DIV) needs_val[o.in[0]] = needs_val[o.in[1]] = 1;
-                if (o.k == OP_POW3 || o.k == OP_CLAMP1 || o.k == OP_RECIP || o.k == OP_SCALEP) needs_val[o.in[0]] = 1;
-                if (o.k == OP_SQRT) needs_val[o.out] = 1;
-            }
-        // reverse sweep, simulated in its execution order: which operations
-        // carry an adjoint, which planes receive a global adjoint (gw), which
-        // contributions store, and the reverse slots of each pointwise group
+        for (int t = 0; t < nops; ++t) {
+            const Op &o = tape[t];
+            for (int i = 0; i < o.nin; ++i)
+                if (o.k == OP_STENCIL || fin_kernel(o.in[i]) != lev[o.out]) used_out[o.in[i]] = 1;
+            if (o.k == OP_MUL || o.k == OP_DIV) needs_val[o.in[0]] = needs_val[o.in[1]] = 1;
+            if (o.k == OP_POW3 || o.k == OP_CLAMP1 || o.k == OP_RECIP || o.k == OP_SCALEP) needs_val[o.in[0]] = 1;
+            if (o.k == OP_SQRT) needs_val[o.out] = 1;
+        }
+        // the reverse sweep, simulated in execution order
         std::vector<char> gw(nval, 0), init(nval, 0);
         seed_add.assign(seeds.size(), 0);
         for (size_t i = 0; i < seeds.size(); ++i) {
             seed_add[i] = init[seeds[i].first];
             gw[seeds[i].first] = init[seeds[i].first] = 1;
         }
-        std::vector<VOp<T>> vop(nops);
-        std::vector<DSt<T>> sop(nops);
-        std::vector<int> rslots(ng, 0), fslots(ng, 0);
-        std::vector<int> rslotof(nval, -1);
-        for (int g = ng - 1; g >= 0; --g) {
-            const std::vector<int> &ids = *fwd[g].second;
-            if (fwd[g].first) {   // stencils: tape order per node, global adjoints
-                for (int t : ids) {
-                    const Op &o = tape[t];
-                    DSt<T> &d = sop[t];
-                    d = DSt<T>{};
-                    if (!gw[o.out]) continue;
-                    const int p = o.in[0];
-                    d.aout = (const T *)(uintptr_t)1;   // live; pointers filled below
-                    gw[p] = 1;
-                    if (!init[p]) { d.assign = 1u; init[p] = 1; }
-                }
-                continue;
-            }
+        std::vector<VOp<T>> rec(nops);
+        for (int t = 0; t < nops; ++t) {
+            rec[t] = VOp<T>{};
+            rec[t].fout = rec[t].rout = -1;
+        }
+        std::vector<int> rslots(L + 1, 0), rslotof(nval, -1);
+        for (int l = L; l >= 0; --l) {
             std::vector<int> freel;
             int top = 0;
             auto alloc = [&]() { if (!freel.empty()) { int q = freel.back(); freel.pop_back(); return q; } return top++; };
-            for (int j = (int)ids.size() - 1; j >= 0; --j) {
-                const int t = ids[j];
+            for (int j = (int)R[l].size() - 1; j >= 0; --j) {
+                const int t = R[l][j];
                 const Op &o = tape[t];
-                VOp<T> &d = vop[t];
-                d = VOp<T>{};
-                d.rout = -1;
+                VOp<T> &d = rec[t];
                 const bool inner = rslotof[o.out] >= 0;
                 if (!gw[o.out] && !inner) continue;
                 d.live = 1;
@@ -564,10 +513,9 @@ template <typename T> struct Engine {
                     freel.push_back(rslotof[o.out]);
                     rslotof[o.out] = -1;
                 }
-                const int nc = (o.k == OP_LIN) ? o.nin : (o.k == OP_MUL || o.k == OP_DIV) ? 2 : 1;
-                for (int i = 0; i < nc; ++i) {
+                for (int i = 0; i < ncontrib(o); ++i) {
                     const int p = o.in[i];
-                    if (pgroup[p] == g) {
+                    if (rin_kernel(p) == l) {
                         d.rint |= 1u << i;
                         if (rslotof[p] < 0) { rslotof[p] = alloc(); d.rassign |= 1u << i; }
                         d.rslot[i] = (short)rslotof[p];
@@ -577,67 +525,45 @@ template <typename T> struct Engine {
                     }
                 }
             }
-            rslots[g] = top;
+            rslots[l] = top;
         }
         for (int p = 0; p < nval; ++p) if (gw[p]) A(p);
         flowed = gw;
-        // forward slots, device form, groups
-        hops.clear();
-        hsts.clear();
-        groups.clear();
-        std::vector<int> fslotof(nval, -1), lastuse(nval, -1);
-        int maxslots = 0;
-        for (int g = 0; g < ng; ++g) {
-            const std::vector<int> &ids = *fwd[g].second;
-            Group G{fwd[g].first, fwd[g].first ? (int)hsts.size() : (int)hops.size(), (int)ids.size(), 0, rslots[g]};
-            if (fwd[g].first) {
-                for (int t : ids) {
-                    const Op &o = tape[t];
-                    DSt<T> d = sop[t];
-                    const bool live = d.aout != nullptr;
-                    d.st = o.st;
-                    d.out = val[o.out];
-                    d.in = val[o.in[0]];
-                    d.aout = live ? adj[o.out] : nullptr;
-                    d.ain = live ? adj[o.in[0]] : nullptr;
-                    hsts.push_back(d);
-                }
-                groups.push_back(G);
-                continue;
-            }
-            for (size_t j = 0; j < ids.size(); ++j) {
-                const Op &o = tape[ids[j]];
+        // forward slots and the rest of each record
+        std::vector<int> fslots(L + 1, 0), fslotof(nval, -1), lastuse(nval, -1);
+        for (int l = 0; l <= L; ++l) {
+            for (size_t j = 0; j < F[l].size(); ++j) {
+                const Op &o = tape[F[l][j]];
                 for (int i = 0; i < o.nin; ++i)
-                    if (pgroup[o.in[i]] == g) lastuse[o.in[i]] = (int)j;
+                    if (fin_kernel(o.in[i]) == l && o.k != OP_STENCIL) lastuse[o.in[i]] = (int)j;
             }
             std::vector<int> freel;
             int top = 0;
-            for (size_t j = 0; j < ids.size(); ++j) {
-                const int t = ids[j];
+            for (size_t j = 0; j < F[l].size(); ++j) {
+                const int t = F[l][j];
                 const Op &o = tape[t];
-                VOp<T> d = vop[t];
+                VOp<T> &d = rec[t];
                 d.k = o.k;
                 d.nin = o.nin;
                 d.param = o.param;
+                d.st = o.st;
                 for (int i = 0; i < o.nin; ++i) {
                     const int p = o.in[i];
                     d.in[i] = val[p];
                     d.c[i] = (T)o.c[i];
-                    if (pgroup[p] == g) {
+                    if (o.k != OP_STENCIL && fin_kernel(p) == l) {
                         d.fint |= 1u << i;
                         d.fslot[i] = (short)fslotof[p];
                     }
-                    if (d.live && !((d.rint >> i) & 1u) && i < ((o.k == OP_LIN) ? o.nin : (o.k == OP_MUL || o.k == OP_DIV) ? 2 : 1))
-                        d.ain[i] = adj[p];
+                    if (d.live && !((d.rint >> i) & 1u) && i < ncontrib(o)) d.ain[i] = adj[p];
                 }
                 for (int i = 0; i < o.nin; ++i) {   // inputs read for the last time free their slots
                     const int p = o.in[i];
-                    if (pgroup[p] == g && lastuse[p] == (int)j && fslotof[p] >= 0) {
+                    if (o.k != OP_STENCIL && fin_kernel(p) == l && lastuse[p] == (int)j && fslotof[p] >= 0) {
                         freel.push_back(fslotof[p]);
                         fslotof[p] = -1;
                     }
                 }
-                d.fout = -1;
                 if (lastuse[o.out] > (int)j) {
                     int q;
                     if (!freel.empty()) { q = freel.back(); freel.pop_back(); } else q = top++;
@@ -647,26 +573,31 @@ template <typename T> struct Engine {
                 d.out = (used_out[o.out] || needs_val[o.out]) ? val[o.out] : nullptr;
                 d.c0 = o.k == OP_SCALEP ? (T)pval[o.param] : (T)o.c0;
                 d.aout = (d.live && gw[o.out]) ? adj[o.out] : nullptr;
-                hops.push_back(d);
             }
-            G.fslots = top;
-            maxslots = std::max(maxslots, std::max(top, rslots[g]));
-            groups.push_back(G);
+            fslots[l] = top;
         }
-        (void)maxslots;
-        int smem = 0, smem_st = 0;
-        for (const Group &G : groups) {
-            if (G.stencil) smem_st = std::max(smem_st, (int)st_bytes(G.n));
-            else smem = std::max(smem, (int)std::max(vm_bytes(G.n, G.fslots), vm_bytes(G.n, G.rslots)));
+        // device form in launch order
+        hfwd.clear();
+        hrev.clear();
+        fgroups.clear();
+        rgroups.clear();
+        int smem = 0;
+        for (int l = 0; l <= L; ++l) {
+            if (F[l].empty()) continue;
+            fgroups.push_back({(int)hfwd.size(), (int)F[l].size(), fslots[l]});
+            for (int t : F[l]) hfwd.push_back(rec[t]);
+            smem = std::max(smem, (int)VmLayout<T>::bytes(ntab, (int)F[l].size(), fslots[l]));
+        }
+        for (int l = L; l >= 0; --l) {
+            if (R[l].empty()) continue;
+            rgroups.push_back({(int)hrev.size(), (int)R[l].size(), rslots[l]});
+            for (int t : R[l]) hrev.push_back(rec[t]);
+            smem = std::max(smem, (int)VmLayout<T>::bytes(ntab, (int)R[l].size(), rslots[l]));
         }
         if (smem > smem_set) {
             check(cudaFuncSetAttribute(kk_vm_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             check(cudaFuncSetAttribute(kk_vm_rev<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             smem_set = smem;
-        }
-        if (smem_st > smem_st_set) {
-            check(cudaFuncSetAttribute(kk_st<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_st));
-            smem_st_set = smem_st;
         }
         nbv = (int)std::min<long long>((N + NTV - 1) / NTV, 8192);
         upload();
@@ -676,6 +607,7 @@ template <typename T> struct Engine {
 
     void upload()
     {
+        check(cudaStreamSynchronize(st));   // earlier kernels may still read the old records
         if (!d_tab) {
             std::vector<DStencil> tab(stencils.size());
             for (size_t i = 0; i < stencils.size(); ++i) {
@@ -686,27 +618,21 @@ template <typename T> struct Engine {
                     tab[i].w[j] = stencils[i].w[j];
                 }
             }
-            ntab = (int)tab.size();
             check(cudaMalloc((void **)&d_tab, sizeof(DStencil) * tab.size()));
             if (err == cudaSuccess)
                 check(cudaMemcpy(d_tab, tab.data(), sizeof(DStencil) * tab.size(), cudaMemcpyHostToDevice));
         }
-        if (hops.size() > cap_ops) {
-            if (d_ops) cudaFree(d_ops);
-            cap_ops = hops.size();
-            check(cudaMalloc((void **)&d_ops, sizeof(VOp<T>) * cap_ops));
-        }
-        if (hsts.size() > cap_sts) {
-            if (d_sts) cudaFree(d_sts);
-            cap_sts = hsts.size();
-            check(cudaMalloc((void **)&d_sts, sizeof(DSt<T>) * cap_sts));
-        }
-        // the previous step's kernels may still read the old tape
-        check(cudaStreamSynchronize(st));
-        if (err == cudaSuccess && !hops.empty())
-            check(cudaMemcpy(d_ops, hops.data(), sizeof(VOp<T>) * hops.size(), cudaMemcpyHostToDevice));
-        if (err == cudaSuccess && !hsts.empty())
-            check(cudaMemcpy(d_sts, hsts.data(), sizeof(DSt<T>) * hsts.size(), cudaMemcpyHostToDevice));
+        auto put_array = [&](std::vector<VOp<T>> &h, VOp<T> *&d, size_t &cap) {
+            if (h.size() > cap) {
+                if (d) cudaFree(d);
+                cap = h.size();
+                check(cudaMalloc((void **)&d, sizeof(VOp<T>) * cap));
+            }
+            if (err == cudaSuccess && !h.empty())
+                check(cudaMemcpy(d, h.data(), sizeof(VOp<T>) * h.size(), cudaMemcpyHostToDevice));
+        };
+        put_array(hfwd, d_fwd, cap_fwd);
+        put_array(hrev, d_rev, cap_rev);
     }
 
     // The kernels of one forward and reverse sweep of the scheduled tape.
@@ -722,12 +648,9 @@ template <typename T> struct Engine {
             }
             kk_leaves<T><<<nb, NTH, 0, st>>>(Lv, N);
         }
-        for (const Group &G : groups) {
-            if (G.stencil)
-                kk_st<T><<<nb, NTH, st_bytes(G.n), st>>>(d_sts + G.off, G.n, d_tab, ntab, nx, ny, 0, N);
-            else
-                kk_vm_fwd<T><<<nbv, NTV, vm_bytes(G.n, G.fslots), st>>>(d_ops + G.off, G.n, N);
-        }
+        for (const Group &G : fgroups)
+            kk_vm_fwd<T><<<nbv, NTV, VmLayout<T>::bytes(ntab, G.n, G.slots), st>>>(d_tab, ntab, d_fwd + G.off, G.n,
+                                                                                   nx, ny, N);
         for (size_t b = 0; b < seeds.size(); b += MAXLEAF) {
             Leaves<T> Lv{};
             Lv.n = (int)std::min<size_t>(MAXLEAF, seeds.size() - b);
@@ -738,13 +661,9 @@ template <typename T> struct Engine {
             }
             kk_leaves<T><<<nb, NTH, 0, st>>>(Lv, N);
         }
-        for (int g = (int)groups.size() - 1; g >= 0; --g) {
-            const Group &G = groups[g];
-            if (G.stencil)
-                kk_st<T><<<nb, NTH, st_bytes(G.n), st>>>(d_sts + G.off, G.n, d_tab, ntab, nx, ny, 1, N);
-            else
-                kk_vm_rev<T><<<nbv, NTV, vm_bytes(G.n, G.rslots), st>>>(d_ops + G.off, G.n, d_pgrad, N);
-        }
+        for (const Group &G : rgroups)
+            kk_vm_rev<T><<<nbv, NTV, VmLayout<T>::bytes(ntab, G.n, G.slots), st>>>(d_tab, ntab, d_rev + G.off, G.n,
+                                                                                   d_pgrad, nx, ny, N);
         check(cudaGetLastError());
     }
 
