@@ -1136,8 +1136,8 @@ struct PicardRow {
 // s_phi holds phi from (x0 - 4, y0 - 2) with row stride SP; s_p, s_ux, s_uy
 // hold p_hat, u^k from (x0 - 2, y0 - 1) with row stride SA; s_mu, s_gx, s_gy
 // are (TX + 4) x (TY + 2) work arrays.
-// jf(ly, lx, gidx, jx, jy) returns j at tile row ly, column pair lx (global
-// index gidx).
+// jf(i, ly, lx, gidx, jx, jy) returns j at row i of the thread's strip (tile
+// row ly), column pair lx (global index gidx).
 template <int TX, int TY, int NT, int VR1, int VR2, int SP, int SA, typename JF>
 __device__ __forceinline__ void picard_strips_body(const KP<float> &P, const float *s_phi, const float *s_p,
                                                    const float *s_ux, const float *s_uy, float *s_mu, float *s_gx,
@@ -1230,7 +1230,7 @@ __device__ __forceinline__ void picard_strips_body(const KP<float> &P, const flo
                 const float2 hh = mul2(f2(0.5f), ir);
                 const long long gidx = (long long)Y * P.nx + X;
                 float2 jxv, jyv;
-                jf(r0 + i, lx, gidx, jxv, jyv);
+                jf(i, r0 + i, lx, gidx, jxv, jyv);
                 *reinterpret_cast<float2 *>(&uox[gidx]) = fma2(Fx, hh, jxv);
                 *reinterpret_cast<float2 *>(&uoy[gidx]) = fma2(Fy, hh, jyv);
             }
@@ -1262,7 +1262,7 @@ k_picard_strips(KP<float> P, const float *__restrict__ phi, const float *__restr
     load_tile<float, WA, HA>(s_uy, uky, x0 - 2, y0 - 1, P, true);
     tiles_ready();
     picard_strips_body<TX, TY, NT, VR1, VR2, WP, WA>(P, s_phi, s_p, s_ux, s_uy, s_mu, s_gx, s_gy, x0, y0,
-                                                     [&](int, int, long long gidx, float2 &a, float2 &b) {
+                                                     [&](int, int, int, long long gidx, float2 &a, float2 &b) {
                                                          a = *reinterpret_cast<const float2 *>(&jx[gidx]);
                                                          b = *reinterpret_cast<const float2 *>(&jy[gidx]);
                                                      },
@@ -1481,14 +1481,33 @@ k_picard_tma(const __grid_constant__ TmaMaps tm, KP<float> P, const float *__res
     const float *src[4] = {phi, phat, ukx, uky};
     int x0, y0;
     tile_origin(TX, TY, x0, y0, P);
-    if (!tile.load(P, tm, src, 12u, x0 - 4, y0 - 2, err)) return;
+    const bool by_tma = tile.issue(P, tm, src, 12u, x0 - 4, y0 - 2);
+    // j of this thread's output strip (one strip per thread), requested while
+    // the windows arrive
+    static_assert((TX / 2) * (TY / VR2) == NT, "one output strip per thread");
+    float2 pjx[VR2], pjy[VR2];
+    {
+        const int lx = 2 * ((int)threadIdx.x % (TX / 2)), r0 = ((int)threadIdx.x / (TX / 2)) * VR2;
+        const int X = x0 + lx;
+#pragma unroll
+        for (int i = 0; i < VR2; ++i) {
+            const int Y = y0 + r0 + i;
+            pjx[i] = pjy[i] = f2(0.0f);
+            if (X < P.nx && Y < P.ny) {
+                const long long gidx = (long long)Y * P.nx + X;
+                pjx[i] = __ldg(reinterpret_cast<const float2 *>(&jx[gidx]));
+                pjy[i] = __ldg(reinterpret_cast<const float2 *>(&jy[gidx]));
+            }
+        }
+    }
+    if (!tile.wait(by_tma, err)) return;
     const float *st = tile.win;
     // p_hat and u^k from (x0 - 2, y0 - 1): one row and two columns into their windows
     picard_strips_body<TX, TY, NT, VR1, VR2, BW, BW>(
         P, st, st + FS + BW + 2, st + 2 * FS + BW + 2, st + 3 * FS + BW + 2, s_mu, s_gx, s_gy, x0, y0,
-        [&](int, int, long long gidx, float2 &a, float2 &b) {
-            a = *reinterpret_cast<const float2 *>(&jx[gidx]);
-            b = *reinterpret_cast<const float2 *>(&jy[gidx]);
+        [&](int i, int, int, long long, float2 &a, float2 &b) {
+            a = pjx[i];
+            b = pjy[i];
         },
         uox, uoy);
 }
