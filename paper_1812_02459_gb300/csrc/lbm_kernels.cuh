@@ -986,10 +986,12 @@ __device__ __forceinline__ void sts2(float *s, int i, float2 v) { *reinterpret_c
 // k_rk_stage: each thread covers a column pair over VR1 / VR2 / VR3 rows of
 // the mu / J / divergence regions, holding the y-neighbours in registers.
 // s_psi holds psi from (x0 - 6, y0 - 6) with row stride SW.
-template <int TX, int TY, int NT, int VR1, int VR2, int VR3, int SW>
+// pb(i, gidx) returns phi_bar at row i of the thread's output strip (global
+// index gidx); it is called only when a != 0.
+template <int TX, int TY, int NT, int VR1, int VR2, int VR3, int SW, typename PB>
 __device__ __forceinline__ void rk_strips_body(const KP<float> &P, const float *s_psi, float *s_mu, float *s_jx,
-                                               float *s_jy, int x0, int y0, const float *__restrict__ phibar,
-                                               float *__restrict__ out, float a, float b)
+                                               float *s_jy, int x0, int y0, PB &&pb, float *__restrict__ out, float a,
+                                               float b)
 {
     using G = RKGeom<TX, TY>;
     constexpr int W4 = G::W4, H4 = G::H4, W2 = G::W2, H2 = G::H2;
@@ -1080,7 +1082,7 @@ __device__ __forceinline__ void rk_strips_body(const KP<float> &P, const float *
                 const float2 v = lds2(s_psi, (r0 + 6 + i) * SW + lx + 6);
                 const long long gidx = (long long)Y * P.nx + X;
                 float2 r = mul2(bb, add2(v, L));
-                if (a != 0.0f) r = fma2(aa, *reinterpret_cast<const float2 *>(&phibar[gidx]), r);
+                if (a != 0.0f) r = fma2(aa, pb(i, gidx), r);
                 *reinterpret_cast<float2 *>(&out[gidx]) = r;
             }
         }
@@ -1102,7 +1104,9 @@ k_rk_strips(KP<float> P, const float *__restrict__ psi, const float *__restrict_
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     load_tile<float, W6, H6>(s_psi, psi, x0 - 6, y0 - 6, P, false);
     tiles_ready();
-    rk_strips_body<TX, TY, NT, VR1, VR2, VR3, W6>(P, s_psi, s_mu, s_jx, s_jy, x0, y0, phibar, out, a, b);
+    rk_strips_body<TX, TY, NT, VR1, VR2, VR3, W6>(
+        P, s_psi, s_mu, s_jx, s_jy, x0, y0,
+        [&](int, long long gidx) { return *reinterpret_cast<const float2 *>(&phibar[gidx]); }, out, a, b);
 }
 
 // Pass 3 for FP32 on grids of even width, same result as k_picard: each
@@ -1447,8 +1451,25 @@ k_rk_tma(const __grid_constant__ TmaMaps tm, KP<float> P, const float *__restric
     const float *src[1] = {psi};
     int x0, y0;
     tile_origin(TX, TY, x0, y0, P);
-    if (!tile.load(P, tm, src, 0u, x0 - 8, y0 - 6, err)) return;
-    rk_strips_body<TX, TY, NT, VR1, VR2, VR3, T::BW>(P, tile.win + 2, s_mu, s_jx, s_jy, x0, y0, phibar, out, a, b);
+    const bool by_tma = tile.issue(P, tm, src, 0u, x0 - 8, y0 - 6);
+    // phi_bar of this thread's output strip (one strip per thread), requested
+    // while the window arrives
+    static_assert((TX / 2) * (TY / VR3) == NT, "one output strip per thread");
+    float2 pbv[VR3];
+#pragma unroll
+    for (int i = 0; i < VR3; ++i) pbv[i] = f2(0.0f);
+    if (a != 0.0f) {
+        const int lx = 2 * ((int)threadIdx.x % (TX / 2)), r0 = ((int)threadIdx.x / (TX / 2)) * VR3;
+        const int X = x0 + lx;
+#pragma unroll
+        for (int i = 0; i < VR3; ++i) {
+            const int Y = y0 + r0 + i;
+            if (X < P.nx && Y < P.ny) pbv[i] = __ldg(reinterpret_cast<const float2 *>(&phibar[(long long)Y * P.nx + X]));
+        }
+    }
+    if (!tile.wait(by_tma, err)) return;
+    rk_strips_body<TX, TY, NT, VR1, VR2, VR3, T::BW>(P, tile.win + 2, s_mu, s_jx, s_jy, x0, y0,
+                                                     [&](int i, long long) { return pbv[i]; }, out, a, b);
 }
 
 // Picard sweep with TMA staging, one CTA per TX x TY tile: windows
