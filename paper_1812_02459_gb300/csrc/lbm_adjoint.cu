@@ -109,13 +109,16 @@ template <typename T> __device__ __forceinline__ void put(T *p, long long k, T v
     else p[k] += v;
 }
 
-template <typename T> __global__ void __launch_bounds__(NTH) kk_leaves(Leaves<T> L, long long N)
+// For B consecutive steps: dst[i][b N + k] (op)= src[i][b sstride + k].
+template <typename T>
+__global__ void __launch_bounds__(NTH) kk_leaves(Leaves<T> L, long long N, int B, long long sstride)
 {
-    GRID_LOOP(k, N) {
+    GRID_LOOP(k, N * B) {
+        const long long b = k / N, s = b * sstride + (k - b * N);
         for (int i = 0; i < L.n; ++i) {
             T v = T(0);
             if (!((L.zero >> i) & 1u))
-                v = ((L.f32 >> i) & 1u) ? (T)((const float *)L.src[i])[k] : ((const T *)L.src[i])[k];
+                v = ((L.f32 >> i) & 1u) ? (T)((const float *)L.src[i])[s] : ((const T *)L.src[i])[s];
             put(L.dst[i], k, v, !((L.add >> i) & 1u));
         }
     }
@@ -177,8 +180,10 @@ __device__ __forceinline__ T gather(const DStencil &S, const T *src, int x, int 
 
 template <typename T>
 __global__ void __launch_bounds__(NTV) kk_vm_fwd(const DStencil *__restrict__ gtab, int ntab,
-                                                const VOp<T> *__restrict__ gops, int nops, int nx, int ny, long long N)
+                                                const VOp<T> *__restrict__ gops, int nops, int nx, int ny, long long N,
+                                                long long Ntot)
 {
+    // Ntot = B N nodes of B consecutive steps: value planes hold B steps
     extern __shared__ __align__(16) unsigned char vm_raw[];
     using Ly = VmLayout<T>;
     DStencil *tab = reinterpret_cast<DStencil *>(vm_raw);
@@ -186,13 +191,14 @@ __global__ void __launch_bounds__(NTV) kk_vm_fwd(const DStencil *__restrict__ gt
     T *sl = reinterpret_cast<T *>(vm_raw + Ly::tab_bytes(ntab) + Ly::ops_bytes(nops));
     stage_records(tab, gtab, sizeof(DStencil) * (size_t)ntab);
     stage_records(ops, gops, sizeof(VOp<T>) * (size_t)nops);
-    GRID_LOOP(k, N) {
-        const int y = (int)(k / nx), x = (int)(k - (long long)y * nx);
+    GRID_LOOP(k, Ntot) {
+        const long long base = (k / N) * N, kk = k - base;
+        const int y = (int)(kk / nx), x = (int)(kk - (long long)y * nx);
         for (int o = 0; o < nops; ++o) {
             const VOp<T> &op = ops[o];
             T r;
             if (op.k == OP_STENCIL) {
-                r = gather(tab[op.st], op.in[0], x, y, 1, nx, ny);
+                r = gather(tab[op.st], op.in[0] + base, x, y, 1, nx, ny);
             } else {
                 const int nin = op.nin;
                 T v[MAXIN];
@@ -224,8 +230,9 @@ __global__ void __launch_bounds__(NTV) kk_vm_fwd(const DStencil *__restrict__ gt
 template <typename T>
 __global__ void __launch_bounds__(NTV) kk_vm_rev(const DStencil *__restrict__ gtab, int ntab,
                                                 const VOp<T> *__restrict__ gops, int nops, double *pgrad, int nx, int ny,
-                                                long long N)
+                                                long long N, long long voff)
 {
+    // the forward values of the step are at offset voff in the value planes
     extern __shared__ __align__(16) unsigned char vm_raw[];
     using Ly = VmLayout<T>;
     DStencil *tab = reinterpret_cast<DStencil *>(vm_raw);
@@ -246,9 +253,9 @@ __global__ void __launch_bounds__(NTV) kk_vm_rev(const DStencil *__restrict__ gt
                 ci[0] = gather(tab[op.st], op.aout, x, y, -1, nx, ny);
             } else {
                 T a = T(0), b = T(0), z = T(0);   // forward values the product needs, requested first
-                if (kind != OP_LIN && kind != OP_SQRT) a = op.in[0][k];
-                if (kind == OP_MUL || kind == OP_DIV) b = op.in[1][k];
-                if (kind == OP_SQRT) z = op.out[k];
+                if (kind != OP_LIN && kind != OP_SQRT) a = op.in[0][voff + k];
+                if (kind == OP_MUL || kind == OP_DIV) b = op.in[1][voff + k];
+                if (kind == OP_SQRT) z = op.out[voff + k];
                 T g = op.aout ? op.aout[k] : T(0);
                 if (op.rout >= 0) g += slot_ref(sl, op.rout);
                 switch (kind) {
@@ -311,8 +318,10 @@ template <typename T> struct Engine {
     long long N = 0;
     cudaStream_t st = nullptr;
     cudaError_t err = cudaSuccess;
-    std::vector<T *> val, adj;        // by plane id, persistent
+    std::vector<T *> val, adj;        // by plane id, persistent; a value plane holds Bcap steps
     int nval = 0;
+    int Bwant = 1, Bcap = 0;          // steps wanted in one forward batch; steps the value planes hold
+    long long leaf_stride = 0;        // elements between two consecutive steps' leaf sources
     std::vector<Op> tape;
     std::vector<Stencil> stencils;
     double pval[NPARAM]{};
@@ -358,6 +367,7 @@ template <typename T> struct Engine {
         val.clear();
         adj.clear();
         nval = 0;
+        Bcap = 0;
         void *bufs[4] = {d_pgrad, d_fwd, d_rev, d_tab};
         for (void *b : bufs) if (b) cudaFree(b);
         d_pgrad = nullptr;
@@ -366,13 +376,29 @@ template <typename T> struct Engine {
         cap_fwd = cap_rev = 0;
         tape_prev.clear();
     }
-    int newplane()
+    int newplane()   // value planes are allocated by schedule(), once the batch size is known
     {
         if (nval == (int)val.size()) {
-            val.push_back(alloc_plane());
+            val.push_back(nullptr);
             adj.push_back(nullptr);
         }
         return nval++;
+    }
+    // Value planes for B steps each: B is Bwant, or fewer if that would take
+    // more than a quarter of the free device memory (16 GB at most).
+    void size_values()
+    {
+        size_t fr = 0, tot = 0;
+        check(cudaMemGetInfo(&fr, &tot));
+        const double per_step = (double)sizeof(T) * (double)N * (double)nval;
+        const double budget = std::min((double)fr / 4.0, 16e9);
+        const int B = std::max(1, std::min(Bwant, (int)(budget / std::max(per_step, 1.0))));
+        if (B > Bcap) {
+            for (T *&p : val) if (p) { cudaFree(p); p = nullptr; }
+            Bcap = B;
+        }
+        for (int i = 0; i < nval; ++i)
+            if (!val[i]) check(cudaMalloc((void **)&val[i], sizeof(T) * (size_t)N * Bcap));
     }
     T *A(int id)
     {
@@ -430,12 +456,18 @@ template <typename T> struct Engine {
         return true;
     }
 
-    // Forward and reverse sweep of the recorded tape, the adjoints of the
-    // seeded planes starting from the seeds.
-    void run()
+    // Build the schedule of the recorded tape unless it is the one built last.
+    void prepare()
     {
         if (!(same_tape(tape, tape_prev) && seeds == seeds_prev)) schedule();
-        if (err == cudaSuccess) launch();
+    }
+    // Forward and reverse sweep of a single step (leaf sources as recorded).
+    void run()
+    {
+        prepare();
+        if (err != cudaSuccess) return;
+        forward(0, 1);
+        reverse(0);
     }
 
     static int ncontrib(const Op &o)   // inputs an operation's product reaches
@@ -447,6 +479,8 @@ template <typename T> struct Engine {
     {
         const int nops = (int)tape.size();
         ntab = (int)stencils.size();
+        size_values();
+        if (err != cudaSuccess) return;
         std::vector<int> lev(nval, -1), made(nval, -1);   // level of a plane (-1: leaf); op making it
         int L = 0;
         for (int t = 0; t < nops; ++t) {
@@ -635,35 +669,46 @@ template <typename T> struct Engine {
         put_array(hrev, d_rev, cap_rev);
     }
 
-    // The kernels of one forward and reverse sweep of the scheduled tape.
-    void launch()
+    // Forward pass of the tape for steps lo .. lo + cnt - 1 (cnt <= Bcap) in
+    // one batch: leaf i of step j is read at its recorded source plus
+    // j * leaf_stride; the step's values land at (j - lo) N in the planes.
+    void forward(int lo, int cnt)
     {
-        for (size_t b = 0; b < leaves.size(); b += MAXLEAF) {   // state planes into the tape, as T
+        for (size_t b = 0; b < leaves.size(); b += MAXLEAF) {
             Leaves<T> Lv{};
             Lv.n = (int)std::min<size_t>(MAXLEAF, leaves.size() - b);
             for (int i = 0; i < Lv.n; ++i) {
                 Lv.dst[i] = val[leaves[b + i].first];
-                Lv.src[i] = leaves[b + i].second;
+                const size_t esz = leaf_f32[b + i] ? sizeof(float) : sizeof(T);
+                Lv.src[i] = (const char *)leaves[b + i].second + esz * (size_t)(leaf_stride * lo);
                 if (leaf_f32[b + i]) Lv.f32 |= 1u << i;
             }
-            kk_leaves<T><<<nb, NTH, 0, st>>>(Lv, N);
+            kk_leaves<T><<<std::max(1, std::min(nb * cnt, 65535)), NTH, 0, st>>>(Lv, N, cnt, leaf_stride);
         }
+        const int nblk = (int)std::min<long long>((N * cnt + NTV - 1) / NTV, 65535);
         for (const Group &G : fgroups)
-            kk_vm_fwd<T><<<nbv, NTV, VmLayout<T>::bytes(ntab, G.n, G.slots), st>>>(d_tab, ntab, d_fwd + G.off, G.n,
-                                                                                   nx, ny, N);
-        for (size_t b = 0; b < seeds.size(); b += MAXLEAF) {
+            kk_vm_fwd<T><<<nblk, NTV, VmLayout<T>::bytes(ntab, G.n, G.slots), st>>>(d_tab, ntab, d_fwd + G.off, G.n,
+                                                                                    nx, ny, N, N * cnt);
+        check(cudaGetLastError());
+    }
+
+    // Reverse pass of batch step b (values at b N), the seeded adjoints
+    // starting from the seeds.
+    void reverse(int b)
+    {
+        for (size_t s0 = 0; s0 < seeds.size(); s0 += MAXLEAF) {
             Leaves<T> Lv{};
-            Lv.n = (int)std::min<size_t>(MAXLEAF, seeds.size() - b);
+            Lv.n = (int)std::min<size_t>(MAXLEAF, seeds.size() - s0);
             for (int i = 0; i < Lv.n; ++i) {
-                Lv.dst[i] = adj[seeds[b + i].first];
-                Lv.src[i] = seeds[b + i].second;
-                if (seed_add[b + i]) Lv.add |= 1u << i;
+                Lv.dst[i] = adj[seeds[s0 + i].first];
+                Lv.src[i] = seeds[s0 + i].second;
+                if (seed_add[s0 + i]) Lv.add |= 1u << i;
             }
-            kk_leaves<T><<<nb, NTH, 0, st>>>(Lv, N);
+            kk_leaves<T><<<nb, NTH, 0, st>>>(Lv, N, 1, 0);
         }
         for (const Group &G : rgroups)
             kk_vm_rev<T><<<nbv, NTV, VmLayout<T>::bytes(ntab, G.n, G.slots), st>>>(d_tab, ntab, d_rev + G.off, G.n,
-                                                                                   d_pgrad, nx, ny, N);
+                                                                                   d_pgrad, nx, ny, N, (long long)b * N);
         check(cudaGetLastError());
     }
 
@@ -679,7 +724,7 @@ template <typename T> struct Engine {
                 Lv.src[i] = f ? adj[ids[b + i]] : nullptr;
                 if (!f) Lv.zero |= 1u << i;
             }
-            kk_leaves<T><<<nb, NTH, 0, st>>>(Lv, N);
+            kk_leaves<T><<<nb, NTH, 0, st>>>(Lv, N, 1, 0);
         }
         check(cudaGetLastError());
     }
@@ -1065,6 +1110,24 @@ template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, 
     cudaStreamSynchronize(h->stream);
     Recorder<D> R(*E, P);
     const int nseg = (A->nsteps + A->every - 1) / A->every;
+    // the step's tape, recorded once: leaf i reads slot i of a stored state,
+    // and a segment's states sit NSTATE planes apart
+    E->reset();
+    StateIds in;
+    for (int i = 0; i < NSTATE; ++i) *slot(in, i) = E->leaf((const T *)A->seg[0] + i * n);
+    StateIds out = R.step(in);
+    for (int i = 0; i < NSTATE; ++i) E->seed(*slot(out, i), lam + i * n);
+    E->Bwant = A->every;
+    E->leaf_stride = (long long)NSTATE * (long long)n;
+    E->prepare();
+    if (E->err != cudaSuccess) return afail(h, LBM_ERR_CUDA, std::string("adjoint: ") + cudaGetErrorString(E->err));
+    const int Bc = std::max(1, E->Bcap);
+    int ids[NSTATE];
+    D *dst[NSTATE];
+    for (int i = 0; i < NSTATE; ++i) {
+        ids[i] = *slot(in, i);
+        dst[i] = lam + i * n;
+    }
     for (int sgi = nseg - 1; sgi >= 0; --sgi) {
         const int c0 = sgi * A->every, len = std::min(A->every, A->nsteps - c0);
         // regenerate the segment's states with the fused forward kernels
@@ -1077,21 +1140,15 @@ template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, 
                 if (st) return st;
             }
         }
-        for (int j = len - 1; j >= 0; --j) {
-            E->reset();
-            const T *sj = (const T *)((char *)A->seg[0] + (size_t)j * NSTATE * pb);
-            StateIds in;
-            for (int i = 0; i < NSTATE; ++i) *slot(in, i) = E->leaf(sj + i * n);
-            StateIds out = R.step(in);
-            for (int i = 0; i < NSTATE; ++i) E->seed(*slot(out, i), lam + i * n);
-            E->run();
-            int ids[NSTATE];
-            D *dst[NSTATE];
-            for (int i = 0; i < NSTATE; ++i) {
-                ids[i] = *slot(in, i);
-                dst[i] = lam + i * n;
+        // from the segment's end, Bc steps at a time: the tape's forward
+        // pass of the batch at once, then the reverse pass step by step
+        for (int hi = len; hi > 0; hi -= Bc) {
+            const int lo = std::max(0, hi - Bc);
+            E->forward(lo, hi - lo);
+            for (int j = hi - 1; j >= lo; --j) {
+                E->reverse(j - lo);
+                E->collect(ids, dst, NSTATE);
             }
-            E->collect(ids, dst, NSTATE);
             if (E->err != cudaSuccess) return afail(h, LBM_ERR_CUDA, std::string("adjoint: ") + cudaGetErrorString(E->err));
         }
     }
