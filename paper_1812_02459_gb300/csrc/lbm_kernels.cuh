@@ -2016,37 +2016,42 @@ k_diag_partial(int nx, int ny, const T *__restrict__ phi, const T *__restrict__ 
     T mx = T(-INFINITY), mn = T(INFINITY);
     for (int y = blockIdx.x; y < ny; y += gridDim.x) {
         const long long r = (long long)y * nx;
-        T a_ph = T(0), a_v = T(0), a_w = T(0), a_wv = T(0);
-        int cnt = 0, npos = 0, nneg = 0;
-        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-            const T ph = phi[r + x], v = uy[r + x];
-            const T w = (T(1) - ph) * T(0.5);
-            a_ph += ph;
-            a_w += w;
-            a_wv += w * v;
-            if (ph > T(0)) ++npos;
-            if (ph < T(0)) {
-                ++nneg;
-                a_v += v;
+        int npos = 0, nneg = 0;
+        // segments of 16 nodes per thread, their loads all issued first
+        for (int xs = threadIdx.x; xs < nx; xs += 16 * blockDim.x) {
+            T a_ph = T(0), a_v = T(0), a_w = T(0), a_wv = T(0);
+            T ph[16], v[16], pp[16], uu[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int x = xs + u * blockDim.x;
+                const bool in = x < nx;
+                ph[u] = in ? phi[r + x] : T(0);
+                v[u] = in ? uy[r + x] : T(0);
+                pp[u] = in ? p[r + x] : T(0);
+                uu[u] = in ? ux[r + x] : T(0);
             }
-            mx = fmax(mx, ph);
-            mn = fmin(mn, ph);
-            n_bad += (int)!isfinite(ph) + (int)!isfinite(p[r + x]) + (int)!isfinite(ux[r + x]) + (int)!isfinite(v);
-            if (++cnt == 16) {
-                s_ph += (double)a_ph;
-                s_v += (double)a_v;
-                s_w += (double)a_w;
-                s_wy += (double)y * (double)a_w;
-                s_wv += (double)a_wv;
-                a_ph = a_v = a_w = a_wv = T(0);
-                cnt = 0;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                if (xs + u * blockDim.x >= nx) break;
+                const T w = (T(1) - ph[u]) * T(0.5);
+                a_ph += ph[u];
+                a_w += w;
+                a_wv += w * v[u];
+                if (ph[u] > T(0)) ++npos;
+                if (ph[u] < T(0)) {
+                    ++nneg;
+                    a_v += v[u];
+                }
+                mx = fmax(mx, ph[u]);
+                mn = fmin(mn, ph[u]);
+                n_bad += (int)!isfinite(ph[u]) + (int)!isfinite(pp[u]) + (int)!isfinite(uu[u]) + (int)!isfinite(v[u]);
             }
+            s_ph += (double)a_ph;
+            s_v += (double)a_v;
+            s_w += (double)a_w;
+            s_wy += (double)y * (double)a_w;
+            s_wv += (double)a_wv;
         }
-        s_ph += (double)a_ph;
-        s_v += (double)a_v;
-        s_w += (double)a_w;
-        s_wy += (double)y * (double)a_w;
-        s_wv += (double)a_wv;
         n_pos += npos;
         n_neg += nneg;
         s_y += (long long)y * nneg;
