@@ -803,76 +803,6 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// Filter pass for FP32 on grids of even width: each thread filters the node
-// pair (x, x+1), x even; every shared-memory read is an aligned float2.
-// The staged windows start at x0 - RP with RP = R rounded up to even.
-template <int TX, int TY, int R> struct FL2Geom {
-    static constexpr int RP = (R + 1) & ~1;
-    static constexpr int WR = TX + 2 * RP, HR = TY + 2 * R;
-    static constexpr int NSCALAR = 3 * WR * HR;
-};
-
-template <int TX, int TY, int R, int NT>
-__global__ void __launch_bounds__(NT)
-k_filter_pairs(KP<float> P, const float *__restrict__ pin, const float *__restrict__ uxin,
-               const float *__restrict__ uyin, float *__restrict__ pout, float *__restrict__ uxout,
-               float *__restrict__ uyout)
-{
-    using G = FL2Geom<TX, TY, R>;
-    constexpr int RP = G::RP, WR = G::WR, HR = G::HR, A = WR * HR;
-    static_assert(TX % 2 == 0 && WR % 2 == 0, "pairs need even widths");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *s_p = reinterpret_cast<float *>(smem_raw);
-    float *s_ux = s_p + A;
-    float *s_uy = s_ux + A;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    load_tile<float, WR, HR>(s_p, pin, x0 - RP, y0 - R, P, false);
-    load_tile<float, WR, HR>(s_ux, uxin, x0 - RP, y0 - R, P, true);
-    load_tile<float, WR, HR>(s_uy, uyin, x0 - RP, y0 - R, P, true);
-    tiles_ready();
-    const float2 a2 = f2(P.fa);
-    for (int t = threadIdx.x; t < (TX / 2) * TY; t += blockDim.x) {
-        const int ly = t / (TX / 2), lx = 2 * (t - ly * (TX / 2));
-        const int X = x0 + lx, Y = y0 + ly;
-        if (X >= P.nx || Y >= P.ny) continue;
-        const int c = (ly + R) * WR + (lx + RP);   // even
-        const float *arr[3] = {s_p, s_ux, s_uy};
-        float2 res[3];
-#pragma unroll
-        for (int v = 0; v < 3; ++v) {
-            const float *sv = arr[v];
-            // row window x - RP .. x + 1 + RP as aligned pairs
-            float2 w[RP + 1];
-#pragma unroll
-            for (int k = 0; k < RP + 1; ++k)
-                w[k] = *reinterpret_cast<const float2 *>(&sv[c - RP + 2 * k]);
-            // w[k] = (x - RP + 2k, x - RP + 2k + 1); node x sits at pair RP/2, lane .x
-            const float2 ctr = w[RP / 2];
-            float2 acc = mul2(f2(2.0f * P.fd[0]), ctr);
-#pragma unroll
-            for (int m = 1; m <= R; ++m) {
-                // x + m and x - m for the lanes (x, x+1)
-                const int e0 = RP + m, e1 = RP + m + 1;   // offsets from x - RP
-                const int w0 = RP - m, w1 = RP - m + 1;
-                const float ex0 = (e0 & 1) ? w[e0 >> 1].y : w[e0 >> 1].x;
-                const float ex1 = (e1 & 1) ? w[e1 >> 1].y : w[e1 >> 1].x;
-                const float wx0 = (w0 & 1) ? w[w0 >> 1].y : w[w0 >> 1].x;
-                const float wx1 = (w1 & 1) ? w[w1 >> 1].y : w[w1 >> 1].x;
-                const float2 up = *reinterpret_cast<const float2 *>(&sv[c + m * WR]);
-                const float2 dn = *reinterpret_cast<const float2 *>(&sv[c - m * WR]);
-                float2 sum = add2(make_float2(ex0, ex1), make_float2(wx0, wx1));
-                sum = add2(sum, add2(up, dn));
-                acc = fma2(f2(P.fd[m]), sum, acc);
-            }
-            res[v] = fma2(make_float2(-a2.x, -a2.y), acc, ctr);
-        }
-        const int gidx = Y * P.nx + X;
-        *reinterpret_cast<float2 *>(&pout[gidx]) = res[0];
-        *reinterpret_cast<float2 *>(&uxout[gidx]) = res[1];
-        *reinterpret_cast<float2 *>(&uyout[gidx]) = res[2];
-    }
-}
-
 // Filtered values of one field at the column pair (X, X+1) over VR rows from
 // ly0, the window s of row stride WR holding the field from column X - RP.
 template <int WR, int R, int VR>
@@ -902,7 +832,8 @@ __device__ __forceinline__ void filter_strip(const KP<float> &P, const float *sv
             const float ex1 = (e1 & 1) ? w[e1 >> 1].y : w[e1 >> 1].x;
             const float wx0 = (w0 & 1) ? w[w0 >> 1].y : w[w0 >> 1].x;
             const float wx1 = (w1 & 1) ? w[w1 >> 1].y : w[w1 >> 1].x;
-            float2 sum = add2(make_float2(ex0, ex1), make_float2(wx0, wx1));
+            // even m: whole register pairs; odd m: pairs straddle, scalar sums
+            float2 sum = (m & 1) ? make_float2(ex0 + wx0, ex1 + wx1) : add2(w[e0 >> 1], w[w0 >> 1]);
             sum = add2(sum, add2(col[R + i + m], col[R + i - m]));
             acc = fma2(f2(P.fd[m]), sum, acc);
         }
@@ -971,13 +902,16 @@ __device__ __forceinline__ float2 pd2(float2 m2, float2 m1, float2 c, float2 p1,
 {
     return fma2(f2(4.0f / 3.0f), add2(m1, p1), fma2(f2(-2.5f), c, mul2(f2(-1.0f / 12.0f), add2(m2, p2))));
 }
+// (the neighbours at distance 1 straddle register pairs: their difference
+// and sum are formed in scalar arithmetic)
 __device__ __forceinline__ float2 pd1x(float2 l, float2 c, float2 r)
 {
-    return pd1(l, make_float2(l.y, c.x), make_float2(c.y, r.x), r);
+    return fma2(f2(2.0f / 3.0f), make_float2(c.y - l.y, r.x - c.x), mul2(f2(1.0f / 12.0f), sub2(l, r)));
 }
 __device__ __forceinline__ float2 pd2x(float2 l, float2 c, float2 r)
 {
-    return pd2(l, make_float2(l.y, c.x), c, make_float2(c.y, r.x), r);
+    return fma2(f2(4.0f / 3.0f), make_float2(l.y + c.y, c.x + r.x),
+                fma2(f2(-2.5f), c, mul2(f2(-1.0f / 12.0f), add2(l, r))));
 }
 __device__ __forceinline__ float2 lds2(const float *s, int i) { return *reinterpret_cast<const float2 *>(s + i); }
 __device__ __forceinline__ void sts2(float *s, int i, float2 v) { *reinterpret_cast<float2 *>(s + i) = v; }
@@ -1120,11 +1054,14 @@ template <int TX, int TY> struct PSGeom {
     static constexpr int NSCALAR = WP * HP + 6 * WA * HA;
 };
 
+// The x-neighbours of the pair, (l.y, c.x) and (c.y, r.x), straddle register
+// pairs: their difference and sum are formed in scalar arithmetic, which
+// costs less than assembling the pairs for FADD2.
 __device__ __forceinline__ void iso_row(float2 l, float2 c, float2 r, float2 &D, float2 &U)
 {
-    const float2 Wv = make_float2(l.y, c.x), E = make_float2(c.y, r.x);
-    D = sub2(E, Wv);
-    U = fma2(f2(1.0f / 3.0f), c, mul2(f2(1.0f / 12.0f), add2(E, Wv)));
+    D = make_float2(c.y - l.y, r.x - c.x);
+    const float2 S = make_float2(c.y + l.y, r.x + c.x);
+    U = fma2(f2(1.0f / 3.0f), c, mul2(f2(1.0f / 12.0f), S));
 }
 __device__ __forceinline__ float2 iso_dx(float2 Ds, float2 Dc, float2 Dn)
 {
@@ -1162,10 +1099,9 @@ __device__ __forceinline__ void picard_strips_body(const KP<float> &P, const flo
             for (int k = 0; k < VR1 + 2; ++k) {
                 const int row = (r0 + k) * SP + lx + 2;
                 const float2 l = lds2(s_phi, row - 2), c = lds2(s_phi, row), r = lds2(s_phi, row + 2);
-                const float2 Wv = make_float2(l.y, c.x), E = make_float2(c.y, r.x);
                 C[k] = c;
-                D[k] = sub2(E, Wv);
-                S[k] = add2(E, Wv);
+                D[k] = make_float2(c.y - l.y, r.x - c.x);
+                S[k] = make_float2(c.y + l.y, r.x + c.x);
             }
 #pragma unroll
             for (int i = 0; i < VR1; ++i) {
@@ -1726,10 +1662,9 @@ k_collide_pairs(const __grid_constant__ TmaMaps tm, KP<float> P, const S *__rest
             for (int k = 0; k < VR1 + 2; ++k) {
                 const int row = (r0 + k) * BW + lx + 4;   // window column of region column lx
                 const float2 l = lds2(s_phi, row - 2), c = lds2(s_phi, row), r = lds2(s_phi, row + 2);
-                const float2 Wv = make_float2(l.y, c.x), E = make_float2(c.y, r.x);
                 C[k] = c;
-                D[k] = sub2(E, Wv);
-                Sm[k] = add2(E, Wv);
+                D[k] = make_float2(c.y - l.y, r.x - c.x);
+                Sm[k] = make_float2(c.y + l.y, r.x + c.x);
             }
 #pragma unroll
             for (int i = 0; i < VR1; ++i) {
