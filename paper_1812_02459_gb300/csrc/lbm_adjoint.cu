@@ -181,9 +181,10 @@ __device__ __forceinline__ T gather(const DStencil &S, const T *src, int x, int 
 template <typename T>
 __global__ void __launch_bounds__(NTV) kk_vm_fwd(const DStencil *__restrict__ gtab, int ntab,
                                                 const VOp<T> *__restrict__ gops, int nops, int nx, int ny, long long N,
-                                                long long Ntot)
+                                                long long Ntot, long long voff)
 {
-    // Ntot = B N nodes of B consecutive steps: value planes hold B steps
+    // Ntot = B N nodes of B consecutive steps, whose values sit from offset
+    // voff in the value planes
     extern __shared__ __align__(16) unsigned char vm_raw[];
     using Ly = VmLayout<T>;
     DStencil *tab = reinterpret_cast<DStencil *>(vm_raw);
@@ -198,13 +199,13 @@ __global__ void __launch_bounds__(NTV) kk_vm_fwd(const DStencil *__restrict__ gt
             const VOp<T> &op = ops[o];
             T r;
             if (op.k == OP_STENCIL) {
-                r = gather(tab[op.st], op.in[0] + base, x, y, 1, nx, ny);
+                r = gather(tab[op.st], op.in[0] + voff + base, x, y, 1, nx, ny);
             } else {
                 const int nin = op.nin;
                 T v[MAXIN];
 #pragma unroll
                 for (int i = 0; i < MAXIN; ++i)   // every input requested before the first is used
-                    if (i < nin) v[i] = ((op.fint >> i) & 1u) ? slot_ref(sl, op.fslot[i]) : op.in[i][k];
+                    if (i < nin) v[i] = ((op.fint >> i) & 1u) ? slot_ref(sl, op.fslot[i]) : op.in[i][voff + k];
                 switch (op.k) {
                 case OP_LIN:
                     r = op.c0;
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(NTV) kk_vm_fwd(const DStencil *__restrict__ gt
                 }
             }
             if (op.fout >= 0) slot_ref(sl, op.fout) = r;
-            if (op.out) op.out[k] = r;
+            if (op.out) op.out[voff + k] = r;
         }
     }
 }
@@ -316,11 +317,14 @@ __global__ void __launch_bounds__(NTV) kk_vm_rev(const DStencil *__restrict__ gt
 template <typename T> struct Engine {
     int nx = 0, ny = 0;
     long long N = 0;
-    cudaStream_t st = nullptr;
+    cudaStream_t st = nullptr;        // forward passes
+    cudaStream_t rst = nullptr;       // reverse passes and collection (st when null)
     cudaError_t err = cudaSuccess;
-    std::vector<T *> val, adj;        // by plane id, persistent; a value plane holds Bcap steps
+    std::vector<T *> val, adj;        // by plane id, persistent; a value plane holds nvbuf buffers of Bcap steps
     int nval = 0;
-    int Bwant = 1, Bcap = 0;          // steps wanted in one forward batch; steps the value planes hold
+    int Bwant = 1, Bcap = 0;          // steps wanted in one forward batch; steps one value buffer holds
+    int nvbuf = 1;                    // value buffers: with two, a batch's forward pass can run while
+                                      // the reverse pass of the previous batch reads the other buffer
     long long leaf_stride = 0;        // elements between two consecutive steps' leaf sources
     std::vector<Op> tape;
     std::vector<Stencil> stencils;
@@ -368,6 +372,7 @@ template <typename T> struct Engine {
         adj.clear();
         nval = 0;
         Bcap = 0;
+        nvbuf = 1;
         void *bufs[4] = {d_pgrad, d_fwd, d_rev, d_tab};
         for (void *b : bufs) if (b) cudaFree(b);
         d_pgrad = nullptr;
@@ -384,22 +389,26 @@ template <typename T> struct Engine {
         }
         return nval++;
     }
-    // Value planes for B steps each: B is Bwant, or fewer if that would take
-    // more than a quarter of the free device memory (16 GB at most).
+    // Value planes of nvbuf buffers of B steps each, within a quarter of the
+    // free device memory (16 GB at most): two buffers when two steps fit,
+    // B = Bwant or as many as fit.  The buffer count is fixed at the first
+    // sizing after release_all().
     void size_values()
     {
         size_t fr = 0, tot = 0;
         check(cudaMemGetInfo(&fr, &tot));
         const double per_step = (double)sizeof(T) * (double)N * (double)nval;
         const double budget = std::min((double)fr / 4.0, 16e9);
-        const int B = std::max(1, std::min(Bwant, (int)(budget / std::max(per_step, 1.0))));
+        if (Bcap == 0) nvbuf = 2.0 * per_step <= budget ? 2 : 1;
+        const int B = std::max(1, std::min(Bwant, (int)(budget / std::max(per_step * nvbuf, 1.0))));
         if (B > Bcap) {
             for (T *&p : val) if (p) { cudaFree(p); p = nullptr; }
             Bcap = B;
         }
         for (int i = 0; i < nval; ++i)
-            if (!val[i]) check(cudaMalloc((void **)&val[i], sizeof(T) * (size_t)N * Bcap));
+            if (!val[i]) check(cudaMalloc((void **)&val[i], sizeof(T) * (size_t)N * Bcap * nvbuf));
     }
+    long long vbase(int vb) const { return (long long)vb * Bcap * N; }   // start of value buffer vb
     T *A(int id)
     {
         if (!adj[id]) adj[id] = alloc_plane();
@@ -642,6 +651,7 @@ template <typename T> struct Engine {
     void upload()
     {
         check(cudaStreamSynchronize(st));   // earlier kernels may still read the old records
+        if (rst && rst != st) check(cudaStreamSynchronize(rst));
         if (!d_tab) {
             std::vector<DStencil> tab(stencils.size());
             for (size_t i = 0; i < stencils.size(); ++i) {
@@ -670,15 +680,15 @@ template <typename T> struct Engine {
     }
 
     // Forward pass of the tape for steps lo .. lo + cnt - 1 (cnt <= Bcap) in
-    // one batch: leaf i of step j is read at its recorded source plus
-    // j * leaf_stride; the step's values land at (j - lo) N in the planes.
-    void forward(int lo, int cnt)
+    // one batch on st: leaf i of step j is read at its recorded source plus
+    // j * leaf_stride; the step's values land at (j - lo) N in value buffer vb.
+    void forward(int lo, int cnt, int vb = 0)
     {
         for (size_t b = 0; b < leaves.size(); b += MAXLEAF) {
             Leaves<T> Lv{};
             Lv.n = (int)std::min<size_t>(MAXLEAF, leaves.size() - b);
             for (int i = 0; i < Lv.n; ++i) {
-                Lv.dst[i] = val[leaves[b + i].first];
+                Lv.dst[i] = val[leaves[b + i].first] + vbase(vb);
                 const size_t esz = leaf_f32[b + i] ? sizeof(float) : sizeof(T);
                 Lv.src[i] = (const char *)leaves[b + i].second + esz * (size_t)(leaf_stride * lo);
                 if (leaf_f32[b + i]) Lv.f32 |= 1u << i;
@@ -688,14 +698,15 @@ template <typename T> struct Engine {
         const int nblk = (int)std::min<long long>((N * cnt + NTV - 1) / NTV, 65535);
         for (const Group &G : fgroups)
             kk_vm_fwd<T><<<nblk, NTV, VmLayout<T>::bytes(ntab, G.n, G.slots), st>>>(d_tab, ntab, d_fwd + G.off, G.n,
-                                                                                    nx, ny, N, N * cnt);
+                                                                                    nx, ny, N, N * cnt, vbase(vb));
         check(cudaGetLastError());
     }
 
-    // Reverse pass of batch step b (values at b N), the seeded adjoints
-    // starting from the seeds.
-    void reverse(int b)
+    // Reverse pass, on rst, of step b of value buffer vb (values at b N in
+    // it), the seeded adjoints starting from the seeds.
+    void reverse(int b, int vb = 0)
     {
+        cudaStream_t s = rst ? rst : st;
         for (size_t s0 = 0; s0 < seeds.size(); s0 += MAXLEAF) {
             Leaves<T> Lv{};
             Lv.n = (int)std::min<size_t>(MAXLEAF, seeds.size() - s0);
@@ -704,17 +715,19 @@ template <typename T> struct Engine {
                 Lv.src[i] = seeds[s0 + i].second;
                 if (seed_add[s0 + i]) Lv.add |= 1u << i;
             }
-            kk_leaves<T><<<nb, NTH, 0, st>>>(Lv, N, 1, 0);
+            kk_leaves<T><<<nb, NTH, 0, s>>>(Lv, N, 1, 0);
         }
         for (const Group &G : rgroups)
-            kk_vm_rev<T><<<nbv, NTV, VmLayout<T>::bytes(ntab, G.n, G.slots), st>>>(d_tab, ntab, d_rev + G.off, G.n,
-                                                                                   d_pgrad, nx, ny, N, (long long)b * N);
+            kk_vm_rev<T><<<nbv, NTV, VmLayout<T>::bytes(ntab, G.n, G.slots), s>>>(d_tab, ntab, d_rev + G.off, G.n,
+                                                                                  d_pgrad, nx, ny, N,
+                                                                                  vbase(vb) + (long long)b * N);
         check(cudaGetLastError());
     }
 
-    // dst[i] = adjoint of plane ids[i] (zero where none flowed).
+    // dst[i] = adjoint of plane ids[i] (zero where none flowed), on rst.
     void collect(const int *ids, T *const *dst, int n)
     {
+        cudaStream_t s = rst ? rst : st;
         for (int b = 0; b < n; b += MAXLEAF) {
             Leaves<T> Lv{};
             Lv.n = std::min(MAXLEAF, n - b);
@@ -724,7 +737,7 @@ template <typename T> struct Engine {
                 Lv.src[i] = f ? adj[ids[b + i]] : nullptr;
                 if (!f) Lv.zero |= 1u << i;
             }
-            kk_leaves<T><<<nb, NTH, 0, st>>>(Lv, N, 1, 0);
+            kk_leaves<T><<<nb, NTH, 0, s>>>(Lv, N, 1, 0);
         }
         check(cudaGetLastError());
     }
@@ -1037,6 +1050,8 @@ struct lbm_adjoint {
     void *eng = nullptr;           // Engine<T> of the handle's arithmetic type
     bool eng64 = false;            // eng is an Engine<double>
     bool ready = false;
+    cudaStream_t rs = nullptr;     // reverse-pass stream (high priority, non-blocking)
+    cudaEvent_t ev[5]{};           // batch forward done (2), batch reverse done (2), sweep done
 };
 
 namespace {
@@ -1057,23 +1072,28 @@ void *state_ptr(lbm_handle *h, int i)
     return r[i - 18];
 }
 
+// The 26 state planes to (out) or from a packed buffer, one launch on the
+// handle's stream.
+template <typename T> cudaError_t copy_state_t(lbm_handle *h, void *buf, bool out)
+{
+    Leaves<T> Lv{};
+    Lv.n = NSTATE;
+    for (int i = 0; i < NSTATE; ++i) {
+        T *packed = (T *)buf + (size_t)i * h->N;
+        Lv.dst[i] = out ? packed : (T *)state_ptr(h, i);
+        Lv.src[i] = out ? state_ptr(h, i) : packed;
+    }
+    kk_leaves<T><<<blocks_for(h->N), NTH, 0, h->stream>>>(Lv, h->N, 1, 0);
+    return cudaGetLastError();
+}
 cudaError_t copy_state_out(lbm_handle *h, void *dst)
 {
-    const size_t pb = h->elem * (size_t)h->N;
-    for (int i = 0; i < NSTATE; ++i) {
-        cudaError_t e = cudaMemcpyAsync((char *)dst + i * pb, state_ptr(h, i), pb, cudaMemcpyDeviceToDevice, h->stream);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    return h->elem == sizeof(double) ? copy_state_t<double>(h, dst, true) : copy_state_t<float>(h, dst, true);
 }
 cudaError_t copy_state_in(lbm_handle *h, const void *src)
 {
-    const size_t pb = h->elem * (size_t)h->N;
-    for (int i = 0; i < NSTATE; ++i) {
-        cudaError_t e = cudaMemcpyAsync(state_ptr(h, i), (const char *)src + i * pb, pb, cudaMemcpyDeviceToDevice, h->stream);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    void *s = const_cast<void *>(src);
+    return h->elem == sizeof(double) ? copy_state_t<double>(h, s, false) : copy_state_t<float>(h, s, false);
 }
 
 // The reverse sweep runs in the handle's arithmetic type T (the adjoint
@@ -1121,36 +1141,81 @@ template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, 
     E->leaf_stride = (long long)NSTATE * (long long)n;
     E->prepare();
     if (E->err != cudaSuccess) return afail(h, LBM_ERR_CUDA, std::string("adjoint: ") + cudaGetErrorString(E->err));
-    const int Bc = std::max(1, E->Bcap);
+    const int Bc = std::max(1, E->Bcap), nvb = E->nvbuf;
     int ids[NSTATE];
     D *dst[NSTATE];
     for (int i = 0; i < NSTATE; ++i) {
         ids[i] = *slot(in, i);
         dst[i] = lam + i * n;
     }
+    // Batches from the last step backwards: each segment from its end, Bc
+    // steps at a time.  Producing a batch (regenerating its segment's states
+    // with the fused forward kernels when it is the segment's last batch,
+    // then the tape's forward pass of the batch at once) runs on the handle's
+    // stream; its reverse pass, step by step, on the reverse stream.  With two
+    // value buffers the next batch is produced while this one is reversed.
+    struct Batch { int seg, lo, hi; bool first; };
+    std::vector<Batch> bl;
     for (int sgi = nseg - 1; sgi >= 0; --sgi) {
-        const int c0 = sgi * A->every, len = std::min(A->every, A->nsteps - c0);
-        // regenerate the segment's states with the fused forward kernels
-        if (copy_state_in(h, A->ckpt[sgi]) != cudaSuccess) return afail(h, LBM_ERR_CUDA, "adjoint: restore");
-        for (int j = 0; j < len; ++j) {
-            if (copy_state_out(h, (char *)A->seg[0] + (size_t)j * NSTATE * pb) != cudaSuccess)
-                return afail(h, LBM_ERR_CUDA, "adjoint: segment store");
-            if (j + 1 < len) {
-                lbm_status st = lbm_internal_step(h);
-                if (st) return st;
+        const int len = std::min(A->every, A->nsteps - sgi * A->every);
+        for (int hi = len; hi > 0; hi -= Bc) bl.push_back({sgi, std::max(0, hi - Bc), hi, hi == len});
+    }
+    if (!A->rs) {
+        int lo_pri = 0, hi_pri = 0;
+        cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri);
+        if (cudaStreamCreateWithPriority(&A->rs, cudaStreamNonBlocking, hi_pri) != cudaSuccess)
+            return afail(h, LBM_ERR_CUDA, "adjoint: reverse stream");
+        for (cudaEvent_t &e : A->ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+                return afail(h, LBM_ERR_CUDA, "adjoint: events");
+    }
+    cudaEvent_t *evF = A->ev, *evR = A->ev + 2;
+    E->rst = A->rs;
+    auto produce = [&](int c) -> lbm_status {
+        const Batch &b = bl[c];
+        const int vb = c % nvb;
+        if (b.first) {
+            if (copy_state_in(h, A->ckpt[b.seg]) != cudaSuccess) return afail(h, LBM_ERR_CUDA, "adjoint: restore");
+            const int len = b.hi;
+            for (int j = 0; j < len; ++j) {
+                if (copy_state_out(h, (char *)A->seg[0] + (size_t)j * NSTATE * pb) != cudaSuccess)
+                    return afail(h, LBM_ERR_CUDA, "adjoint: segment store");
+                if (j + 1 < len) {
+                    lbm_status st = lbm_internal_step(h);
+                    if (st) return st;
+                }
             }
         }
-        // from the segment's end, Bc steps at a time: the tape's forward
-        // pass of the batch at once, then the reverse pass step by step
-        for (int hi = len; hi > 0; hi -= Bc) {
-            const int lo = std::max(0, hi - Bc);
-            E->forward(lo, hi - lo);
-            for (int j = hi - 1; j >= lo; --j) {
-                E->reverse(j - lo);
-                E->collect(ids, dst, NSTATE);
-            }
-            if (E->err != cudaSuccess) return afail(h, LBM_ERR_CUDA, std::string("adjoint: ") + cudaGetErrorString(E->err));
+        if (c >= nvb) cudaStreamWaitEvent(h->stream, evR[vb], 0);   // the buffer's last reader
+        E->forward(b.lo, b.hi - b.lo, vb);
+        cudaEventRecord(evF[vb], h->stream);
+        return LBM_OK;
+    };
+    auto consume = [&](int c) {
+        const Batch &b = bl[c];
+        const int vb = c % nvb;
+        cudaStreamWaitEvent(A->rs, evF[vb], 0);
+        for (int j = b.hi - 1; j >= b.lo; --j) {
+            E->reverse(j - b.lo, vb);
+            E->collect(ids, dst, NSTATE);
         }
+        cudaEventRecord(evR[vb], A->rs);
+    };
+    lbm_status pst = LBM_OK;
+    for (int c = 0; c < nvb - 1 && c < (int)bl.size() && !pst; ++c) pst = produce(c);
+    for (int c = 0; c < (int)bl.size() && !pst; ++c) {
+        if (c + nvb - 1 < (int)bl.size()) pst = produce(c + nvb - 1);
+        if (!pst) consume(c);
+        if (!pst && E->err != cudaSuccess)
+            pst = afail(h, LBM_ERR_CUDA, std::string("adjoint: ") + cudaGetErrorString(E->err));
+    }
+    // join: the handle's stream waits for the reverse stream's work
+    cudaEventRecord(A->ev[4], A->rs);
+    cudaStreamWaitEvent(h->stream, A->ev[4], 0);
+    E->rst = nullptr;
+    if (pst) {
+        cudaStreamSynchronize(h->stream);
+        return pst;
     }
     // through the initialisation from (phi0, p0, u0)
     E->reset();
@@ -1184,6 +1249,9 @@ void lbm_internal_adjoint_free(lbm_handle *h)
     if (!A) return;
     for (void *p : A->ckpt) cudaFree(p);
     for (void *p : A->seg) cudaFree(p);
+    if (A->rs) cudaStreamSynchronize(A->rs);
+    for (cudaEvent_t e : A->ev) if (e) cudaEventDestroy(e);
+    if (A->rs) cudaStreamDestroy(A->rs);
     cudaFree(A->init4);
     cudaFree(A->final_state);
     cudaFree(A->lam);
