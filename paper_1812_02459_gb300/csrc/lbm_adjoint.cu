@@ -24,6 +24,7 @@
 #include <cstring>
 #include <initializer_list>
 #include <string>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -79,8 +80,7 @@ int blocks_for(long long N) { return (int)std::min<long long>((N + NTH - 1) / NT
 template <typename T> struct VOp {   // one operation as the level kernels run it
     int k, nin, param, live, st;
     unsigned fint;          // bit i: input i is read from forward slot fslot[i]
-    unsigned rint;          // bit i: the adjoint of input i goes to reverse slot rslot[i]
-    unsigned rassign;       // bit i: that contribution (slot or global) stores instead of adding
+    unsigned rassign;       // bit i: the contribution to reverse slot rslot[i] stores instead of adding
     short fslot[MAXIN], rslot[MAXIN];
     short fout, rout;       // forward slot of the output; reverse slot with its in-kernel adjoint (-1: none)
     T *out;                 // global plane of the output (null: not needed outside its kernel)
@@ -88,7 +88,10 @@ template <typename T> struct VOp {   // one operation as the level kernels run i
     T c[MAXIN];
     T c0;                   // OP_LIN constant; OP_SCALEP parameter value
     const T *aout;          // global adjoint of the output (null: none reaches it from outside)
-    T *ain[MAXIN];          // global adjoints of the inputs from outside the kernel
+};
+template <typename T> struct VFlush {   // end of a reverse kernel: dst (=) += slot
+    T *dst;
+    int slot, assign;
 };
 struct DStencil {
     int n;
@@ -141,9 +144,10 @@ __device__ __forceinline__ void stage_records(void *dst, const void *src, size_t
 template <typename T> struct VmLayout {
     static __host__ __device__ size_t tab_bytes(int ntab) { return (sizeof(DStencil) * (size_t)ntab + 15) / 16 * 16; }
     static __host__ __device__ size_t ops_bytes(int nops) { return (sizeof(VOp<T>) * (size_t)nops + 15) / 16 * 16; }
-    static __host__ __device__ size_t bytes(int ntab, int nops, int slots)
+    static __host__ __device__ size_t fl_bytes(int nfl) { return (sizeof(VFlush<T>) * (size_t)nfl + 15) / 16 * 16; }
+    static __host__ __device__ size_t bytes(int ntab, int nops, int slots, int nfl = 0)
     {
-        return tab_bytes(ntab) + ops_bytes(nops) + sizeof(T) * NTV * (size_t)slots;
+        return tab_bytes(ntab) + ops_bytes(nops) + fl_bytes(nfl) + sizeof(T) * NTV * (size_t)slots;
     }
 };
 
@@ -230,17 +234,22 @@ __global__ void __launch_bounds__(NTV) kk_vm_fwd(const DStencil *__restrict__ gt
 
 template <typename T>
 __global__ void __launch_bounds__(NTV) kk_vm_rev(const DStencil *__restrict__ gtab, int ntab,
-                                                const VOp<T> *__restrict__ gops, int nops, double *pgrad, int nx, int ny,
+                                                const VOp<T> *__restrict__ gops, int nops,
+                                                const VFlush<T> *__restrict__ gfl, int nfl, double *pgrad, int nx, int ny,
                                                 long long N, long long voff)
 {
-    // the forward values of the step are at offset voff in the value planes
+    // the forward values of the step are at offset voff in the value planes;
+    // every contribution goes to a slot, and the slots holding the adjoints
+    // of planes outside the kernel are flushed at the end
     extern __shared__ __align__(16) unsigned char vm_raw[];
     using Ly = VmLayout<T>;
     DStencil *tab = reinterpret_cast<DStencil *>(vm_raw);
     VOp<T> *ops = reinterpret_cast<VOp<T> *>(vm_raw + Ly::tab_bytes(ntab));
-    T *sl = reinterpret_cast<T *>(vm_raw + Ly::tab_bytes(ntab) + Ly::ops_bytes(nops));
+    VFlush<T> *fl = reinterpret_cast<VFlush<T> *>(vm_raw + Ly::tab_bytes(ntab) + Ly::ops_bytes(nops));
+    T *sl = reinterpret_cast<T *>(vm_raw + Ly::tab_bytes(ntab) + Ly::ops_bytes(nops) + Ly::fl_bytes(nfl));
     stage_records(tab, gtab, sizeof(DStencil) * (size_t)ntab);
     stage_records(ops, gops, sizeof(VOp<T>) * (size_t)nops);
+    stage_records(fl, gfl, sizeof(VFlush<T>) * (size_t)nfl);
     double pacc[NPARAM] = {};
     GRID_LOOP(k, N) {
         const int y = (int)(k / nx), x = (int)(k - (long long)y * nx);
@@ -283,14 +292,21 @@ __global__ void __launch_bounds__(NTV) kk_vm_rev(const DStencil *__restrict__ gt
 #pragma unroll
             for (int i = 0; i < MAXIN; ++i) {
                 if (i >= nc) break;
-                const bool as = (op.rassign >> i) & 1u;
-                if ((op.rint >> i) & 1u) {
-                    T &q = slot_ref(sl, op.rslot[i]);
-                    q = as ? ci[i] : q + ci[i];
-                } else {
-                    put(op.ain[i], k, ci[i], as);
-                }
+                T &q = slot_ref(sl, op.rslot[i]);
+                q = ((op.rassign >> i) & 1u) ? ci[i] : q + ci[i];
             }
+        }
+        constexpr int FB = 8;   // flushes whose old values are requested together
+        for (int f0 = 0; f0 < nfl; f0 += FB) {
+            T old[FB];
+#pragma unroll
+            for (int i = 0; i < FB; ++i) {
+                old[i] = T(0);
+                if (f0 + i < nfl && !fl[f0 + i].assign) old[i] = fl[f0 + i].dst[k];
+            }
+#pragma unroll
+            for (int i = 0; i < FB; ++i)
+                if (f0 + i < nfl) fl[f0 + i].dst[k] = old[i] + slot_ref(sl, fl[f0 + i].slot);
         }
     }
     __shared__ double red[NPARAM][NTV / 32];
@@ -336,11 +352,13 @@ template <typename T> struct Engine {
     std::vector<std::pair<int, const T *>> seeds;       // plane, adjoint source
     std::vector<char> flowed;                           // planes given a global adjoint by run()
     // schedule and device form
-    struct Group { int off, n, slots; };
+    struct Group { int off, n, slots, nfl, foff; };   // reverse: nfl flush records from foff
     std::vector<Group> fgroups, rgroups;                // launch order
     std::vector<VOp<T>> hfwd, hrev;
+    std::vector<VFlush<T>> hfl;
     VOp<T> *d_fwd = nullptr, *d_rev = nullptr;
-    size_t cap_fwd = 0, cap_rev = 0;
+    VFlush<T> *d_fl = nullptr;
+    size_t cap_fwd = 0, cap_rev = 0, cap_fl = 0;
     DStencil *d_tab = nullptr;
     int ntab = 0, nbv = 1;
     int smem_set = 0;
@@ -350,11 +368,23 @@ template <typename T> struct Engine {
 
     void check(cudaError_t e) { if (e != cudaSuccess && err == cudaSuccess) err = e; }
 
-    T *alloc_plane()
+    std::vector<void *> val_chunks, adj_chunks;   // planes are carved from a few allocations
+    // Give each plane ids[j] without storage its own elems-element slice
+    // (256-byte aligned) of one new allocation.
+    void carve(std::vector<T *> &planes, const std::vector<int> &ids, size_t elems, std::vector<void *> &chunks)
     {
-        T *p = nullptr;
-        check(cudaMalloc((void **)&p, sizeof(T) * (size_t)N));
-        return p;
+        if (ids.empty()) return;
+        const size_t stride = (sizeof(T) * elems + 255) / 256 * 256;
+        void *b = nullptr;
+        check(cudaMalloc(&b, stride * ids.size()));
+        if (err != cudaSuccess) return;
+        chunks.push_back(b);
+        for (size_t j = 0; j < ids.size(); ++j) planes[ids[j]] = (T *)((char *)b + stride * j);
+    }
+    void free_chunks(std::vector<void *> &chunks)
+    {
+        for (void *b : chunks) cudaFree(b);
+        chunks.clear();
     }
     void reset()
     {
@@ -366,19 +396,20 @@ template <typename T> struct Engine {
     }
     void release_all()
     {
-        for (T *p : val) if (p) cudaFree(p);
-        for (T *p : adj) if (p) cudaFree(p);
+        free_chunks(val_chunks);
+        free_chunks(adj_chunks);
         val.clear();
         adj.clear();
         nval = 0;
         Bcap = 0;
         nvbuf = 1;
-        void *bufs[4] = {d_pgrad, d_fwd, d_rev, d_tab};
+        void *bufs[5] = {d_pgrad, d_fwd, d_rev, d_tab, d_fl};
         for (void *b : bufs) if (b) cudaFree(b);
         d_pgrad = nullptr;
         d_fwd = d_rev = nullptr;
         d_tab = nullptr;
-        cap_fwd = cap_rev = 0;
+        d_fl = nullptr;
+        cap_fwd = cap_rev = cap_fl = 0;
         tape_prev.clear();
     }
     int newplane()   // value planes are allocated by schedule(), once the batch size is known
@@ -402,18 +433,16 @@ template <typename T> struct Engine {
         if (Bcap == 0) nvbuf = 2.0 * per_step <= budget ? 2 : 1;
         const int B = std::max(1, std::min(Bwant, (int)(budget / std::max(per_step * nvbuf, 1.0))));
         if (B > Bcap) {
-            for (T *&p : val) if (p) { cudaFree(p); p = nullptr; }
+            free_chunks(val_chunks);
+            std::fill(val.begin(), val.end(), nullptr);
             Bcap = B;
         }
+        std::vector<int> need;
         for (int i = 0; i < nval; ++i)
-            if (!val[i]) check(cudaMalloc((void **)&val[i], sizeof(T) * (size_t)N * Bcap * nvbuf));
+            if (!val[i]) need.push_back(i);
+        carve(val, need, (size_t)N * Bcap * nvbuf, val_chunks);
     }
     long long vbase(int vb) const { return (long long)vb * Bcap * N; }   // start of value buffer vb
-    T *A(int id)
-    {
-        if (!adj[id]) adj[id] = alloc_plane();
-        return adj[id];
-    }
     template <typename U> int leaf(const U *src)
     {
         static_assert(sizeof(U) == sizeof(T) || sizeof(U) == sizeof(float), "leaf type");
@@ -539,7 +568,11 @@ template <typename T> struct Engine {
             rec[t] = VOp<T>{};
             rec[t].fout = rec[t].rout = -1;
         }
-        std::vector<int> rslots(L + 1, 0), rslotof(nval, -1);
+        // adjoints of planes outside a reverse kernel are collected in slots
+        // too and flushed to global memory once, at the kernel's end
+        std::vector<int> rslots(L + 1, 0), rslotof(nval, -1), gslotof(nval, -1);
+        std::vector<std::vector<std::pair<int, int>>> flush(L + 1);   // plane, slot
+        std::vector<std::vector<char>> flush_as(L + 1);
         for (int l = L; l >= 0; --l) {
             std::vector<int> freel;
             int top = 0;
@@ -559,18 +592,30 @@ template <typename T> struct Engine {
                 for (int i = 0; i < ncontrib(o); ++i) {
                     const int p = o.in[i];
                     if (rin_kernel(p) == l) {
-                        d.rint |= 1u << i;
                         if (rslotof[p] < 0) { rslotof[p] = alloc(); d.rassign |= 1u << i; }
                         d.rslot[i] = (short)rslotof[p];
                     } else {
-                        gw[p] = 1;
-                        if (!init[p]) { d.rassign |= 1u << i; init[p] = 1; }
+                        if (gslotof[p] < 0) {
+                            gslotof[p] = alloc();
+                            d.rassign |= 1u << i;
+                            flush[l].push_back({p, gslotof[p]});
+                        }
+                        d.rslot[i] = (short)gslotof[p];
                     }
                 }
             }
+            for (auto &f : flush[l]) {
+                flush_as[l].push_back(!init[f.first]);
+                gw[f.first] = init[f.first] = 1;
+                gslotof[f.first] = -1;
+            }
             rslots[l] = top;
         }
-        for (int p = 0; p < nval; ++p) if (gw[p]) A(p);
+        std::vector<int> need;
+        for (int p = 0; p < nval; ++p)
+            if (gw[p] && !adj[p]) need.push_back(p);
+        carve(adj, need, (size_t)N, adj_chunks);
+        if (err != cudaSuccess) return;
         flowed = gw;
         // forward slots and the rest of each record
         std::vector<int> fslots(L + 1, 0), fslotof(nval, -1), lastuse(nval, -1);
@@ -598,7 +643,6 @@ template <typename T> struct Engine {
                         d.fint |= 1u << i;
                         d.fslot[i] = (short)fslotof[p];
                     }
-                    if (d.live && !((d.rint >> i) & 1u) && i < ncontrib(o)) d.ain[i] = adj[p];
                 }
                 for (int i = 0; i < o.nin; ++i) {   // inputs read for the last time free their slots
                     const int p = o.in[i];
@@ -622,20 +666,25 @@ template <typename T> struct Engine {
         // device form in launch order
         hfwd.clear();
         hrev.clear();
+        hfl.clear();
         fgroups.clear();
         rgroups.clear();
         int smem = 0;
         for (int l = 0; l <= L; ++l) {
             if (F[l].empty()) continue;
-            fgroups.push_back({(int)hfwd.size(), (int)F[l].size(), fslots[l]});
+            fgroups.push_back({(int)hfwd.size(), (int)F[l].size(), fslots[l], 0, 0});
             for (int t : F[l]) hfwd.push_back(rec[t]);
             smem = std::max(smem, (int)VmLayout<T>::bytes(ntab, (int)F[l].size(), fslots[l]));
         }
         for (int l = L; l >= 0; --l) {
             if (R[l].empty()) continue;
-            rgroups.push_back({(int)hrev.size(), (int)R[l].size(), rslots[l]});
+            const int nfl = (int)flush[l].size();
+            rgroups.push_back({(int)hrev.size(), (int)R[l].size(), rslots[l], nfl, 0});
             for (int t : R[l]) hrev.push_back(rec[t]);
-            smem = std::max(smem, (int)VmLayout<T>::bytes(ntab, (int)R[l].size(), rslots[l]));
+            rgroups.back().foff = (int)hfl.size();
+            for (int i = 0; i < nfl; ++i)
+                hfl.push_back({adj[flush[l][i].first], flush[l][i].second, flush_as[l][i] ? 1 : 0});
+            smem = std::max(smem, (int)VmLayout<T>::bytes(ntab, (int)R[l].size(), rslots[l], nfl));
         }
         if (smem > smem_set) {
             check(cudaFuncSetAttribute(kk_vm_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -666,17 +715,19 @@ template <typename T> struct Engine {
             if (err == cudaSuccess)
                 check(cudaMemcpy(d_tab, tab.data(), sizeof(DStencil) * tab.size(), cudaMemcpyHostToDevice));
         }
-        auto put_array = [&](std::vector<VOp<T>> &h, VOp<T> *&d, size_t &cap) {
+        auto put_array = [&](auto &h, auto *&d, size_t &cap) {
+            using E = typename std::remove_reference<decltype(h)>::type::value_type;
             if (h.size() > cap) {
                 if (d) cudaFree(d);
                 cap = h.size();
-                check(cudaMalloc((void **)&d, sizeof(VOp<T>) * cap));
+                check(cudaMalloc((void **)&d, sizeof(E) * cap));
             }
             if (err == cudaSuccess && !h.empty())
-                check(cudaMemcpy(d, h.data(), sizeof(VOp<T>) * h.size(), cudaMemcpyHostToDevice));
+                check(cudaMemcpy(d, h.data(), sizeof(E) * h.size(), cudaMemcpyHostToDevice));
         };
         put_array(hfwd, d_fwd, cap_fwd);
         put_array(hrev, d_rev, cap_rev);
+        put_array(hfl, d_fl, cap_fl);
     }
 
     // Forward pass of the tape for steps lo .. lo + cnt - 1 (cnt <= Bcap) in
@@ -718,9 +769,8 @@ template <typename T> struct Engine {
             kk_leaves<T><<<nb, NTH, 0, s>>>(Lv, N, 1, 0);
         }
         for (const Group &G : rgroups)
-            kk_vm_rev<T><<<nbv, NTV, VmLayout<T>::bytes(ntab, G.n, G.slots), s>>>(d_tab, ntab, d_rev + G.off, G.n,
-                                                                                  d_pgrad, nx, ny, N,
-                                                                                  vbase(vb) + (long long)b * N);
+            kk_vm_rev<T><<<nbv, NTV, VmLayout<T>::bytes(ntab, G.n, G.slots, G.nfl), s>>>(
+                d_tab, ntab, d_rev + G.off, G.n, d_fl + G.foff, G.nfl, d_pgrad, nx, ny, N, vbase(vb) + (long long)b * N);
         check(cudaGetLastError());
     }
 
