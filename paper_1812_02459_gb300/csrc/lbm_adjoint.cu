@@ -420,15 +420,16 @@ template <typename T> struct Engine {
         }
         return nval++;
     }
-    // Value planes of nvbuf buffers of B steps each, within a quarter of the
-    // free device memory (16 GB at most): two buffers when two steps fit,
-    // B = Bwant or as many as fit.  The buffer count is fixed at the first
-    // sizing after release_all().
-    void size_values()
+    // Value planes (those with stored[p] set) of nvbuf buffers of B steps
+    // each, within a quarter of the free device memory (16 GB at most): two
+    // buffers when two steps fit, B = Bwant or as many as fit.  The buffer
+    // count is fixed at the first sizing after release_all().
+    void size_values(const std::vector<char> &stored)
     {
         size_t fr = 0, tot = 0;
         check(cudaMemGetInfo(&fr, &tot));
-        const double per_step = (double)sizeof(T) * (double)N * (double)nval;
+        const double nst = (double)std::count(stored.begin(), stored.end(), 1);
+        const double per_step = (double)sizeof(T) * (double)N * nst;
         const double budget = std::min((double)fr / 4.0, 16e9);
         if (Bcap == 0) nvbuf = 2.0 * per_step <= budget ? 2 : 1;
         const int B = std::max(1, std::min(Bwant, (int)(budget / std::max(per_step * nvbuf, 1.0))));
@@ -439,7 +440,7 @@ template <typename T> struct Engine {
         }
         std::vector<int> need;
         for (int i = 0; i < nval; ++i)
-            if (!val[i]) need.push_back(i);
+            if (stored[i] && !val[i]) need.push_back(i);
         carve(val, need, (size_t)N * Bcap * nvbuf, val_chunks);
     }
     long long vbase(int vb) const { return (long long)vb * Bcap * N; }   // start of value buffer vb
@@ -517,8 +518,6 @@ template <typename T> struct Engine {
     {
         const int nops = (int)tape.size();
         ntab = (int)stencils.size();
-        size_values();
-        if (err != cudaSuccess) return;
         std::vector<int> lev(nval, -1), made(nval, -1);   // level of a plane (-1: leaf); op making it
         int L = 0;
         for (int t = 0; t < nops; ++t) {
@@ -556,6 +555,12 @@ template <typename T> struct Engine {
             if (o.k == OP_POW3 || o.k == OP_CLAMP1 || o.k == OP_RECIP || o.k == OP_SCALEP) needs_val[o.in[0]] = 1;
             if (o.k == OP_SQRT) needs_val[o.out] = 1;
         }
+        // planes kept in global memory: the leaves, planes read outside the
+        // forward kernel making them, and values the reverse sweep reads
+        std::vector<char> stored(nval, 0);
+        for (int p = 0; p < nval; ++p) stored[p] = made[p] < 0 || used_out[p] || needs_val[p];
+        size_values(stored);
+        if (err != cudaSuccess) return;
         // the reverse sweep, simulated in execution order
         std::vector<char> gw(nval, 0), init(nval, 0);
         seed_add.assign(seeds.size(), 0);
