@@ -93,6 +93,37 @@ template <typename T> struct VFlush {   // end of a reverse kernel: dst (=) += s
     T *dst;
     int slot, assign;
 };
+// One live operation of a reverse kernel, in execution order.  Every global
+// value it reads was staged into a slot beforehand by a prefetch entry.
+template <typename T> struct VRop {
+    int k, nc, param, st;   // kind, contributions, parameter, stencil
+    unsigned rassign;       // bit i: contribution i stores to its slot instead of adding
+    short rslot[MAXIN];     // slot receiving contribution i
+    short rout;             // slot with the in-kernel adjoint of the output (-1: none)
+    short sa, sb, sz, sg;   // staged slots of in[0], in[1], out values and the outer output adjoint (-1: none)
+    short stap;             // first staged slot of a stencil's taps (transpose gather)
+    T c[MAXIN];
+    T c0;
+};
+// A global value staged into slot `slot` ahead of use: p[voff + k] for a
+// value plane, else p at the periodic neighbour (x + dx, y + dy).
+template <typename T> struct VPre {
+    const T *p;
+    short slot;
+    signed char dx, dy;
+    int val;
+};
+// Reverse phase: ops [o0, o0 + no) run once entries [e0, e0 + ne) have landed.
+struct VPhase { int o0, no, e0, ne; };
+template <typename T> struct DW {   // a stencil's taps' weights in T
+    int n;
+    T w[MAXST];
+};
+// records are copied to shared memory in 8-byte words
+static_assert(sizeof(VRop<float>) % 8 == 0 && sizeof(VRop<double>) % 8 == 0, "VRop size");
+static_assert(sizeof(VPre<float>) % 8 == 0 && sizeof(VPre<double>) % 8 == 0, "VPre size");
+static_assert(sizeof(DW<float>) % 8 == 0 && sizeof(DW<double>) % 8 == 0, "DW size");
+static_assert(sizeof(VPhase) % 8 == 0, "VPhase size");
 struct DStencil {
     int n;
     int dx[MAXST], dy[MAXST];
@@ -144,10 +175,9 @@ __device__ __forceinline__ void stage_records(void *dst, const void *src, size_t
 template <typename T> struct VmLayout {
     static __host__ __device__ size_t tab_bytes(int ntab) { return (sizeof(DStencil) * (size_t)ntab + 15) / 16 * 16; }
     static __host__ __device__ size_t ops_bytes(int nops) { return (sizeof(VOp<T>) * (size_t)nops + 15) / 16 * 16; }
-    static __host__ __device__ size_t fl_bytes(int nfl) { return (sizeof(VFlush<T>) * (size_t)nfl + 15) / 16 * 16; }
-    static __host__ __device__ size_t bytes(int ntab, int nops, int slots, int nfl = 0)
+    static __host__ __device__ size_t bytes(int ntab, int nops, int slots)
     {
-        return tab_bytes(ntab) + ops_bytes(nops) + fl_bytes(nfl) + sizeof(T) * NTV * (size_t)slots;
+        return tab_bytes(ntab) + ops_bytes(nops) + sizeof(T) * NTV * (size_t)slots;
     }
 };
 
@@ -232,68 +262,137 @@ __global__ void __launch_bounds__(NTV) kk_vm_fwd(const DStencil *__restrict__ gt
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(NTV) kk_vm_rev(const DStencil *__restrict__ gtab, int ntab,
-                                                const VOp<T> *__restrict__ gops, int nops,
-                                                const VFlush<T> *__restrict__ gfl, int nfl, double *pgrad, int nx, int ny,
-                                                long long N, long long voff)
+// Asynchronous 4- or 8-byte copy global -> shared (cp.async, sm_80 and
+// later); the issuing thread waits for its own groups.
+template <typename T> __device__ __forceinline__ void cp_async_val(T *dst, const T *src)
 {
-    // the forward values of the step are at offset voff in the value planes;
-    // every contribution goes to a slot, and the slots holding the adjoints
-    // of planes outside the kernel are flushed at the end
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (sizeof(T) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NW> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NW) : "memory"); }
+
+// Shared memory of a reverse kernel: tap weights, operation records,
+// prefetch entries, phases, flushes, then the slots (NTV values per slot).
+template <typename T> struct RevLayout {
+    static __host__ __device__ size_t al(size_t b) { return (b + 15) / 16 * 16; }
+    static __host__ __device__ size_t w(int ntab) { return al(sizeof(DW<T>) * (size_t)ntab); }
+    static __host__ __device__ size_t o(int nops) { return al(sizeof(VRop<T>) * (size_t)nops); }
+    static __host__ __device__ size_t e(int npre) { return al(sizeof(VPre<T>) * (size_t)npre); }
+    static __host__ __device__ size_t p(int nph) { return al(sizeof(VPhase) * (size_t)nph); }
+    static __host__ __device__ size_t f(int nfl) { return al(sizeof(VFlush<T>) * (size_t)nfl); }
+    static __host__ __device__ size_t bytes(int ntab, int nops, int npre, int nph, int nfl, int slots)
+    {
+        return w(ntab) + o(nops) + e(npre) + p(nph) + f(nfl) + sizeof(T) * NTV * (size_t)slots;
+    }
+};
+
+// Records of one reverse kernel (device pointers into the engine's arrays).
+template <typename T> struct RevArgs {
+    const DW<T> *tw;
+    const VRop<T> *ops;
+    const VPre<T> *pre;
+    const VPhase *ph;
+    const VFlush<T> *fl;
+    int ntab, nops, npre, nph, nfl;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NTV) kk_vm_rev(RevArgs<T> A, double *pgrad, int nx, int ny, long long N,
+                                                long long voff)
+{
+    // The forward values of the step are at offset voff in the value planes.
+    // A node's global reads are staged into slots a phase ahead of the ops
+    // that use them (two staging buffers alternate), so a phase's loads are
+    // in flight while the previous phase computes.  Every contribution goes
+    // to a slot; the slots holding the adjoints of planes outside the kernel
+    // are flushed at the end.
     extern __shared__ __align__(16) unsigned char vm_raw[];
-    using Ly = VmLayout<T>;
-    DStencil *tab = reinterpret_cast<DStencil *>(vm_raw);
-    VOp<T> *ops = reinterpret_cast<VOp<T> *>(vm_raw + Ly::tab_bytes(ntab));
-    VFlush<T> *fl = reinterpret_cast<VFlush<T> *>(vm_raw + Ly::tab_bytes(ntab) + Ly::ops_bytes(nops));
-    T *sl = reinterpret_cast<T *>(vm_raw + Ly::tab_bytes(ntab) + Ly::ops_bytes(nops) + Ly::fl_bytes(nfl));
-    stage_records(tab, gtab, sizeof(DStencil) * (size_t)ntab);
-    stage_records(ops, gops, sizeof(VOp<T>) * (size_t)nops);
-    stage_records(fl, gfl, sizeof(VFlush<T>) * (size_t)nfl);
+    using Ly = RevLayout<T>;
+    unsigned char *q = vm_raw;
+    DW<T> *tw = reinterpret_cast<DW<T> *>(q); q += Ly::w(A.ntab);
+    VRop<T> *ops = reinterpret_cast<VRop<T> *>(q); q += Ly::o(A.nops);
+    VPre<T> *pre = reinterpret_cast<VPre<T> *>(q); q += Ly::e(A.npre);
+    VPhase *ph = reinterpret_cast<VPhase *>(q); q += Ly::p(A.nph);
+    VFlush<T> *fl = reinterpret_cast<VFlush<T> *>(q); q += Ly::f(A.nfl);
+    T *sl = reinterpret_cast<T *>(q);
+    stage_records(tw, A.tw, sizeof(DW<T>) * (size_t)A.ntab);
+    stage_records(ops, A.ops, sizeof(VRop<T>) * (size_t)A.nops);
+    stage_records(pre, A.pre, sizeof(VPre<T>) * (size_t)A.npre);
+    stage_records(ph, A.ph, sizeof(VPhase) * (size_t)A.nph);
+    stage_records(fl, A.fl, sizeof(VFlush<T>) * (size_t)A.nfl);
+    const int nph = A.nph, nfl = A.nfl;
     double pacc[NPARAM] = {};
     GRID_LOOP(k, N) {
         const int y = (int)(k / nx), x = (int)(k - (long long)y * nx);
-        for (int o = nops - 1; o >= 0; --o) {
-            const VOp<T> &op = ops[o];
-            if (!op.live) continue;
-            const int kind = op.k;
-            T ci[MAXIN];
-            int nc = 1;
-            if (kind == OP_STENCIL) {   // transpose: gathered from the output adjoint around the node
-                ci[0] = gather(tab[op.st], op.aout, x, y, -1, nx, ny);
-            } else {
-                T a = T(0), b = T(0), z = T(0);   // forward values the product needs, requested first
-                if (kind != OP_LIN && kind != OP_SQRT) a = op.in[0][voff + k];
-                if (kind == OP_MUL || kind == OP_DIV) b = op.in[1][voff + k];
-                if (kind == OP_SQRT) z = op.out[voff + k];
-                T g = op.aout ? op.aout[k] : T(0);
-                if (op.rout >= 0) g += slot_ref(sl, op.rout);
-                switch (kind) {
-                case OP_LIN:
-                    nc = op.nin;
-#pragma unroll
-                    for (int i = 0; i < MAXIN; ++i) ci[i] = op.c[i] * g;
-                    break;
-                case OP_SCALEP: {
-                    ci[0] = op.c0 * g;
-                    const double d = (double)a * (double)g;
-#pragma unroll
-                    for (int q = 0; q < NPARAM; ++q) pacc[q] += q == op.param ? d : 0.0;
-                    break;
+        auto issue = [&](int p) {
+            const VPhase P = ph[p];
+            for (int e = P.e0; e < P.e0 + P.ne; ++e) {
+                const VPre<T> E = pre[e];
+                const T *src;
+                if (E.val) src = E.p + voff + k;
+                else {
+                    int xx = x + E.dx, yy = y + E.dy;
+                    xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+                    yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+                    src = E.p + (long long)yy * nx + xx;
                 }
-                case OP_MUL: ci[0] = b * g; ci[1] = a * g; nc = 2; break;
-                case OP_DIV: ci[0] = g / b; ci[1] = -(g * a / (b * b)); nc = 2; break;
-                case OP_POW3: ci[0] = T(3) * a * a * g; break;
-                case OP_SQRT: ci[0] = g / (T(2) * z); break;
-                case OP_CLAMP1: ci[0] = (a >= T(-1) && a <= T(1)) ? g : T(0); break;
-                default: ci[0] = -(g / (a * a)); break;   // OP_RECIP
-                }
+                cp_async_val(&slot_ref(sl, E.slot), src);
             }
+            cp_async_commit();
+        };
+        if (nph > 0) issue(0);
+        for (int p = 0; p < nph; ++p) {
+            if (p + 1 < nph) {
+                issue(p + 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            const VPhase P = ph[p];
+            for (int o = P.o0; o < P.o0 + P.no; ++o) {
+                const VRop<T> &op = ops[o];
+                const int kind = op.k;
+                T ci[MAXIN];
+                const int nc = op.nc;
+                if (kind == OP_STENCIL) {   // transpose: the staged taps of the output adjoint around the node
+                    const DW<T> &W = tw[op.st];
+                    T acc = T(0);
+                    for (int j = 0; j < W.n; ++j) acc += W.w[j] * slot_ref(sl, op.stap + j);
+                    ci[0] = acc;
+                } else {
+                    const T a = op.sa >= 0 ? slot_ref(sl, op.sa) : T(0);
+                    const T b = op.sb >= 0 ? slot_ref(sl, op.sb) : T(0);
+                    const T z = op.sz >= 0 ? slot_ref(sl, op.sz) : T(0);
+                    T g = op.sg >= 0 ? slot_ref(sl, op.sg) : T(0);
+                    if (op.rout >= 0) g += slot_ref(sl, op.rout);
+                    switch (kind) {
+                    case OP_LIN:
 #pragma unroll
-            for (int i = 0; i < MAXIN; ++i) {
-                if (i >= nc) break;
-                T &q = slot_ref(sl, op.rslot[i]);
-                q = ((op.rassign >> i) & 1u) ? ci[i] : q + ci[i];
+                        for (int i = 0; i < MAXIN; ++i) ci[i] = op.c[i] * g;
+                        break;
+                    case OP_SCALEP: {
+                        ci[0] = op.c0 * g;
+                        const double d = (double)a * (double)g;
+#pragma unroll
+                        for (int q = 0; q < NPARAM; ++q) pacc[q] += q == op.param ? d : 0.0;
+                        break;
+                    }
+                    case OP_MUL: ci[0] = b * g; ci[1] = a * g; break;
+                    case OP_DIV: ci[0] = g / b; ci[1] = -(g * a / (b * b)); break;
+                    case OP_POW3: ci[0] = T(3) * a * a * g; break;
+                    case OP_SQRT: ci[0] = g / (T(2) * z); break;
+                    case OP_CLAMP1: ci[0] = (a >= T(-1) && a <= T(1)) ? g : T(0); break;
+                    default: ci[0] = -(g / (a * a)); break;   // OP_RECIP
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < MAXIN; ++i) {
+                    if (i >= nc) break;
+                    T &r = slot_ref(sl, op.rslot[i]);
+                    r = ((op.rassign >> i) & 1u) ? ci[i] : r + ci[i];
+                }
             }
         }
         constexpr int FB = 8;   // flushes whose old values are requested together
@@ -352,13 +451,23 @@ template <typename T> struct Engine {
     std::vector<std::pair<int, const T *>> seeds;       // plane, adjoint source
     std::vector<char> flowed;                           // planes given a global adjoint by run()
     // schedule and device form
-    struct Group { int off, n, slots, nfl, foff; };   // reverse: nfl flush records from foff
-    std::vector<Group> fgroups, rgroups;                // launch order
-    std::vector<VOp<T>> hfwd, hrev;
+    struct Group { int off, n, slots; };
+    struct RGroup { int op0, nops, pre0, npre, ph0, nph, fl0, nfl, slots; };
+    std::vector<Group> fgroups;                         // launch order
+    std::vector<RGroup> rgroups;
+    std::vector<VOp<T>> hfwd;
+    std::vector<VRop<T>> hrop;
+    std::vector<VPre<T>> hpre;
+    std::vector<VPhase> hph;
     std::vector<VFlush<T>> hfl;
-    VOp<T> *d_fwd = nullptr, *d_rev = nullptr;
+    VOp<T> *d_fwd = nullptr;
+    VRop<T> *d_rop = nullptr;
+    VPre<T> *d_pre = nullptr;
+    VPhase *d_ph = nullptr;
     VFlush<T> *d_fl = nullptr;
-    size_t cap_fwd = 0, cap_rev = 0, cap_fl = 0;
+    DW<T> *d_tw = nullptr;
+    size_t cap_fwd = 0, cap_rop = 0, cap_pre = 0, cap_ph = 0, cap_fl = 0;
+    static constexpr int STAGE = 16;                    // staged loads per reverse phase (more for a wide stencil)
     DStencil *d_tab = nullptr;
     int ntab = 0, nbv = 1;
     int smem_set = 0;
@@ -403,13 +512,17 @@ template <typename T> struct Engine {
         nval = 0;
         Bcap = 0;
         nvbuf = 1;
-        void *bufs[5] = {d_pgrad, d_fwd, d_rev, d_tab, d_fl};
+        void *bufs[8] = {d_pgrad, d_fwd, d_rop, d_pre, d_ph, d_fl, d_tab, d_tw};
         for (void *b : bufs) if (b) cudaFree(b);
         d_pgrad = nullptr;
-        d_fwd = d_rev = nullptr;
-        d_tab = nullptr;
+        d_fwd = nullptr;
+        d_rop = nullptr;
+        d_pre = nullptr;
+        d_ph = nullptr;
         d_fl = nullptr;
-        cap_fwd = cap_rev = cap_fl = 0;
+        d_tab = nullptr;
+        d_tw = nullptr;
+        cap_fwd = cap_rop = cap_pre = cap_ph = cap_fl = 0;
         tape_prev.clear();
     }
     int newplane()   // value planes are allocated by schedule(), once the batch size is known
@@ -670,26 +783,32 @@ template <typename T> struct Engine {
         }
         // device form in launch order
         hfwd.clear();
-        hrev.clear();
+        hrop.clear();
+        hpre.clear();
+        hph.clear();
         hfl.clear();
         fgroups.clear();
         rgroups.clear();
         int smem = 0;
         for (int l = 0; l <= L; ++l) {
             if (F[l].empty()) continue;
-            fgroups.push_back({(int)hfwd.size(), (int)F[l].size(), fslots[l], 0, 0});
+            fgroups.push_back({(int)hfwd.size(), (int)F[l].size(), fslots[l]});
             for (int t : F[l]) hfwd.push_back(rec[t]);
             smem = std::max(smem, (int)VmLayout<T>::bytes(ntab, (int)F[l].size(), fslots[l]));
         }
         for (int l = L; l >= 0; --l) {
-            if (R[l].empty()) continue;
+            std::vector<int> ex;   // live operations in execution order
+            for (int j = (int)R[l].size() - 1; j >= 0; --j)
+                if (rec[R[l][j]].live) ex.push_back(R[l][j]);
             const int nfl = (int)flush[l].size();
-            rgroups.push_back({(int)hrev.size(), (int)R[l].size(), rslots[l], nfl, 0});
-            for (int t : R[l]) hrev.push_back(rec[t]);
-            rgroups.back().foff = (int)hfl.size();
+            if (ex.empty() && nfl == 0) continue;
+            add_rgroup(ex, rslots[l], rec);
+            RGroup &G = rgroups.back();
+            G.fl0 = (int)hfl.size();
+            G.nfl = nfl;
             for (int i = 0; i < nfl; ++i)
                 hfl.push_back({adj[flush[l][i].first], flush[l][i].second, flush_as[l][i] ? 1 : 0});
-            smem = std::max(smem, (int)VmLayout<T>::bytes(ntab, (int)R[l].size(), rslots[l], nfl));
+            smem = std::max(smem, (int)RevLayout<T>::bytes(ntab, G.nops, G.npre, G.nph, G.nfl, G.slots));
         }
         if (smem > smem_set) {
             check(cudaFuncSetAttribute(kk_vm_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -700,6 +819,91 @@ template <typename T> struct Engine {
         upload();
         tape_prev = tape;
         seeds_prev = seeds;
+    }
+
+    // Reverse records of one kernel: the live operations ex (execution
+    // order) split into phases of at most STAGE staged loads (a stencil with
+    // more taps gets a phase of its own); phase p stages into buffer p % 2 of
+    // Sb slots after the kernel's `base` accumulation slots.
+    void add_rgroup(const std::vector<int> &ex, int base, const std::vector<VOp<T>> &rec)
+    {
+        struct Load { const T *p; int dx, dy, val; };
+        std::vector<std::vector<Load>> loads(ex.size());
+        for (size_t j = 0; j < ex.size(); ++j) {
+            const Op &o = tape[ex[j]];
+            const VOp<T> &d = rec[ex[j]];
+            auto &L = loads[j];
+            if (o.k == OP_STENCIL) {
+                const Stencil &S = stencils[o.st];
+                for (int i = 0; i < S.n; ++i) L.push_back({d.aout, -S.dx[i], -S.dy[i], 0});
+            } else {
+                if (o.k != OP_LIN && o.k != OP_SQRT) L.push_back({d.in[0], 0, 0, 1});
+                if (o.k == OP_MUL || o.k == OP_DIV) L.push_back({d.in[1], 0, 0, 1});
+                if (o.k == OP_SQRT) L.push_back({d.out, 0, 0, 1});
+                if (d.aout) L.push_back({d.aout, 0, 0, 0});
+            }
+        }
+        // phase boundaries
+        std::vector<std::pair<int, int>> ranges;   // [first op, end op)
+        int sb = 0;
+        for (size_t j = 0, first = 0, cnt = 0; j <= ex.size(); ++j) {
+            const size_t need = j < ex.size() ? loads[j].size() : 0;
+            if (j == ex.size() || (cnt + need > (size_t)STAGE && j > first)) {
+                if (j > first) {
+                    ranges.push_back({(int)first, (int)j});
+                    sb = std::max(sb, (int)cnt);
+                }
+                first = j;
+                cnt = 0;
+            }
+            cnt += need;
+        }
+        RGroup G{};
+        G.op0 = (int)hrop.size();
+        G.pre0 = (int)hpre.size();
+        G.ph0 = (int)hph.size();
+        G.nph = (int)ranges.size();
+        G.slots = base + sb * std::min(2, G.nph);
+        for (int p = 0; p < G.nph; ++p) {
+            VPhase P{ranges[p].first, ranges[p].second - ranges[p].first, (int)hpre.size() - G.pre0, 0};
+            int cnt = 0;
+            auto stage = [&](const Load &ld) {
+                const int s = base + (p % 2) * sb + cnt++;
+                hpre.push_back({ld.p, (short)s, (signed char)ld.dx, (signed char)ld.dy, ld.val});
+                return s;
+            };
+            for (int j = ranges[p].first; j < ranges[p].second; ++j) {
+                const Op &o = tape[ex[j]];
+                const VOp<T> &d = rec[ex[j]];
+                VRop<T> r{};
+                r.k = o.k;
+                r.nc = ncontrib(o);
+                r.param = o.param;
+                r.st = o.st;
+                r.rassign = d.rassign;
+                for (int i = 0; i < MAXIN; ++i) { r.rslot[i] = d.rslot[i]; r.c[i] = d.c[i]; }
+                r.rout = d.rout;
+                r.c0 = d.c0;
+                r.sa = r.sb = r.sz = r.sg = r.stap = -1;
+                const auto &L = loads[j];
+                if (o.k == OP_STENCIL) {
+                    r.stap = (short)(base + (p % 2) * sb + cnt);
+                    for (const Load &ld : L) stage(ld);
+                } else {
+                    size_t i = 0;
+                    if (o.k != OP_LIN && o.k != OP_SQRT) r.sa = (short)stage(L[i++]);
+                    if (o.k == OP_MUL || o.k == OP_DIV) r.sb = (short)stage(L[i++]);
+                    if (o.k == OP_SQRT) r.sz = (short)stage(L[i++]);
+                    if (d.aout) r.sg = (short)stage(L[i++]);
+                }
+                hrop.push_back(r);
+            }
+            P.ne = cnt;
+            hph.push_back(P);
+        }
+        G.nops = (int)hrop.size() - G.op0;
+        G.npre = (int)hpre.size() - G.pre0;
+        rgroups.push_back(G);
     }
 
     void upload()
@@ -719,6 +923,15 @@ template <typename T> struct Engine {
             check(cudaMalloc((void **)&d_tab, sizeof(DStencil) * tab.size()));
             if (err == cudaSuccess)
                 check(cudaMemcpy(d_tab, tab.data(), sizeof(DStencil) * tab.size(), cudaMemcpyHostToDevice));
+            std::vector<DW<T>> tw(stencils.size());
+            for (size_t i = 0; i < stencils.size(); ++i) {
+                tw[i] = DW<T>{};
+                tw[i].n = stencils[i].n;
+                for (int j = 0; j < stencils[i].n; ++j) tw[i].w[j] = (T)stencils[i].w[j];
+            }
+            check(cudaMalloc((void **)&d_tw, sizeof(DW<T>) * tw.size()));
+            if (err == cudaSuccess)
+                check(cudaMemcpy(d_tw, tw.data(), sizeof(DW<T>) * tw.size(), cudaMemcpyHostToDevice));
         }
         auto put_array = [&](auto &h, auto *&d, size_t &cap) {
             using E = typename std::remove_reference<decltype(h)>::type::value_type;
@@ -731,7 +944,9 @@ template <typename T> struct Engine {
                 check(cudaMemcpy(d, h.data(), sizeof(E) * h.size(), cudaMemcpyHostToDevice));
         };
         put_array(hfwd, d_fwd, cap_fwd);
-        put_array(hrev, d_rev, cap_rev);
+        put_array(hrop, d_rop, cap_rop);
+        put_array(hpre, d_pre, cap_pre);
+        put_array(hph, d_ph, cap_ph);
         put_array(hfl, d_fl, cap_fl);
     }
 
@@ -773,9 +988,12 @@ template <typename T> struct Engine {
             }
             kk_leaves<T><<<nb, NTH, 0, s>>>(Lv, N, 1, 0);
         }
-        for (const Group &G : rgroups)
-            kk_vm_rev<T><<<nbv, NTV, VmLayout<T>::bytes(ntab, G.n, G.slots, G.nfl), s>>>(
-                d_tab, ntab, d_rev + G.off, G.n, d_fl + G.foff, G.nfl, d_pgrad, nx, ny, N, vbase(vb) + (long long)b * N);
+        for (const RGroup &G : rgroups) {
+            const RevArgs<T> A{d_tw, d_rop + G.op0, d_pre + G.pre0, d_ph + G.ph0, d_fl + G.fl0,
+                               ntab, G.nops, G.npre, G.nph, G.nfl};
+            kk_vm_rev<T><<<nbv, NTV, RevLayout<T>::bytes(ntab, G.nops, G.npre, G.nph, G.nfl, G.slots), s>>>(
+                A, d_pgrad, nx, ny, N, vbase(vb) + (long long)b * N);
+        }
         check(cudaGetLastError());
     }
 
