@@ -226,6 +226,18 @@ lbm_status lbm_adjoint_end(lbm_handle *h, const double *dL_dphi, double *dL_dphi
                            double *dL_dsigma, double *dL_dM);
 
 /*
+ * lbm_adjoint_engine -- how the last lbm_adjoint_end on h ran the
+ * vector-Jacobian products of the step: 1 when by level kernels compiled
+ * for this tape at run time (the step's plane operations written out as
+ * straight-line CUDA C++ and compiled once per tape structure with NVRTC
+ * for sm_103a), 0 when by the tape interpreter kernels (NVRTC not found,
+ * compilation failed, or LBM_ADJOINT_COMPILED=0 in the environment), -1
+ * before any reverse sweep or for a NULL handle.  Both give the same
+ * gradients up to rounding order.
+ */
+int lbm_adjoint_engine(const lbm_handle *h);
+
+/*
  * lbm_field_sums_noalloc -- the sums of lbm_diagnostics for fields the
  * caller holds on the device, computed without allocating device memory.
  * The paper has no counterpart: this is an operational entry point.  It is

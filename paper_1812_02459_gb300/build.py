@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "liblbm.so")
 SOURCES = [os.path.join(CSRC, n) for n in ("lbm_api.cu", "lbm_noalloc.cu", "lbm_adjoint.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "lbm_kernels.cuh"), os.path.join(CSRC, "lbm_internal.h"),
-                  os.path.join(INCLUDE, "lbm.h")]
+                  os.path.join(CSRC, "lbm_jit.h"), os.path.join(INCLUDE, "lbm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -35,7 +35,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I", INCLUDE, "-o", tmp, *SOURCES]
+           "-I", INCLUDE, "-o", tmp, *SOURCES, "-ldl"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.run(cmd, check=True)

@@ -23,6 +23,7 @@
 #include <cstdint>
 #include <cstring>
 #include <initializer_list>
+#include <map>
 #include <string>
 #include <type_traits>
 #include <utility>
@@ -30,6 +31,7 @@
 
 #include "lbm.h"
 #include "lbm_internal.h"
+#include "lbm_jit.h"
 
 namespace {
 
@@ -468,6 +470,12 @@ template <typename T> struct Engine {
     DW<T> *d_tw = nullptr;
     size_t cap_fwd = 0, cap_rop = 0, cap_pre = 0, cap_ph = 0, cap_fl = 0;
     static constexpr int STAGE = 16;                    // staged loads per reverse phase (more for a wide stencil)
+    // compiled level kernels: the schedule written out as straight-line
+    // CUDA C++ (one kernel per level and direction), plane pointers and
+    // coefficients passed in one argument struct
+    struct JKernel { cudaKernel_t k = nullptr; std::vector<unsigned long long> pack; };
+    std::vector<JKernel> jfwd, jrev;
+    bool jit = false;                                   // the compiled kernels run the scheduled tape
     DStencil *d_tab = nullptr;
     int ntab = 0, nbv = 1;
     int smem_set = 0;
@@ -796,6 +804,7 @@ template <typename T> struct Engine {
             for (int t : F[l]) hfwd.push_back(rec[t]);
             smem = std::max(smem, (int)VmLayout<T>::bytes(ntab, (int)F[l].size(), fslots[l]));
         }
+        std::vector<std::vector<int>> rex;   // per reverse group: its live operations in execution order
         for (int l = L; l >= 0; --l) {
             std::vector<int> ex;   // live operations in execution order
             for (int j = (int)R[l].size() - 1; j >= 0; --j)
@@ -803,6 +812,7 @@ template <typename T> struct Engine {
             const int nfl = (int)flush[l].size();
             if (ex.empty() && nfl == 0) continue;
             add_rgroup(ex, rslots[l], rec);
+            rex.push_back(ex);
             RGroup &G = rgroups.back();
             G.fl0 = (int)hfl.size();
             G.nfl = nfl;
@@ -816,9 +826,218 @@ template <typename T> struct Engine {
             smem_set = smem;
         }
         nbv = (int)std::min<long long>((N + NTV - 1) / NTV, 8192);
+        compile_levels(rec, rex);
         upload();
         tape_prev = tape;
         seeds_prev = seeds;
+    }
+
+    // Arguments of one compiled kernel: distinct plane pointers, coefficients.
+    struct ArgPack {
+        std::vector<const void *> ptr;
+        std::map<const void *, int> at;
+        std::vector<T> coef;
+        std::string p(const void *q)
+        {
+            auto it = at.find(q);
+            if (it == at.end()) { it = at.emplace(q, (int)ptr.size()).first; ptr.push_back(q); }
+            return "A.p[" + std::to_string(it->second) + "]";
+        }
+        std::string c(double v)
+        {
+            coef.push_back((T)v);
+            return "A.c[" + std::to_string(coef.size() - 1) + "]";
+        }
+        std::string decl(const std::string &name) const
+        {
+            return "struct " + name + " { T *p[" + std::to_string(std::max<size_t>(1, ptr.size())) + "]; T c[" +
+                   std::to_string(std::max<size_t>(1, coef.size())) + "]; };\n";
+        }
+        std::vector<unsigned long long> pack() const   // the struct's bytes
+        {
+            const size_t np = std::max<size_t>(1, ptr.size()), nc = std::max<size_t>(1, coef.size());
+            std::vector<unsigned long long> w(np + (sizeof(T) * nc + 7) / 8, 0ull);
+            std::memcpy(w.data(), ptr.data(), sizeof(void *) * ptr.size());
+            std::memcpy((char *)w.data() + 8 * np, coef.data(), sizeof(T) * coef.size());
+            return w;
+        }
+    };
+    static std::string S(int i) { return std::to_string(i); }
+
+    // Forward level kernel gi: the records of fgroups[gi] in order, a
+    // thread per node of a batch of steps; slot q is the variable fq.
+    std::string gen_fwd(int gi, ArgPack &A)
+    {
+        const Group &G = fgroups[gi];
+        std::string b;
+        for (int j = 0; j < G.n; ++j) {
+            const VOp<T> &d = hfwd[G.off + j];
+            b += "        {\n";
+            if (d.k == OP_STENCIL) {
+                const Stencil &St = stencils[d.st];
+                const std::string src = A.p(d.in[0]);
+                b += "            T r = T(0);\n";
+                for (int i = 0; i < St.n; ++i)
+                    b += "            r += " + A.c(St.w[i]) + " * __ldg(" + src + " + voff + base + nbi(x, y, " + S(St.dx[i]) +
+                         ", " + S(St.dy[i]) + ", nx, ny));\n";
+            } else {
+                for (int i = 0; i < d.nin; ++i)
+                    b += "            const T v" + S(i) + " = " +
+                         (((d.fint >> i) & 1u) ? "f" + S(d.fslot[i]) : "__ldg(" + A.p(d.in[i]) + " + voff + k)") + ";\n";
+                switch (d.k) {
+                case OP_LIN:
+                    b += "            T r = " + A.c((double)d.c0) + ";\n";
+                    for (int i = 0; i < d.nin; ++i) b += "            r += " + A.c((double)d.c[i]) + " * v" + S(i) + ";\n";
+                    break;
+                case OP_SCALEP: b += "            const T r = " + A.c((double)d.c0) + " * v0;\n"; break;
+                case OP_MUL: b += "            const T r = v0 * v1;\n"; break;
+                case OP_DIV: b += "            const T r = v0 / v1;\n"; break;
+                case OP_POW3: b += "            const T r = v0 * v0 * v0;\n"; break;
+                case OP_SQRT: b += "            const T r = sqrt(v0);\n"; break;
+                case OP_CLAMP1: b += "            const T r = v0 < T(-1) ? T(-1) : (v0 > T(1) ? T(1) : v0);\n"; break;
+                default: b += "            const T r = T(1) / v0;\n"; break;   // OP_RECIP
+                }
+            }
+            if (d.fout >= 0) b += "            f" + S(d.fout) + " = r;\n";
+            if (d.out) b += "            " + A.p(d.out) + "[voff + k] = r;\n";
+            b += "        }\n";
+        }
+        std::string f = A.decl("KF" + S(gi));
+        f += "extern \"C\" __global__ void __launch_bounds__(128, 4) f" + S(gi) +
+             "(const KF" + S(gi) + " A, long long N, long long Ntot, long long voff, int nx, int ny)\n{\n"
+             "    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Ntot; "
+             "k += (long long)gridDim.x * blockDim.x) {\n"
+             "        const long long base = (k / N) * N, kk = k - base;\n"
+             "        const int y = (int)(kk / nx), x = (int)(kk - (long long)y * nx);\n";
+        for (int q = 0; q < G.slots; ++q) f += "        T f" + S(q) + " = T(0);\n";
+        return f + b + "    }\n}\n";
+    }
+
+    // Reverse level kernel gi: the live operations ex in execution order,
+    // a thread per node; accumulation slot q is the variable sq; the slots
+    // of outer planes are flushed at the end.
+    std::string gen_rev(int gi, const std::vector<int> &ex, const std::vector<VOp<T>> &rec, int nslots, ArgPack &A)
+    {
+        const RGroup &G = rgroups[gi];
+        std::string b;
+        bool pgr = false;
+        for (int t : ex) {
+            const Op &o = tape[t];
+            const VOp<T> &d = rec[t];
+            const int nc = ncontrib(o);
+            b += "        {\n";
+            if (o.k == OP_STENCIL) {   // transpose: gathered from the output adjoint around the node
+                const Stencil &St = stencils[o.st];
+                const std::string src = A.p(d.aout);
+                b += "            T c0 = T(0);\n";
+                for (int i = 0; i < St.n; ++i)
+                    b += "            c0 += " + A.c(St.w[i]) + " * __ldg(" + src + " + nbi(x, y, " + S(-St.dx[i]) + ", " +
+                         S(-St.dy[i]) + ", nx, ny));\n";
+            } else {
+                b += "            T g = " + (d.aout ? "__ldg(" + A.p(d.aout) + " + k)" : std::string("T(0)")) +
+                     (d.rout >= 0 ? " + s" + S(d.rout) : std::string("")) + ";\n";
+                if (o.k != OP_LIN && o.k != OP_SQRT) b += "            const T a = __ldg(" + A.p(d.in[0]) + " + voff + k);\n";
+                if (o.k == OP_MUL || o.k == OP_DIV) b += "            const T bb = __ldg(" + A.p(d.in[1]) + " + voff + k);\n";
+                if (o.k == OP_SQRT) b += "            const T z = __ldg(" + A.p(d.out) + " + voff + k);\n";
+                switch (o.k) {
+                case OP_LIN:
+                    for (int i = 0; i < nc; ++i) b += "            const T c" + S(i) + " = " + A.c((double)d.c[i]) + " * g;\n";
+                    break;
+                case OP_SCALEP:
+                    b += "            const T c0 = " + A.c((double)d.c0) + " * g;\n";
+                    b += "            q" + S(o.param) + " += (double)a * (double)g;\n";
+                    pgr = true;
+                    break;
+                case OP_MUL: b += "            const T c0 = bb * g, c1 = a * g;\n"; break;
+                case OP_DIV: b += "            const T c0 = g / bb, c1 = -(g * a / (bb * bb));\n"; break;
+                case OP_POW3: b += "            const T c0 = T(3) * a * a * g;\n"; break;
+                case OP_SQRT: b += "            const T c0 = g / (T(2) * z);\n"; break;
+                case OP_CLAMP1: b += "            const T c0 = (a >= T(-1) && a <= T(1)) ? g : T(0);\n"; break;
+                default: b += "            const T c0 = -(g / (a * a));\n"; break;   // OP_RECIP
+                }
+            }
+            for (int i = 0; i < nc; ++i) {
+                const std::string q = "s" + S(d.rslot[i]);
+                b += "            " + q + " = " + (((d.rassign >> i) & 1u) ? "c" + S(i) : q + " + c" + S(i)) + ";\n";
+            }
+            b += "        }\n";
+        }
+        for (int i = 0; i < G.nfl; ++i) {
+            const VFlush<T> &F = hfl[G.fl0 + i];
+            const std::string dst = A.p(F.dst);
+            b += "        " + dst + "[k] = " + (F.assign ? std::string("") : dst + "[k] + ") + "s" + S(F.slot) + ";\n";
+        }
+        std::string f = A.decl("KR" + S(gi));
+        f += "extern \"C\" __global__ void __launch_bounds__(128, 4) r" + S(gi) + "(const KR" + S(gi) +
+             " A, double *pgrad, long long N, long long voff, int nx, int ny)\n{\n"
+             "    double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;\n"
+             "    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < N; "
+             "k += (long long)gridDim.x * blockDim.x) {\n"
+             "        const int y = (int)(k / nx), x = (int)(k - (long long)y * nx);\n";
+        for (int q = 0; q < nslots; ++q) f += "        T s" + S(q) + " = T(0);\n";
+        f += b + "    }\n";
+        if (pgr) f += "    pgrad_add(q0, q1, q2, q3, pgrad);\n";
+        return f + "}\n";
+    }
+
+    // Write the schedule out as compiled level kernels (unless switched off
+    // by LBM_ADJOINT_COMPILED=0); jit says whether they run this tape.
+    void compile_levels(const std::vector<VOp<T>> &rec, const std::vector<std::vector<int>> &rex)
+    {
+        jit = false;
+        jfwd.assign(fgroups.size(), JKernel{});
+        jrev.assign(rgroups.size(), JKernel{});
+        const char *sw = getenv("LBM_ADJOINT_COMPILED");
+        if (sw && sw[0] == '0') return;
+        static_assert(NPARAM == 4, "generated kernels sum four parameter gradients");
+        std::string src = std::string("typedef ") + (sizeof(T) == 8 ? "double" : "float") + " T;\n" +
+            "__device__ __forceinline__ long long nbi(int x, int y, int dx, int dy, int nx, int ny)\n{\n"
+            "    int xx = x + dx, yy = y + dy;\n"
+            "    xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);\n"
+            "    yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);\n"
+            "    return (long long)yy * nx + xx;\n}\n"
+            "__device__ __forceinline__ void pgrad_add(double q0, double q1, double q2, double q3, double *pg)\n{\n"
+            "    __shared__ double red[4][32];\n"
+            "    double v[4] = {q0, q1, q2, q3};\n"
+            "    for (int q = 0; q < 4; ++q) {\n"
+            "        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);\n"
+            "        if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v[q];\n"
+            "    }\n"
+            "    __syncthreads();\n"
+            "    if (threadIdx.x < 4) {\n"
+            "        double t = 0.0;\n"
+            "        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];\n"
+            "        if (t != 0.0) atomicAdd(pg + threadIdx.x, t);\n"
+            "    }\n}\n";
+        std::vector<ArgPack> af(fgroups.size()), ar(rgroups.size());
+        for (size_t g = 0; g < fgroups.size(); ++g) src += gen_fwd((int)g, af[g]);
+        for (size_t g = 0; g < rgroups.size(); ++g) {
+            int nslots = 0;   // accumulation slots: every slot a record or flush names
+            for (int t : rex[g]) {
+                const VOp<T> &d = rec[t];
+                for (int i = 0; i < ncontrib(tape[t]); ++i) nslots = std::max(nslots, d.rslot[i] + 1);
+                nslots = std::max(nslots, d.rout + 1);
+            }
+            for (int i = 0; i < rgroups[g].nfl; ++i) nslots = std::max(nslots, hfl[rgroups[g].fl0 + i].slot + 1);
+            src += gen_rev((int)g, rex[g], rec, nslots, ar[g]);
+        }
+        cudaLibrary_t lib = lbm_jit::library(src);
+        if (!lib) {
+            static bool told = false;
+            if (!told) fprintf(stderr, "lbm adjoint: compiled level kernels unavailable (%s); interpreting the tape\n",
+                               lbm_jit::reason().c_str());
+            told = true;
+            return;
+        }
+        for (size_t g = 0; g < fgroups.size(); ++g) {
+            if (cudaLibraryGetKernel(&jfwd[g].k, lib, ("f" + S((int)g)).c_str()) != cudaSuccess) { cudaGetLastError(); return; }
+            jfwd[g].pack = af[g].pack();
+        }
+        for (size_t g = 0; g < rgroups.size(); ++g) {
+            if (cudaLibraryGetKernel(&jrev[g].k, lib, ("r" + S((int)g)).c_str()) != cudaSuccess) { cudaGetLastError(); return; }
+            jrev[g].pack = ar[g].pack();
+        }
+        jit = true;
     }
 
     // Reverse records of one kernel: the live operations ex (execution
@@ -967,9 +1186,18 @@ template <typename T> struct Engine {
             kk_leaves<T><<<std::max(1, std::min(nb * cnt, 65535)), NTH, 0, st>>>(Lv, N, cnt, leaf_stride);
         }
         const int nblk = (int)std::min<long long>((N * cnt + NTV - 1) / NTV, 65535);
-        for (const Group &G : fgroups)
-            kk_vm_fwd<T><<<nblk, NTV, VmLayout<T>::bytes(ntab, G.n, G.slots), st>>>(d_tab, ntab, d_fwd + G.off, G.n,
-                                                                                    nx, ny, N, N * cnt, vbase(vb));
+        if (jit) {
+            long long Nn = N, Ntot = N * cnt, voff = vbase(vb);
+            int nxx = nx, nyy = ny;
+            for (JKernel &J : jfwd) {
+                void *args[] = {J.pack.data(), &Nn, &Ntot, &voff, &nxx, &nyy};
+                check(cudaLaunchKernel((const void *)J.k, dim3(nblk), dim3(NTV), args, 0, st));
+            }
+        } else {
+            for (const Group &G : fgroups)
+                kk_vm_fwd<T><<<nblk, NTV, VmLayout<T>::bytes(ntab, G.n, G.slots), st>>>(
+                    d_tab, ntab, d_fwd + G.off, G.n, nx, ny, N, N * cnt, vbase(vb));
+        }
         check(cudaGetLastError());
     }
 
@@ -988,11 +1216,21 @@ template <typename T> struct Engine {
             }
             kk_leaves<T><<<nb, NTH, 0, s>>>(Lv, N, 1, 0);
         }
-        for (const RGroup &G : rgroups) {
-            const RevArgs<T> A{d_tw, d_rop + G.op0, d_pre + G.pre0, d_ph + G.ph0, d_fl + G.fl0,
-                               ntab, G.nops, G.npre, G.nph, G.nfl};
-            kk_vm_rev<T><<<nbv, NTV, RevLayout<T>::bytes(ntab, G.nops, G.npre, G.nph, G.nfl, G.slots), s>>>(
-                A, d_pgrad, nx, ny, N, vbase(vb) + (long long)b * N);
+        if (jit) {
+            long long Nn = N, voff = vbase(vb) + (long long)b * N;
+            int nxx = nx, nyy = ny;
+            double *pg = d_pgrad;
+            for (JKernel &J : jrev) {
+                void *args[] = {J.pack.data(), &pg, &Nn, &voff, &nxx, &nyy};
+                check(cudaLaunchKernel((const void *)J.k, dim3(nbv), dim3(NTV), args, 0, s));
+            }
+        } else {
+            for (const RGroup &G : rgroups) {
+                const RevArgs<T> A{d_tw, d_rop + G.op0, d_pre + G.pre0, d_ph + G.ph0, d_fl + G.fl0,
+                                   ntab, G.nops, G.npre, G.nph, G.nfl};
+                kk_vm_rev<T><<<nbv, NTV, RevLayout<T>::bytes(ntab, G.nops, G.npre, G.nph, G.nfl, G.slots), s>>>(
+                    A, d_pgrad, nx, ny, N, vbase(vb) + (long long)b * N);
+            }
         }
         check(cudaGetLastError());
     }
@@ -1324,6 +1562,7 @@ struct lbm_adjoint {
     bool eng64 = false;            // eng is an Engine<double>
     bool ready = false;
     cudaStream_t rs = nullptr;     // reverse-pass stream (high priority, non-blocking)
+    int engine = -1;               // last reverse sweep: 1 compiled level kernels, 0 interpreter
     cudaEvent_t ev[5]{};           // batch forward done (2), batch reverse done (2), sweep done
 };
 
@@ -1482,6 +1721,7 @@ template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, 
         if (!pst && E->err != cudaSuccess)
             pst = afail(h, LBM_ERR_CUDA, std::string("adjoint: ") + cudaGetErrorString(E->err));
     }
+    const bool step_jit = E->jit;
     // join: the handle's stream waits for the reverse stream's work
     cudaEventRecord(A->ev[4], A->rs);
     cudaStreamWaitEvent(h->stream, A->ev[4], 0);
@@ -1497,6 +1737,7 @@ template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, 
     StateIds s0 = R.init(phi0, p0, ux0, uy0);
     for (int i = 0; i < NSTATE; ++i) E->seed(*slot(s0, i), lam + i * n);
     E->run();
+    A->engine = step_jit && E->jit ? 1 : 0;
     std::vector<D> g(n, D(0));
     if (E->flowed[phi0]) cudaMemcpyAsync(g.data(), E->adj[phi0], pd, cudaMemcpyDeviceToHost, h->stream);
     double pg[NPARAM];
@@ -1586,6 +1827,11 @@ lbm_status lbm_adjoint_begin(lbm_handle *h, int nsteps, int checkpoint_every)
     if (e != cudaSuccess) return afail(h, LBM_ERR_CUDA, std::string("adjoint forward: ") + cudaGetErrorString(e));
     A->ready = true;
     return LBM_OK;
+}
+
+int lbm_adjoint_engine(const lbm_handle *h)
+{
+    return h && h->adj ? h->adj->engine : -1;
 }
 
 lbm_status lbm_adjoint_end(lbm_handle *h, const double *dL_dphi, double *dL_dphi0, double *dL_dsigma,

@@ -48,7 +48,7 @@ EXPORTS = ("lbm_create", "lbm_step", "lbm_fields", "lbm_fields_device", "lbm_set
            "lbm_diagnostics", "lbm_check", "lbm_get_state", "lbm_set_state",
            "lbm_profile", "lbm_profile_read", "lbm_kernel_name", "lbm_kernel_variant",
            "lbm_field_sums_noalloc", "lbm_noalloc_last_error",
-           "lbm_adjoint_begin", "lbm_adjoint_end",
+           "lbm_adjoint_begin", "lbm_adjoint_end", "lbm_adjoint_engine",
            "lbm_device_bytes", "lbm_destroy", "lbm_last_error")
 LBM_NKERNELS = 4
 
@@ -100,6 +100,8 @@ def load(path=None):
     L.lbm_adjoint_begin.argtypes = [vp, C.c_int, C.c_int]
     L.lbm_adjoint_end.restype = C.c_int
     L.lbm_adjoint_end.argtypes = [vp, _dp, _dp, _dp, _dp]
+    L.lbm_adjoint_engine.restype = C.c_int
+    L.lbm_adjoint_engine.argtypes = [vp]
     L.lbm_device_bytes.restype = C.c_size_t
     L.lbm_device_bytes.argtypes = [vp]
     L.lbm_destroy.restype = None
@@ -255,6 +257,10 @@ class Sim:
         ds = C.c_double(); dm = C.c_double()
         self._ck(self._lib.lbm_adjoint_end(self._h, _ptr(seed), _ptr(g), C.byref(ds), C.byref(dm)))
         return g, ds.value, dm.value
+
+    def adjoint_engine(self):
+        """1: the last reverse sweep ran compiled level kernels; 0: the tape interpreter; -1: none yet."""
+        return int(self._lib.lbm_adjoint_engine(self._h))
 
     def device_bytes(self):
         return int(self._lib.lbm_device_bytes(self._h))
