@@ -24,11 +24,12 @@ def case(n=20, R=5.0):
     return prm, fields, target
 
 
-def gpu_grad(prm, fields, target, steps, every, precision):
+def gpu_grad(prm, fields, target, steps, every, precision, engine=1):
     s = lbm.Sim(prm, *fields, precision=precision)
     s.adjoint_begin(steps, every)
     phiT = s.fields()[0]
     g, ds, dm = s.adjoint_end(phiT - target)
+    assert s.adjoint_engine() == engine   # 1: compiled level kernels, 0: tape interpreter
     loss = 0.5 * float(((phiT - target) ** 2).sum())
     s.close()
     return loss, g, ds, dm
@@ -78,6 +79,21 @@ def test_adjoint_fp64_matches_gpu_finite_differences():
     assert ds == pytest.approx(fd_s, rel=1e-6)
     assert dm == pytest.approx(fd_m, rel=1e-6)
     assert float((g * v).sum()) == pytest.approx(fd_v, rel=1e-6)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+def test_interpreter_matches_compiled_levels(monkeypatch, precision, tol):
+    """The tape interpreter (the fallback when run-time compilation is not
+    available) and the compiled level kernels apply the same
+    vector-Jacobian products; only the rounding order differs."""
+    prm, fields, target = case()
+    comp = gpu_grad(prm, fields, target, 7, 3, precision, engine=1)
+    monkeypatch.setenv("LBM_ADJOINT_COMPILED", "0")
+    interp = gpu_grad(prm, fields, target, 7, 3, precision, engine=0)
+    assert interp[0] == comp[0]   # same forward trajectory
+    assert np.abs(interp[1] - comp[1]).max() <= tol * np.abs(comp[1]).max()
+    assert interp[2] == pytest.approx(comp[2], rel=tol)
+    assert interp[3] == pytest.approx(comp[3], rel=tol)
 
 
 def test_autograd_function_and_fp32():
