@@ -60,6 +60,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=4096, help="grid is n x n")
+    ap.add_argument("--adjoint-n", type=int, default=256, help="side of the adjoint side measurement's grid")
+    ap.add_argument("--adjoint-steps", type=int, default=200, help="steps of the adjoint side measurement")
     ap.add_argument("--precision", default="fp32", choices=("fp32", "fp64"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -388,8 +390,8 @@ def run_ours(args):
             variants[prec] = {"MLUPS": round(N / ms_v / 1e3, 1), "ms_per_step": round(ms_v, 4), "steps": k,
                               "vs_fp32": round((N / ms_v / 1e3) / (N / (ms_max / args.steps) / 1e3), 4)}
             v.close()
-        an, asteps, aevery = 256, 200, 22
-        aprm, afields = inputs.translating_drop(n=an, R=32.0, U0=0.01)
+        an, asteps, aevery = args.adjoint_n, args.adjoint_steps, 22
+        aprm, afields = inputs.translating_drop(n=an, R=an / 8.0, U0=0.01)
 
         def adjoint_run(nsteps):
             a = lbm.Sim(aprm, *afields, precision="fp32", stream=stream.cuda_stream)

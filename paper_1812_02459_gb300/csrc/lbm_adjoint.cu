@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(NTH) kk_leaves(Leaves<T> L, long long N, int B
     }
 }
 
-constexpr int NTV = 128;   // threads of a level kernel
+constexpr int NTV = 128;   // threads of a level kernel (the compiled ones map them to 32 x 4 nodes)
 
 // Copy records (8-byte aligned) into shared memory; every thread of the
 // block takes part and the block waits for the copy.
@@ -542,7 +542,7 @@ template <typename T> struct Engine {
         return nval++;
     }
     // Value planes (those with stored[p] set) of nvbuf buffers of B steps
-    // each, within a quarter of the free device memory (16 GB at most): two
+    // each, within a quarter of the free device memory: two
     // buffers when two steps fit, B = Bwant or as many as fit.  The buffer
     // count is fixed at the first sizing after release_all().
     void size_values(const std::vector<char> &stored)
@@ -551,7 +551,7 @@ template <typename T> struct Engine {
         check(cudaMemGetInfo(&fr, &tot));
         const double nst = (double)std::count(stored.begin(), stored.end(), 1);
         const double per_step = (double)sizeof(T) * (double)N * nst;
-        const double budget = std::min((double)fr / 4.0, 16e9);
+        const double budget = (double)fr / 4.0;
         if (Bcap == 0) nvbuf = 2.0 * per_step <= budget ? 2 : 1;
         const int B = std::max(1, std::min(Bwant, (int)(budget / std::max(per_step * nvbuf, 1.0))));
         if (B > Bcap) {
@@ -905,10 +905,12 @@ template <typename T> struct Engine {
         std::string f = A.decl("KF" + S(gi));
         f += "extern \"C\" __global__ void __launch_bounds__(128, 4) f" + S(gi) +
              "(const KF" + S(gi) + " A, long long N, long long Ntot, long long voff, int nx, int ny)\n{\n"
-             "    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Ntot; "
-             "k += (long long)gridDim.x * blockDim.x) {\n"
-             "        const long long base = (k / N) * N, kk = k - base;\n"
-             "        const int y = (int)(kk / nx), x = (int)(kk - (long long)y * nx);\n";
+             "    const long long tiles_x = (nx + 31) / 32, tpp = tiles_x * ((ny + 3) / 4), ntiles = tpp * (Ntot / N);\n"
+             "    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {\n"
+             "        int x, y;\n"
+             "        long long k;\n"
+             "        if (!tile_node(t, tiles_x, tpp, nx, ny, N, x, y, k)) continue;\n"
+             "        const long long base = k - ((long long)y * nx + x);\n";
         for (int q = 0; q < G.slots; ++q) f += "        T f" + S(q) + " = T(0);\n";
         return f + b + "    }\n}\n";
     }
@@ -971,9 +973,11 @@ template <typename T> struct Engine {
         f += "extern \"C\" __global__ void __launch_bounds__(128, 4) r" + S(gi) + "(const KR" + S(gi) +
              " A, double *pgrad, long long N, long long voff, int nx, int ny)\n{\n"
              "    double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;\n"
-             "    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < N; "
-             "k += (long long)gridDim.x * blockDim.x) {\n"
-             "        const int y = (int)(k / nx), x = (int)(k - (long long)y * nx);\n";
+             "    const long long tiles_x = (nx + 31) / 32, tpp = tiles_x * ((ny + 3) / 4);\n"
+             "    for (long long t = blockIdx.x; t < tpp; t += gridDim.x) {\n"
+             "        int x, y;\n"
+             "        long long k;\n"
+             "        if (!tile_node(t, tiles_x, tpp, nx, ny, N, x, y, k)) continue;\n";
         for (int q = 0; q < nslots; ++q) f += "        T s" + S(q) + " = T(0);\n";
         f += b + "    }\n";
         if (pgr) f += "    pgrad_add(q0, q1, q2, q3, pgrad);\n";
@@ -996,6 +1000,16 @@ template <typename T> struct Engine {
             "    xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);\n"
             "    yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);\n"
             "    return (long long)yy * nx + xx;\n}\n"
+            "// Node of this thread in tile t of a batch: tiles of 32 x 4 nodes (a warp per\n"
+            "// row, so vertical stencil taps are mostly shared through L1), tiles_x per\n"
+            "// row of tiles, tpp per step; false outside the grid.\n"
+            "__device__ __forceinline__ bool tile_node(long long t, long long tiles_x, long long tpp, int nx, int ny,\n"
+            "                                          long long N, int &x, int &y, long long &k)\n{\n"
+            "    const long long b = t / tpp, r = t - b * tpp, ty = r / tiles_x;\n"
+            "    x = (int)(r - ty * tiles_x) * 32 + (int)(threadIdx.x & 31);\n"
+            "    y = (int)ty * 4 + (int)(threadIdx.x >> 5);\n"
+            "    k = b * N + (long long)y * nx + x;\n"
+            "    return x < nx && y < ny;\n}\n"
             "__device__ __forceinline__ void pgrad_add(double q0, double q1, double q2, double q3, double *pg)\n{\n"
             "    __shared__ double red[4][32];\n"
             "    double v[4] = {q0, q1, q2, q3};\n"
