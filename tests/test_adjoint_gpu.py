@@ -59,6 +59,42 @@ def test_adjoint_fp64_matches_oracle_adjoint():
     assert dm == pytest.approx(gm.item(), rel=1e-10)
 
 
+# Tape structures other than the default one: each compiles its own level
+# kernels (the source depends on the flux correction, the number of Picard
+# sweeps, the filter order); gravity adds terms to the force.
+STRUCTURES = {
+    "no_flux_correction": dict(flux_correction=0),
+    "picard1_no_filter": dict(picard_iters=1, filter_order=0),
+    "picard3_sf5": dict(picard_iters=3, filter_order=5),
+    "sf7_gravity": dict(filter_order=7, gx=2e-6, gy=-3e-6, g_rho_ref=1.0),
+}
+
+
+@pytest.mark.parametrize("name", sorted(STRUCTURES))
+def test_compiled_levels_other_tape_structures(name):
+    """A 24 x 20 (non-square) drop carried by a uniform flow, 5 steps in
+    checkpoint segments of 2: the compiled FP64 sweep against the oracle
+    adjoint for each tape structure."""
+    nx, ny, R = 24, 20, 5.0
+    prm = inputs.base_params(M=0.1, sigma=5e-3, rho_H=100.0, rho_L=1.0, **STRUCTURES[name])
+    phi0 = inputs.drop(nx, ny, R, nx / 2, ny / 2, prm["W"])
+    fields = (phi0, np.zeros((ny, nx)), np.full((ny, nx), 0.01), np.zeros((ny, nx)))
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(float)
+    target = np.tanh(2.0 * (R + 0.5 - np.hypot(xx - nx / 2 - 0.7, yy - ny / 2)) / prm["W"])
+    steps = 5
+    loss, g, ds, dm = gpu_grad(prm, fields, target, steps, 2, "fp64")
+    phi = T(fields[0]).requires_grad_(True)
+    sig = T(prm["sigma"]).requires_grad_(True)
+    M = T(prm["M"]).requires_grad_(True)
+    r = tr.run(prm, phi, T(fields[1]), T(fields[2]), T(fields[3]), sig, M, steps)
+    lt = 0.5 * ((r["phi"] - T(target)) ** 2).sum()
+    gphi, gs, gm = torch.autograd.grad(lt, [phi, sig, M])
+    assert loss == pytest.approx(lt.item(), rel=1e-12)
+    assert np.abs(g - gphi.numpy()).max() <= 1e-10 * np.abs(gphi.numpy()).max()
+    assert ds == pytest.approx(gs.item(), rel=1e-10)
+    assert dm == pytest.approx(gm.item(), rel=1e-10)
+
+
 def test_adjoint_fp64_matches_gpu_finite_differences():
     prm, fields, target = case(n=24, R=6.0)
     steps = 10
