@@ -151,6 +151,19 @@ lbm_status lbm_set_fields(lbm_handle *h, const double *phi0, const double *p0,
 lbm_status lbm_diagnostics(lbm_handle *h, double *out);
 
 /*
+ * lbm_diagnostics_async -- the sums of lbm_diagnostics, enqueued on the
+ * handle's stream without waiting: the reduction kernels, then a copy of the
+ * LBM_NDIAG doubles into host out.  out (caller-owned) must stay valid until
+ * the stream has passed the copy (cudaStreamSynchronize or an event recorded
+ * after the call); it should be page-locked host memory, otherwise the copy
+ * is staged by the driver and may wait.  Calls on one handle are ordered by
+ * the stream, so a later call never overwrites an earlier result before it
+ * has been copied.  Lets a caller read back every step's sums while the next
+ * step already runs.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA.
+ */
+lbm_status lbm_diagnostics_async(lbm_handle *h, double *out);
+
+/*
  * lbm_check -- LBM_ERR_NONFINITE if any field value is NaN/Inf,
  * LBM_ERR_RANGE if phi leaves [-1-delta, 1+delta], LBM_ERR_CUDA if a kernel
  * of an earlier step gave up a bounded wait for a tile copy (its tile was

@@ -608,7 +608,7 @@ lbm_status init_impl(lbm_handle *h, const double *phi0, const double *p0, const 
 }
 
 template <typename T>
-lbm_status diag_impl(lbm_handle *h, double *out)
+lbm_status diag_impl(lbm_handle *h, double *out, bool sync = true)
 {
     const KP<T> &P = kp_of<T>(h);
     k_diag_partial<T><<<h->diag_blocks, DIAG_THREADS, 0, h->stream>>>(
@@ -618,7 +618,7 @@ lbm_status diag_impl(lbm_handle *h, double *out)
     CK(h, cudaGetLastError(), "diagnostics launch");
     CK(h, cudaMemcpyAsync(out, h->diag_out, sizeof(double) * NDIAG, cudaMemcpyDeviceToHost, h->stream),
        "diagnostics copy");
-    CK(h, cudaStreamSynchronize(h->stream), "diagnostics sync");
+    if (sync) CK(h, cudaStreamSynchronize(h->stream), "diagnostics sync");
     return LBM_OK;
 }
 
@@ -883,6 +883,13 @@ lbm_status lbm_diagnostics(lbm_handle *h, double *out)
     if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
     if (!out) return fail(h, LBM_ERR_ARG, "out must be non-NULL");
     return h->grid.precision == LBM_FP64 ? diag_impl<double>(h, out) : diag_impl<float>(h, out);
+}
+
+lbm_status lbm_diagnostics_async(lbm_handle *h, double *out)
+{
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
+    if (!out) return fail(h, LBM_ERR_ARG, "out must be non-NULL");
+    return h->grid.precision == LBM_FP64 ? diag_impl<double>(h, out, false) : diag_impl<float>(h, out, false);
 }
 
 lbm_status lbm_check(lbm_handle *h, double delta)

@@ -45,7 +45,7 @@ class LbmError(RuntimeError):
 
 
 EXPORTS = ("lbm_create", "lbm_step", "lbm_fields", "lbm_fields_device", "lbm_set_fields",
-           "lbm_diagnostics", "lbm_check", "lbm_get_state", "lbm_set_state",
+           "lbm_diagnostics", "lbm_diagnostics_async", "lbm_check", "lbm_get_state", "lbm_set_state",
            "lbm_profile", "lbm_profile_read", "lbm_kernel_name", "lbm_kernel_variant",
            "lbm_field_sums_noalloc", "lbm_noalloc_last_error",
            "lbm_adjoint_begin", "lbm_adjoint_end", "lbm_adjoint_engine",
@@ -78,6 +78,8 @@ def load(path=None):
     L.lbm_set_fields.argtypes = [vp, _dp, _dp, _dp, _dp]
     L.lbm_diagnostics.restype = C.c_int
     L.lbm_diagnostics.argtypes = [vp, _dp]
+    L.lbm_diagnostics_async.restype = C.c_int
+    L.lbm_diagnostics_async.argtypes = [vp, _dp]
     L.lbm_check.restype = C.c_int
     L.lbm_check.argtypes = [vp, C.c_double]
     L.lbm_get_state.restype = C.c_int
@@ -190,9 +192,14 @@ class Sim:
     def step(self, n=1):
         self._ck(self._lib.lbm_step(self._h, int(n)))
 
-    def fields(self):
+    def fields(self, out=None):
+        """(phi, p, ux, uy) as host float64 [ny, nx] arrays; out: four caller-owned
+        contiguous float64 arrays to fill (page-locked ones copy fastest)."""
         shp = (self.ny, self.nx)
-        out = [np.empty(shp) for _ in range(4)]
+        if out is None:
+            out = [np.empty(shp) for _ in range(4)]
+        elif len(out) != 4 or any(a.dtype != np.float64 or a.shape != shp or not a.flags.c_contiguous for a in out):
+            raise ValueError("out must be four contiguous float64 arrays of shape (ny, nx)")
         self._ck(self._lib.lbm_fields(self._h, *[_ptr(a) for a in out]))
         return tuple(out)
 
@@ -211,6 +218,14 @@ class Sim:
         o = np.empty(LBM_NDIAG) if out is None else out
         self._ck(self._lib.lbm_diagnostics(self._h, _ptr(o)))
         return o
+
+    def diagnostics_async(self, out):
+        """Enqueue the sums into out (a page-locked float64 array of LBM_NDIAG,
+        e.g. a pinned torch tensor's .numpy()); valid once the stream has passed."""
+        if out.dtype != np.float64 or out.size < LBM_NDIAG or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous float64 array of LBM_NDIAG values")
+        self._ck(self._lib.lbm_diagnostics_async(self._h, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
 
     def check(self, delta=0.05):
         return self._lib.lbm_check(self._h, C.c_double(delta))

@@ -202,6 +202,33 @@ def test_diagnostics_match_oracle(precision):
         assert dg[1] == do[1] and dg[2] == do[2]
 
 
+def test_diagnostics_async_matches_sync():
+    """lbm_diagnostics_async enqueues the same sums; three calls in flight,
+    read after one synchronisation, equal the synchronous ones of a twin run."""
+    import torch
+    prm, fields = inputs.rising_bubble(nx=48, ny=96, R=8.0, yc=30.0)
+    a = lbm.Sim(prm, *fields, precision="fp32")
+    b = lbm.Sim(prm, *fields, precision="fp32")
+    bufs = [torch.empty(lbm.LBM_NDIAG, dtype=torch.float64, pin_memory=True).numpy() for _ in range(3)]
+    ref = []
+    for buf in bufs:
+        a.step(5)
+        a.diagnostics_async(buf)
+        b.step(5)
+        ref.append(b.diagnostics().copy())
+    torch.cuda.synchronize()
+    for got, want in zip(bufs, ref):
+        assert np.allclose(got, want, rtol=1e-12, atol=0.0)
+    assert not np.allclose(ref[0], ref[2], rtol=1e-12, atol=0.0)   # the three results differ
+    with pytest.raises(ValueError):
+        a.diagnostics_async(np.empty(3))
+    outs = [torch.empty((96, 48), dtype=torch.float64, pin_memory=True).numpy() for _ in range(4)]
+    for x, y in zip(a.fields(out=outs), a.fields()):   # into caller-owned page-locked arrays
+        assert np.array_equal(x, y)
+    with pytest.raises(ValueError):
+        a.fields(out=[np.empty((48, 96))] * 4)
+
+
 def test_zero_steps_and_conservation_fp32():
     prm, fields = inputs.static_drop(n=40, R=10.0)
     g = lbm.Sim(prm, *fields, precision="fp32")
