@@ -1939,25 +1939,27 @@ __device__ __forceinline__ double warp_min(double v)
     return v;
 }
 
+constexpr int DSEG = 8;   // nodes a thread sums in T before adding to the FP64 sums
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_diag_partial(int nx, int ny, const T *__restrict__ phi, const T *__restrict__ p, const T *__restrict__ ux,
                const T *__restrict__ uy, double *__restrict__ part)
 {
     // block b takes rows b, b + gridDim.x, ...; each thread accumulates at
-    // most 16 nodes of a row in T before adding the segment to FP64 sums
+    // most DSEG nodes of a row in T before adding the segment to FP64 sums
     double s_ph = 0.0, s_v = 0.0, s_w = 0.0, s_wy = 0.0, s_wv = 0.0;
     long long n_pos = 0, n_neg = 0, s_y = 0, n_bad = 0;
     T mx = T(-INFINITY), mn = T(INFINITY);
     for (int y = blockIdx.x; y < ny; y += gridDim.x) {
         const long long r = (long long)y * nx;
         int npos = 0, nneg = 0;
-        // segments of 16 nodes per thread, their loads all issued first
-        for (int xs = threadIdx.x; xs < nx; xs += 16 * blockDim.x) {
+        // segments of DSEG nodes per thread, their loads all issued first
+        for (int xs = threadIdx.x; xs < nx; xs += DSEG * blockDim.x) {
             T a_ph = T(0), a_v = T(0), a_w = T(0), a_wv = T(0);
-            T ph[16], v[16], pp[16], uu[16];
+            T ph[DSEG], v[DSEG], pp[DSEG], uu[DSEG];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
+            for (int u = 0; u < DSEG; ++u) {
                 const int x = xs + u * blockDim.x;
                 const bool in = x < nx;
                 ph[u] = in ? phi[r + x] : T(0);
@@ -1966,7 +1968,7 @@ k_diag_partial(int nx, int ny, const T *__restrict__ phi, const T *__restrict__ 
                 uu[u] = in ? ux[r + x] : T(0);
             }
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
+            for (int u = 0; u < DSEG; ++u) {
                 if (xs + u * blockDim.x >= nx) break;
                 const T w = (T(1) - ph[u]) * T(0.5);
                 a_ph += ph[u];
