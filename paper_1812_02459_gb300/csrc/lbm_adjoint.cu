@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(NTH) kk_leaves(Leaves<T> L, long long N, int B
     }
 }
 
-constexpr int NTV = 128;   // threads of a level kernel (the compiled ones map them to 32 x 4 nodes)
+constexpr int NTV = 128;   // threads of an interpreter level kernel
 
 // Copy records (8-byte aligned) into shared memory; every thread of the
 // block takes part and the block waits for the copy.
@@ -476,6 +476,9 @@ template <typename T> struct Engine {
     struct JKernel { cudaKernel_t k = nullptr; std::vector<unsigned long long> pack; };
     std::vector<JKernel> jfwd, jrev;
     bool jit = false;                                   // the compiled kernels run the scheduled tape
+    static constexpr int JTY = 4;                       // compiled kernels: a block is a tile of 32 x JTY nodes
+    static constexpr int JT = 32 * JTY;                 // threads of a compiled level kernel
+    static std::string bounds() { return "__launch_bounds__(" + std::to_string(JT) + ", " + std::to_string(512 / JT) + ")"; }
     DStencil *d_tab = nullptr;
     int ntab = 0, nbv = 1;
     int smem_set = 0;
@@ -903,9 +906,9 @@ template <typename T> struct Engine {
             b += "        }\n";
         }
         std::string f = A.decl("KF" + S(gi));
-        f += "extern \"C\" __global__ void __launch_bounds__(128, 4) f" + S(gi) +
+        f += "extern \"C\" __global__ void " + bounds() + " f" + S(gi) +
              "(const KF" + S(gi) + " A, long long N, long long Ntot, long long voff, int nx, int ny)\n{\n"
-             "    const long long tiles_x = (nx + 31) / 32, tpp = tiles_x * ((ny + 3) / 4), ntiles = tpp * (Ntot / N);\n"
+             "    const long long tiles_x = (nx + 31) / 32, tpp = tiles_x * ((ny + JTY - 1) / JTY), ntiles = tpp * (Ntot / N);\n"
              "    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {\n"
              "        int x, y;\n"
              "        long long k;\n"
@@ -970,10 +973,10 @@ template <typename T> struct Engine {
             b += "        " + dst + "[k] = " + (F.assign ? std::string("") : dst + "[k] + ") + "s" + S(F.slot) + ";\n";
         }
         std::string f = A.decl("KR" + S(gi));
-        f += "extern \"C\" __global__ void __launch_bounds__(128, 4) r" + S(gi) + "(const KR" + S(gi) +
+        f += "extern \"C\" __global__ void " + bounds() + " r" + S(gi) + "(const KR" + S(gi) +
              " A, double *pgrad, long long N, long long voff, int nx, int ny)\n{\n"
              "    double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;\n"
-             "    const long long tiles_x = (nx + 31) / 32, tpp = tiles_x * ((ny + 3) / 4);\n"
+             "    const long long tiles_x = (nx + 31) / 32, tpp = tiles_x * ((ny + JTY - 1) / JTY);\n"
              "    for (long long t = blockIdx.x; t < tpp; t += gridDim.x) {\n"
              "        int x, y;\n"
              "        long long k;\n"
@@ -995,19 +998,20 @@ template <typename T> struct Engine {
         if (sw && sw[0] == '0') return;
         static_assert(NPARAM == 4, "generated kernels sum four parameter gradients");
         std::string src = std::string("typedef ") + (sizeof(T) == 8 ? "double" : "float") + " T;\n" +
+            "constexpr int JTY = " + S(JTY) + ";\n" +
             "__device__ __forceinline__ long long nbi(int x, int y, int dx, int dy, int nx, int ny)\n{\n"
             "    int xx = x + dx, yy = y + dy;\n"
             "    xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);\n"
             "    yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);\n"
             "    return (long long)yy * nx + xx;\n}\n"
-            "// Node of this thread in tile t of a batch: tiles of 32 x 4 nodes (a warp per\n"
+            "// Node of this thread in tile t of a batch: tiles of 32 x JTY nodes (a warp per\n"
             "// row, so vertical stencil taps are mostly shared through L1), tiles_x per\n"
             "// row of tiles, tpp per step; false outside the grid.\n"
             "__device__ __forceinline__ bool tile_node(long long t, long long tiles_x, long long tpp, int nx, int ny,\n"
             "                                          long long N, int &x, int &y, long long &k)\n{\n"
             "    const long long b = t / tpp, r = t - b * tpp, ty = r / tiles_x;\n"
             "    x = (int)(r - ty * tiles_x) * 32 + (int)(threadIdx.x & 31);\n"
-            "    y = (int)ty * 4 + (int)(threadIdx.x >> 5);\n"
+            "    y = (int)ty * JTY + (int)(threadIdx.x >> 5);\n"
             "    k = b * N + (long long)y * nx + x;\n"
             "    return x < nx && y < ny;\n}\n"
             "__device__ __forceinline__ void pgrad_add(double q0, double q1, double q2, double q3, double *pg)\n{\n"
@@ -1205,7 +1209,8 @@ template <typename T> struct Engine {
             int nxx = nx, nyy = ny;
             for (JKernel &J : jfwd) {
                 void *args[] = {J.pack.data(), &Nn, &Ntot, &voff, &nxx, &nyy};
-                check(cudaLaunchKernel((const void *)J.k, dim3(nblk), dim3(NTV), args, 0, st));
+                check(cudaLaunchKernel((const void *)J.k, dim3(std::max(1, (int)std::min<long long>((Ntot + JT - 1) / JT, 65535))),
+                                       dim3(JT), args, 0, st));
             }
         } else {
             for (const Group &G : fgroups)
@@ -1236,7 +1241,8 @@ template <typename T> struct Engine {
             double *pg = d_pgrad;
             for (JKernel &J : jrev) {
                 void *args[] = {J.pack.data(), &pg, &Nn, &voff, &nxx, &nyy};
-                check(cudaLaunchKernel((const void *)J.k, dim3(nbv), dim3(NTV), args, 0, s));
+                check(cudaLaunchKernel((const void *)J.k, dim3(std::max(1, (int)std::min<long long>((Nn + JT - 1) / JT, 8192))),
+                                       dim3(JT), args, 0, s));
             }
         } else {
             for (const RGroup &G : rgroups) {
