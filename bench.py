@@ -47,6 +47,13 @@ PROFILES = os.path.join(ROOT, "profiles")
 #   filter: read p_hat, u_hat(2); write p, u(2)                      -> 6
 KIND_WORDS = {"k_collide_stream": 48.0, "k_rk_stage": 8.0 / 3.0, "k_picard": 8.0, "k_filter": 6.0}
 VARIANT_WORDS = {"k_collide_pairs": 46.0}
+# Mixed-precision storage: the 34 population words of k_collide_pairs take 2
+# bytes, the 12 scalar words and the other kernels' 30 stay FP32:
+# 34 * 2 + (12 + 30) * 4 = 236 bytes per node and step.
+MIXED_STEP_BYTES = 34 * 2 + (12 + 30) * 4
+# The least a step must move (all intermediates on chip): populations read and
+# written once, phi, u^n, u^{n-1} read and phi, u^{n+1} written (8 words).
+B_MIN = {"fp32": 18 * 2 * 4 + 8 * 4, "mixed": 18 * 2 * 2 + 8 * 4}
 
 
 def algo_words(kind, variant):
@@ -401,7 +408,11 @@ def run_ours(args):
             torch.cuda.synchronize(dev)
             ms_v = a0.elapsed_time(a1) / k
             variants[prec] = {"MLUPS": round(N / ms_v / 1e3, 1), "ms_per_step": round(ms_v, 4), "steps": k,
-                              "vs_fp32": round((N / ms_v / 1e3) / (N / (ms_max / args.steps) / 1e3), 4)}
+                              "vs_fp32": round((N / ms_v / 1e3) / (N / (ms_max / args.steps) / 1e3), 4),
+                              "step_roofline": {"algorithmic_bytes_per_node": MIXED_STEP_BYTES,
+                                                "frac": round(MIXED_STEP_BYTES * N / (ms_v / 1e3) / 1e9 / peak, 4),
+                                                "b_min_bytes_per_node": B_MIN["mixed"],
+                                                "b_min_frac": round(B_MIN["mixed"] * N / (ms_v / 1e3) / 1e9 / peak, 4)}}
             v.close()
         an, asteps, aevery = args.adjoint_n, args.adjoint_steps, 22
         aprm, afields = inputs.translating_drop(n=an, R=an / 8.0, U0=0.01)
@@ -462,7 +473,10 @@ def run_ours(args):
             "roofline": roofline,
             "step_roofline": {"algorithmic_bytes_per_node": step_bytes / N,
                               "achieved_GBps": round(step_bytes / (ms_max / args.steps / 1e3) / 1e9, 1),
-                              "frac": round(step_bytes / (ms_max / args.steps / 1e3) / 1e9 / peak, 4)},
+                              "frac": round(step_bytes / (ms_max / args.steps / 1e3) / 1e9 / peak, 4),
+                              "b_min_bytes_per_node": B_MIN["fp32"] * elem // 4,
+                              "b_min_frac": round(B_MIN["fp32"] * elem // 4 * N / (ms_max / args.steps / 1e3) / 1e9
+                                                  / peak, 4)},
             "kernels": kernels,
             "variants": variants,
             "gpu_launches": gpu_launches,
