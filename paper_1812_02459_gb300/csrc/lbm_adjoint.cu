@@ -473,9 +473,10 @@ template <typename T> struct Engine {
     // compiled level kernels: the schedule written out as straight-line
     // CUDA C++ (one kernel per level and direction), plane pointers and
     // coefficients passed in one argument struct
-    struct JKernel { cudaKernel_t k = nullptr; std::vector<unsigned long long> pack; };
+    struct JKernel { cudaKernel_t k = nullptr; std::vector<unsigned long long> pack, pack_sw; int np = 0; };
     std::vector<JKernel> jfwd, jrev;
     bool jit = false;                                   // the compiled kernels run the scheduled tape
+    bool pingpong = false;                              // reverse packs with the state adjoints exchanged exist
     static constexpr int JTY = 4;                       // compiled kernels: a block is a tile of 32 x JTY nodes
     static constexpr int JT = 32 * JTY;                 // threads of a compiled level kernel
     static std::string bounds() { return "__launch_bounds__(" + std::to_string(JT) + ", " + std::to_string(512 / JT) + ")"; }
@@ -994,6 +995,7 @@ template <typename T> struct Engine {
         jit = false;
         jfwd.assign(fgroups.size(), JKernel{});
         jrev.assign(rgroups.size(), JKernel{});
+        pingpong = false;
         const char *sw = getenv("LBM_ADJOINT_COMPILED");
         if (sw && sw[0] == '0') return;
         static_assert(NPARAM == 4, "generated kernels sum four parameter gradients");
@@ -1054,6 +1056,7 @@ template <typename T> struct Engine {
         for (size_t g = 0; g < rgroups.size(); ++g) {
             if (cudaLibraryGetKernel(&jrev[g].k, lib, ("r" + S((int)g)).c_str()) != cudaSuccess) { cudaGetLastError(); return; }
             jrev[g].pack = ar[g].pack();
+            jrev[g].np = (int)ar[g].ptr.size();
         }
         jit = true;
     }
@@ -1220,12 +1223,43 @@ template <typename T> struct Engine {
         check(cudaGetLastError());
     }
 
+    // Let consecutive reverse passes of a step tape hand the state adjoint
+    // over without copies: a second argument pack of each compiled reverse
+    // kernel has the adjoint planes of the output state (the seeds, out[i])
+    // and of the input state (the leaves, in[i]) exchanged.  A pass with
+    // pack v reads its seeds from one set and leaves the input state's
+    // adjoint in the other, where the next pass, with pack 1 - v, finds its
+    // seeds.  Needs distinct, disjoint output and input planes, seeded by
+    // assignment, and every leaf reached by the sweep (so the leaf planes
+    // are overwritten, not added to, by each pass); false otherwise.
+    bool enable_pingpong(const int *in, const int *out, int n)
+    {
+        pingpong = false;
+        if (!jit || (int)seeds.size() != n) return false;
+        std::map<const void *, const void *> sw;
+        for (int i = 0; i < n; ++i) {
+            if (seeds[i].first != out[i] || seed_add[i] || !flowed[in[i]] || !adj[in[i]] || !adj[out[i]]) return false;
+            if (!sw.emplace(adj[out[i]], adj[in[i]]).second || !sw.emplace(adj[in[i]], adj[out[i]]).second) return false;
+        }
+        for (JKernel &J : jrev) {
+            J.pack_sw = J.pack;
+            for (int i = 0; i < J.np; ++i) {
+                auto it = sw.find((const void *)(uintptr_t)J.pack[i]);
+                if (it != sw.end()) J.pack_sw[i] = (unsigned long long)(uintptr_t)it->second;
+            }
+        }
+        pingpong = true;
+        return true;
+    }
+
     // Reverse pass, on rst, of step b of value buffer vb (values at b N in
-    // it), the seeded adjoints starting from the seeds.
-    void reverse(int b, int vb = 0)
+    // it).  ver < 0: the seeded adjoints start from the seeds; ver 0 / 1
+    // (compiled kernels with ping-pong): argument pack ver, seeded first
+    // only when seed is set.
+    void reverse(int b, int vb = 0, int ver = -1, bool seed = true)
     {
         cudaStream_t s = rst ? rst : st;
-        for (size_t s0 = 0; s0 < seeds.size(); s0 += MAXLEAF) {
+        for (size_t s0 = 0; seed && s0 < seeds.size(); s0 += MAXLEAF) {
             Leaves<T> Lv{};
             Lv.n = (int)std::min<size_t>(MAXLEAF, seeds.size() - s0);
             for (int i = 0; i < Lv.n; ++i) {
@@ -1240,7 +1274,7 @@ template <typename T> struct Engine {
             int nxx = nx, nyy = ny;
             double *pg = d_pgrad;
             for (JKernel &J : jrev) {
-                void *args[] = {J.pack.data(), &pg, &Nn, &voff, &nxx, &nyy};
+                void *args[] = {(ver == 1 ? J.pack_sw : J.pack).data(), &pg, &Nn, &voff, &nxx, &nyy};
                 check(cudaLaunchKernel((const void *)J.k, dim3(std::max(1, (int)std::min<long long>((Nn + JT - 1) / JT, 8192))),
                                        dim3(JT), args, 0, s));
             }
@@ -1545,7 +1579,8 @@ template <typename T> struct Recorder {
         o.ux = E.sten(ukx, S_FILTER);
         o.uy = E.sten(uky, S_FILTER);
         o.uhx = ukx; o.uhy = uky;
-        o.upx = s.ux; o.upy = s.uy;
+        o.upx = E.lin({{s.ux, 1.0}});   // u^{n-1} of the next step, a plane of its own
+        o.upy = E.lin({{s.uy, 1.0}});
         return o;
     }
 
@@ -1674,12 +1709,17 @@ template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, 
     E->prepare();
     if (E->err != cudaSuccess) return afail(h, LBM_ERR_CUDA, std::string("adjoint: ") + cudaGetErrorString(E->err));
     const int Bc = std::max(1, E->Bcap), nvb = E->nvbuf;
-    int ids[NSTATE];
+    int ids[NSTATE], ido[NSTATE];
     D *dst[NSTATE];
     for (int i = 0; i < NSTATE; ++i) {
         ids[i] = *slot(in, i);
+        ido[i] = *slot(out, i);
         dst[i] = lam + i * n;
     }
+    // compiled kernels: consecutive passes hand the state adjoint over by
+    // exchanging argument packs instead of collecting and re-seeding it
+    const bool pp = E->enable_pingpong(ids, ido, NSTATE);
+    int passes = 0;
     // Batches from the last step backwards: each segment from its end, Bc
     // steps at a time.  Producing a batch (regenerating its segment's states
     // with the fused forward kernels when it is the segment's last batch,
@@ -1727,9 +1767,13 @@ template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, 
         const Batch &b = bl[c];
         const int vb = c % nvb;
         cudaStreamWaitEvent(A->rs, evF[vb], 0);
-        for (int j = b.hi - 1; j >= b.lo; --j) {
-            E->reverse(j - b.lo, vb);
-            E->collect(ids, dst, NSTATE);
+        for (int j = b.hi - 1; j >= b.lo; --j, ++passes) {
+            if (pp) {
+                E->reverse(j - b.lo, vb, passes % 2, passes == 0);
+            } else {
+                E->reverse(j - b.lo, vb);
+                E->collect(ids, dst, NSTATE);
+            }
         }
         cudaEventRecord(evR[vb], A->rs);
     };
@@ -1742,6 +1786,8 @@ template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, 
             pst = afail(h, LBM_ERR_CUDA, std::string("adjoint: ") + cudaGetErrorString(E->err));
     }
     const bool step_jit = E->jit;
+    // the last pass left the input state's adjoint in the planes of pack (passes - 1) % 2
+    if (!pst && pp && passes > 0) E->collect((passes - 1) % 2 == 0 ? ids : ido, dst, NSTATE);
     // join: the handle's stream waits for the reverse stream's work
     cudaEventRecord(A->ev[4], A->rs);
     cudaStreamWaitEvent(h->stream, A->ev[4], 0);
