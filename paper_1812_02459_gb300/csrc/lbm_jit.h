@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <map>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -71,10 +72,13 @@ inline Nvrtc &nvrtc()
 }
 
 // The loaded library of a source on the current device, compiled on first
-// request; nullptr (and reason() set) on failure.
+// request; nullptr (and reason() set) on failure.  Serialised by one lock, so
+// handles used from several threads share the cache safely.
 inline cudaLibrary_t library(const std::string &src)
 {
     static std::map<std::pair<int, std::string>, cudaLibrary_t> cache;
+    static std::mutex lock;
+    std::lock_guard<std::mutex> guard(lock);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
     auto key = std::make_pair(dev, src);
