@@ -519,14 +519,14 @@ template <typename T>
 lbm_status upload_plane(lbm_handle *h, void *dst, const double *src)
 {
     const size_t n = (size_t)h->N;
-    if (sizeof(T) == sizeof(double)) {
+    if constexpr (sizeof(T) == sizeof(double)) {
         CK(h, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "upload");
-        return LBM_OK;
+    } else {
+        CK(h, cudaMemcpyAsync(staging(h), src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "upload");
+        k_cast<double, T><<<(int)std::min<long long>((h->N + 255) / 256, 4096), 256, 0, h->stream>>>(
+            staging(h), (T *)dst, h->N);
+        CK(h, cudaGetLastError(), "upload cast");
     }
-    CK(h, cudaMemcpyAsync(staging(h), src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "upload");
-    k_cast<double, T><<<(int)std::min<long long>((h->N + 255) / 256, 4096), 256, 0, h->stream>>>(
-        staging(h), (T *)dst, h->N);
-    CK(h, cudaGetLastError(), "upload cast");
     return LBM_OK;
 }
 
