@@ -38,7 +38,7 @@ constexpr int FS_TX = 64, FS_TY = 64, FS_VR = 8;     // FP32 filter: tile, rows 
 constexpr int RT_NT = 256, RT_MINB = 4;
 constexpr int PT_TX = 64, PT_TY = 16, PT_NT = 128, PT_VR1 = 6, PT_VR2 = 4, PT_MINB = 5;
 constexpr int FT_TX = 64, FT_TY = 32, FT_VR = 4, FT_MINB = 4;
-constexpr int CP_TX = 60, CP_TY = 14, CP_VR1 = 3;   // collide+stream on node pairs
+constexpr int CP_TX = 60, CP_TY = 14, CP_VR1 = 2;   // collide+stream on node pairs
 constexpr int DIAG_THREADS = 256;
 constexpr int DIAG_MAX_BLOCKS = 1216;    // 8 x 152 SMs
 
