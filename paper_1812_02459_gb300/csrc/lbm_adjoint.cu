@@ -569,6 +569,8 @@ template <typename T> struct Engine {
         carve(val, need, (size_t)N * Bcap * nvbuf, val_chunks);
     }
     long long vbase(int vb) const { return (long long)vb * Bcap * N; }   // start of value buffer vb
+    // Value plane of leaf i for step j of value buffer vb.
+    T *leaf_dst(int i, int vb, int j) { return val[leaves[i].first] + vbase(vb) + (long long)j * N; }
     template <typename U> int leaf(const U *src)
     {
         static_assert(sizeof(U) == sizeof(T) || sizeof(U) == sizeof(float), "leaf type");
@@ -1193,9 +1195,10 @@ template <typename T> struct Engine {
     // Forward pass of the tape for steps lo .. lo + cnt - 1 (cnt <= Bcap) in
     // one batch on st: leaf i of step j is read at its recorded source plus
     // j * leaf_stride; the step's values land at (j - lo) N in value buffer vb.
-    void forward(int lo, int cnt, int vb = 0)
+    // With leaves_in_place the leaf values are already in value buffer vb.
+    void forward(int lo, int cnt, int vb = 0, bool leaves_in_place = false)
     {
-        for (size_t b = 0; b < leaves.size(); b += MAXLEAF) {
+        for (size_t b = 0; !leaves_in_place && b < leaves.size(); b += MAXLEAF) {
             Leaves<T> Lv{};
             Lv.n = (int)std::min<size_t>(MAXLEAF, leaves.size() - b);
             for (int i = 0; i < Lv.n; ++i) {
@@ -1657,6 +1660,18 @@ cudaError_t copy_state_out(lbm_handle *h, void *dst)
 {
     return h->elem == sizeof(double) ? copy_state_t<double>(h, dst, true) : copy_state_t<float>(h, dst, true);
 }
+// The 26 state planes to 26 separate planes, one launch on the handle's stream.
+template <typename T> cudaError_t copy_state_to(lbm_handle *h, T *const *dst)
+{
+    Leaves<T> Lv{};
+    Lv.n = NSTATE;
+    for (int i = 0; i < NSTATE; ++i) {
+        Lv.dst[i] = dst[i];
+        Lv.src[i] = state_ptr(h, i);
+    }
+    kk_leaves<T><<<blocks_for(h->N), NTH, 0, h->stream>>>(Lv, h->N, 1, 0);
+    return cudaGetLastError();
+}
 cudaError_t copy_state_in(lbm_handle *h, const void *src)
 {
     void *s = const_cast<void *>(src);
@@ -1743,23 +1758,35 @@ template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, 
     }
     cudaEvent_t *evF = A->ev, *evR = A->ev + 2;
     E->rst = A->rs;
+    // When a batch holds a whole segment, regeneration stores each state
+    // straight into the batch's leaf value planes: no segment buffer and no
+    // copy of the leaves before the tape's forward pass.
+    const bool direct = Bc >= A->every;
     auto produce = [&](int c) -> lbm_status {
         const Batch &b = bl[c];
         const int vb = c % nvb;
+        if (direct && c >= nvb) cudaStreamWaitEvent(h->stream, evR[vb], 0);   // the buffer's last reader
         if (b.first) {
             if (copy_state_in(h, A->ckpt[b.seg]) != cudaSuccess) return afail(h, LBM_ERR_CUDA, "adjoint: restore");
             const int len = b.hi;
             for (int j = 0; j < len; ++j) {
-                if (copy_state_out(h, (char *)A->seg[0] + (size_t)j * NSTATE * pb) != cudaSuccess)
-                    return afail(h, LBM_ERR_CUDA, "adjoint: segment store");
+                cudaError_t e;
+                if (direct) {
+                    D *to[NSTATE];
+                    for (int i = 0; i < NSTATE; ++i) to[i] = E->leaf_dst(i, vb, j);
+                    e = copy_state_to<D>(h, to);
+                } else {
+                    e = copy_state_out(h, (char *)A->seg[0] + (size_t)j * NSTATE * pb);
+                }
+                if (e != cudaSuccess) return afail(h, LBM_ERR_CUDA, "adjoint: segment store");
                 if (j + 1 < len) {
                     lbm_status st = lbm_internal_step(h);
                     if (st) return st;
                 }
             }
         }
-        if (c >= nvb) cudaStreamWaitEvent(h->stream, evR[vb], 0);   // the buffer's last reader
-        E->forward(b.lo, b.hi - b.lo, vb);
+        if (!direct && c >= nvb) cudaStreamWaitEvent(h->stream, evR[vb], 0);   // the buffer's last reader
+        E->forward(b.lo, b.hi - b.lo, vb, direct);
         cudaEventRecord(evF[vb], h->stream);
         return LBM_OK;
     };
