@@ -247,6 +247,10 @@ lbm_status lbm_adjoint_end(lbm_handle *h, const double *dL_dphi, double *dL_dphi
  * compilation failed, or LBM_ADJOINT_COMPILED=0 in the environment), -1
  * before any reverse sweep or for a NULL handle.  Both give the same
  * gradients up to rounding order.
+ * The reverse sweep runs the tape's forward passes in batches of up to a
+ * checkpoint segment's steps, fewer if the value planes would exceed a
+ * quarter of the free device memory; LBM_ADJOINT_BATCH=<k> in the
+ * environment caps a batch at k steps (same gradients, less memory).
  */
 int lbm_adjoint_engine(const lbm_handle *h);
 

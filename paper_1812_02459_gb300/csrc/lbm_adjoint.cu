@@ -1612,7 +1612,7 @@ struct lbm_adjoint {
     int nsteps = 0, every = 1;
     size_t planeb = 0;
     std::vector<void *> ckpt;      // checkpoints: NSTATE planes each
-    std::vector<void *> seg;       // one segment of states
+    std::vector<void *> seg;       // one segment of states (when a segment spans several batches)
     void *init4 = nullptr;         // phi0, p0, ux0, uy0
     void *final_state = nullptr;   // state after nsteps
     void *lam = nullptr;           // adjoint state, NSTATE planes
@@ -1716,14 +1716,18 @@ template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, 
     // and a segment's states sit NSTATE planes apart
     E->reset();
     StateIds in;
-    for (int i = 0; i < NSTATE; ++i) *slot(in, i) = E->leaf((const T *)A->seg[0] + i * n);
+    // leaf i is slot i of a stored state; its source is set below when the
+    // segment buffer is used
+    for (int i = 0; i < NSTATE; ++i) *slot(in, i) = E->leaf((const T *)nullptr);
     StateIds out = R.step(in);
     for (int i = 0; i < NSTATE; ++i) E->seed(*slot(out, i), lam + i * n);
     E->Bwant = A->every;
+    if (const char *cap = getenv("LBM_ADJOINT_BATCH"))   // at most this many steps per batch
+        E->Bwant = std::max(1, std::min(A->every, atoi(cap)));
     E->leaf_stride = (long long)NSTATE * (long long)n;
     E->prepare();
     if (E->err != cudaSuccess) return afail(h, LBM_ERR_CUDA, std::string("adjoint: ") + cudaGetErrorString(E->err));
-    const int Bc = std::max(1, E->Bcap), nvb = E->nvbuf;
+    const int Bc = std::max(1, std::min(E->Bcap, E->Bwant)), nvb = E->nvbuf;
     int ids[NSTATE], ido[NSTATE];
     D *dst[NSTATE];
     for (int i = 0; i < NSTATE; ++i) {
@@ -1762,6 +1766,13 @@ template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, 
     // straight into the batch's leaf value planes: no segment buffer and no
     // copy of the leaves before the tape's forward pass.
     const bool direct = Bc >= A->every;
+    if (!direct) {
+        if (!A->seg[0] && cudaMalloc(&A->seg[0], sizeof(T) * n * NSTATE * (size_t)A->every) != cudaSuccess) {
+            cudaGetLastError();
+            return afail(h, LBM_ERR_OOM, "adjoint: segment buffer");
+        }
+        for (int i = 0; i < NSTATE; ++i) E->leaves[i].second = (const T *)A->seg[0] + i * n;
+    }
     auto produce = [&](int c) -> lbm_status {
         const Batch &b = bl[c];
         const int vb = c % nvb;
@@ -1897,8 +1908,7 @@ lbm_status lbm_adjoint_begin(lbm_handle *h, int nsteps, int checkpoint_every)
               alloc(&A->lam, sizeof(double) * (size_t)h->N * NSTATE);
     A->ckpt.assign(nseg, nullptr);
     for (int i = 0; ok && i < nseg; ++i) ok = alloc(&A->ckpt[i], sb);
-    A->seg.assign(1, nullptr);
-    ok = ok && alloc(&A->seg[0], sb * (size_t)checkpoint_every);
+    A->seg.assign(1, nullptr);   // allocated by the reverse sweep if a segment spans several batches
     if (!ok) {
         cudaGetLastError();
         lbm_internal_adjoint_free(h);

@@ -117,6 +117,22 @@ def test_adjoint_fp64_matches_gpu_finite_differences():
     assert float((g * v).sum()) == pytest.approx(fd_v, rel=1e-6)
 
 
+def test_segments_in_several_batches(monkeypatch):
+    """Segments of 3 steps reversed in batches of at most 2 steps (the path
+    with a segment buffer, taken when the value planes of a whole segment do
+    not fit): the same gradients as whole-segment batches -- the phi0
+    gradient bit for bit, sigma and M up to the order of their FP64 atomic
+    sums."""
+    prm, fields, target = case()
+    ref = gpu_grad(prm, fields, target, 7, 3, "fp64")
+    monkeypatch.setenv("LBM_ADJOINT_BATCH", "2")
+    got = gpu_grad(prm, fields, target, 7, 3, "fp64")
+    assert got[0] == ref[0]
+    assert np.array_equal(got[1], ref[1])
+    assert got[2] == pytest.approx(ref[2], rel=1e-12)
+    assert got[3] == pytest.approx(ref[3], rel=1e-12)
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
 def test_interpreter_matches_compiled_levels(monkeypatch, precision, tol):
     """The tape interpreter (the fallback when run-time compilation is not
