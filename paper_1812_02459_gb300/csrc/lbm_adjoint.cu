@@ -6,16 +6,20 @@
 // roots, the clamp of rho(phi), periodic stencils (isotropic gradient and
 // Laplacian, fourth-order differences, the selective filter, the streaming
 // shifts) and scalings by the differentiable parameters kappa, beta, M and
-// 1/tau_f -- each executed by a small kernel and recorded.  Each operation
-// has a hand-written vector-Jacobian product; the reverse sweep applies them
-// in reverse order.  The operations are executed a level at a time: the
-// stencils and pointwise operations between two layers of stencils run as
-// one kernel that applies them node by node, so a step costs one launch per
-// level in each direction.  Across steps, sqrt(N)-style checkpointing keeps every
-// k-th state, regenerates a segment with the fused forward kernels and
-// reverses it step by step.  Periodic axes, FP64 or FP32 populations; the
-// reverse sweep runs in the handle's arithmetic type, with the parameter
-// gradients summed in FP64.
+// 1/tau_f -- and recorded.  Each operation has a hand-written
+// vector-Jacobian product; the reverse sweep applies them in reverse order.
+// The operations run a level at a time: the stencils and pointwise
+// operations between two layers of stencils form one kernel that applies
+// them node by node, so a step costs one launch per level in each
+// direction.  The schedule of a tape (levels, per-thread slots, flushes) is
+// written out as straight-line CUDA C++ and compiled at run time (lbm_jit.h);
+// interpreter kernels that read the same schedule from operation records are
+// the fallback.  Across steps, sqrt(N)-style checkpointing keeps every k-th
+// state, regenerates a segment with the fused forward kernels and reverses
+// it step by step, the tape's forward passes of a segment batched and
+// overlapped with the reverse passes on a second stream.  Periodic axes,
+// FP64 or FP32 populations; the reverse sweep runs in the handle's arithmetic
+// type, with the parameter gradients summed in FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
