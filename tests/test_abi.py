@@ -83,3 +83,26 @@ def test_invalid_rates_and_sizes_rejected():
     prm, fields = inputs.static_drop(n=16, R=4.0)
     with pytest.raises(KeyError):
         lbm.Sim(prm, *fields, precision="fp8")
+
+
+def test_null_handle_rejected_without_cuda():
+    """Every entry point given a NULL handle (or a NULL required pointer)
+    returns LBM_ERR_ARG -- or -1 / nothing where that is its documented
+    answer -- before any CUDA call, so this runs without a GPU."""
+    L = lbm.load()
+    ARG = 1
+    d = np.zeros(lbm.LBM_NDIAG)
+    pd = d.ctypes.data_as(C.POINTER(C.c_double))
+    assert L.lbm_step(None, 1) == ARG
+    assert L.lbm_diagnostics(None, pd) == ARG
+    assert L.lbm_diagnostics_async(None, pd) == ARG
+    assert L.lbm_check(None, C.c_double(0.01)) == ARG
+    assert L.lbm_fields(None, pd, pd, pd, pd) == ARG
+    assert L.lbm_set_fields(None, pd, pd, pd, pd) == ARG
+    assert L.lbm_adjoint_begin(None, 4, 2) == ARG
+    assert L.lbm_adjoint_end(None, pd, pd, pd, pd) == ARG
+    assert L.lbm_adjoint_engine(None) == -1
+    assert L.lbm_profile(None, 1) == ARG
+    L.lbm_destroy(None)
+    assert L.lbm_diagnostics_async(None, pd) == ARG
+    assert L.lbm_last_error(None) == b"NULL handle"
