@@ -46,6 +46,8 @@ def lib():
         L.orc_create.argtypes = [C.POINTER(OrcParams), _dp, _dp, _dp, _dp, C.POINTER(C.c_void_p)]
         L.orc_step.restype = C.c_int
         L.orc_step.argtypes = [C.c_void_p, C.c_int]
+        L.orc_step_ch.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
+        L.orc_step_ch.restype = C.c_int
         L.orc_fields.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
         L.orc_state.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, _dp, _dp]
         L.orc_set_state.argtypes = [C.c_void_p] + [_dp] * 10
@@ -245,6 +247,13 @@ class Sim:
         rc = lib().orc_step(self._h, C.c_int(n))
         if rc != 0:
             raise FloatingPointError(f"oracle step returned {rc} (non-finite field)")
+
+    def step_ch(self, ux, uy, n=1):
+        """n steps of the Cahn-Hilliard part alone under the prescribed velocity (ux, uy)."""
+        ux, uy = _f64(ux), _f64(uy)
+        rc = lib().orc_step_ch(self._h, C.c_int(n), _ptr(ux), _ptr(uy))
+        if rc != 0:
+            raise FloatingPointError(f"oracle CH step returned {rc} (non-finite phi)")
 
     def fields(self):
         shp = (self.ny, self.nx)

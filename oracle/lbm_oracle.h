@@ -80,6 +80,10 @@ void orc_rk3(int n, const double *phibar, double *out, orc_rhs_fn L, void *ctx);
 int  orc_create(const orc_params *prm, const double *phi0, const double *p0,
                 const double *ux0, const double *uy0, orc_sim **out);
 int  orc_step(orc_sim *s, int n);
+/* n steps of the Cahn-Hilliard part alone under the prescribed velocity
+   (ux, uy) [ny][nx] (held for the n steps): collide and stream f, phi_bar,
+   TVD-RK3.  Returns 2 on a non-finite phi. */
+int  orc_step_ch(orc_sim *s, int n, const double *ux, const double *uy);
 void orc_fields(const orc_sim *s, double *phi, double *p, double *ux, double *uy);
 void orc_state(const orc_sim *s, double *f, double *g, double *uhx, double *uhy,
                double *upx, double *upy);
