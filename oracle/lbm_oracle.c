@@ -35,10 +35,11 @@
  * transfer function; the RK3 growth factor; conservation of sum(phi); a flat
  * interface staying put; the Laplace law; viscous decay of a shear wave;
  * hydrostatic balance; Galilean translation of a drop; a layered channel
- * against its 1-D steady solution; removal of normal diffusion by q.
- * Parity unpinned: the F_m = J.grad u force term (below what any of these
- * resolves) and the choice of u_hat inside the filtered-equilibrium reading
- * above (a reading, not a law); both are covered only by GPU-oracle parity.
+ * against its 1-D steady solution; removal of normal diffusion by q; the
+ * azimuthal acceleration Omega J_r that F_m = J.grad u alone gives a
+ * non-equilibrium drop in rigid rotation.
+ * The choice of u_hat inside the filtered-equilibrium reading above is a
+ * reading, not a law, and has no pin beyond GPU-oracle parity.
  */
 #include "lbm_oracle.h"
 

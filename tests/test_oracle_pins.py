@@ -469,3 +469,61 @@ def test_layered_channel_viscous_stress(rho_ref):
     num = ux[:, 0]
     assert abs(num.max() / u_ref.max() - 1) < 5e-3
     assert np.abs(num - u_ref).max() < 8e-3 * u_ref.max()
+
+
+def _ring_mean_azimuthal(ux, uy, X, Y, r, edges):
+    ut = (-Y * ux + X * uy) / np.maximum(r, 1e-12)
+    return np.array([ut[(r >= a) & (r < b)].mean() for a, b in zip(edges[:-1], edges[1:])])
+
+
+def test_diffusive_momentum_force_on_rigid_rotation():
+    """F_m = J.grad u (Sec. II.B Eq. reformNS), J = (d rho/d phi) M grad mu.
+
+    A drop whose tanh profile is twice as wide as W (so mu varies across it)
+    sits in rigid rotation u = Omega (-y, x).  Rigid rotation has no strain,
+    so F_nu vanishes, and F_p, F_s, F_g are radial by symmetry: the only
+    azimuthal force is F_m, whose azimuthal part is Omega J_r.  Over T steps
+    the ring-averaged u_theta therefore gains T <Omega J_r / rho>.  A run with
+    sigma = 0 (mu = 0, so J = 0) supplies every other drift of the discrete
+    flow, and mu of Sec. II.A Eq. (chemical) is evaluated here by spectral
+    derivatives of phi.  A dropped, transposed (J_a d_b u_a, which is -F_m
+    for a rotation), sign-flipped or d rho/d phi-less F_m misses by >= 99%."""
+    n, R, W0, Om, T = 64, 10.0, 8.0, 1e-3, 20
+    prm = inputs.base_params(rho_H=100.0, rho_L=1.0, nu_H=0.01, nu_L=0.01, sigma=0.02, M=0.2)
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    X, Y = x - n / 2, y - n / 2
+    r = np.hypot(X, Y)
+    phi0 = np.tanh(2 * (R - r) / W0)
+    env = np.clip((R + 22 - r) / 12.0, 0, 1)          # rigid out to r = R + 10, at rest beyond R + 22
+    env = env * env * (3 - 2 * env)
+    ux0, uy0 = -Om * Y * env, Om * X * env
+    edges = np.arange(0, R + 10, 1.0)
+    u_start = _ring_mean_azimuthal(ux0, uy0, X, Y, r, edges)
+    gain = []
+    for sig in (prm["sigma"], 0.0):
+        s = oracle.Sim(dict(prm, sigma=sig), phi0, np.zeros((n, n)), ux0, uy0)
+        s.step(T)
+        phi, _, ux, uy = s.fields()
+        gain.append(_ring_mean_azimuthal(ux, uy, X, Y, r, edges) - u_start)
+        if sig > 0:
+            phiT = phi
+    measured = gain[0] - gain[1]
+
+    k = 2 * np.pi * np.fft.fftfreq(n)
+    KY, KX = np.meshgrid(k, k, indexing="ij")
+    kap, bet = 3 * prm["sigma"] * prm["W"] / 8, 3 * prm["sigma"] / (4 * prm["W"])
+    drho = (prm["rho_H"] - prm["rho_L"]) / 2
+
+    def predicted(ph):
+        P = np.fft.fft2(ph)
+        mu = 4 * bet * (ph ** 3 - ph) - kap * np.real(np.fft.ifft2(-(KX ** 2 + KY ** 2) * P))
+        Mu = np.fft.fft2(mu)
+        Jx = drho * prm["M"] * np.real(np.fft.ifft2(1j * KX * Mu))
+        Jy = drho * prm["M"] * np.real(np.fft.ifft2(1j * KY * Mu))
+        c = np.clip(ph, -1, 1)
+        rho = prm["rho_H"] * (1 + c) / 2 + prm["rho_L"] * (1 - c) / 2
+        return T * _ring_mean_azimuthal(-Om * Jy / rho, Om * Jx / rho, X, Y, r, edges)
+
+    expect = 0.5 * (predicted(phi0) + predicted(phiT))
+    assert np.abs(expect).max() > 1e-3 * Om * R          # the effect is resolved
+    assert np.linalg.norm(measured - expect) < 0.25 * np.linalg.norm(expect)
