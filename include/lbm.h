@@ -113,7 +113,11 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params,
  * lbm_step -- advance n >= 0 time steps (the whole Sec. III update each
  * step: fields and forces, collision and streaming of both lattices, the
  * RK3 finite-difference correction, the implicit velocity, the filter).
- * Asynchronous on the handle's stream.
+ * Asynchronous on the handle's stream.  Errors: LBM_ERR_ARG for n < 0;
+ * LBM_ERR_STATE once a synchronising call has reported that a kernel gave
+ * up a bounded wait for a tile copy (see lbm_check): that step left its tile
+ * un-updated and a copy landing late may still write the kernel's shared
+ * memory, so the handle refuses further steps and must be destroyed.
  */
 lbm_status lbm_step(lbm_handle *h, int n);
 
@@ -167,9 +171,27 @@ lbm_status lbm_diagnostics_async(lbm_handle *h, double *out);
  * lbm_check -- LBM_ERR_NONFINITE if any field value is NaN/Inf,
  * LBM_ERR_RANGE if phi leaves [-1-delta, 1+delta], LBM_ERR_CUDA if a kernel
  * of an earlier step gave up a bounded wait for a tile copy (its tile was
- * then not updated), else LBM_OK.  Synchronises the stream.
+ * then not updated), else LBM_OK.  Synchronises the stream.  The device
+ * word that records a given-up wait is also read by lbm_fields,
+ * lbm_diagnostics, lbm_get_state and the adjoint calls, which then return
+ * LBM_ERR_CUDA; from then on lbm_step returns LBM_ERR_STATE.
  */
 lbm_status lbm_check(lbm_handle *h, double delta);
+
+/*
+ * lbm_set_check -- periodic finite and range check inside lbm_step.  With
+ * every = k > 0, lbm_step enqueues the sums of lbm_diagnostics after every
+ * k-th step on the handle's stream, into page-locked host memory the handle
+ * owns, without waiting for them.  Each later lbm_step call first looks at
+ * the last such result the stream has already passed (it never waits): if
+ * it counted a non-finite value it returns LBM_ERR_NONFINITE, if phi left
+ * [-1-delta, 1+delta] it returns LBM_ERR_RANGE, before issuing any work,
+ * and keeps returning it until lbm_set_fields or lbm_set_state.  At most one
+ * check is in flight; every = 0 (the default) turns the check off.
+ * lbm_check remains the synchronising check.  Errors: LBM_ERR_ARG (every < 0,
+ * delta < 0), LBM_ERR_CUDA (page-locked allocation).
+ */
+lbm_status lbm_set_check(lbm_handle *h, int every, double delta);
 
 /*
  * lbm_get_state / lbm_set_state -- the full state between steps, as host

@@ -1642,7 +1642,7 @@ void *state_ptr(lbm_handle *h, int i)
     const size_t pb = h->elem * (size_t)h->N;
     if (i < 9) return (char *)h->f[h->cur] + i * pb;
     if (i < 18) return (char *)h->g[h->cur] + (i - 9) * pb;
-    void *r[8] = {h->phi, h->pf, h->ux[h->ucur], h->uy[h->ucur], h->uhx, h->uhy, h->ux[1 - h->ucur], h->uy[1 - h->ucur]};
+    void *r[8] = {phi_cur(h), h->pf, h->ux[h->ucur], h->uy[h->ucur], h->uhx, h->uhy, h->ux[1 - h->ucur], h->uy[1 - h->ucur]};
     return r[i - 18];
 }
 
@@ -1919,7 +1919,7 @@ lbm_status lbm_adjoint_begin(lbm_handle *h, int nsteps, int checkpoint_every)
         return afail(h, LBM_ERR_OOM, "adjoint: checkpoint allocation");
     }
     // the initial fields: phi0, p0, u0 of the fresh state
-    cudaMemcpyAsync(A->init4, h->phi, pb, cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemcpyAsync(A->init4, phi_cur(h), pb, cudaMemcpyDeviceToDevice, h->stream);
     cudaMemcpyAsync((char *)A->init4 + pb, h->pf, pb, cudaMemcpyDeviceToDevice, h->stream);
     cudaMemcpyAsync((char *)A->init4 + 2 * pb, h->ux[h->ucur], pb, cudaMemcpyDeviceToDevice, h->stream);
     cudaMemcpyAsync((char *)A->init4 + 3 * pb, h->uy[h->ucur], pb, cudaMemcpyDeviceToDevice, h->stream);
@@ -1932,6 +1932,8 @@ lbm_status lbm_adjoint_begin(lbm_handle *h, int nsteps, int checkpoint_every)
     if (copy_state_out(h, A->final_state) != cudaSuccess) return afail(h, LBM_ERR_CUDA, "adjoint: final copy");
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return afail(h, LBM_ERR_CUDA, std::string("adjoint forward: ") + cudaGetErrorString(e));
+    lbm_status pst = lbm_internal_poll_device_error(h);
+    if (pst) return pst;
     A->ready = true;
     return LBM_OK;
 }
@@ -1949,7 +1951,7 @@ lbm_status lbm_adjoint_end(lbm_handle *h, const double *dL_dphi, double *dL_dphi
     if (!dL_dphi) return afail(h, LBM_ERR_ARG, "dL_dphi must be non-NULL");
     lbm_status st = h->grid.precision == LBM_FP64 ? run_reverse<double>(h, dL_dphi, dL_dphi0, dL_dsigma, dL_dM)
                                                   : run_reverse<float>(h, dL_dphi, dL_dphi0, dL_dsigma, dL_dM);
-    return st;
+    return st ? st : lbm_internal_poll_device_error(h);
 }
 
 }  // extern "C"

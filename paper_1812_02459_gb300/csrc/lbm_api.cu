@@ -375,11 +375,13 @@ lbm_status step_impl(lbm_handle *h)
     const KP<T> &P = kp_of<T>(h);
     cudaStream_t st = h->stream;
     const int c = h->cur, u = h->ucur;
-    T *phi = (T *)h->phi, *pf = (T *)h->pf;
+    // phi^n; the other phi slot holds phi^{n-1} (the phi the stored
+    // populations were collided with) and receives phi^{n+1}
+    T *phi = (T *)h->phi[h->pcur], *phin = (T *)h->phi[1 - h->pcur], *pf = (T *)h->pf;
     T *uxc = (T *)h->ux[u], *uyc = (T *)h->uy[u], *uxp = (T *)h->ux[1 - u], *uyp = (T *)h->uy[1 - u];
     T *uhx = (T *)h->uhx, *uhy = (T *)h->uhy;
-    const T *phibar_old = (const T *)h->phibar[h->acur], *phat_old = (const T *)h->phat[h->acur];
-    T *phibar = (T *)h->phibar[1 - h->acur], *phat = (T *)h->phat[1 - h->acur];
+    const T *dbar_old = (const T *)h->dbar[h->acur], *phat_old = (const T *)h->phat[h->acur];
+    T *dbar = (T *)h->dbar[1 - h->acur], *phat = (T *)h->phat[1 - h->acur];
     T *jx = (T *)h->jx, *jy = (T *)h->jy;
 
     {   // fields, forces, collision of f and g, pull streaming, post-stream moments
@@ -398,7 +400,7 @@ lbm_status step_impl(lbm_handle *h)
                 const int ntiles = ((P.nx + CP_TX - 1) / CP_TX) * ((P.ny + CP_TY - 1) / CP_TY);
                 k_collide_pairs<S, CP_TX, CP_TY, CP_VR1><<<ntiles, GC::NT, GC::Tile::BYTES, st>>>(
                     maps, P, (const S *)h->f[c], (const S *)h->g[c], (S *)h->f[1 - c], (S *)h->g[1 - c], phi, pf,
-                    uxc, uyc, uxp, uyp, uhx, uhy, phibar, phat, jx, jy, h->dev_err);
+                    uxc, uyc, uxp, uyp, uhx, uhy, dbar, phat, jx, jy, h->dev_err);
                 done = true;
             }
         }
@@ -407,36 +409,40 @@ lbm_status step_impl(lbm_handle *h)
                                               : k_collide_stream<T, S, CS_TX, CS_TY, false>;
             kern<<<grid, (CS_TX + 2) * (CS_TY + 2), smem_cs<T>(), st>>>(
                 P, (const S *)h->f[c], (const S *)h->g[c], (S *)h->f[1 - c], (S *)h->g[1 - c], phi, pf, uxc, uyc,
-                uxp, uyp, uhx, uhy, phibar_old, phat_old, phibar, phat, jx, jy);
+                uxp, uyp, uhx, uhy, phin, dbar_old, phat_old, dbar, phat, jx, jy);
         }
     }
-    {   // TVD-RK3 finite-difference correction: phi_bar -> phi^{n+1}
+    {   // TVD-RK3 finite-difference correction in increments over phi^n:
+        // dbar -> d1 -> d2 -> phi^{n+1} = phi^n + d3
         dim3 grid((P.nx + RK_TX - 1) / RK_TX, (P.ny + RK_TY - 1) / RK_TY);
         const size_t sm = smem_rk<T>();
-        const T *src[3] = {phibar, (const T *)h->s1, (const T *)h->s2};
-        T *dst[3] = {(T *)h->s1, (T *)h->s2, phi};
+        const T *src[3] = {dbar, (const T *)h->s1, (const T *)h->s2};
+        T *dst[3] = {(T *)h->s1, (T *)h->s2, phin};
         const T ca[3] = {T(0), T(0.75), T(1.0 / 3.0)}, cb[3] = {T(1), T(0.25), T(2.0 / 3.0)};
         for (int k = 0; k < 3; ++k) {
             Timed tm(h, 1);
+            const int last = k == 2;
             bool done = false;
             if constexpr (std::is_same<T, float>::value) {
                 if (h->tma) {   // TMA-staged windows, one CTA per tile
                     using GT = RKTGeom<RK_TX, RK_TY>;
                     TmaMaps maps{};
-                    lbm_status r = tmap(h, src[k], GT::BW, GT::BH, &maps.m[0]);
+                    lbm_status r = tmap(h, phi, GT::BW, GT::BH, &maps.m[0]);
+                    if (!r) r = tmap(h, src[k], GT::BW, GT::BH, &maps.m[1]);
                     if (r) return r;
                     k_rk_tma<RK_TX, RK_TY, RT_NT, RS_VR1, RS_VR2, RS_VR3, RT_MINB>
-                        <<<grid.x * grid.y, RT_NT, GT::Tile::BYTES, st>>>(maps, P, src[k], phibar, dst[k], ca[k],
-                                                                         cb[k], h->dev_err);
+                        <<<grid.x * grid.y, RT_NT, GT::Tile::BYTES, st>>>(maps, P, phi, src[k], dbar, dst[k],
+                                                                         ca[k], cb[k], last, h->dev_err);
                     done = true;
                 } else if (P.nx % 2 == 0) {   // column-pair strips, paired FP32 arithmetic
                     k_rk_strips<RK_TX, RK_TY, RS_NT, RS_VR1, RS_VR2, RS_VR3><<<grid, RS_NT, sm, st>>>(
-                        P, src[k], phibar, dst[k], ca[k], cb[k]);
+                        P, phi, src[k], dbar, dst[k], ca[k], cb[k], last);
                     done = true;
                 }
             }
             if (!done)
-                k_rk_stage<T, RK_TX, RK_TY, RK_NT><<<grid, RK_NT, sm, st>>>(P, src[k], phibar, dst[k], ca[k], cb[k]);
+                k_rk_stage<T, RK_TX, RK_TY, RK_NT><<<grid, RK_NT, sm, st>>>(P, phi, src[k], dbar, dst[k], ca[k],
+                                                                          cb[k], last);
         }
     }
     {   // implicit velocity by Picard sweeps; the last sweep lands in u_hat
@@ -452,26 +458,26 @@ lbm_status step_impl(lbm_handle *h)
                 if (h->tma) {   // TMA-staged windows, one CTA per tile
                     using GT = PCTGeom<PT_TX, PT_TY>;
                     TmaMaps maps{};
-                    const void *planes[4] = {phi, phat, ix, iy};
+                    const void *planes[4] = {phin, phat, ix, iy};
                     for (int f = 0; f < 4; ++f) {
                         lbm_status r = tmap(h, planes[f], GT::BW, GT::BH, &maps.m[f]);
                         if (r) return r;
                     }
                     const int ntiles = ((P.nx + PT_TX - 1) / PT_TX) * ((P.ny + PT_TY - 1) / PT_TY);
                     k_picard_tma<PT_TX, PT_TY, PT_NT, PT_VR1, PT_VR2, PT_MINB>
-                        <<<ntiles, PT_NT, GT::Tile::BYTES, st>>>(maps, P, phi, phat, jx, jy, ix, iy, ox, oy,
+                        <<<ntiles, PT_NT, GT::Tile::BYTES, st>>>(maps, P, phin, phat, jx, jy, ix, iy, ox, oy,
                                                                  h->dev_err);
                     continue;
                 }
                 if (P.nx % 2 == 0) {   // column-pair strips, paired FP32 arithmetic
                     dim3 gs((P.nx + PS_TX - 1) / PS_TX, (P.ny + PS_TY - 1) / PS_TY);
                     k_picard_strips<PS_TX, PS_TY, PS_NT, PS_VR1, PS_VR2>
-                        <<<gs, PS_NT, sizeof(float) * PSGeom<PS_TX, PS_TY>::NSCALAR, st>>>(P, phi, phat, jx, jy, ix, iy,
+                        <<<gs, PS_NT, sizeof(float) * PSGeom<PS_TX, PS_TY>::NSCALAR, st>>>(P, phin, phat, jx, jy, ix, iy,
                                                                                          ox, oy);
                     continue;
                 }
             }
-            k_picard<T, PC_TX, PC_TY, PC_NT><<<grid, PC_NT, smem_pc<T>(), st>>>(P, phi, phat, jx, jy, ix, iy, ox, oy);
+            k_picard<T, PC_TX, PC_TY, PC_NT><<<grid, PC_NT, smem_pc<T>(), st>>>(P, phin, phat, jx, jy, ix, iy, ox, oy);
         }
     }
     // selective filter of (p_hat, u_hat) -> (p_f, u_f^{n+1}); u^{n-1} slot is reused
@@ -507,6 +513,7 @@ lbm_status step_impl(lbm_handle *h)
     h->cur ^= 1;
     h->ucur ^= 1;
     h->acur ^= 1;
+    h->pcur ^= 1;
     return LBM_OK;
 }
 
@@ -583,7 +590,8 @@ template <typename T, typename S>
 lbm_status init_impl(lbm_handle *h, const double *phi0, const double *p0, const double *ux0, const double *uy0)
 {
     lbm_status st;
-    if ((st = upload_plane<T>(h, h->phi, phi0))) return st;
+    h->pcur = 0;
+    if ((st = upload_plane<T>(h, h->phi[0], phi0))) return st;
     if ((st = upload_plane<T>(h, h->pf, p0))) return st;
     if ((st = upload_plane<T>(h, h->ux[0], ux0))) return st;
     if ((st = upload_plane<T>(h, h->uy[0], uy0))) return st;
@@ -595,15 +603,20 @@ lbm_status init_impl(lbm_handle *h, const double *phi0, const double *p0, const 
     CK(h, cudaMemcpyAsync(h->uy[1], h->uy[0], b, cudaMemcpyDeviceToDevice, h->stream), "init copy");
     CK(h, cudaMemcpyAsync(h->uhx, h->ux[0], b, cudaMemcpyDeviceToDevice, h->stream), "init copy");
     CK(h, cudaMemcpyAsync(h->uhy, h->uy[0], b, cudaMemcpyDeviceToDevice, h->stream), "init copy");
+    // the previous-step slot of phi equals phi: the stored populations sum to it
+    CK(h, cudaMemcpyAsync(h->phi[1], h->phi[0], b, cudaMemcpyDeviceToDevice, h->stream), "init copy");
     h->acur = 0;
     const KP<T> &P = kp_of<T>(h);
     int blocks = (int)std::min<long long>((P.N + 255) / 256, 4096);
-    k_init<T, S><<<blocks, 256, 0, h->stream>>>(P, (const T *)h->phi, (const T *)h->pf, (const T *)h->ux[0],
+    k_init<T, S><<<blocks, 256, 0, h->stream>>>(P, (const T *)h->phi[0], (const T *)h->pf, (const T *)h->ux[0],
                                                  (const T *)h->uy[0], (S *)h->f[0], (S *)h->g[0],
-                                                 (T *)h->phibar[0], (T *)h->phat[0]);
+                                                 (T *)h->dbar[0], (T *)h->phat[0]);
     CK(h, cudaGetLastError(), "init kernel");
     CK(h, cudaStreamSynchronize(h->stream), "init sync");
     h->fresh_init = true;
+    h->chk_pending = false;
+    h->chk_status = LBM_OK;
+    h->chk_count = 0;
     return LBM_OK;
 }
 
@@ -612,7 +625,7 @@ lbm_status diag_impl(lbm_handle *h, double *out, bool sync = true)
 {
     const KP<T> &P = kp_of<T>(h);
     k_diag_partial<T><<<h->diag_blocks, DIAG_THREADS, 0, h->stream>>>(
-        P.nx, P.ny, (const T *)h->phi, (const T *)h->pf, (const T *)h->ux[h->ucur], (const T *)h->uy[h->ucur],
+        P.nx, P.ny, (const T *)phi_cur(h), (const T *)h->pf, (const T *)h->ux[h->ucur], (const T *)h->uy[h->ucur],
         h->diag_part);
     k_diag_final<<<1, 32 * NDIAG, 0, h->stream>>>(h->diag_blocks, h->diag_part, h->diag_out);
     CK(h, cudaGetLastError(), "diagnostics launch");
@@ -626,7 +639,7 @@ template <typename T>
 lbm_status fields_impl(lbm_handle *h, double *phi, double *p, double *ux, double *uy)
 {
     lbm_status st;
-    if ((st = download_plane<T>(h, phi, h->phi))) return st;
+    if ((st = download_plane<T>(h, phi, phi_cur(h)))) return st;
     if ((st = download_plane<T>(h, p, h->pf))) return st;
     if ((st = download_plane<T>(h, ux, h->ux[h->ucur]))) return st;
     if ((st = download_plane<T>(h, uy, h->uy[h->ucur]))) return st;
@@ -642,18 +655,21 @@ template <typename S> S host_store(float v) { return S(v); }
 template <> __half host_store<__half>(float v) { return __float2half_rn(v * 16384.0f); }
 
 // Rebuild full population sets on the host from reduced-precision storage:
-// f_q, g_q - 3 w_q p_hat stored for q = 1..8; f_0, g_0 from the moments.
+// f_q, g_q - 3 w_q p_hat stored for q = 1..8; f_0, g_0 from the moments
+// (phi_bar = phi of the previous step + dbar).
 template <typename T, typename S>
 lbm_status decode_mixed(lbm_handle *h, double *f, double *g)
 {
     const size_t n = (size_t)h->N;
     std::vector<S> fs(9 * n), gs(9 * n);
-    std::vector<T> pb(n), ph(n);
+    std::vector<T> pb(n), db(n), ph(n);
     CK(h, cudaMemcpyAsync(fs.data(), h->f[h->cur], 9 * n * sizeof(S), cudaMemcpyDeviceToHost, h->stream), "state");
     CK(h, cudaMemcpyAsync(gs.data(), h->g[h->cur], 9 * n * sizeof(S), cudaMemcpyDeviceToHost, h->stream), "state");
-    CK(h, cudaMemcpyAsync(pb.data(), h->phibar[h->acur], n * sizeof(T), cudaMemcpyDeviceToHost, h->stream), "state");
+    CK(h, cudaMemcpyAsync(pb.data(), h->phi[1 - h->pcur], n * sizeof(T), cudaMemcpyDeviceToHost, h->stream), "state");
+    CK(h, cudaMemcpyAsync(db.data(), h->dbar[h->acur], n * sizeof(T), cudaMemcpyDeviceToHost, h->stream), "state");
     CK(h, cudaMemcpyAsync(ph.data(), h->phat[h->acur], n * sizeof(T), cudaMemcpyDeviceToHost, h->stream), "state");
     CK(h, cudaStreamSynchronize(h->stream), "state sync");
+    for (size_t k = 0; k < n; ++k) pb[k] += db[k];
     for (size_t k = 0; k < n; ++k) {
         T sf = T(0), sg = T(0);
         for (int q = 1; q < 9; ++q) {
@@ -670,8 +686,10 @@ lbm_status decode_mixed(lbm_handle *h, double *f, double *g)
     return LBM_OK;
 }
 
+// The stored populations are collided next against phi (given to both phi
+// slots), so their sum enters as dbar = sum f - phi.
 template <typename T, typename S>
-lbm_status encode_mixed(lbm_handle *h, const double *f, const double *g)
+lbm_status encode_mixed(lbm_handle *h, const double *f, const double *g, const double *phi)
 {
     const size_t n = (size_t)h->N;
     std::vector<S> fs(9 * n), gs(9 * n);
@@ -682,7 +700,7 @@ lbm_status encode_mixed(lbm_handle *h, const double *f, const double *g)
             sf += (T)f[q * n + k];
             sg += (T)g[q * n + k];
         }
-        pb[k] = sf;
+        pb[k] = sf - (T)phi[k];
         ph[k] = sg * T(1.0 / 3.0);
         fs[k] = host_store<S>(0.0f);
         gs[k] = host_store<S>(0.0f);
@@ -693,7 +711,7 @@ lbm_status encode_mixed(lbm_handle *h, const double *f, const double *g)
     }
     CK(h, cudaMemcpyAsync(h->f[0], fs.data(), 9 * n * sizeof(S), cudaMemcpyHostToDevice, h->stream), "state");
     CK(h, cudaMemcpyAsync(h->g[0], gs.data(), 9 * n * sizeof(S), cudaMemcpyHostToDevice, h->stream), "state");
-    CK(h, cudaMemcpyAsync(h->phibar[0], pb.data(), n * sizeof(T), cudaMemcpyHostToDevice, h->stream), "state");
+    CK(h, cudaMemcpyAsync(h->dbar[0], pb.data(), n * sizeof(T), cudaMemcpyHostToDevice, h->stream), "state");
     CK(h, cudaMemcpyAsync(h->phat[0], ph.data(), n * sizeof(T), cudaMemcpyHostToDevice, h->stream), "state");
     CK(h, cudaStreamSynchronize(h->stream), "state sync");
     return LBM_OK;
@@ -730,14 +748,16 @@ lbm_status set_state_impl(lbm_handle *h, const double *f, const double *g, const
     h->ucur = 0;
     h->acur = 0;
     if (Mixed<T, S>::on) {
-        if ((st = encode_mixed<T, S>(h, f, g))) return st;
+        if ((st = encode_mixed<T, S>(h, f, g, phi))) return st;
     } else {
         for (int q = 0; q < 9; ++q) {
             if ((st = upload_field<S>(h, (S *)h->f[0] + q * n, f + q * n))) return st;
             if ((st = upload_field<S>(h, (S *)h->g[0] + q * n, g + q * n))) return st;
         }
     }
-    if ((st = upload_field<T>(h, h->phi, phi))) return st;
+    h->pcur = 0;
+    if ((st = upload_field<T>(h, h->phi[0], phi))) return st;
+    CK(h, cudaMemcpyAsync(h->phi[1], h->phi[0], sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream), "set_state copy");
     if ((st = upload_field<T>(h, h->pf, p))) return st;
     if ((st = upload_field<T>(h, h->ux[0], ux))) return st;
     if ((st = upload_field<T>(h, h->uy[0], uy))) return st;
@@ -746,13 +766,28 @@ lbm_status set_state_impl(lbm_handle *h, const double *f, const double *g, const
     if ((st = upload_field<T>(h, h->ux[1], upx))) return st;
     if ((st = upload_field<T>(h, h->uy[1], upy))) return st;
     CK(h, cudaStreamSynchronize(h->stream), "set_state sync");
+    h->chk_pending = false;
+    h->chk_status = LBM_OK;
+    h->chk_count = 0;
     return LBM_OK;
 }
 
 }  // namespace
 
+lbm_status lbm_internal_poll_device_error(lbm_handle *h)
+{
+    unsigned derr = 0;
+    CK(h, cudaMemcpy(&derr, h->dev_err, sizeof derr, cudaMemcpyDeviceToHost), "read device error word");
+    if (derr) h->failed = true;
+    if (h->failed)
+        return fail(h, LBM_ERR_CUDA, "a kernel gave up a bounded wait for a TMA tile copy; its tile was not "
+                                     "updated and a late copy may still write shared memory: destroy the handle");
+    return LBM_OK;
+}
+
 lbm_status lbm_internal_step(lbm_handle *h)
 {
+    if (h->failed) return fail(h, LBM_ERR_STATE, "an earlier step gave up a tile-copy wait: destroy the handle");
     h->fresh_init = false;
     return dispatch(h->grid.precision, [&](auto tp, auto sp) {
         TS_TYPES(tp, sp);
@@ -785,7 +820,7 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params, const doub
     // one arena: 2x9 f planes, 2x9 g planes, then the scalar planes, 256-byte aligned each
     const size_t plane = round_up((size_t)h->N * h->elem, 256);
     const size_t pplane = round_up((size_t)h->N * 9 * h->pop_elem, 256);
-    const int nscalar = 22;   // phi, pf, ux[2], uy[2], uhx, uhy, phibar[2], phat[2], jx, jy, s1, s2, tk[2][2], 2 spare
+    const int nscalar = 22;   // phi[2], pf, ux[2], uy[2], uhx, uhy, dbar[2], phat[2], jx, jy, s1, s2, tk[2][2], 1 spare
     h->diag_blocks = std::min(grid->ny, DIAG_MAX_BLOCKS);   // rows per block: ny / blocks
     const size_t diag_bytes = round_up(sizeof(double) * (size_t)(h->diag_blocks + 1) * NDIAG, 256);
     h->arena_bytes = 4 * pplane + nscalar * plane + diag_bytes + 256;   // + the device error word
@@ -801,11 +836,11 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params, const doub
     h->f[1] = a; a += pplane;
     h->g[0] = a; a += pplane;
     h->g[1] = a; a += pplane;
-    void **sc[] = {&h->phi, &h->pf, &h->ux[0], &h->ux[1], &h->uy[0], &h->uy[1], &h->uhx, &h->uhy,
-                   &h->phibar[0], &h->phibar[1], &h->phat[0], &h->phat[1], &h->jx, &h->jy, &h->s1, &h->s2,
+    void **sc[] = {&h->phi[0], &h->phi[1], &h->pf, &h->ux[0], &h->ux[1], &h->uy[0], &h->uy[1], &h->uhx, &h->uhy,
+                   &h->dbar[0], &h->dbar[1], &h->phat[0], &h->phat[1], &h->jx, &h->jy, &h->s1, &h->s2,
                    &h->tk[0][0], &h->tk[0][1], &h->tk[1][0], &h->tk[1][1]};
     for (void **pp : sc) { *pp = a; a += plane; }
-    a += 2 * plane;
+    a += 1 * plane;
     h->diag_part = (double *)a;
     h->diag_out = h->diag_part + (size_t)h->diag_blocks * NDIAG;
     h->dev_err = (unsigned *)(h->arena + h->arena_bytes - 256);
@@ -837,21 +872,52 @@ lbm_status lbm_step(lbm_handle *h, int n)
 {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
     if (n < 0) return fail(h, LBM_ERR_ARG, "n must be >= 0");
+    if (h->failed) return fail(h, LBM_ERR_STATE, "an earlier step gave up a tile-copy wait: destroy the handle");
+    if (h->chk_pending && cudaEventQuery(h->chk_ev) == cudaSuccess) {   // never waits
+        h->chk_pending = false;
+        const double *d = h->chk_host;
+        if (d[10] > 0) h->chk_status = LBM_ERR_NONFINITE;
+        else if (d[8] > 1.0 + h->chk_delta || d[9] < -1.0 - h->chk_delta) h->chk_status = LBM_ERR_RANGE;
+    }
+    if (h->chk_status == LBM_ERR_NONFINITE) return fail(h, h->chk_status, "periodic check: non-finite field value");
+    if (h->chk_status == LBM_ERR_RANGE) return fail(h, h->chk_status, "periodic check: phi outside [-1-delta, 1+delta]");
     if (n > 0) h->fresh_init = false;
     return dispatch(h->grid.precision, [&](auto tp, auto sp) {
         TS_TYPES(tp, sp);
         for (int t = 0; t < n; ++t) {
             lbm_status st = step_impl<T, S>(h);
             if (st) return st;
+            if (h->chk_every > 0 && ++h->chk_count % h->chk_every == 0 && !h->chk_pending) {
+                st = diag_impl<T>(h, h->chk_host, false);
+                if (st) return st;
+                CK(h, cudaEventRecord(h->chk_ev, h->stream), "check event");
+                h->chk_pending = true;
+            }
         }
         return LBM_OK;
     });
 }
 
+lbm_status lbm_set_check(lbm_handle *h, int every, double delta)
+{
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
+    if (every < 0 || !(delta >= 0)) return fail(h, LBM_ERR_ARG, "every must be >= 0 and delta >= 0");
+    if (every > 0 && !h->chk_host) {
+        CK(h, cudaMallocHost((void **)&h->chk_host, sizeof(double) * NDIAG), "cudaMallocHost(check)");
+        CK(h, cudaEventCreateWithFlags(&h->chk_ev, cudaEventDisableTiming), "cudaEventCreate(check)");
+    }
+    h->chk_every = every;
+    h->chk_delta = delta;
+    h->chk_count = 0;
+    return LBM_OK;
+}
+
 lbm_status lbm_fields(lbm_handle *h, double *phi, double *p, double *ux, double *uy)
 {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
-    return h->grid.precision == LBM_FP64 ? fields_impl<double>(h, phi, p, ux, uy) : fields_impl<float>(h, phi, p, ux, uy);
+    lbm_status st =
+        h->grid.precision == LBM_FP64 ? fields_impl<double>(h, phi, p, ux, uy) : fields_impl<float>(h, phi, p, ux, uy);
+    return st ? st : lbm_internal_poll_device_error(h);
 }
 
 lbm_status lbm_fields_device(lbm_handle *h, void *phi, void *p, void *ux, void *uy, int dtype)
@@ -862,7 +928,7 @@ lbm_status lbm_fields_device(lbm_handle *h, void *phi, void *p, void *ux, void *
         return fail(h, LBM_ERR_ARG, "dtype must match the handle's arithmetic type (0 double, 1 float)");
     const size_t b = h->elem * (size_t)h->N;
     void *dst[4] = {phi, p, ux, uy};
-    const void *src[4] = {h->phi, h->pf, h->ux[h->ucur], h->uy[h->ucur]};
+    const void *src[4] = {phi_cur(h), h->pf, h->ux[h->ucur], h->uy[h->ucur]};
     for (int k = 0; k < 4; ++k)
         if (dst[k]) CK(h, cudaMemcpyAsync(dst[k], src[k], b, cudaMemcpyDeviceToDevice, h->stream), "fields_device");
     return LBM_OK;
@@ -882,7 +948,8 @@ lbm_status lbm_diagnostics(lbm_handle *h, double *out)
 {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
     if (!out) return fail(h, LBM_ERR_ARG, "out must be non-NULL");
-    return h->grid.precision == LBM_FP64 ? diag_impl<double>(h, out) : diag_impl<float>(h, out);
+    lbm_status st = h->grid.precision == LBM_FP64 ? diag_impl<double>(h, out) : diag_impl<float>(h, out);
+    return st ? st : lbm_internal_poll_device_error(h);
 }
 
 lbm_status lbm_diagnostics_async(lbm_handle *h, double *out)
@@ -895,11 +962,8 @@ lbm_status lbm_diagnostics_async(lbm_handle *h, double *out)
 lbm_status lbm_check(lbm_handle *h, double delta)
 {
     double d[NDIAG];
-    lbm_status st = lbm_diagnostics(h, d);
+    lbm_status st = lbm_diagnostics(h, d);   // includes the device error word
     if (st) return st;
-    unsigned derr = 0;
-    CK(h, cudaMemcpy(&derr, h->dev_err, sizeof derr, cudaMemcpyDeviceToHost), "read device error word");
-    if (derr) return fail(h, LBM_ERR_CUDA, "a bounded wait for a TMA tile copy gave up; the step is incomplete");
     if (d[10] > 0) return fail(h, LBM_ERR_NONFINITE, "non-finite field value");
     if (d[8] > 1.0 + delta || d[9] < -1.0 - delta) return fail(h, LBM_ERR_RANGE, "phi outside [-1-delta, 1+delta]");
     return LBM_OK;
@@ -909,10 +973,11 @@ lbm_status lbm_get_state(lbm_handle *h, double *f, double *g, double *phi, doubl
                          double *uhx, double *uhy, double *upx, double *upy)
 {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
-    return dispatch(h->grid.precision, [&](auto tp, auto sp) {
+    lbm_status st = dispatch(h->grid.precision, [&](auto tp, auto sp) {
         TS_TYPES(tp, sp);
         return get_state_impl<T, S>(h, f, g, phi, p, ux, uy, uhx, uhy, upx, upy);
     });
+    return st ? st : lbm_internal_poll_device_error(h);
 }
 
 lbm_status lbm_set_state(lbm_handle *h, const double *f, const double *g, const double *phi, const double *p,
@@ -992,6 +1057,8 @@ void lbm_destroy(lbm_handle *h)
     lbm_internal_adjoint_free(h);
     for (auto &m : h->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
     for (auto e : h->pool) cudaEventDestroy(e);
+    if (h->chk_ev) cudaEventDestroy(h->chk_ev);
+    if (h->chk_host) cudaFreeHost(h->chk_host);
     if (h->arena) cudaFree(h->arena);
     delete h;
 }

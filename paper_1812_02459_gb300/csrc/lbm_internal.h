@@ -23,11 +23,13 @@ struct lbm_handle {
     size_t arena_bytes = 0;
     void *f[2]{}, *g[2]{};
     int cur = 0;                       // which population buffer holds the state
-    void *phi = nullptr, *pf = nullptr, *ux[2]{}, *uy[2]{};
+    void *phi[2]{};                    // phi[pcur] = phi^n; the other slot holds the phi of the
+    int pcur = 0;                      // previous step until the RK3 pass writes phi^{n+1} there
+    void *pf = nullptr, *ux[2]{}, *uy[2]{};
     int ucur = 0;                      // ux[ucur] = filtered u^n, ux[1-ucur] = u^{n-1}
     void *uhx = nullptr, *uhy = nullptr;
-    void *phibar[2]{}, *phat[2]{};     // post-stream moments, double-buffered:
-    int acur = 0;                      // slot acur = moments of the stored populations
+    void *dbar[2]{}, *phat[2]{};       // post-stream moments, double-buffered: dbar = phi_bar - phi
+    int acur = 0;                      // of the collision; slot acur = moments of the stored populations
     void *jx = nullptr, *jy = nullptr;
     void *s1 = nullptr, *s2 = nullptr, *tk[2][2]{};
     double *diag_part = nullptr, *diag_out = nullptr;
@@ -55,7 +57,27 @@ struct lbm_handle {
     bool tma = false;
     std::vector<TmaEntry> tmaps;
     unsigned *dev_err = nullptr;
+    // set once a synchronising call has seen *dev_err != 0; sticky: lbm_step
+    // refuses to run on such a handle
+    bool failed = false;
+    // periodic check of lbm_set_check: every chk_every steps the sums go to
+    // page-locked chk_host behind event chk_ev; a later lbm_step reads them
+    int chk_every = 0;
+    double chk_delta = 0.0;
+    long long chk_count = 0;
+    double *chk_host = nullptr;
+    cudaEvent_t chk_ev = nullptr;
+    bool chk_pending = false;
+    lbm_status chk_status = LBM_OK;
 };
+
+// After a synchronisation of the handle's stream: LBM_ERR_CUDA (and the
+// sticky failed flag) if a kernel gave up a bounded tile-copy wait
+// (lbm_api.cu).
+lbm_status lbm_internal_poll_device_error(lbm_handle *h);
+
+// The plane of phi^n.
+inline void *phi_cur(const lbm_handle *h) { return h->phi[h->pcur]; }
 
 // Issue one step on the handle's stream (lbm_api.cu).
 lbm_status lbm_internal_step(lbm_handle *h);

@@ -179,10 +179,17 @@ __device__ __forceinline__ T fd4_d2(const T *s, int i)
            T(1.0 / 12.0);
 }
 
-// Reciprocal and reciprocal square root: IEEE in FP64 (the parity build);
-// the hardware approximations (<= 2 ulp) in FP32, whose results are compared
-// with the oracle at FP32 tolerances.
-__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+// Reciprocal and reciprocal square root: IEEE in FP64 (the parity build).
+// In FP32 the reciprocal is the hardware approximation refined by one
+// Newton step, r + r (1 - x r), which leaves it within about half an ulp
+// at two FMAs (the correctly rounded __frcp_rn measured 13% slower in the
+// collide kernel); the reciprocal square root (the normal n of the FD
+// correction) is the hardware approximation (<= 2 ulp).
+__device__ __forceinline__ float rcp(float x)
+{
+    const float r = __fdividef(1.0f, x);
+    return __fmaf_rn(r, __fmaf_rn(-x, r, 1.0f), r);
+}
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
@@ -274,6 +281,11 @@ __device__ __forceinline__ void from_moments(const T m[9], T f[9])
 // tile node pulls f_i(x) = f*_i(x - c_i) (halfway bounce-back at walls),
 // writes it once, and emits phi_bar = sum f (Eq. compute_phi),
 // p_hat = cs^2 sum g (Eq. p) and j = sum c g (first part of Eq. u).
+// phi_bar is emitted as its increment dbar = phi_bar - phi over the phi the
+// collision used: the CH populations are collided as deviations from
+// phi e_0 (the moments of phi e_0 removed from m and m_eq), so dbar is a sum
+// of small terms and keeps its relative precision in FP32, where an O(1)
+// phi_bar would lose a unit roundoff of phi to every step.
 // ---------------------------------------------------------------------------
 template <int TX, int TY> struct CSGeom {
     static constexpr int W3 = TX + 6, H3 = TY + 6;   // phi window (ring 3)
@@ -335,14 +347,19 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
                  const T *__restrict__ ux, const T *__restrict__ uy,
                  const T *__restrict__ upx, const T *__restrict__ upy,
                  const T *__restrict__ uhx, const T *__restrict__ uhy,
-                 const T *__restrict__ phibar_old, const T *__restrict__ phat_old,
-                 T *__restrict__ phibar, T *__restrict__ phat,
+                 const T *__restrict__ phi_prev, const T *__restrict__ dbar_old,
+                 const T *__restrict__ phat_old,
+                 T *__restrict__ dbar, T *__restrict__ phat,
                  T *__restrict__ jxo, T *__restrict__ jyo)
 {
     // One thread per node of the collision region (tile + ring 1): the
-    // launch uses exactly A1 threads.  phibar_old / phat_old are the
-    // post-stream moments of the stored populations (read only when the
-    // populations are stored in reduced precision).
+    // launch uses exactly A1 threads.  The CH populations are carried as
+    // deviations from the rest state of the node's phi: f'_0 = f_0 - phi,
+    // f'_i = f_i (i > 0), so their post-stream sum is the small increment
+    // dbar = phi_bar - phi, free of the rounding of an O(1) sum.  phi_prev,
+    // dbar_old and phat_old give the post-stream moments of the stored
+    // populations (phi_bar = phi_prev + dbar_old, p_hat); they are read only
+    // when the populations are stored in reduced precision.
     using G = CSGeom<TX, TY>;
     constexpr int W3 = G::W3, W2 = G::W2, H2 = G::H2, W1 = G::W1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -370,7 +387,7 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
     const bool ghost = (!P.px && (X < 0 || X >= P.nx)) || (!P.py && (Y < 0 || Y >= P.ny));
     int fxm, fym;
     const int gidx = map_axis(Y, P.ny, P.py, fym) * P.nx + map_axis(X, P.nx, P.px, fxm);
-    T f[9], g[9], upx_ = T(0), upy_ = T(0), uhx_ = T(0), uhy_ = T(0);
+    T f[9], g[9], upx_ = T(0), upy_ = T(0), uhx_ = T(0), uhy_ = T(0), pprev = T(0);
     if (!ghost) {
         const unsigned N32 = P.N32;
         if constexpr (Mixed<T, S>::on) {
@@ -384,7 +401,9 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
                 sf += f[q];
                 sg += g[q];
             }
-            f[0] = __ldg(&phibar_old[gidx]) - sf;
+            // f_0 - phi_prev; the node's phi is subtracted once the window is staged
+            f[0] = __ldg(&dbar_old[gidx]) - sf;
+            pprev = __ldg(&phi_prev[gidx]);
             g[0] = T(3) * ph0 - sg;
         } else {
 #pragma unroll
@@ -428,6 +447,7 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
         const int i3 = (ly + 2) * W3 + (lx + 2);
 
         const T ph = s_phi[i3];
+        f[0] = Mixed<T, S>::on ? (pprev - ph) + f[0] : f[0] - ph;   // f'_0
         T rho, ir, nu;
         rho_nu(P, ph, rho, ir, nu);
         const T mu = s_mu[i2];
@@ -452,11 +472,12 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
         const T ay = (u1 - sgn * upy_) + u0 * dxuy + u1 * dyuy;
         const T u2 = u0 * u0 + u1 * u1;
 
-        // ---- CH populations
+        // ---- CH populations, as deviations from phi e_0: the moments of
+        // phi e_0, (phi, -4 phi, 4 phi, 0, ...), are left out of m and m_eq
         {
             T m[9];
             const T em = P.eta * mu;
-            const T meq[9] = {ph, T(2) * em - T(4) * ph + T(3) * ph * u2, T(4) * ph - T(3) * em - T(3) * ph * u2,
+            const T meq[9] = {T(0), T(2) * em + T(3) * ph * u2, -T(3) * em - T(3) * ph * u2,
                               ph * u0, -ph * u0, ph * u1, -ph * u1, ph * (u0 * u0 - u1 * u1), ph * u0 * u1};
             const T mF[9] = {T(0), T(0), T(0), ph * ax, -ph * ax, ph * ay, -ph * ay, T(0), T(0)};
             if constexpr (FAST) {
@@ -561,14 +582,19 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
                 gout[o] = Codec<S, T>::store(gv[q] - T(3) * T(lattice_w(q)) * pn);
             }
         } else {
+            fout[nidx] = Codec<S, T>::store(s_phi[(ky + 3) * W3 + (kx + 3)] + fv[0]);
+#pragma unroll
+            for (int q = 1; q < 9; ++q) {
+                const unsigned o = (unsigned)nidx + (unsigned)q * N32;
+                fout[o] = Codec<S, T>::store(fv[q]);
+            }
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
                 const unsigned o = (unsigned)nidx + (unsigned)q * N32;
-                fout[o] = Codec<S, T>::store(fv[q]);
                 gout[o] = Codec<S, T>::store(gv[q]);
             }
         }
-        phibar[nidx] = sf;
+        dbar[nidx] = sf;
         phat[nidx] = pn;
         jxo[nidx] = sgx;
         jyo[nidx] = sgy;
@@ -577,24 +603,31 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
 
 // ---------------------------------------------------------------------------
 // Pass 2: one stage of the TVD-RK3 correction (Sec. III.A Eq. TVD-3order)
-//   out = a * phi_bar + b * (psi + L(psi)),  L(psi) = div(lambda J_phi + q),
+//   psi^(k) = a phi_bar + b (psi^(k-1) + L(psi^(k-1))),  L(psi) = div(lambda J_phi + q),
 //   J_phi = (|grad psi| - 2(1 - psi^2)/W) n,  q = -M (grad mu_psi . n) n,
 //   n = grad psi / |grad psi|,  mu_psi = 4 beta (psi^3 - psi) - kappa lap psi,
 // every derivative by fourth-order central differences (Eq. fourOrder_FDM).
-// The composite stencil reaches 6 nodes, so the CTA stages psi with ring 6,
-// mu_psi on ring 4 and J_d on ring 2.
+// The stages are carried as increments over the step's phi^n: with
+// phi_bar = phi^n + dbar and psi^(k) = phi^n + d^(k), a stage computes
+//   d^(k) = a dbar + b (d^(k-1) + L(phi^n + d^(k-1)))     (d^(0) = dbar),
+// and the last stage writes phi^{n+1} = phi^n + d^(3).  The increments are
+// small, so the arithmetic that combines the stages keeps their relative
+// precision, and phi is rounded once per step.  The composite stencil
+// reaches 6 nodes, so the CTA stages psi with ring 6, mu_psi on ring 4 and
+// J_d on ring 2.
 // ---------------------------------------------------------------------------
 template <int TX, int TY> struct RKGeom {
     static constexpr int W6 = TX + 12, H6 = TY + 12;
     static constexpr int W4 = TX + 8, H4 = TY + 8;
     static constexpr int W2 = TX + 4, H2 = TY + 4;
     static constexpr int NSCALAR = W6 * H6 + W4 * H4 + 2 * W2 * H2;
+    static_assert(W6 * H6 <= 2 * W2 * H2, "the d window fits the J arrays it precedes");
 };
 
 template <typename T, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT)
-k_rk_stage(KP<T> P, const T *__restrict__ psi, const T *__restrict__ phibar, T *__restrict__ out,
-           T a, T b)
+k_rk_stage(KP<T> P, const T *__restrict__ phi, const T *__restrict__ din, const T *__restrict__ dbar,
+           T *__restrict__ out, T a, T b, int last)
 {
     using G = RKGeom<TX, TY>;
     constexpr int W6 = G::W6, H6 = G::H6, W4 = G::W4, H4 = G::H4, W2 = G::W2, H2 = G::H2;
@@ -603,10 +636,14 @@ k_rk_stage(KP<T> P, const T *__restrict__ psi, const T *__restrict__ phibar, T *
     T *s_mu = s_psi + W6 * H6;
     T *s_jx = s_mu + W4 * H4;
     T *s_jy = s_jx + W2 * H2;
+    T *s_d = s_jx;   // d window, consumed before J is written
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
 
-    load_tile<T, W6, H6>(s_psi, psi, x0 - 6, y0 - 6, P, false);
+    load_tile<T, W6, H6>(s_psi, phi, x0 - 6, y0 - 6, P, false);
+    load_tile<T, W6, H6>(s_d, din, x0 - 6, y0 - 6, P, false);
     tiles_ready();
+    for (int t = threadIdx.x; t < W6 * H6; t += blockDim.x) s_psi[t] += s_d[t];
+    __syncthreads();
 
     for (int t = threadIdx.x; t < W4 * H4; t += blockDim.x) {
         int ly = t / W4, lx = t - ly * W4;
@@ -646,11 +683,10 @@ k_rk_stage(KP<T> P, const T *__restrict__ psi, const T *__restrict__ phibar, T *
         if (X >= P.nx || Y >= P.ny) continue;
         int i2 = (ly + 2) * W2 + (lx + 2);
         T L = fd4_d1<T, 1>(s_jx, i2) + fd4_d1<T, W2>(s_jy, i2);
-        T v = s_psi[(ly + 6) * W6 + (lx + 6)];
         long long gidx = (long long)Y * P.nx + X;
-        T r = b * (v + L);
-        if (a != T(0)) r = a * phibar[gidx] + r;
-        out[gidx] = r;
+        T r = b * (din[gidx] + L);
+        if (a != T(0)) r = a * dbar[gidx] + r;
+        out[gidx] = last ? phi[gidx] + r : r;
     }
 }
 
@@ -920,12 +956,11 @@ __device__ __forceinline__ void sts2(float *s, int i, float2 v) { *reinterpret_c
 // k_rk_stage: each thread covers a column pair over VR1 / VR2 / VR3 rows of
 // the mu / J / divergence regions, holding the y-neighbours in registers.
 // s_psi holds psi from (x0 - 6, y0 - 6) with row stride SW.
-// pb(i, gidx) returns phi_bar at row i of the thread's output strip (global
-// index gidx); it is called only when a != 0.
-template <int TX, int TY, int NT, int VR1, int VR2, int VR3, int SW, typename PB>
+// emit(i, gidx, L) receives L(psi) at row i of the thread's output strip
+// (global index gidx of its first column) and writes the stage's result.
+template <int TX, int TY, int NT, int VR1, int VR2, int VR3, int SW, typename EMIT>
 __device__ __forceinline__ void rk_strips_body(const KP<float> &P, const float *s_psi, float *s_mu, float *s_jx,
-                                               float *s_jy, int x0, int y0, PB &&pb, float *__restrict__ out, float a,
-                                               float b)
+                                               float *s_jy, int x0, int y0, EMIT &&emit)
 {
     using G = RKGeom<TX, TY>;
     constexpr int W4 = G::W4, H4 = G::H4, W2 = G::W2, H2 = G::H2;
@@ -996,9 +1031,8 @@ __device__ __forceinline__ void rk_strips_body(const KP<float> &P, const float *
     }
     __syncthreads();
 
-    {   // psi + div J on the tile, J offset 2, psi offset 6
+    {   // div J on the tile, J offset 2
         constexpr int NP = TX / 2, NI = NP * (TY / VR3);
-        const float2 bb = f2(b), aa = f2(a);
         for (int it = threadIdx.x; it < NI; it += NT) {
             const int lx = 2 * (it % NP), r0 = (it / NP) * VR3;
             const int X = x0 + lx;
@@ -1013,11 +1047,7 @@ __device__ __forceinline__ void rk_strips_body(const KP<float> &P, const float *
                 const int jrow = (r0 + 2 + i) * W2 + lx + 2;
                 const float2 L = add2(pd1x(lds2(s_jx, jrow - 2), lds2(s_jx, jrow), lds2(s_jx, jrow + 2)),
                                       pd1(w[i], w[i + 1], w[i + 3], w[i + 4]));
-                const float2 v = lds2(s_psi, (r0 + 6 + i) * SW + lx + 6);
-                const long long gidx = (long long)Y * P.nx + X;
-                float2 r = mul2(bb, add2(v, L));
-                if (a != 0.0f) r = fma2(aa, pb(i, gidx), r);
-                *reinterpret_cast<float2 *>(&out[gidx]) = r;
+                emit(i, (long long)Y * P.nx + X, L);
             }
         }
     }
@@ -1025,8 +1055,8 @@ __device__ __forceinline__ void rk_strips_body(const KP<float> &P, const float *
 
 template <int TX, int TY, int NT, int VR1, int VR2, int VR3>
 __global__ void __launch_bounds__(NT, 3)
-k_rk_strips(KP<float> P, const float *__restrict__ psi, const float *__restrict__ phibar, float *__restrict__ out,
-            float a, float b)
+k_rk_strips(KP<float> P, const float *__restrict__ phi, const float *__restrict__ din,
+            const float *__restrict__ dbar, float *__restrict__ out, float a, float b, int last)
 {
     using G = RKGeom<TX, TY>;
     constexpr int W6 = G::W6, H6 = G::H6, W4 = G::W4, H4 = G::H4, W2 = G::W2, H2 = G::H2;
@@ -1035,12 +1065,21 @@ k_rk_strips(KP<float> P, const float *__restrict__ psi, const float *__restrict_
     float *s_mu = s_psi + W6 * H6;
     float *s_jx = s_mu + W4 * H4;
     float *s_jy = s_jx + W2 * H2;
+    float *s_d = s_jx;   // d window, consumed before J is written
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    load_tile<float, W6, H6>(s_psi, psi, x0 - 6, y0 - 6, P, false);
+    load_tile<float, W6, H6>(s_psi, phi, x0 - 6, y0 - 6, P, false);
+    load_tile<float, W6, H6>(s_d, din, x0 - 6, y0 - 6, P, false);
     tiles_ready();
+    for (int t = threadIdx.x; t < W6 * H6; t += NT) s_psi[t] += s_d[t];
+    __syncthreads();
+    const float2 aa = f2(a), bb = f2(b);
     rk_strips_body<TX, TY, NT, VR1, VR2, VR3, W6>(
-        P, s_psi, s_mu, s_jx, s_jy, x0, y0,
-        [&](int, long long gidx) { return *reinterpret_cast<const float2 *>(&phibar[gidx]); }, out, a, b);
+        P, s_psi, s_mu, s_jx, s_jy, x0, y0, [&](int, long long gidx, float2 L) {
+            float2 r = mul2(bb, add2(*reinterpret_cast<const float2 *>(&din[gidx]), L));
+            if (a != 0.0f) r = fma2(aa, *reinterpret_cast<const float2 *>(&dbar[gidx]), r);
+            if (last) r = add2(*reinterpret_cast<const float2 *>(&phi[gidx]), r);
+            *reinterpret_cast<float2 *>(&out[gidx]) = r;
+        });
 }
 
 // Pass 3 for FP32 on grids of even width, same result as k_picard: each
@@ -1308,12 +1347,18 @@ template <int NF, int BW, int BH, int EXTRA> struct TmaTile {
     }
 
     // Make the staged windows readable by every thread; false (for the whole
-    // CTA) when the TMA wait gave up, after recording it in *err.
+    // CTA) when the TMA wait gave up, after recording it in *err and giving
+    // the copies in flight a second bounded wait to land before the CTA
+    // leaves (a copy that lands after that can still write this shared
+    // memory: the host then refuses further steps on the handle).
     __device__ __forceinline__ bool wait(bool by_tma, unsigned *err)
     {
         if (by_tma && threadIdx.x == 0) {
             *flag = mbar_wait_bounded(bar, 0) ? 1 : 0;
-            if (!*flag) atomicOr(err, 1u);
+            if (!*flag) {
+                atomicOr(err, 1u);
+                mbar_wait_bounded(bar, 0);
+            }
         }
         __syncthreads();
         if (!by_tma) return true;
@@ -1362,50 +1407,72 @@ k_filter_tma(const __grid_constant__ TmaMaps tm, KP<float> P, const float *__res
     filter_strips_body<TX, TY, R, VR, BW>(P, sp, sp + FS, sp + 2 * FS, x0, y0, pout, uxout, uyout);
 }
 
-// RK3 stage with TMA staging, one CTA per TX x TY tile: window
-// (TX + 16) x (TY + 12) of psi from (x0 - 8, y0 - 6); mu and J in the work
-// area.
+// RK3 stage with TMA staging, one CTA per TX x TY tile: windows
+// (TX + 16) x (TY + 12) of phi^n and of the incoming increment d from
+// (x0 - 8, y0 - 6).  psi = phi^n + d is formed in the phi window; mu and J
+// then use a work area that begins at the consumed d window.
 template <int TX, int TY> struct RKTGeom {
     using G = RKGeom<TX, TY>;
     static constexpr int BW = TX + 16, BH = TY + 12;
-    static constexpr int EXTRA = G::W4 * G::H4 + 2 * G::W2 * G::H2;
-    using Tile = TmaTile<1, BW, BH, EXTRA>;
+    static constexpr int FS = (BW * BH + 31) / 32 * 32;
+    static constexpr int WORK = G::W4 * G::H4 + 2 * G::W2 * G::H2;
+    static_assert(WORK >= FS && (BW * BH) % 4 == 0, "the work area covers the d window");
+    using Tile = TmaTile<2, BW, BH, WORK - FS>;
 };
 
 template <int TX, int TY, int NT, int VR1, int VR2, int VR3, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
-k_rk_tma(const __grid_constant__ TmaMaps tm, KP<float> P, const float *__restrict__ psi,
-         const float *__restrict__ phibar, float *__restrict__ out, float a, float b, unsigned *err)
+k_rk_tma(const __grid_constant__ TmaMaps tm, KP<float> P, const float *__restrict__ phi,
+         const float *__restrict__ din, const float *__restrict__ dbar, float *__restrict__ out, float a, float b,
+         int last, unsigned *err)
 {
     using T = RKTGeom<TX, TY>;
     using G = RKGeom<TX, TY>;
+    constexpr int BW = T::BW, FS = T::FS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     typename T::Tile tile(smem_raw);
-    float *s_mu = tile.work;
+    float *s_mu = tile.win + FS;
     float *s_jx = s_mu + G::W4 * G::H4;
     float *s_jy = s_jx + G::W2 * G::H2;
-    const float *src[1] = {psi};
+    const float *src[2] = {phi, din};
     int x0, y0;
     tile_origin(TX, TY, x0, y0, P);
     const bool by_tma = tile.issue(P, tm, src, 0u, x0 - 8, y0 - 6);
-    // phi_bar of this thread's output strip (one strip per thread), requested
-    // while the window arrives
+    // dbar of this thread's output strip (one strip per thread), requested
+    // while the windows arrive
     static_assert((TX / 2) * (TY / VR3) == NT, "one output strip per thread");
-    float2 pbv[VR3];
+    const int lx = 2 * ((int)threadIdx.x % (TX / 2)), r0 = ((int)threadIdx.x / (TX / 2)) * VR3;
+    float2 pbv[VR3];   // dbar, then a dbar + b d
 #pragma unroll
     for (int i = 0; i < VR3; ++i) pbv[i] = f2(0.0f);
     if (a != 0.0f) {
-        const int lx = 2 * ((int)threadIdx.x % (TX / 2)), r0 = ((int)threadIdx.x / (TX / 2)) * VR3;
         const int X = x0 + lx;
 #pragma unroll
         for (int i = 0; i < VR3; ++i) {
             const int Y = y0 + r0 + i;
-            if (X < P.nx && Y < P.ny) pbv[i] = __ldg(reinterpret_cast<const float2 *>(&phibar[(long long)Y * P.nx + X]));
+            if (X < P.nx && Y < P.ny) pbv[i] = __ldg(reinterpret_cast<const float2 *>(&dbar[(long long)Y * P.nx + X]));
         }
     }
     if (!tile.wait(by_tma, err)) return;
-    rk_strips_body<TX, TY, NT, VR1, VR2, VR3, T::BW>(P, tile.win + 2, s_mu, s_jx, s_jy, x0, y0,
-                                                     [&](int i, long long) { return pbv[i]; }, out, a, b);
+    // the part of the stage's increment that needs no stencil, a dbar + b d,
+    // at this thread's strip; then psi = phi^n + d over the window
+    const float2 aa = f2(a), bb = f2(b);
+#pragma unroll
+    for (int i = 0; i < VR3; ++i) pbv[i] = fma2(aa, pbv[i], mul2(bb, lds2(tile.win + FS, (r0 + i + 6) * BW + lx + 8)));
+    __syncthreads();
+    for (int k = 4 * (int)threadIdx.x; k < BW * T::BH; k += 4 * NT) {
+        float4 p = *reinterpret_cast<const float4 *>(tile.win + k);
+        const float4 d = *reinterpret_cast<const float4 *>(tile.win + FS + k);
+        p.x += d.x; p.y += d.y; p.z += d.z; p.w += d.w;
+        *reinterpret_cast<float4 *>(tile.win + k) = p;
+    }
+    __syncthreads();
+    rk_strips_body<TX, TY, NT, VR1, VR2, VR3, T::BW>(
+        P, tile.win + 2, s_mu, s_jx, s_jy, x0, y0, [&](int i, long long gidx, float2 L) {
+            float2 r = fma2(bb, L, pbv[i]);
+            if (last) r = add2(__ldg(reinterpret_cast<const float2 *>(&phi[gidx])), r);
+            *reinterpret_cast<float2 *>(&out[gidx]) = r;
+        });
 }
 
 // Picard sweep with TMA staging, one CTA per TX x TY tile: windows
@@ -1596,7 +1663,7 @@ k_collide_pairs(const __grid_constant__ TmaMaps tm, KP<float> P, const S *__rest
                 const S *__restrict__ gin, S *__restrict__ fout, S *__restrict__ gout,
                 const float *__restrict__ phi, const float *__restrict__ pfl, const float *__restrict__ ux,
                 const float *__restrict__ uy, const float *__restrict__ upx, const float *__restrict__ upy,
-                const float *__restrict__ uhx, const float *__restrict__ uhy, float *__restrict__ phibar,
+                const float *__restrict__ uhx, const float *__restrict__ uhy, float *__restrict__ dbar,
                 float *__restrict__ phat, float *__restrict__ jxo, float *__restrict__ jyo, unsigned *err)
 {
     using G = CPGeom<TX, TY>;
@@ -1685,13 +1752,14 @@ k_collide_pairs(const __grid_constant__ TmaMaps tm, KP<float> P, const S *__rest
     __syncthreads();
 
     // ---- forces and collision of this pair
-    float2 f[9], g[9];
+    float2 f[9], g[9], phc = f2(0.0f);
 #pragma unroll
     for (int q = 0; q < 9; ++q) f[q] = g[q] = f2(0.0f);
     if (!ghost) {
         const int i2 = (warp + 1) * W2 + 2 + 2 * lane;   // region of mu, grad phi
         const int iw = (warp + 2) * BW + 6 + 2 * lane;   // windows of phi, p, u
         const float2 ph = lds2(s_phi, iw);
+        phc = ph;
         float2 rho, ir, nu;
         rho_nu(P, ph.x, rho.x, ir.x, nu.x);
         rho_nu(P, ph.y, rho.y, ir.y, nu.y);
@@ -1717,15 +1785,16 @@ k_collide_pairs(const __grid_constant__ TmaMaps tm, KP<float> P, const S *__rest
         const float2 u00 = mul2(u0, u0), u11 = mul2(u1, u1), u01 = mul2(u0, u1);
         const float2 u2 = add2(u00, u11), uxy = sub2(u00, u11);
 
-        {   // CH populations: only m3, m5 relax at a rate other than 1
+        {   // CH populations: only m3, m5 relax at a rate other than 1; the
+            // populations are deviations from phi e_0 (see k_collide_stream)
             const float2 s = f2(P.sf[3]), oms = f2(1.0f - P.sf[3]), hs = f2(1.0f - 0.5f * P.sf[3]);
             const float2 m3 = m3i, m5 = m5i;
             const float2 em = mul2(f2(P.eta), mu), ph3u2 = mul2(f2(3.0f), mul2(ph, u2));
             const float2 pax = mul2(ph, ax), pay = mul2(ph, ay);
             float2 m[9];
-            m[0] = ph;
-            m[1] = fma2(f2(2.0f), em, fma2(f2(-4.0f), ph, ph3u2));
-            m[2] = fma2(f2(4.0f), ph, fma2(f2(-3.0f), em, mul2(m1, ph3u2)));
+            m[0] = f2(0.0f);
+            m[1] = fma2(f2(2.0f), em, ph3u2);
+            m[2] = fma2(f2(-3.0f), em, mul2(m1, ph3u2));
             m[3] = fma2(oms, m3, fma2(s, mul2(ph, u0), mul2(hs, pax)));
             m[4] = mul2(mul2(m1, ph), fma2(f2(0.5f), ax, u0));
             m[5] = fma2(oms, m5, fma2(s, mul2(ph, u1), mul2(hs, pay)));
@@ -1830,14 +1899,13 @@ k_collide_pairs(const __grid_constant__ TmaMaps tm, KP<float> P, const S *__rest
             Codec2<S>::store(gout + o, fma2(f2(-3.0f * lattice_w(q)), pn, gv[q]));
         }
     } else {
+        Codec2<S>::store(fout + nidx, add2(phc, fv[0]));
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const unsigned o = (unsigned)nidx + (unsigned)q * N32;
-            Codec2<S>::store(fout + o, fv[q]);
-            Codec2<S>::store(gout + o, gv[q]);
-        }
+        for (int q = 1; q < 9; ++q) Codec2<S>::store(fout + (unsigned)nidx + (unsigned)q * N32, fv[q]);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Codec2<S>::store(gout + (unsigned)nidx + (unsigned)q * N32, gv[q]);
     }
-    sts2(phibar, nidx, sf);
+    sts2(dbar, nidx, sf);
     sts2(phat, nidx, pn);
     sts2(jxo, nidx, jx);
     sts2(jyo, nidx, jy);
@@ -1851,7 +1919,7 @@ template <typename T, typename S>
 __global__ void k_init(KP<T> P, const T *__restrict__ phi, const T *__restrict__ p,
                        const T *__restrict__ ux, const T *__restrict__ uy,
                        S *__restrict__ f, S *__restrict__ g,
-                       T *__restrict__ phibar, T *__restrict__ phat)
+                       T *__restrict__ dbar, T *__restrict__ phat)
 {
     const long long N = P.N;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < N;
@@ -1881,14 +1949,11 @@ __global__ void k_init(KP<T> P, const T *__restrict__ phi, const T *__restrict__
         T fv[9], gv[9];
         from_moments(mf, fv);
         from_moments(mg, gv);
-        T sf = T(0), sg = T(0);
+        T sg = T(0);
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            sf += fv[q];
-            sg += gv[q];
-        }
+        for (int q = 0; q < 9; ++q) sg += gv[q];
         const T pn = sg * T(1.0 / 3.0);
-        phibar[k] = sf;
+        dbar[k] = T(0);   // sum f_eq = phi: the post-stream increment starts at zero
         phat[k] = pn;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {

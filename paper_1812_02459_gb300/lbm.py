@@ -45,7 +45,7 @@ class LbmError(RuntimeError):
 
 
 EXPORTS = ("lbm_create", "lbm_step", "lbm_fields", "lbm_fields_device", "lbm_set_fields",
-           "lbm_diagnostics", "lbm_diagnostics_async", "lbm_check", "lbm_get_state", "lbm_set_state",
+           "lbm_diagnostics", "lbm_diagnostics_async", "lbm_check", "lbm_set_check", "lbm_get_state", "lbm_set_state",
            "lbm_profile", "lbm_profile_read", "lbm_kernel_name", "lbm_kernel_variant",
            "lbm_field_sums_noalloc", "lbm_noalloc_last_error",
            "lbm_adjoint_begin", "lbm_adjoint_end", "lbm_adjoint_engine",
@@ -82,6 +82,8 @@ def load(path=None):
     L.lbm_diagnostics_async.argtypes = [vp, _dp]
     L.lbm_check.restype = C.c_int
     L.lbm_check.argtypes = [vp, C.c_double]
+    L.lbm_set_check.restype = C.c_int
+    L.lbm_set_check.argtypes = [vp, C.c_int, C.c_double]
     L.lbm_get_state.restype = C.c_int
     L.lbm_get_state.argtypes = [vp] + [_dp] * 10
     L.lbm_set_state.restype = C.c_int
@@ -229,6 +231,10 @@ class Sim:
 
     def check(self, delta=0.05):
         return self._lib.lbm_check(self._h, C.c_double(delta))
+
+    def set_check(self, every, delta=0.05):
+        """Let step() check the sums every `every` steps without waiting (0: off)."""
+        self._ck(self._lib.lbm_set_check(self._h, int(every), C.c_double(delta)))
 
     def state(self):
         shp = (self.ny, self.nx)

@@ -63,6 +63,7 @@ static cudaError_t fake_libkernel(cudaKernel_t *k, cudaLibrary_t, const char *)
 #include "../paper_1812_02459_gb300/csrc/lbm_adjoint.cu"
 
 lbm_status lbm_internal_step(lbm_handle *) { return LBM_OK; }   // not reached: no sweep runs here
+lbm_status lbm_internal_poll_device_error(lbm_handle *) { return LBM_OK; }   // not reached either
 
 namespace {
 

@@ -292,3 +292,23 @@ def test_general_relaxation_rates(precision):
     z = np.zeros_like(phi)
     o, g = run_both(prm, (phi, z, z, z), 60, precision)
     assert_parity(o, g, TOL[precision], tol_pu=pu_tol(precision))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_srt_equal_rates(precision):
+    """The single-relaxation-time limit of the MRT collisions (every rate
+    equal, Sec. III.A below Eq. CH_Sf): s^f = 1/tau_f and s^g = 1/tau_g on
+    all nine moments, with equal viscosities so that tau_g is uniform.  The
+    zeroth CH moment then relaxes at 1/tau_f too, so the LBE only partly
+    inherits the corrected phi; the general collision path runs."""
+    nx, ny = 40, 30
+    prm = inputs.base_params(rho_H=10.0, sigma=3e-3, periodic_y=0, gy=-1e-6)
+    tau_f = 0.5 + prm["M"] / (prm["eta"] / 3.0)
+    tau_g = 3.0 * prm["nu_H"] + 0.5
+    prm["s_f"] = [1.0 / tau_f] * 9
+    prm["s_g"] = [1.0 / tau_g] * 9
+    phi = inputs.drop(nx, ny, 8.0, 20.0, 14.0, prm["W"])
+    z = np.zeros_like(phi)
+    o, g = run_both(prm, (phi, z, z, z), 60, precision)
+    assert g.kernel_variants()["k_collide_stream"] == "k_collide_stream"
+    assert_parity(o, g, TOL[precision], tol_pu=pu_tol(precision))
