@@ -30,6 +30,7 @@ class OrcParams(C.Structure):
         ("filter_order", C.c_int), ("filter_a", C.c_double),
         ("picard_iters", C.c_int), ("picard_zeta", C.c_double),
         ("grad_eps", C.c_double),
+        ("flags", C.c_uint),
     ]
 
 
@@ -89,6 +90,7 @@ def make_params(nx, ny, prm):
     p.picard_iters = int(prm.get("picard_iters", 2))
     p.picard_zeta = prm.get("picard_zeta", 0.0)
     p.grad_eps = prm.get("grad_eps", 1e-4)
+    p.flags = int(prm.get("flags", 0))
     return p
 
 
@@ -144,6 +146,14 @@ def _arr9(a):
 def collide_f(f, fe, F, s):
     out = (C.c_double * 9)()
     lib().orc_collide_f(_arr9(f), _arr9(fe), _arr9(F), _arr9(s), out)
+    return np.array(out[:])
+
+
+def strain_moments(g, geq, s, rho, Fx, Fy, ux, uy):
+    """(S_xx, S_xy, S_yy) of Sec. III.B Eq. (Fmu) at one node."""
+    out = (C.c_double * 3)()
+    lib().orc_strain_moments(_arr9(g), _arr9(geq), _arr9(s), C.c_double(rho), C.c_double(Fx), C.c_double(Fy),
+                             C.c_double(ux), C.c_double(uy), out)
     return np.array(out[:])
 
 

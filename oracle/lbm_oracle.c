@@ -249,6 +249,34 @@ void orc_collide_g(const double g[9], const double geq_f[9], const double geq_ha
     matvec(g_Minv, ms, out);
 }
 
+/* Strain rate grad u + grad u^T from the non-equilibrium part of the NS
+   populations, Sec. III.B Eq. (Fmu) (whose sum is printed over f; the
+   populations of the NS equation are g):
+     grad u + grad u^T = [(s_7 - s_1)(F.u) I - s_7 (F u + u F)] / (2 rho cs^2)
+                         - sum_i c_i c_i [M^-1 S M (g - g_eq)]_i / cs^2 .
+   out = (S_xx, S_xy, S_yy); s are the NS rates with s_7 = 1/tau_g. */
+void orc_strain_moments(const double g[9], const double geq[9], const double s[9], double rho,
+                        double Fx, double Fy, double ux, double uy, double out[3])
+{
+    orc_init_tables();
+    double d[9], m[9], h[9];
+    for (int k = 0; k < Q; ++k) d[k] = g[k] - geq[k];
+    matvec(g_M, d, m);
+    for (int k = 0; k < Q; ++k) m[k] *= s[k];
+    matvec(g_Minv, m, h);
+    double pxx = 0.0, pxy = 0.0, pyy = 0.0;
+    for (int i = 0; i < Q; ++i) {
+        double cx = g_c[2 * i], cy = g_c[2 * i + 1];
+        pxx += cx * cx * h[i];
+        pxy += cx * cy * h[i];
+        pyy += cy * cy * h[i];
+    }
+    double Fu = Fx * ux + Fy * uy, a = 1.0 / (2.0 * rho * CS2);
+    out[0] = ((s[7] - s[1]) * Fu - s[7] * 2.0 * Fx * ux) * a - pxx / CS2;
+    out[1] = -s[7] * (Fx * uy + ux * Fy) * a - pxy / CS2;
+    out[2] = ((s[7] - s[1]) * Fu - s[7] * 2.0 * Fy * uy) * a - pyy / CS2;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Padded fields: a field with G ghost layers on every side.  Ghosts wrap on */
 /* periodic axes and mirror about the halfway wall otherwise, multiplied by  */
@@ -637,13 +665,13 @@ static void vel_grads(const orc_sim *s, const double *ux, const double *uy,
    F_p = -p grad rho, F_nu = nu (grad u + grad u^T).grad rho, F_m = J.grad u,
    F_g = (rho - rho_ref) g (rho_ref = 0: rho g as printed; otherwise gravity is
    measured against the hydrostatic pressure of a fluid of density rho_ref). */
-static void total_force(const orc_sim *s, const fields_t *F, const double *p,
-                        const double *dxux, const double *dyux, const double *dxuy,
-                        const double *dyuy, size_t k, double *Fx, double *Fy)
+static void force_with_strain(const orc_sim *s, const fields_t *F, const double *p,
+                              const double *dxux, const double *dyux, const double *dxuy,
+                              const double *dyuy, double Sxx, double Sxy, double Syy, size_t k,
+                              double *Fx, double *Fy)
 {
     const orc_params *q = &s->p;
     double Fpx = -p[k] * F->grx[k], Fpy = -p[k] * F->gry[k];
-    double Sxx = 2.0 * dxux[k], Sxy = dyux[k] + dxuy[k], Syy = 2.0 * dyuy[k];
     double Fnx = F->nu[k] * (Sxx * F->grx[k] + Sxy * F->gry[k]);
     double Fny = F->nu[k] * (Sxy * F->grx[k] + Syy * F->gry[k]);
     double Fmx = F->Jx[k] * dxux[k] + F->Jy[k] * dyux[k];
@@ -651,6 +679,16 @@ static void total_force(const orc_sim *s, const fields_t *F, const double *p,
     double Fgx = (F->rho[k] - q->g_rho_ref) * q->gx, Fgy = (F->rho[k] - q->g_rho_ref) * q->gy;
     *Fx = Fpx + F->Fsx[k] + Fnx + Fmx + Fgx;
     *Fy = Fpy + F->Fsy[k] + Fny + Fmy + Fgy;
+}
+
+/* The total force with the strain rate grad u + grad u^T of F_nu taken from
+   the velocity gradients (isotropic stencils). */
+static void total_force(const orc_sim *s, const fields_t *F, const double *p,
+                        const double *dxux, const double *dyux, const double *dxuy,
+                        const double *dyuy, size_t k, double *Fx, double *Fy)
+{
+    force_with_strain(s, F, p, dxux, dyux, dxuy, dyuy, 2.0 * dxux[k], dyux[k] + dxuy[k], 2.0 * dyuy[k], k, Fx,
+                      Fy);
 }
 
 int orc_create(const orc_params *prm, const double *phi0, const double *p0,
@@ -774,7 +812,20 @@ static int step_once(orc_sim *s)
         double num = 0.0, den = 0.0;
         for (size_t k = 0; k < N; ++k) {
             double Fx, Fy;
-            total_force(s, &F, phat, dxux, dyux, dxuy, dyuy, k, &Fx, &Fy);
+            if (q->flags & 1u) {
+                /* F_nu's strain rate from the post-stream g (Eq. Fmu), with
+                   g_eq(p_hat, u^k) and, in its forcing term, the force of this
+                   sweep without F_nu (the part Eq. Fmu does not need itself) */
+                double gl[9], ge[9], S[3], F0x, F0y;
+                for (int c = 0; c < Q; ++c) gl[c] = s->g[c * N + k];
+                orc_geq(phat[k], ukx[k], uky[k], ge);
+                force_with_strain(s, &F, phat, dxux, dyux, dxuy, dyuy, 0.0, 0.0, 0.0, k, &F0x, &F0y);
+                sg[7] = sg[8] = 1.0 / (F.nu[k] / CS2 + 0.5);
+                orc_strain_moments(gl, ge, sg, F.rho[k], F0x, F0y, ukx[k], uky[k], S);
+                force_with_strain(s, &F, phat, dxux, dyux, dxuy, dyuy, S[0], S[1], S[2], k, &Fx, &Fy);
+            } else {
+                total_force(s, &F, phat, dxux, dyux, dxuy, dyuy, k, &Fx, &Fy);
+            }
             unx[k] = jx[k] + Fx / (2.0 * F.rho[k]);
             uny[k] = jy[k] + Fy / (2.0 * F.rho[k]);
             num += hypot(unx[k] - ukx[k], uny[k] - uky[k]);

@@ -43,6 +43,7 @@ typedef struct {
     int picard_iters;     /* sweeps of the implicit velocity update (maximum when zeta>0) */
     double picard_zeta;   /* 0: fixed number of sweeps; >0: stop when the residual < zeta */
     double grad_eps;      /* regularisation of |grad phi| inside n = grad phi / |grad phi| */
+    unsigned flags;       /* bit 0: F_nu of the Picard sweeps takes its strain rate from Eq. (Fmu) */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
@@ -61,6 +62,8 @@ void orc_collide_f(const double f[9], const double feq[9], const double F[9],
                    const double s[9], double out[9]);
 void orc_collide_g(const double g[9], const double geq_f[9], const double geq_hat[9],
                    const double G[9], const double s[9], double out[9]);
+void orc_strain_moments(const double g[9], const double geq[9], const double s[9], double rho,
+                        double Fx, double Fy, double ux, double uy, double out[3]);
 
 /* Stencils on full periodic/walled fields; parity +1 even, -1 odd about a wall. */
 void orc_grad_iso(int nx, int ny, int px, int py, int parity, const double *in,

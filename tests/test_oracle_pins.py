@@ -527,3 +527,72 @@ def test_diffusive_momentum_force_on_rigid_rotation():
     expect = 0.5 * (predicted(phi0) + predicted(phiT))
     assert np.abs(expect).max() > 1e-3 * Om * R          # the effect is resolved
     assert np.linalg.norm(measured - expect) < 0.25 * np.linalg.norm(expect)
+
+
+# ---- strain rate from the non-equilibrium moments (Sec. III.B Eq. Fmu) -----
+
+def _single_phase_state(n, nu, steps, ux0, uy0, **kw):
+    prm = inputs.base_params(rho_H=3.0, rho_L=1.0, nu_H=nu, nu_L=nu, filter_order=0, **kw)
+    z = np.zeros((n, n))
+    s = oracle.Sim(prm, np.ones((n, n)), z, ux0, uy0)
+    s.step(steps)
+    sg = list(prm["s_g"])
+    sg[7] = sg[8] = 1.0 / (nu / CS2 + 0.5)
+    return prm, s.state(), sg
+
+
+def test_strain_moments_vanish_in_uniform_acceleration():
+    """A uniform flow under a uniform body force stays uniform (grad u = 0),
+    while the forcing leaves a non-equilibrium part in g: the forcing term of
+    Eq. (Fmu) must cancel it exactly, so the strain rate is zero to round-off
+    (it is ~1e-6 without that term, or with s_1 for s_7)."""
+    n, nu, gx, gy = 12, 0.05, 1e-4, -3e-5
+    one = np.ones((n, n))
+    prm, st, sg = _single_phase_state(n, nu, 30, 0.01 * one, -0.005 * one, gx=gx, gy=gy)
+    for (j, i) in ((5, 5), (0, 11), (7, 2)):
+        g = st["g"][:, j, i]
+        ux, uy = st["uhx"][j, i], st["uhy"][j, i]
+        geq = oracle.geq(g.sum() * CS2, ux, uy)
+        S = oracle.strain_moments(g, geq, sg, 3.0, 3.0 * gx, 3.0 * gy, ux, uy)
+        S0 = oracle.strain_moments(g, geq, sg, 3.0, 0.0, 0.0, ux, uy)
+        assert np.abs(S0).max() > 1e-7
+        assert np.abs(S).max() < 1e-12
+
+
+def test_strain_moments_match_shear_wave():
+    """The non-equilibrium sum of Eq. (Fmu) gives d u_x/dy of a decaying shear
+    wave u_x = U sin(ky) exp(-nu k^2 t) (no force)."""
+    n, nu, U, T = 32, 0.05, 1e-3, 100
+    y = np.mgrid[0:n, 0:n][0].astype(float)
+    k = 2 * math.pi / n
+    prm, st, sg = _single_phase_state(n, nu, T, U * np.sin(k * y), np.zeros((n, n)))
+    got, want = [], []
+    for j in range(n):
+        g = st["g"][:, j, 3]
+        ux, uy = st["uhx"][j, 3], st["uhy"][j, 3]
+        S = oracle.strain_moments(g, oracle.geq(g.sum() * CS2, ux, uy), sg, 3.0, 0.0, 0.0, ux, uy)
+        got.append(S)
+        want.append(U * k * math.cos(k * j) * math.exp(-nu * k * k * T))
+    got, want = np.array(got), np.array(want)
+    assert np.abs(got[:, 1] - want).max() < 2e-3 * np.abs(want).max()
+    assert np.abs(got[:, [0, 2]]).max() < 2e-3 * np.abs(want).max()
+
+
+@pytest.mark.slow
+def test_layered_channel_with_moment_strain():
+    """The layered channel of test_layered_channel_viscous_stress with F_nu's
+    strain rate from Eq. (Fmu) in the Picard sweeps (flags bit 0): the same
+    1-D steady profile (a sign slip or a halved sum in the moment strain
+    breaks it)."""
+    orig = inputs.base_params
+
+    def with_flag(**kw):
+        d = orig(**kw)
+        d["flags"] = 1
+        return d
+
+    inputs.base_params = with_flag
+    try:
+        test_layered_channel_viscous_stress(0.0)
+    finally:
+        inputs.base_params = orig
