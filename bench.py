@@ -37,20 +37,21 @@ PROFILES = os.path.join(ROOT, "profiles")
 
 # Algorithmic words (4 bytes in FP32, 8 in FP64) per node and launch of each
 # kernel: every persistent plane it needs read once and written once; what
-# stays on chip is not counted.
-#   collide+stream: read 18 populations + phi, p, u(2), u_prev(2), u_hat(2);
-#                   write 18 populations + phi_bar, p_hat, j(2)       -> 48
+# stays on chip is not counted.  FP32 handles carry phi as phi_hi + phi_lo.
+#   collide+stream: read 18 populations + phi, phi_lo, p, u(2), u_prev(2),
+#                   u_hat(2); write 18 populations + dbar, p_hat, j(2) -> 49
 #     k_collide_pairs (default rates) does not need the rest populations
-#     f_0, g_0, whose rate-1 relaxation discards them: reads 16       -> 46
-#   RK3 stage: read psi (+ phi_bar in stages 2, 3); write the stage  -> 2, 3, 3
-#   Picard sweep: read phi, p_hat, j(2), u^k(2); write u^{k+1}(2)    -> 8
-#   filter: read p_hat, u_hat(2); write p, u(2)                      -> 6
-KIND_WORDS = {"k_collide_stream": 48.0, "k_rk_stage": 8.0 / 3.0, "k_picard": 8.0, "k_filter": 6.0}
-VARIANT_WORDS = {"k_collide_pairs": 46.0}
+#     f_0, g_0, whose rate-1 relaxation discards them: reads 16       -> 47
+#   RK3 stages over a step: (phi, dbar) -> d1; (phi, d1, dbar) -> d2;
+#     (phi, d2, dbar) -> phi^{n+1}, phi_lo: 3 + 4 + 5 words          -> 4 per launch
+#   Picard sweep: read phi, p_hat, j(2), u^k(2); write u^{k+1}(2)     -> 8
+#   filter: read p_hat, u_hat(2); write p, u(2)                       -> 6
+KIND_WORDS = {"k_collide_stream": 49.0, "k_rk_stage": 4.0, "k_picard": 8.0, "k_filter": 6.0}
+VARIANT_WORDS = {"k_collide_pairs": 47.0}
 # Mixed-precision storage: the 34 population words of k_collide_pairs take 2
-# bytes, the 12 scalar words and the other kernels' 30 stay FP32:
-# 34 * 2 + (12 + 30) * 4 = 236 bytes per node and step.
-MIXED_STEP_BYTES = 34 * 2 + (12 + 30) * 4
+# bytes, the 13 scalar words and the other kernels' 34 (two Picard sweeps)
+# stay FP32: 34 * 2 + (13 + 34) * 4 = 256 bytes per node and step.
+MIXED_STEP_BYTES = 34 * 2 + (13 + 34) * 4
 # The least a step must move (all intermediates on chip): populations read and
 # written once, phi, u^n, u^{n-1} read and phi, u^{n+1} written (8 words).
 B_MIN = {"fp32": 18 * 2 * 4 + 8 * 4, "mixed": 18 * 2 * 2 + 8 * 4}
@@ -270,7 +271,7 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     v = n * n * args.steps / dt / 1e6
     sample = (f"capillary wave {n}x{n} (same parameters as the 4096^2 workload), one oracle step "
-              f"per bench step, FP64, single thread on {cpu_model()}")
+              f"per bench step, FP64, single thread on {cpu_model()} ({os.cpu_count()} cores on the host)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
@@ -278,7 +279,8 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": f"capillary wave {n}x{n} sample of the 4096x4096 workload, rho ratio 1000",
                    "nx": n, "ny": n, "precision": "fp64"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -451,9 +453,9 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cn, cs = 512, 20
         v, dt = oracle_mlups(cn, cs)
-        cpu = {"value": round(v, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": round(v, 3), "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                "sample": f"capillary wave {cn}x{cn}, same parameters, {cs} steps ({dt:.1f} s), FP64 oracle, "
-                         f"single thread on {cpu_model()}"}
+                         f"single thread on {cpu_model()} ({os.cpu_count()} cores on the host)"}
 
     diag = sim.diagnostics()
     ok = diag[10] == 0

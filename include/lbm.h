@@ -122,6 +122,24 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params,
 lbm_status lbm_step(lbm_handle *h, int n);
 
 /*
+ * lbm_step_ch -- advance n >= 0 steps of the Cahn-Hilliard part alone under
+ * a prescribed velocity, as in the interface-capturing tests of
+ * Sec. IV.A-B where the flow is given: each step takes mu from phi
+ * (Eq. chemical), collides the CH populations with f_eq(phi, mu, u) and the
+ * source F_i of d_t u + u.grad u (Eqs. feq_CH, Fi, with d_t u = u - u of the
+ * previous step), streams them and applies the RK3 finite-difference
+ * correction (Eq. TVD-3order).  The velocity of step k is
+ * tfac[k] * (ux, uy): ux, uy are host [ny][nx] doubles and tfac a host array
+ * of n factors, or NULL for 1 (a separable time dependence such as the
+ * cos(pi t/T) of the single-vortex field needs no upload per step).  The
+ * NS populations, p and u_hat are left as they are; the last step's
+ * velocity becomes the state's velocity and its previous one.  Asynchronous
+ * after the upload of ux, uy.  Errors: LBM_ERR_ARG (n < 0, NULL ux or uy,
+ * reduced-precision populations), LBM_ERR_STATE as lbm_step.
+ */
+lbm_status lbm_step_ch(lbm_handle *h, int n, const double *ux, const double *uy, const double *tfac);
+
+/*
  * lbm_fields -- copy phi, the filtered kinematic pressure p, and the
  * filtered velocity (ux, uy) into host [ny][nx] double arrays.  A NULL
  * pointer skips that field.  Synchronises the stream.

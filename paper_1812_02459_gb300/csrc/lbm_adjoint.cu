@@ -1676,10 +1676,15 @@ template <typename T> cudaError_t copy_state_to(lbm_handle *h, T *const *dst)
     kk_leaves<T><<<blocks_for(h->N), NTH, 0, h->stream>>>(Lv, h->N, 1, 0);
     return cudaGetLastError();
 }
+// The checkpoints hold phi_hi only: a restored FP32 state starts with
+// phi_lo = 0, so regeneration follows the forward run to within the rounding
+// of phi (the sweep itself reads phi_hi).
 cudaError_t copy_state_in(lbm_handle *h, const void *src)
 {
     void *s = const_cast<void *>(src);
-    return h->elem == sizeof(double) ? copy_state_t<double>(h, s, false) : copy_state_t<float>(h, s, false);
+    if (h->elem == sizeof(double)) return copy_state_t<double>(h, s, false);
+    cudaError_t e = cudaMemsetAsync(h->philo, 0, sizeof(float) * (size_t)h->N, h->stream);
+    return e != cudaSuccess ? e : copy_state_t<float>(h, s, false);
 }
 
 // The reverse sweep runs in the handle's arithmetic type T (the adjoint

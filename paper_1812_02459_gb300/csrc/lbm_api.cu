@@ -258,6 +258,9 @@ lbm_status set_smem_limits(lbm_handle *h)
     CK(h, cudaFuncSetAttribute(k_collide_stream<T, S, CS_TX, CS_TY, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cs<T>()),
        "cudaFuncSetAttribute(collide_stream)");
+    CK(h, cudaFuncSetAttribute(k_collide_ch<T, CS_TX, CS_TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(sizeof(T) * CHGeom<CS_TX, CS_TY>::NSCALAR)),
+       "cudaFuncSetAttribute(collide_ch)");
     CK(h, cudaFuncSetAttribute(k_rk_stage<T, RK_TX, RK_TY, RK_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem_rk<T>()),
        "cudaFuncSetAttribute(rk_stage)");
@@ -369,6 +372,47 @@ lbm_status launch_filter_r(lbm_handle *h, const T *pin, const T *uxi, const T *u
     return LBM_OK;
 }
 
+// TVD-RK3 finite-difference correction (Sec. III.A Eq. TVD-3order) in
+// increments over phi^n: dbar -> d1 -> d2 -> phi^{n+1} = phi^n + d3 (written
+// to phin, with phi_lo updated for FP32 handles).
+template <typename T>
+lbm_status rk3_impl(lbm_handle *h, T *phi, T *phin, T *dbar, T *philo)
+{
+    const KP<T> &P = kp_of<T>(h);
+    cudaStream_t st = h->stream;
+    dim3 grid((P.nx + RK_TX - 1) / RK_TX, (P.ny + RK_TY - 1) / RK_TY);
+    const size_t sm = smem_rk<T>();
+    const T *src[3] = {dbar, (const T *)h->s1, (const T *)h->s2};
+    T *dst[3] = {(T *)h->s1, (T *)h->s2, phin};
+    const T ca[3] = {T(0), T(0.75), T(1.0 / 3.0)}, cb[3] = {T(1), T(0.25), T(2.0 / 3.0)};
+    for (int k = 0; k < 3; ++k) {
+        Timed tm(h, 1);
+        const int last = k == 2;
+        bool done = false;
+        if constexpr (std::is_same<T, float>::value) {
+            if (h->tma) {   // TMA-staged windows, one CTA per tile
+                using GT = RKTGeom<RK_TX, RK_TY>;
+                TmaMaps maps{};
+                lbm_status r = tmap(h, phi, GT::BW, GT::BH, &maps.m[0]);
+                if (!r) r = tmap(h, src[k], GT::BW, GT::BH, &maps.m[1]);
+                if (r) return r;
+                k_rk_tma<RK_TX, RK_TY, RT_NT, RS_VR1, RS_VR2, RS_VR3, RT_MINB>
+                    <<<grid.x * grid.y, RT_NT, GT::Tile::BYTES, st>>>(maps, P, phi, src[k], dbar, dst[k],
+                                                                     ca[k], cb[k], last, philo, h->dev_err);
+                done = true;
+            } else if (P.nx % 2 == 0) {   // column-pair strips, paired FP32 arithmetic
+                k_rk_strips<RK_TX, RK_TY, RS_NT, RS_VR1, RS_VR2, RS_VR3><<<grid, RS_NT, sm, st>>>(
+                    P, phi, src[k], dbar, dst[k], ca[k], cb[k], last, philo);
+                done = true;
+            }
+        }
+        if (!done)
+            k_rk_stage<T, RK_TX, RK_TY, RK_NT><<<grid, RK_NT, sm, st>>>(P, phi, src[k], dbar, dst[k], ca[k],
+                                                                      cb[k], last, philo);
+    }
+    return LBM_OK;
+}
+
 template <typename T, typename S>
 lbm_status step_impl(lbm_handle *h)
 {
@@ -382,6 +426,7 @@ lbm_status step_impl(lbm_handle *h)
     T *uhx = (T *)h->uhx, *uhy = (T *)h->uhy;
     const T *dbar_old = (const T *)h->dbar[h->acur], *phat_old = (const T *)h->phat[h->acur];
     T *dbar = (T *)h->dbar[1 - h->acur], *phat = (T *)h->phat[1 - h->acur];
+    T *philo = sizeof(T) == sizeof(float) ? (T *)h->philo : nullptr;   // low part of phi (FP32)
     T *jx = (T *)h->jx, *jy = (T *)h->jy;
 
     {   // fields, forces, collision of f and g, pull streaming, post-stream moments
@@ -400,7 +445,7 @@ lbm_status step_impl(lbm_handle *h)
                 const int ntiles = ((P.nx + CP_TX - 1) / CP_TX) * ((P.ny + CP_TY - 1) / CP_TY);
                 k_collide_pairs<S, CP_TX, CP_TY, CP_VR1><<<ntiles, GC::NT, GC::Tile::BYTES, st>>>(
                     maps, P, (const S *)h->f[c], (const S *)h->g[c], (S *)h->f[1 - c], (S *)h->g[1 - c], phi, pf,
-                    uxc, uyc, uxp, uyp, uhx, uhy, dbar, phat, jx, jy, h->dev_err);
+                    uxc, uyc, uxp, uyp, uhx, uhy, (const float *)philo, dbar, phat, jx, jy, h->dev_err);
                 done = true;
             }
         }
@@ -409,41 +454,12 @@ lbm_status step_impl(lbm_handle *h)
                                               : k_collide_stream<T, S, CS_TX, CS_TY, false>;
             kern<<<grid, (CS_TX + 2) * (CS_TY + 2), smem_cs<T>(), st>>>(
                 P, (const S *)h->f[c], (const S *)h->g[c], (S *)h->f[1 - c], (S *)h->g[1 - c], phi, pf, uxc, uyc,
-                uxp, uyp, uhx, uhy, phin, dbar_old, phat_old, dbar, phat, jx, jy);
+                uxp, uyp, uhx, uhy, phin, dbar_old, phat_old, philo, dbar, phat, jx, jy);
         }
     }
-    {   // TVD-RK3 finite-difference correction in increments over phi^n:
-        // dbar -> d1 -> d2 -> phi^{n+1} = phi^n + d3
-        dim3 grid((P.nx + RK_TX - 1) / RK_TX, (P.ny + RK_TY - 1) / RK_TY);
-        const size_t sm = smem_rk<T>();
-        const T *src[3] = {dbar, (const T *)h->s1, (const T *)h->s2};
-        T *dst[3] = {(T *)h->s1, (T *)h->s2, phin};
-        const T ca[3] = {T(0), T(0.75), T(1.0 / 3.0)}, cb[3] = {T(1), T(0.25), T(2.0 / 3.0)};
-        for (int k = 0; k < 3; ++k) {
-            Timed tm(h, 1);
-            const int last = k == 2;
-            bool done = false;
-            if constexpr (std::is_same<T, float>::value) {
-                if (h->tma) {   // TMA-staged windows, one CTA per tile
-                    using GT = RKTGeom<RK_TX, RK_TY>;
-                    TmaMaps maps{};
-                    lbm_status r = tmap(h, phi, GT::BW, GT::BH, &maps.m[0]);
-                    if (!r) r = tmap(h, src[k], GT::BW, GT::BH, &maps.m[1]);
-                    if (r) return r;
-                    k_rk_tma<RK_TX, RK_TY, RT_NT, RS_VR1, RS_VR2, RS_VR3, RT_MINB>
-                        <<<grid.x * grid.y, RT_NT, GT::Tile::BYTES, st>>>(maps, P, phi, src[k], dbar, dst[k],
-                                                                         ca[k], cb[k], last, h->dev_err);
-                    done = true;
-                } else if (P.nx % 2 == 0) {   // column-pair strips, paired FP32 arithmetic
-                    k_rk_strips<RK_TX, RK_TY, RS_NT, RS_VR1, RS_VR2, RS_VR3><<<grid, RS_NT, sm, st>>>(
-                        P, phi, src[k], dbar, dst[k], ca[k], cb[k], last);
-                    done = true;
-                }
-            }
-            if (!done)
-                k_rk_stage<T, RK_TX, RK_TY, RK_NT><<<grid, RK_NT, sm, st>>>(P, phi, src[k], dbar, dst[k], ca[k],
-                                                                          cb[k], last);
-        }
+    {   // TVD-RK3 finite-difference correction: phi^n + dbar -> phi^{n+1}
+        lbm_status r = rk3_impl<T>(h, phi, phin, dbar, philo);
+        if (r) return r;
     }
     {   // implicit velocity by Picard sweeps; the last sweep lands in u_hat
         dim3 grid((P.nx + PC_TX - 1) / PC_TX, (P.ny + PC_TY - 1) / PC_TY);
@@ -555,6 +571,89 @@ lbm_status download_plane(lbm_handle *h, double *dst, const void *src)
     return LBM_OK;
 }
 
+// n steps of the Cahn-Hilliard part alone under u = tfac[k] (ux, uy) at
+// step k (tfac NULL: 1); the NS lattice, p and u_hat are left as they are.
+template <typename T>
+lbm_status step_ch_impl(lbm_handle *h, int n, const double *ux, const double *uy, const double *tfac)
+{
+    if (n == 0) return LBM_OK;
+    const KP<T> &P = kp_of<T>(h);
+    cudaStream_t st = h->stream;
+    const size_t b = sizeof(T) * (size_t)h->N;
+    T *u0x = (T *)h->tk[0][0], *u0y = (T *)h->tk[0][1];   // the prescribed field (Picard scratch)
+    lbm_status r;
+    if ((r = upload_plane<T>(h, u0x, ux))) return r;
+    if ((r = upload_plane<T>(h, u0y, uy))) return r;
+    // g stays put: both population buffers hold it, so the buffer flips below are harmless
+    CK(h, cudaMemcpyAsync(h->g[1 - h->cur], h->g[h->cur], 9 * b, cudaMemcpyDeviceToDevice, st), "ch copy g");
+    CK(h, cudaMemcpyAsync(h->phat[1 - h->acur], h->phat[h->acur], b, cudaMemcpyDeviceToDevice, st), "ch copy p");
+    T *philo = sizeof(T) == sizeof(float) ? (T *)h->philo : nullptr;
+    using G = CHGeom<CS_TX, CS_TY>;
+    dim3 grid((P.nx + CS_TX - 1) / CS_TX, (P.ny + CS_TY - 1) / CS_TY);
+    for (int k = 0; k < n; ++k) {
+        const T us = tfac ? (T)tfac[k] : T(1);
+        // u of the previous step: the state's at the first step, then the prescribed one
+        const T *upx = k == 0 ? (const T *)h->ux[1 - h->ucur] : u0x;
+        const T *upy = k == 0 ? (const T *)h->uy[1 - h->ucur] : u0y;
+        const T ups = k == 0 ? T(1) : (tfac ? (T)tfac[k - 1] : T(1));
+        T *phi = (T *)h->phi[h->pcur], *phin = (T *)h->phi[1 - h->pcur];
+        T *dbar = (T *)h->dbar[1 - h->acur];
+        {
+            Timed tm(h, 0);
+            k_collide_ch<T, CS_TX, CS_TY><<<grid, (CS_TX + 2) * (CS_TY + 2), sizeof(T) * G::NSCALAR, st>>>(
+                P, (const T *)h->f[h->cur], (T *)h->f[1 - h->cur], phi, philo, u0x, u0y, us, upx, upy, ups, dbar);
+        }
+        if ((r = rk3_impl<T>(h, phi, phin, dbar, philo))) return r;
+        CK(h, cudaGetLastError(), "kernel launch");
+        h->cur ^= 1;
+        h->acur ^= 1;
+        h->pcur ^= 1;
+    }
+    // u of the last step becomes the state's velocity and its previous one
+    const T ul = tfac ? (T)tfac[n - 1] : T(1);
+    const int blocks = (int)std::min<long long>((h->N + 255) / 256, 4096);
+    for (int s2 = 0; s2 < 2; ++s2) {
+        k_scale<T><<<blocks, 256, 0, st>>>(u0x, ul, (T *)h->ux[s2], h->N);
+        k_scale<T><<<blocks, 256, 0, st>>>(u0y, ul, (T *)h->uy[s2], h->N);
+    }
+    CK(h, cudaGetLastError(), "kernel launch");
+    return LBM_OK;
+}
+
+// phi^n from host doubles: FP32 handles keep it as phi_hi + phi_lo.
+template <typename T>
+lbm_status upload_phi(lbm_handle *h, const double *src)
+{
+    if constexpr (sizeof(T) == sizeof(double)) {
+        return upload_plane<T>(h, h->phi[h->pcur], src);
+    } else {
+        const size_t n = (size_t)h->N;
+        CK(h, cudaMemcpyAsync(staging(h), src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "upload");
+        k_split<<<(int)std::min<long long>((h->N + 255) / 256, 4096), 256, 0, h->stream>>>(
+            staging(h), (float *)h->phi[h->pcur], (float *)h->philo, h->N);
+        CK(h, cudaGetLastError(), "upload split");
+        return LBM_OK;
+    }
+}
+
+// phi^n to host doubles (phi_hi + phi_lo for FP32 handles).
+template <typename T>
+lbm_status download_phi(lbm_handle *h, double *dst)
+{
+    if (!dst) return LBM_OK;
+    if constexpr (sizeof(T) == sizeof(double)) {
+        return download_plane<T>(h, dst, phi_cur(h));
+    } else {
+        const size_t n = (size_t)h->N;
+        k_join<<<(int)std::min<long long>((h->N + 255) / 256, 4096), 256, 0, h->stream>>>(
+            (const float *)phi_cur(h), (const float *)h->philo, staging(h), h->N);
+        CK(h, cudaGetLastError(), "download join");
+        CK(h, cudaMemcpyAsync(dst, staging(h), n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "download");
+        CK(h, cudaStreamSynchronize(h->stream), "download sync");
+        return LBM_OK;
+    }
+}
+
 template <typename T>
 lbm_status upload_field(lbm_handle *h, void *dst, const double *src)
 {
@@ -591,7 +690,7 @@ lbm_status init_impl(lbm_handle *h, const double *phi0, const double *p0, const 
 {
     lbm_status st;
     h->pcur = 0;
-    if ((st = upload_plane<T>(h, h->phi[0], phi0))) return st;
+    if ((st = upload_phi<T>(h, phi0))) return st;
     if ((st = upload_plane<T>(h, h->pf, p0))) return st;
     if ((st = upload_plane<T>(h, h->ux[0], ux0))) return st;
     if ((st = upload_plane<T>(h, h->uy[0], uy0))) return st;
@@ -639,7 +738,7 @@ template <typename T>
 lbm_status fields_impl(lbm_handle *h, double *phi, double *p, double *ux, double *uy)
 {
     lbm_status st;
-    if ((st = download_plane<T>(h, phi, phi_cur(h)))) return st;
+    if ((st = download_phi<T>(h, phi))) return st;
     if ((st = download_plane<T>(h, p, h->pf))) return st;
     if ((st = download_plane<T>(h, ux, h->ux[h->ucur]))) return st;
     if ((st = download_plane<T>(h, uy, h->uy[h->ucur]))) return st;
@@ -756,7 +855,18 @@ lbm_status set_state_impl(lbm_handle *h, const double *f, const double *g, const
         }
     }
     h->pcur = 0;
-    if ((st = upload_field<T>(h, h->phi[0], phi))) return st;
+    if constexpr (sizeof(T) == sizeof(double)) {
+        if ((st = upload_field<T>(h, h->phi[0], phi))) return st;
+    } else {   // phi_hi + phi_lo
+        std::vector<float> hi(n), lo(n);
+        for (size_t k = 0; k < n; ++k) {
+            hi[k] = (float)phi[k];
+            lo[k] = (float)(phi[k] - (double)hi[k]);
+        }
+        CK(h, cudaMemcpyAsync(h->phi[0], hi.data(), n * sizeof(float), cudaMemcpyHostToDevice, h->stream), "upload");
+        CK(h, cudaMemcpyAsync(h->philo, lo.data(), n * sizeof(float), cudaMemcpyHostToDevice, h->stream), "upload");
+        CK(h, cudaStreamSynchronize(h->stream), "upload sync");
+    }
     CK(h, cudaMemcpyAsync(h->phi[1], h->phi[0], sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream), "set_state copy");
     if ((st = upload_field<T>(h, h->pf, p))) return st;
     if ((st = upload_field<T>(h, h->ux[0], ux))) return st;
@@ -820,7 +930,7 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params, const doub
     // one arena: 2x9 f planes, 2x9 g planes, then the scalar planes, 256-byte aligned each
     const size_t plane = round_up((size_t)h->N * h->elem, 256);
     const size_t pplane = round_up((size_t)h->N * 9 * h->pop_elem, 256);
-    const int nscalar = 22;   // phi[2], pf, ux[2], uy[2], uhx, uhy, dbar[2], phat[2], jx, jy, s1, s2, tk[2][2], 1 spare
+    const int nscalar = 23;   // phi[2], philo, pf, ux[2], uy[2], uhx, uhy, dbar[2], phat[2], jx, jy, s1, s2, tk[2][2], 1 spare
     h->diag_blocks = std::min(grid->ny, DIAG_MAX_BLOCKS);   // rows per block: ny / blocks
     const size_t diag_bytes = round_up(sizeof(double) * (size_t)(h->diag_blocks + 1) * NDIAG, 256);
     h->arena_bytes = 4 * pplane + nscalar * plane + diag_bytes + 256;   // + the device error word
@@ -836,7 +946,7 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params, const doub
     h->f[1] = a; a += pplane;
     h->g[0] = a; a += pplane;
     h->g[1] = a; a += pplane;
-    void **sc[] = {&h->phi[0], &h->phi[1], &h->pf, &h->ux[0], &h->ux[1], &h->uy[0], &h->uy[1], &h->uhx, &h->uhy,
+    void **sc[] = {&h->phi[0], &h->phi[1], &h->philo, &h->pf, &h->ux[0], &h->ux[1], &h->uy[0], &h->uy[1], &h->uhx, &h->uhy,
                    &h->dbar[0], &h->dbar[1], &h->phat[0], &h->phat[1], &h->jx, &h->jy, &h->s1, &h->s2,
                    &h->tk[0][0], &h->tk[0][1], &h->tk[1][0], &h->tk[1][1]};
     for (void **pp : sc) { *pp = a; a += plane; }
@@ -896,6 +1006,19 @@ lbm_status lbm_step(lbm_handle *h, int n)
         }
         return LBM_OK;
     });
+}
+
+lbm_status lbm_step_ch(lbm_handle *h, int n, const double *ux, const double *uy, const double *tfac)
+{
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
+    if (n < 0) return fail(h, LBM_ERR_ARG, "n must be >= 0");
+    if (!ux || !uy) return fail(h, LBM_ERR_ARG, "ux, uy must be non-NULL");
+    if (h->grid.precision != LBM_FP64 && h->grid.precision != LBM_FP32)
+        return fail(h, LBM_ERR_ARG, "the Cahn-Hilliard-only step needs FP64 or FP32 populations");
+    if (h->failed) return fail(h, LBM_ERR_STATE, "an earlier step gave up a tile-copy wait: destroy the handle");
+    if (n > 0) h->fresh_init = false;
+    return h->grid.precision == LBM_FP64 ? step_ch_impl<double>(h, n, ux, uy, tfac)
+                                         : step_ch_impl<float>(h, n, ux, uy, tfac);
 }
 
 lbm_status lbm_set_check(lbm_handle *h, int every, double delta)

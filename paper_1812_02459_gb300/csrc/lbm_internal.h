@@ -25,6 +25,7 @@ struct lbm_handle {
     int cur = 0;                       // which population buffer holds the state
     void *phi[2]{};                    // phi[pcur] = phi^n; the other slot holds the phi of the
     int pcur = 0;                      // previous step until the RK3 pass writes phi^{n+1} there
+    void *philo = nullptr;             // FP32 arithmetic: phi = phi[pcur] + philo (float pair)
     void *pf = nullptr, *ux[2]{}, *uy[2]{};
     int ucur = 0;                      // ux[ucur] = filtered u^n, ux[1-ucur] = u^{n-1}
     void *uhx = nullptr, *uhy = nullptr;

@@ -194,6 +194,15 @@ __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
 
+// The rounding error of s = a + b (Knuth's TwoSum, exact in IEEE arithmetic):
+// a + b = s + err.  phi is carried as phi_hi + phi_lo, each step adding its
+// increment r to phi_hi and keeping what the rounding of the sum drops.
+template <typename T> __device__ __forceinline__ T two_sum_err(T a, T b, T s)
+{
+    const T bp = s - a, ap = s - bp;
+    return (a - ap) + (b - bp);
+}
+
 // Density, its reciprocal and the kinematic viscosity at a node (Sec. II.B
 // Eq. rho, Sec. III.B Eq. dynamic_vis), with phi clamped to [-1,1] here only.
 template <typename T>
@@ -348,7 +357,7 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
                  const T *__restrict__ upx, const T *__restrict__ upy,
                  const T *__restrict__ uhx, const T *__restrict__ uhy,
                  const T *__restrict__ phi_prev, const T *__restrict__ dbar_old,
-                 const T *__restrict__ phat_old,
+                 const T *__restrict__ phat_old, const T *__restrict__ philo,
                  T *__restrict__ dbar, T *__restrict__ phat,
                  T *__restrict__ jxo, T *__restrict__ jyo)
 {
@@ -359,7 +368,9 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
     // dbar = phi_bar - phi, free of the rounding of an O(1) sum.  phi_prev,
     // dbar_old and phat_old give the post-stream moments of the stored
     // populations (phi_bar = phi_prev + dbar_old, p_hat); they are read only
-    // when the populations are stored in reduced precision.
+    // when the populations are stored in reduced precision.  philo (FP32
+    // handles, else NULL) holds the low part of phi = phi_hi + phi_lo: the
+    // collision relaxes m_0 to the whole of it, so phi_lo enters dbar.
     using G = CSGeom<TX, TY>;
     constexpr int W3 = G::W3, W2 = G::W2, H2 = G::H2, W1 = G::W1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -387,7 +398,7 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
     const bool ghost = (!P.px && (X < 0 || X >= P.nx)) || (!P.py && (Y < 0 || Y >= P.ny));
     int fxm, fym;
     const int gidx = map_axis(Y, P.ny, P.py, fym) * P.nx + map_axis(X, P.nx, P.px, fxm);
-    T f[9], g[9], upx_ = T(0), upy_ = T(0), uhx_ = T(0), uhy_ = T(0), pprev = T(0);
+    T f[9], g[9], upx_ = T(0), upy_ = T(0), uhx_ = T(0), uhy_ = T(0), pprev = T(0), plo = T(0);
     if (!ghost) {
         const unsigned N32 = P.N32;
         if constexpr (Mixed<T, S>::on) {
@@ -413,6 +424,7 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
                 g[q] = Codec<S, T>::load(__ldg(&gin[o]));
             }
         }
+        if (philo) plo = __ldg(&philo[gidx]);
         upx_ = __ldg(&upx[gidx]);
         upy_ = __ldg(&upy[gidx]);
         uhx_ = __ldg(&uhx[gidx]);
@@ -477,7 +489,7 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
         {
             T m[9];
             const T em = P.eta * mu;
-            const T meq[9] = {T(0), T(2) * em + T(3) * ph * u2, -T(3) * em - T(3) * ph * u2,
+            const T meq[9] = {plo, T(2) * em + T(3) * ph * u2 - T(4) * plo, T(4) * plo - T(3) * em - T(3) * ph * u2,
                               ph * u0, -ph * u0, ph * u1, -ph * u1, ph * (u0 * u0 - u1 * u1), ph * u0 * u1};
             const T mF[9] = {T(0), T(0), T(0), ph * ax, -ph * ax, ph * ay, -ph * ay, T(0), T(0)};
             if constexpr (FAST) {
@@ -602,6 +614,109 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
 }
 
 // ---------------------------------------------------------------------------
+// Pass 1 of the Cahn-Hilliard part alone, under a prescribed velocity (the
+// interface-capturing tests of Sec. IV.A-B, where the flow is given):
+// mu = 4 beta (phi^3 - phi) - kappa lap phi, the CH collision with
+// f_eq(phi, mu, u) and the source F_i of a = (u - u_prev) + u.grad u
+// (Eqs. feq_CH, Fi), pull streaming and dbar = phi_bar - phi.  The NS
+// lattice is not touched.  The velocity is u = us * u0 and the previous
+// step's up_s * up; one node per thread of the collision region, the general
+// relaxation of every moment, populations stored in T.
+// ---------------------------------------------------------------------------
+template <int TX, int TY> struct CHGeom {
+    static constexpr int W2 = TX + 4, H2 = TY + 4;   // phi, u windows (ring 2)
+    static constexpr int W1 = TX + 2, H1 = TY + 2;   // collision region (ring 1)
+    static constexpr int A2 = W2 * H2, A1 = W1 * H1;
+    static constexpr int NSCALAR = 3 * A2 + 9 * A1;
+};
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__((TX + 2) * (TY + 2))
+k_collide_ch(KP<T> P, const T *__restrict__ fin, T *__restrict__ fout, const T *__restrict__ phi,
+             const T *__restrict__ philo, const T *__restrict__ u0x, const T *__restrict__ u0y, T us,
+             const T *__restrict__ upx, const T *__restrict__ upy, T ups, T *__restrict__ dbar)
+{
+    using G = CHGeom<TX, TY>;
+    constexpr int W2 = G::W2, H2 = G::H2, W1 = G::W1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s_phi = reinterpret_cast<T *>(smem_raw);
+    T *s_ux = s_phi + G::A2;
+    T *s_uy = s_ux + G::A2;
+    T *s_f = s_uy + G::A2;   // [9][A1]
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int t = threadIdx.x;
+    const int ly = t / W1, lx = t - ly * W1;
+    const int X = x0 - 1 + lx, Y = y0 - 1 + ly;
+    const bool ghost = (!P.px && (X < 0 || X >= P.nx)) || (!P.py && (Y < 0 || Y >= P.ny));
+    int fl;
+    const int gidx = map_axis(Y, P.ny, P.py, fl) * P.nx + map_axis(X, P.nx, P.px, fl);
+    T f[9], plo = T(0), upx_ = T(0), upy_ = T(0);
+    if (!ghost) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) f[q] = __ldg(&fin[(size_t)gidx + (size_t)q * P.N]);
+        if (philo) plo = __ldg(&philo[gidx]);
+        upx_ = ups * __ldg(&upx[gidx]);
+        upy_ = ups * __ldg(&upy[gidx]);
+    }
+    load_tile<T, W2, H2>(s_phi, phi, x0 - 2, y0 - 2, P, false);
+    load_tile<T, W2, H2>(s_ux, u0x, x0 - 2, y0 - 2, P, true);
+    load_tile<T, W2, H2>(s_uy, u0y, x0 - 2, y0 - 2, P, true);
+    tiles_ready();
+
+    if (!ghost) {
+        const int i2 = (ly + 1) * W2 + (lx + 1);
+        const T ph = s_phi[i2];
+        const T mu = T(4) * P.beta * (ph * ph * ph - ph) - P.kappa * iso_lap<T, W2>(s_phi, i2);
+        T dxux, dyux, dxuy, dyuy;
+        iso_grad<T, W2>(s_ux, i2, dxux, dyux);
+        iso_grad<T, W2>(s_uy, i2, dxuy, dyuy);
+        const T u0 = us * s_ux[i2], u1 = us * s_uy[i2];
+        dxux *= us; dyux *= us; dxuy *= us; dyuy *= us;
+        const T ax = (u0 - upx_) + u0 * dxux + u1 * dyux;
+        const T ay = (u1 - upy_) + u0 * dxuy + u1 * dyuy;
+        const T u2 = u0 * u0 + u1 * u1, em = P.eta * mu;
+        // deviations from phi_hi e_0, m_0 relaxing to phi_hi + phi_lo (as in k_collide_stream)
+        f[0] -= ph;
+        const T meq[9] = {plo, T(2) * em + T(3) * ph * u2 - T(4) * plo, T(4) * plo - T(3) * em - T(3) * ph * u2,
+                          ph * u0, -ph * u0, ph * u1, -ph * u1, ph * (u0 * u0 - u1 * u1), ph * u0 * u1};
+        const T mF[9] = {T(0), T(0), T(0), ph * ax, -ph * ax, ph * ay, -ph * ay, T(0), T(0)};
+        T m[9];
+        to_moments(f, m);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) m[k] = m[k] - P.sf[k] * (m[k] - meq[k]) + (T(1) - T(0.5) * P.sf[k]) * mF[k];
+        from_moments(m, f);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) s_f[q * G::A1 + t] = f[q];
+    }
+    __syncthreads();
+
+    constexpr int cxv[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    constexpr int cyv[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    constexpr int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    for (int k = threadIdx.x; k < TX * TY; k += blockDim.x) {
+        const int ky = k / TX, kx = k - ky * TX;
+        const int Xn = x0 + kx, Yn = y0 + ky;
+        if (Xn >= P.nx || Yn >= P.ny) continue;
+        const size_t nidx = (size_t)Yn * P.nx + Xn;
+        const int c1 = (ky + 1) * W1 + (kx + 1);
+        const bool edge = (!P.px && (Xn == 0 || Xn == P.nx - 1)) || (!P.py && (Yn == 0 || Yn == P.ny - 1));
+        T sf = T(0);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            int src = q * G::A1 + c1 - cyv[q] * W1 - cxv[q];
+            if (edge) {
+                const int SX = Xn - cxv[q], SY = Yn - cyv[q];
+                if ((!P.px && (SX < 0 || SX >= P.nx)) || (!P.py && (SY < 0 || SY >= P.ny))) src = opp[q] * G::A1 + c1;
+            }
+            const T v = s_f[src];
+            sf += v;
+            fout[nidx + (size_t)q * P.N] = q == 0 ? s_phi[(ky + 2) * W2 + (kx + 2)] + v : v;
+        }
+        dbar[nidx] = sf;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Pass 2: one stage of the TVD-RK3 correction (Sec. III.A Eq. TVD-3order)
 //   psi^(k) = a phi_bar + b (psi^(k-1) + L(psi^(k-1))),  L(psi) = div(lambda J_phi + q),
 //   J_phi = (|grad psi| - 2(1 - psi^2)/W) n,  q = -M (grad mu_psi . n) n,
@@ -627,7 +742,7 @@ template <int TX, int TY> struct RKGeom {
 template <typename T, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT)
 k_rk_stage(KP<T> P, const T *__restrict__ phi, const T *__restrict__ din, const T *__restrict__ dbar,
-           T *__restrict__ out, T a, T b, int last)
+           T *__restrict__ out, T a, T b, int last, T *__restrict__ philo)
 {
     using G = RKGeom<TX, TY>;
     constexpr int W6 = G::W6, H6 = G::H6, W4 = G::W4, H4 = G::H4, W2 = G::W2, H2 = G::H2;
@@ -686,7 +801,12 @@ k_rk_stage(KP<T> P, const T *__restrict__ phi, const T *__restrict__ din, const 
         long long gidx = (long long)Y * P.nx + X;
         T r = b * (din[gidx] + L);
         if (a != T(0)) r = a * dbar[gidx] + r;
-        out[gidx] = last ? phi[gidx] + r : r;
+        if (last) {
+            const T h = phi[gidx], s = h + r;
+            if (philo) philo[gidx] = two_sum_err(h, r, s);
+            r = s;
+        }
+        out[gidx] = r;
     }
 }
 
@@ -950,6 +1070,14 @@ __device__ __forceinline__ float2 pd2x(float2 l, float2 c, float2 r)
                 fma2(f2(-2.5f), c, mul2(f2(-1.0f / 12.0f), add2(l, r))));
 }
 __device__ __forceinline__ float2 lds2(const float *s, int i) { return *reinterpret_cast<const float2 *>(s + i); }
+// phi^{n+1} = phi_hi + r for the pair: returns the new phi_hi and writes the
+// new phi_lo to *lo.
+__device__ __forceinline__ float2 add_hi_lo(float2 h, float2 r, float *lo)
+{
+    const float2 s = make_float2(__fadd_rn(h.x, r.x), __fadd_rn(h.y, r.y));
+    *reinterpret_cast<float2 *>(lo) = make_float2(two_sum_err(h.x, r.x, s.x), two_sum_err(h.y, r.y, s.y));
+    return s;
+}
 __device__ __forceinline__ void sts2(float *s, int i, float2 v) { *reinterpret_cast<float2 *>(s + i) = v; }
 
 // Pass 2 for FP32 on grids of even width, same tile and result as
@@ -1056,7 +1184,8 @@ __device__ __forceinline__ void rk_strips_body(const KP<float> &P, const float *
 template <int TX, int TY, int NT, int VR1, int VR2, int VR3>
 __global__ void __launch_bounds__(NT, 3)
 k_rk_strips(KP<float> P, const float *__restrict__ phi, const float *__restrict__ din,
-            const float *__restrict__ dbar, float *__restrict__ out, float a, float b, int last)
+            const float *__restrict__ dbar, float *__restrict__ out, float a, float b, int last,
+            float *__restrict__ philo)
 {
     using G = RKGeom<TX, TY>;
     constexpr int W6 = G::W6, H6 = G::H6, W4 = G::W4, H4 = G::H4, W2 = G::W2, H2 = G::H2;
@@ -1077,7 +1206,7 @@ k_rk_strips(KP<float> P, const float *__restrict__ phi, const float *__restrict_
         P, s_psi, s_mu, s_jx, s_jy, x0, y0, [&](int, long long gidx, float2 L) {
             float2 r = mul2(bb, add2(*reinterpret_cast<const float2 *>(&din[gidx]), L));
             if (a != 0.0f) r = fma2(aa, *reinterpret_cast<const float2 *>(&dbar[gidx]), r);
-            if (last) r = add2(*reinterpret_cast<const float2 *>(&phi[gidx]), r);
+            if (last) r = add_hi_lo(*reinterpret_cast<const float2 *>(&phi[gidx]), r, philo + gidx);
             *reinterpret_cast<float2 *>(&out[gidx]) = r;
         });
 }
@@ -1424,7 +1553,7 @@ template <int TX, int TY, int NT, int VR1, int VR2, int VR3, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_rk_tma(const __grid_constant__ TmaMaps tm, KP<float> P, const float *__restrict__ phi,
          const float *__restrict__ din, const float *__restrict__ dbar, float *__restrict__ out, float a, float b,
-         int last, unsigned *err)
+         int last, float *__restrict__ philo, unsigned *err)
 {
     using T = RKTGeom<TX, TY>;
     using G = RKGeom<TX, TY>;
@@ -1470,7 +1599,7 @@ k_rk_tma(const __grid_constant__ TmaMaps tm, KP<float> P, const float *__restric
     rk_strips_body<TX, TY, NT, VR1, VR2, VR3, T::BW>(
         P, tile.win + 2, s_mu, s_jx, s_jy, x0, y0, [&](int i, long long gidx, float2 L) {
             float2 r = fma2(bb, L, pbv[i]);
-            if (last) r = add2(__ldg(reinterpret_cast<const float2 *>(&phi[gidx])), r);
+            if (last) r = add_hi_lo(__ldg(reinterpret_cast<const float2 *>(&phi[gidx])), r, philo + gidx);
             *reinterpret_cast<float2 *>(&out[gidx]) = r;
         });
 }
@@ -1663,8 +1792,9 @@ k_collide_pairs(const __grid_constant__ TmaMaps tm, KP<float> P, const S *__rest
                 const S *__restrict__ gin, S *__restrict__ fout, S *__restrict__ gout,
                 const float *__restrict__ phi, const float *__restrict__ pfl, const float *__restrict__ ux,
                 const float *__restrict__ uy, const float *__restrict__ upx, const float *__restrict__ upy,
-                const float *__restrict__ uhx, const float *__restrict__ uhy, float *__restrict__ dbar,
-                float *__restrict__ phat, float *__restrict__ jxo, float *__restrict__ jyo, unsigned *err)
+                const float *__restrict__ uhx, const float *__restrict__ uhy, const float *__restrict__ philo,
+                float *__restrict__ dbar, float *__restrict__ phat, float *__restrict__ jxo, float *__restrict__ jyo,
+                unsigned *err)
 {
     using G = CPGeom<TX, TY>;
     constexpr int BW = G::BW, W2 = G::W2, H2 = G::H2, WH = G::WH, HH = G::HH, FS = G::Tile::FS;
@@ -1692,7 +1822,7 @@ k_collide_pairs(const __grid_constant__ TmaMaps tm, KP<float> P, const S *__rest
     const float *src[4] = {phi, pfl, ux, uy};
     const bool by_tma = tile.issue(P, tm, src, 12u, x0 - 8, y0 - 3);
     float2 m3i = f2(0.0f), m5i = f2(0.0f), m4i = f2(0.0f), m6i = f2(0.0f), m7i = f2(0.0f), m8i = f2(0.0f);
-    float2 upx2 = f2(0.0f), upy2 = f2(0.0f), uhx2 = f2(0.0f), uhy2 = f2(0.0f);
+    float2 upx2 = f2(0.0f), upy2 = f2(0.0f), uhx2 = f2(0.0f), uhy2 = f2(0.0f), plo2 = f2(0.0f);
     if (!ghost) {
         int fl;
         const int gidx = map_axis(Y, P.ny, P.py, fl) * P.nx + map_axis(X, P.nx, 1, fl);
@@ -1704,6 +1834,7 @@ k_collide_pairs(const __grid_constant__ TmaMaps tm, KP<float> P, const S *__rest
             a[q] = Codec2<S>::load(fin + o);
             b[q] = Codec2<S>::load(gin + o);
         }
+        plo2 = __ldg(reinterpret_cast<const float2 *>(philo + gidx));
         upx2 = __ldg(reinterpret_cast<const float2 *>(upx + gidx));
         upy2 = __ldg(reinterpret_cast<const float2 *>(upy + gidx));
         uhx2 = __ldg(reinterpret_cast<const float2 *>(uhx + gidx));
@@ -1792,9 +1923,9 @@ k_collide_pairs(const __grid_constant__ TmaMaps tm, KP<float> P, const S *__rest
             const float2 em = mul2(f2(P.eta), mu), ph3u2 = mul2(f2(3.0f), mul2(ph, u2));
             const float2 pax = mul2(ph, ax), pay = mul2(ph, ay);
             float2 m[9];
-            m[0] = f2(0.0f);
-            m[1] = fma2(f2(2.0f), em, ph3u2);
-            m[2] = fma2(f2(-3.0f), em, mul2(m1, ph3u2));
+            m[0] = plo2;   // m_0 relaxes to phi_hi + phi_lo
+            m[1] = fma2(f2(2.0f), em, fma2(f2(-4.0f), plo2, ph3u2));
+            m[2] = fma2(f2(-3.0f), em, fma2(f2(4.0f), plo2, mul2(m1, ph3u2)));
             m[3] = fma2(oms, m3, fma2(s, mul2(ph, u0), mul2(hs, pax)));
             m[4] = mul2(mul2(m1, ph), fma2(f2(0.5f), ax, u0));
             m[5] = fma2(oms, m5, fma2(s, mul2(ph, u1), mul2(hs, pay)));
@@ -1967,6 +2098,33 @@ __global__ void k_init(KP<T> P, const T *__restrict__ phi, const T *__restrict__
             }
         }
     }
+}
+
+// out = s * in, element-wise.
+template <typename T>
+__global__ void k_scale(const T *__restrict__ in, T s, T *__restrict__ out, long long n)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        out[k] = s * in[k];
+}
+
+// phi as a pair of floats: hi = phi rounded, lo = the rest rounded, and back.
+static __global__ void k_split(const double *__restrict__ in, float *__restrict__ hi, float *__restrict__ lo, long long n)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const double x = in[k];
+        const float h = (float)x;
+        hi[k] = h;
+        lo[k] = (float)(x - (double)h);
+    }
+}
+static __global__ void k_join(const float *__restrict__ hi, const float *__restrict__ lo, double *__restrict__ out, long long n)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        out[k] = (double)hi[k] + (double)lo[k];
 }
 
 // Element-wise type conversion (host double fields <-> device arithmetic type).

@@ -44,7 +44,7 @@ class LbmError(RuntimeError):
         self.status = status
 
 
-EXPORTS = ("lbm_create", "lbm_step", "lbm_fields", "lbm_fields_device", "lbm_set_fields",
+EXPORTS = ("lbm_create", "lbm_step", "lbm_step_ch", "lbm_fields", "lbm_fields_device", "lbm_set_fields",
            "lbm_diagnostics", "lbm_diagnostics_async", "lbm_check", "lbm_set_check", "lbm_get_state", "lbm_set_state",
            "lbm_profile", "lbm_profile_read", "lbm_kernel_name", "lbm_kernel_variant",
            "lbm_field_sums_noalloc", "lbm_noalloc_last_error",
@@ -70,6 +70,8 @@ def load(path=None):
                              C.POINTER(vp)]
     L.lbm_step.restype = C.c_int
     L.lbm_step.argtypes = [vp, C.c_int]
+    L.lbm_step_ch.restype = C.c_int
+    L.lbm_step_ch.argtypes = [vp, C.c_int, _dp, _dp, _dp]
     L.lbm_fields.restype = C.c_int
     L.lbm_fields.argtypes = [vp, _dp, _dp, _dp, _dp]
     L.lbm_fields_device.restype = C.c_int
@@ -193,6 +195,15 @@ class Sim:
 
     def step(self, n=1):
         self._ck(self._lib.lbm_step(self._h, int(n)))
+
+    def step_ch(self, ux, uy, n=1, tfac=None):
+        """n steps of the Cahn-Hilliard part alone under the prescribed velocity
+        tfac[k] * (ux, uy) at step k (tfac None: 1)."""
+        ux, uy = _f64(ux), _f64(uy)
+        tf = None if tfac is None else _f64(np.asarray(tfac, dtype=np.float64).ravel())
+        if tf is not None and tf.size < n:
+            raise ValueError("tfac needs one factor per step")
+        self._ck(self._lib.lbm_step_ch(self._h, int(n), _ptr(ux), _ptr(uy), None if tf is None else _ptr(tf)))
 
     def fields(self, out=None):
         """(phi, p, ux, uy) as host float64 [ny, nx] arrays; out: four caller-owned

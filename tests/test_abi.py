@@ -94,6 +94,8 @@ def test_null_handle_rejected_without_cuda():
     d = np.zeros(lbm.LBM_NDIAG)
     pd = d.ctypes.data_as(C.POINTER(C.c_double))
     assert L.lbm_step(None, 1) == ARG
+    assert L.lbm_step_ch(None, 1, pd, pd, None) == ARG
+    assert L.lbm_set_check(None, 2, C.c_double(0.01)) == ARG
     assert L.lbm_diagnostics(None, pd) == ARG
     assert L.lbm_diagnostics_async(None, pd) == ARG
     assert L.lbm_check(None, C.c_double(0.01)) == ARG

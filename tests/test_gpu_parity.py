@@ -2,19 +2,19 @@
 
 Error measure: max |gpu - oracle| / max |oracle| per field.
 FP64: at most 1e-12 for every field after the stated number of steps.
-FP32: the order parameter phi at most 1e-5 for density ratios <= 100 and
-5e-5 at ratio 1000; the pressure p and velocity u at most 5e-4 (2e-3 at
-ratio 1000 over many steps).  phi gains
-about one unit roundoff (2^-24) per step, so 200 steps stay below 1e-5; at
-ratio 1000 the factor (1 + phi) in rho(phi) cancels near phi = -1 and carries
-(rho_H/rho_L) 2^-25 ~ 3e-5 relative error into rho.  p and u are small
-residuals of O(kappa |grad phi|^2) forces and derivatives of phi: their FP32
-error relative to their own maximum measures 1e-5 .. 4e-4 and is a property of
-FP32 arithmetic on this problem, since the FP64 build of the same kernels
-matches the oracle to 1e-12.  At density ratio 1000 p is a residual of the
-large density contrast (rho(phi) of Sec. II.B spans three decades) and its
-FP32 error measures 5e-4 .. 9e-4 of max|p| (256x512 bubble, 64^2 and 66^2
-capillary waves, either kernel family): bound 2e-3 there.
+FP32: every field at most 1e-5 at density ratios up to 100 (phi, p, u after
+200 steps measure <= 8e-9, 4e-6, 8e-6 on the 64^2 static drop).  The FP32
+path carries phi as a pair of floats (phi_hi + phi_lo) and the step's change
+of phi as increments (the post-stream sum and the RK3 stages, Sec. III.A
+Eq. TVD-3order), so phi is not rounded to 24 bits near +-1, where rho(phi)
+of Sec. II.B Eq. (rho) would multiply the rounding by rho_H/rho_L.
+At density ratio 1000, p and u stay at most 1e-4 (phi at 1e-5): the kinematic
+pressure p = p'/rho (Sec. II.B, below Eq. reformNS) jumps by the density
+ratio across the interface, where F_p = -p grad rho and grad p nearly cancel
+in the NS source (Eq. Gi), and the FP32 rounding of grad phi and of the
+surface-tension tensor kappa(|grad phi|^2 I - grad phi grad phi) enters that
+residual amplified by the jump: p measures 2.4e-5 .. 2.7e-5 (64^2, 66^2
+capillary waves, 200 steps) and 1.4e-5 (256x512 bubble), u <= 5.2e-5.
 """
 import math
 
@@ -27,9 +27,7 @@ from paper_1812_02459_gb300 import inputs, lbm
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
-TOL_FP32_PU = 5e-4          # p, u in FP32 (see the module docstring)
-TOL_FP32_PHI_R1000 = 5e-5   # phi in FP32 at density ratio 1000
-TOL_FP32_PU_R1000 = 2e-3    # p, u in FP32 at density ratio 1000 (see the module docstring)
+TOL_FP32_PU_R1000 = 1e-4    # p, u in FP32 at density ratio 1000 (see the module docstring)
 
 
 def rel_err(a, b):
@@ -49,6 +47,7 @@ def assert_parity(o, g, tol, names=("phi", "p", "ux", "uy"), tol_pu=None):
     """tol applies to phi (and to every field unless tol_pu is given for p, u)."""
     of, gf = o.fields(), g.fields()
     errs = {n: rel_err(b, a) for n, a, b in zip(names, of, gf)}
+    print("parity", g.precision, " ".join(f"{n}={e:.2e}" for n, e in errs.items()))
     for n, e in errs.items():
         t = tol if (n == "phi" or tol_pu is None) else tol_pu
         assert e <= t, f"{n}: {e:.3e} > {t:.0e} ({errs})"
@@ -56,7 +55,7 @@ def assert_parity(o, g, tol, names=("phi", "p", "ux", "uy"), tol_pu=None):
 
 
 def pu_tol(precision):
-    return TOL_FP32_PU if precision == "fp32" else None
+    return None
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -83,8 +82,8 @@ def test_ragged_walls_gravity_fp32():
     prm = inputs.base_params(rho_H=20.0, sigma=5e-3, gy=-2e-6, periodic_y=0)
     phi = inputs.drop(nx, ny, 9.0, 20.0, 19.0, prm["W"])
     z = np.zeros_like(phi)
-    o, g = run_both(prm, (phi, z, z, z), 60, "fp32")
-    assert_parity(o, g, TOL["fp32"], tol_pu=TOL_FP32_PU)
+    o, g = run_both(prm, (phi, z, z, z), 200, "fp32")
+    assert_parity(o, g, TOL["fp32"])
 
 
 @pytest.mark.parametrize("nx,ny,px,py", [(46, 37, 1, 0), (46, 38, 0, 0), (12, 12, 1, 1), (130, 18, 0, 1),
@@ -101,7 +100,7 @@ def test_even_width_fp32(nx, ny, px, py):
     phi = inputs.drop(nx, ny, R, nx / 2 + 0.3, ny / 2 - 0.2, prm["W"])
     z = np.zeros_like(phi)
     o, g = run_both(prm, (phi, z, z, z), 60, "fp32")
-    assert_parity(o, g, TOL["fp32"], tol_pu=TOL_FP32_PU)
+    assert_parity(o, g, TOL["fp32"])
 
 
 @pytest.mark.parametrize("order,picard,flux", [(0, 2, 1), (5, 1, 1), (7, 3, 1), (9, 2, 1), (11, 2, 0)])
@@ -114,8 +113,8 @@ def test_even_width_filter_orders_sweeps_fp32(order, picard, flux):
                              filter_a=0.3, flux_correction=flux, periodic_x=0, periodic_y=0)
     phi = inputs.drop(nx, ny, 9.0, 22.0, 19.0, prm["W"])
     z = np.zeros_like(phi)
-    o, g = run_both(prm, (phi, z, z, z), 60, "fp32")
-    assert_parity(o, g, TOL["fp32"], tol_pu=TOL_FP32_PU)
+    o, g = run_both(prm, (phi, z, z, z), 200, "fp32")
+    assert_parity(o, g, TOL["fp32"])
 
 
 @pytest.mark.parametrize("n", [48, 49])
@@ -247,7 +246,7 @@ def test_rising_bubble_256x512_fp32():
     """The rising-bubble workload (rho ratio 1000, walls) at its full size."""
     prm, fields = inputs.rising_bubble()
     o, g = run_both(prm, fields, 40, "fp32")
-    assert_parity(o, g, TOL_FP32_PHI_R1000, tol_pu=TOL_FP32_PU_R1000)
+    assert_parity(o, g, TOL["fp32"], tol_pu=TOL_FP32_PU_R1000)
 
 
 def test_full_size_capillary_wave_sampled_fp32():
@@ -276,7 +275,7 @@ def test_full_size_capillary_wave_sampled_fp32():
             ga = a[y0:y0 + P, x0:x0 + P][ys, m:P - m]
             ob = b[ys, m:P - m]
             scale = max(np.abs(b).max(), 1e-30)
-            tol = TOL["fp32"] if name == "phi" else TOL_FP32_PU
+            tol = TOL["fp32"]
             assert np.abs(ga - ob).max() / scale <= tol, name
 
 
