@@ -88,8 +88,19 @@ typedef struct {
     int picard_iters;       /* sweeps of u = j + F(u)/(2 rho) per step (Eq. u), >= 1 */
     double picard_zeta;     /* must be 0: fixed sweep count (residual stop is not offered) */
     double grad_eps;        /* eps in n = grad phi / sqrt(|grad phi|^2 + eps^2), > 0 */
-    unsigned flags;         /* reserved, must be 0 */
+    unsigned flags;         /* 0, or LBM_FLAG_STRAIN_MOMENTS */
 } lbm_params;
+
+/* flags: the Picard sweeps take the strain rate grad u + grad u^T of F_nu
+ * from the non-equilibrium part of the step's post-stream NS populations
+ * (Sec. III.B Eq. Fmu, whose sum over f is read as one over g) instead of
+ * the isotropic stencils:
+ *   S = [(s_7 - s_1)(F0.u) I - s_7 (F0 u + u F0)] / (2 rho cs^2)
+ *       - sum_i c_i c_i [M^-1 S^g M (g - g_eq(p_hat, u^k))]_i / cs^2,
+ * with F0 the sweep's force without F_nu.  F_m still uses the stencils, as
+ * does the collision.  FP64 and FP32 populations only; the sweeps then run
+ * the one-node-per-thread kernel. */
+#define LBM_FLAG_STRAIN_MOMENTS 1u
 
 typedef struct lbm_handle lbm_handle;
 
@@ -102,7 +113,8 @@ typedef struct lbm_handle lbm_handle;
  * handle.  Errors: LBM_ERR_ARG for invalid sizes or parameters (tau_f or
  * tau_g <= 1/2, a rate outside [0,2], rho <= 0, W <= 0, a outside (0,1], a
  * filter order other than 0/5/7/9/11, picard_iters < 1, picard_zeta != 0,
- * flags != 0), LBM_ERR_OOM, LBM_ERR_CUDA.
+ * undefined flags, LBM_FLAG_STRAIN_MOMENTS with 16-bit populations),
+ * LBM_ERR_OOM, LBM_ERR_CUDA.
  */
 lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params,
                       const double *phi0, const double *p0,

@@ -164,7 +164,10 @@ lbm_status validate(const lbm_grid *gr, const lbm_params *p)
     if (p->picard_iters < 1 || p->picard_iters > 64) return fail(nullptr, LBM_ERR_ARG, "picard_iters must be in [1, 64]");
     if (p->picard_zeta != 0.0) return fail(nullptr, LBM_ERR_ARG, "picard_zeta must be 0 (fixed sweep count)");
     if (!(p->grad_eps > 0)) return fail(nullptr, LBM_ERR_ARG, "grad_eps must be > 0");
-    if (p->flags != 0) return fail(nullptr, LBM_ERR_ARG, "flags must be 0");
+    if (p->flags & ~(unsigned)LBM_FLAG_STRAIN_MOMENTS)
+        return fail(nullptr, LBM_ERR_ARG, "flags: only LBM_FLAG_STRAIN_MOMENTS is defined");
+    if ((p->flags & LBM_FLAG_STRAIN_MOMENTS) && gr->precision != LBM_FP64 && gr->precision != LBM_FP32)
+        return fail(nullptr, LBM_ERR_ARG, "LBM_FLAG_STRAIN_MOMENTS needs FP64 or FP32 populations");
     if (!std::isfinite(p->gx) || !std::isfinite(p->gy)) return fail(nullptr, LBM_ERR_ARG, "gravity must be finite");
     if (!(p->g_rho_ref >= 0) || !std::isfinite(p->g_rho_ref)) return fail(nullptr, LBM_ERR_ARG, "g_rho_ref must be >= 0");
     return LBM_OK;
@@ -464,6 +467,8 @@ lbm_status step_impl(lbm_handle *h)
     {   // implicit velocity by Picard sweeps; the last sweep lands in u_hat
         dim3 grid((P.nx + PC_TX - 1) / PC_TX, (P.ny + PC_TY - 1) / PC_TY);
         const int K = h->prm.picard_iters;
+        // F_nu's strain rate from the step's post-stream NS populations (flags bit 0)
+        const T *gpop = (h->prm.flags & LBM_FLAG_STRAIN_MOMENTS) ? (const T *)h->g[1 - c] : nullptr;
         for (int k = 0; k < K; ++k) {
             const T *ix = k == 0 ? uxc : (const T *)h->tk[(k - 1) & 1][0];
             const T *iy = k == 0 ? uyc : (const T *)h->tk[(k - 1) & 1][1];
@@ -471,7 +476,7 @@ lbm_status step_impl(lbm_handle *h)
             T *oy = k == K - 1 ? uhy : (T *)h->tk[k & 1][1];
             Timed tm(h, 2);
             if constexpr (std::is_same<T, float>::value) {
-                if (h->tma) {   // TMA-staged windows, one CTA per tile
+                if (h->tma && !gpop) {   // TMA-staged windows, one CTA per tile
                     using GT = PCTGeom<PT_TX, PT_TY>;
                     TmaMaps maps{};
                     const void *planes[4] = {phin, phat, ix, iy};
@@ -485,7 +490,7 @@ lbm_status step_impl(lbm_handle *h)
                                                                  h->dev_err);
                     continue;
                 }
-                if (P.nx % 2 == 0) {   // column-pair strips, paired FP32 arithmetic
+                if (P.nx % 2 == 0 && !gpop) {   // column-pair strips, paired FP32 arithmetic
                     dim3 gs((P.nx + PS_TX - 1) / PS_TX, (P.ny + PS_TY - 1) / PS_TY);
                     k_picard_strips<PS_TX, PS_TY, PS_NT, PS_VR1, PS_VR2>
                         <<<gs, PS_NT, sizeof(float) * PSGeom<PS_TX, PS_TY>::NSCALAR, st>>>(P, phin, phat, jx, jy, ix, iy,
@@ -493,7 +498,8 @@ lbm_status step_impl(lbm_handle *h)
                     continue;
                 }
             }
-            k_picard<T, PC_TX, PC_TY, PC_NT><<<grid, PC_NT, smem_pc<T>(), st>>>(P, phin, phat, jx, jy, ix, iy, ox, oy);
+            k_picard<T, PC_TX, PC_TY, PC_NT><<<grid, PC_NT, smem_pc<T>(), st>>>(P, phin, phat, jx, jy, ix, iy, ox, oy,
+                                                                              gpop);
         }
     }
     // selective filter of (p_hat, u_hat) -> (p_f, u_f^{n+1}); u^{n-1} slot is reused
@@ -1165,7 +1171,9 @@ const char *lbm_kernel_variant(const lbm_handle *h, int kind)
     case 0:
         return (f32 && h->tma && h->grid.periodic_x && default_rates(h->prm)) ? "k_collide_pairs" : "k_collide_stream";
     case 1: return f32 && h->tma ? "k_rk_tma" : (f32 && even ? "k_rk_strips" : "k_rk_stage");
-    case 2: return f32 && h->tma ? "k_picard_tma" : (f32 && even ? "k_picard_strips" : "k_picard");
+    case 2:
+        if (h->prm.flags & LBM_FLAG_STRAIN_MOMENTS) return "k_picard";
+        return f32 && h->tma ? "k_picard_tma" : (f32 && even ? "k_picard_strips" : "k_picard");
     default:
         if (h->prm.filter_order == 0) return "none";
         return f32 && h->tma ? "k_filter_tma" : (f32 && even ? "k_filter_strips" : "k_filter");

@@ -217,6 +217,10 @@ __device__ __forceinline__ void rho_nu(const KP<T> &P, T phi, T &rho, T &irho, T
 
 // Lattice weights (Sec. III.A, below Eq. D2Q9).
 __device__ __forceinline__ float lattice_w(int q) { return q == 0 ? 4.0f / 9.0f : (q < 5 ? 1.0f / 9.0f : 1.0f / 36.0f); }
+template <typename T> __device__ __forceinline__ T lattice_w_t(int q)
+{
+    return q == 0 ? T(4) / T(9) : (q < 5 ? T(1) / T(9) : T(1) / T(36));
+}
 
 // Reduced-precision population storage (S narrower than T).  Only the
 // deviations from the rest equilibria are stored in S: the CH rest
@@ -822,12 +826,18 @@ template <int TX, int TY> struct PCGeom {
     static constexpr int NSCALAR = W2 * H2 + 6 * W1 * H1;
 };
 
+// With gpop (the step's post-stream NS populations, [9][N]) the strain rate
+// grad u + grad u^T of F_nu comes from their non-equilibrium part instead of
+// the isotropic stencils (Sec. III.B Eq. Fmu, read for g):
+//   S = [(s_7 - s_1)(F0.u) I - s_7 (F0 u + u F0)] / (2 rho cs^2)
+//       - sum_i c_i c_i [M^-1 S^g M (g - g_eq(p_hat, u^k))]_i / cs^2,
+// F0 being this sweep's force without F_nu.
 template <typename T, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT)
 k_picard(KP<T> P, const T *__restrict__ phi, const T *__restrict__ phat,
          const T *__restrict__ jx, const T *__restrict__ jy,
          const T *__restrict__ ukx, const T *__restrict__ uky,
-         T *__restrict__ uox, T *__restrict__ uoy)
+         T *__restrict__ uox, T *__restrict__ uoy, const T *__restrict__ gpop)
 {
     using G = PCGeom<TX, TY>;
     constexpr int W2 = G::W2, H2 = G::H2, W1 = G::W1, H1 = G::H1, A1 = W1 * H1;
@@ -894,9 +904,40 @@ k_picard(KP<T> P, const T *__restrict__ phi, const T *__restrict__ phat,
         T dxux, dyux, dxuy, dyuy;
         iso_grad<T, W1>(s_ux, i1, dxux, dyux);
         iso_grad<T, W1>(s_uy, i1, dxuy, dyuy);
-        const T Sxx = T(2) * dxux, Sxy = dyux + dxuy, Syy = T(2) * dyuy;
-        const T Fx = -pc * grx + Fsx + nu * (Sxx * grx + Sxy * gry) + (Jx * dxux + Jy * dyux) + (rho - P.g_rho_ref) * P.gx;
-        const T Fy = -pc * gry + Fsy + nu * (Sxy * grx + Syy * gry) + (Jx * dxuy + Jy * dyuy) + (rho - P.g_rho_ref) * P.gy;
+        T Sxx = T(2) * dxux, Sxy = dyux + dxuy, Syy = T(2) * dyuy;
+        const T F0x = -pc * grx + Fsx + (Jx * dxux + Jy * dyux) + (rho - P.g_rho_ref) * P.gx;
+        const T F0y = -pc * gry + Fsy + (Jx * dxuy + Jy * dyuy) + (rho - P.g_rho_ref) * P.gy;
+        if (gpop) {   // strain rate from the non-equilibrium moments
+            const T u0 = s_ux[i1], u1 = s_uy[i1];
+            constexpr int cxv[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+            constexpr int cyv[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+            const T u2 = u0 * u0 + u1 * u1;
+            T d[9], m[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const T cu = T(cxv[q]) * u0 + T(cyv[q]) * u1;
+                const T geq = lattice_w_t<T>(q) * (T(3) * pc + T(3) * cu + T(4.5) * cu * cu - T(1.5) * u2);
+                d[q] = gpop[(size_t)gidx + (size_t)q * P.N] - geq;
+            }
+            to_moments(d, m);
+            const T s78 = rcp(nu * T(3) + T(0.5));
+#pragma unroll
+            for (int k = 0; k < 9; ++k) m[k] *= k < 7 ? P.sg[k] : s78;
+            from_moments(m, d);
+            T pxx = T(0), pxy = T(0), pyy = T(0);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                pxx += T(cxv[q] * cxv[q]) * d[q];
+                pxy += T(cxv[q] * cyv[q]) * d[q];
+                pyy += T(cyv[q] * cyv[q]) * d[q];
+            }
+            const T Fu = F0x * u0 + F0y * u1, a = T(1.5) * ir;   // 1 / (2 rho cs^2)
+            Sxx = ((s78 - P.sg[1]) * Fu - s78 * T(2) * F0x * u0) * a - T(3) * pxx;
+            Sxy = -s78 * (F0x * u1 + u0 * F0y) * a - T(3) * pxy;
+            Syy = ((s78 - P.sg[1]) * Fu - s78 * T(2) * F0y * u1) * a - T(3) * pyy;
+        }
+        const T Fx = F0x + nu * (Sxx * grx + Sxy * gry);
+        const T Fy = F0y + nu * (Sxy * grx + Syy * gry);
         const T h = T(0.5) * ir;
         uox[gidx] = jx[gidx] + Fx * h;
         uoy[gidx] = jy[gidx] + Fy * h;

@@ -59,7 +59,7 @@ def test_struct_layout_matches_header(tmp_path):
     (dict(picard_iters=0), "picard_iters"),
     (dict(picard_zeta=1e-3), "picard_zeta"),
     (dict(grad_eps=0.0), "grad_eps"),
-    (dict(flags=1), "flags"),
+    (dict(flags=2), "flags"),
 ])
 def test_invalid_parameters_rejected(change, msg):
     prm, fields = inputs.static_drop(n=16, R=4.0)
@@ -67,6 +67,15 @@ def test_invalid_parameters_rejected(change, msg):
     with pytest.raises(lbm.LbmError) as e:
         lbm.Sim(prm, *fields)
     assert e.value.status == 1 and msg in str(e.value)
+
+
+@pytest.mark.parametrize("precision", ["mix_bf16", "mix_fp16"])
+def test_strain_moments_flag_needs_full_precision(precision):
+    prm, fields = inputs.static_drop(n=16, R=4.0)
+    prm["flags"] = 1
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Sim(prm, *fields, precision=precision)
+    assert e.value.status == 1 and "STRAIN_MOMENTS" in str(e.value)
 
 
 def test_invalid_rates_and_sizes_rejected():

@@ -311,3 +311,24 @@ def test_srt_equal_rates(precision):
     o, g = run_both(prm, (phi, z, z, z), 60, precision)
     assert g.kernel_variants()["k_collide_stream"] == "k_collide_stream"
     assert_parity(o, g, TOL[precision], tol_pu=pu_tol(precision))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("nx", [45, 46])
+def test_strain_rate_from_moments(precision, nx):
+    """LBM_FLAG_STRAIN_MOMENTS: the Picard sweeps take F_nu's strain rate
+    from the non-equilibrium moments of the post-stream g (Sec. III.B
+    Eq. Fmu) against the oracle doing the same; the stencil form differs
+    from it by far more than the tolerance."""
+    ny = 37
+    phi, p, ux, uy = inputs.random_fields(nx, ny, seed=3, u_amp=5e-3)
+    prm = inputs.base_params(rho_H=20.0, nu_H=0.05, nu_L=0.01, sigma=5e-3, gy=-2e-6, periodic_y=0, flags=1)
+    o, g = run_both(prm, (phi, p, ux, uy), 60, precision)
+    assert g.kernel_variants()["k_picard"] == "k_picard"
+    assert_parity(o, g, TOL[precision], tol_pu=pu_tol(precision))
+    prm0 = dict(prm, flags=0)
+    o0 = oracle.Sim(prm0, phi, p, ux, uy)
+    o0.step(60)
+    d = max(rel_err(a, b) for a, b in zip(o.fields()[1:], o0.fields()[1:]))
+    print("moments vs stencils", d)
+    assert d > 100 * TOL[precision]
