@@ -1,8 +1,12 @@
 """FP64 PyTorch-CPU restatement of one lattice step, for the adjoint -- TEST INFRASTRUCTURE.
 
-A second plain implementation of the step of lbm_oracle.c (periodic domains
-only), written with whole-array torch operations so that torch.autograd can
-differentiate it.  Its reverse-mode gradients are the oracle adjoint against
+A second plain implementation of the step of lbm_oracle.c, written with
+whole-array torch operations so that torch.autograd can differentiate it.
+Walls (an axis that is not periodic) follow lbm_oracle.c: halfway bounce-back
+for the populations, and for the stencils a ghost across a wall is the mirror
+image about the halfway wall times the field's parity along that axis --
++1 for phi, p and the quantities even in the wall-normal coordinate, -1 for
+u (no slip) and for the odd ones (the normal component of a gradient).  Its reverse-mode gradients are the oracle adjoint against
 which the GPU adjoint is checked.  It is pinned to the C oracle (forward
 fields equal to round-off) and to central finite differences of the C oracle
 (gradients), both in tests/test_adjoint_oracle.py.  It follows the same
@@ -38,43 +42,72 @@ MMAT = torch.tensor(MROWS, dtype=DT)
 MINV = torch.linalg.inv(MMAT)
 
 
-def at(a, dx, dy):
-    """a(x + dx, y + dy) on a periodic grid."""
-    return torch.roll(a, shifts=(-dy, -dx), dims=(-2, -1))
+# Which axes are periodic, set from the parameters by init_state() and step().
+AXES = {"px": True, "py": True}
+EVEN, ODD = (1.0, 1.0), (-1.0, -1.0)
+OPP = tuple(next(r for r in range(9) if CX[r] == -CX[q] and CY[r] == -CY[q]) for q in range(9))
 
 
-def grad_iso(a):
+def set_axes(prm):
+    AXES["px"] = bool(prm.get("periodic_x", 1))
+    AXES["py"] = bool(prm.get("periodic_y", 1))
+
+
+def _axis(n, d, periodic):
+    """Source index of x + d along an axis of n nodes, and whether it crossed a wall."""
+    i = torch.arange(n) + d
+    if periodic:
+        return i % n, torch.zeros(n, dtype=torch.bool)
+    crossed = (i < 0) | (i >= n)
+    return torch.where(i < 0, -1 - i, torch.where(i >= n, 2 * n - 1 - i, i)), crossed
+
+
+def at(a, dx, dy, par=EVEN):
+    """a(x + dx, y + dy): periodic axes wrap; across a wall the ghost is the
+    mirror image about the halfway wall times par = (parity along x, along y)
+    (a parity 0 makes the ghost zero)."""
+    if AXES["px"] and AXES["py"]:
+        return torch.roll(a, shifts=(-dy, -dx), dims=(-2, -1))
+    ny, nx = a.shape[-2:]
+    ix, cx = _axis(nx, dx, AXES["px"])
+    iy, cy = _axis(ny, dy, AXES["py"])
+    sx = torch.where(cx, torch.tensor(float(par[0]), dtype=DT), torch.tensor(1.0, dtype=DT))
+    sy = torch.where(cy, torch.tensor(float(par[1]), dtype=DT), torch.tensor(1.0, dtype=DT))
+    return a[..., iy, :][..., ix] * (sy[:, None] * sx[None, :])
+
+
+def grad_iso(a, par=EVEN):
     """Isotropic gradient, Sec. III.B Eq. (dicretized)."""
-    gx = sum(WQ[q] * CX[q] * at(a, CX[q], CY[q]) for q in range(1, 9)) / CS2
-    gy = sum(WQ[q] * CY[q] * at(a, CX[q], CY[q]) for q in range(1, 9)) / CS2
+    gx = sum(WQ[q] * CX[q] * at(a, CX[q], CY[q], par) for q in range(1, 9)) / CS2
+    gy = sum(WQ[q] * CY[q] * at(a, CX[q], CY[q], par) for q in range(1, 9)) / CS2
     return gx, gy
 
 
-def lap_iso(a):
+def lap_iso(a, par=EVEN):
     """Isotropic Laplacian, Sec. III.B Eq. (dicretized)."""
-    return sum(2.0 * WQ[q] * (at(a, CX[q], CY[q]) - a) for q in range(1, 9)) / CS2
+    return sum(2.0 * WQ[q] * (at(a, CX[q], CY[q], par) - a) for q in range(1, 9)) / CS2
 
 
-def d1(a, axis):
+def d1(a, axis, par=EVEN):
     """Fourth-order central first derivative, Sec. III.A Eq. (fourOrder_FDM)."""
-    s = (lambda k: at(a, k, 0)) if axis == 0 else (lambda k: at(a, 0, k))
+    s = (lambda k: at(a, k, 0, par)) if axis == 0 else (lambda k: at(a, 0, k, par))
     return (s(-2) - 8.0 * s(-1) + 8.0 * s(1) - s(2)) / 12.0
 
 
-def d2(a, axis):
+def d2(a, axis, par=EVEN):
     """Five-point fourth-order second derivative."""
-    s = (lambda k: at(a, k, 0)) if axis == 0 else (lambda k: at(a, 0, k))
+    s = (lambda k: at(a, k, 0, par)) if axis == 0 else (lambda k: at(a, 0, k, par))
     return (-s(-2) + 16.0 * s(-1) - 30.0 * a + 16.0 * s(1) - s(2)) / 12.0
 
 
-def selective_filter(a, order, alpha):
+def selective_filter(a, order, alpha, par=EVEN):
     """Explicit selective filter, Sec. III.B Eq. (filter), App. B."""
     if not order:
         return a
     d = FILTERS[order]
     acc = 2.0 * d[0] * a
     for m in range(1, len(d)):
-        acc = acc + d[m] * (at(a, m, 0) + at(a, -m, 0) + at(a, 0, m) + at(a, 0, -m))
+        acc = acc + d[m] * (at(a, m, 0, par) + at(a, -m, 0, par) + at(a, 0, m, par) + at(a, 0, -m, par))
     return a - alpha * acc
 
 
@@ -107,7 +140,7 @@ def u_independent_forces(prm, phi, p, kappa, beta, M):
     gx, gy = grad_iso(phi)
     txx, txy, tyy = gx * gx + gy * gy - gx * gx, -gx * gy, gx * gx + gy * gy - gy * gy
     dtxx, _ = grad_iso(txx)
-    dtxy_x, dtxy_y = grad_iso(txy)
+    dtxy_x, dtxy_y = grad_iso(txy, ODD)   # -gx gy: odd along both axes
     _, dtyy = grad_iso(tyy)
     fsx, fsy = kappa * (dtxx + dtxy_y), kappa * (dtxy_x + dtyy)
     mx, my = grad_iso(mu)
@@ -118,8 +151,8 @@ def u_independent_forces(prm, phi, p, kappa, beta, M):
 
 def total_force(prm, F, p, ux, uy):
     """F = F_p + F_s + F_nu + F_m + F_g of Sec. II.B Eq. (reformNS), F_g = (rho - rho_ref) g."""
-    dxux, dyux = grad_iso(ux)
-    dxuy, dyuy = grad_iso(uy)
+    dxux, dyux = grad_iso(ux, ODD)
+    dxuy, dyuy = grad_iso(uy, ODD)
     sxx, sxy, syy = 2 * dxux, dyux + dxuy, 2 * dyuy
     g_rel = F["rho"] - prm.get("g_rho_ref", 0.0)
     fx = (-p * F["grx"] + F["Fsx"] + F["nu"] * (sxx * F["grx"] + sxy * F["gry"])
@@ -182,8 +215,18 @@ def unmom(m):
 
 
 def stream(fs):
-    """Pull streaming on a periodic grid: f_i(x) = f*_i(x - c_i)."""
-    return torch.stack([at(fs[q], -CX[q], -CY[q]) for q in range(9)])
+    """Pull streaming f_i(x) = f*_i(x - c_i); a source across a wall returns
+    the node's own opposite population (halfway bounce-back)."""
+    if AXES["px"] and AXES["py"]:
+        return torch.stack([at(fs[q], -CX[q], -CY[q]) for q in range(9)])
+    ny, nx = fs.shape[-2:]
+    out = []
+    for q in range(9):
+        _, cx = _axis(nx, -CX[q], AXES["px"])
+        _, cy = _axis(ny, -CY[q], AXES["py"])
+        crossed = (cy[:, None] | cx[None, :]).to(DT)
+        out.append(at(fs[q], -CX[q], -CY[q], (0.0, 0.0)) + crossed * fs[OPP[q]])
+    return torch.stack(out)
 
 
 def fd_rhs(prm, psi, kappa, beta, M):
@@ -198,11 +241,13 @@ def fd_rhs(prm, psi, kappa, beta, M):
         dmn = d1(mu, 0) * nx + d1(mu, 1) * ny
         jx = jx - M * dmn * nx
         jy = jy - M * dmn * ny
-    return d1(jx, 0) + d1(jy, 1)
+    # J_x is odd along x and even along y, J_y the reverse
+    return d1(jx, 0, (-1.0, 1.0)) + d1(jy, 1, (1.0, -1.0))
 
 
 def init_state(prm, phi0, p0, ux0, uy0, sigma, M):
     """f = f_eq(phi0, mu(phi0), u0), g = g_eq(p0, u0) (initial populations)."""
+    set_axes(prm)
     kappa, beta, _ = coefficients(prm, sigma, M)
     mu = chem(phi0, kappa, beta)
     return dict(f=feq(phi0, mu, ux0, uy0, prm["eta"]), g=geq(p0, ux0, uy0), phi=phi0, p=p0,
@@ -212,6 +257,7 @@ def init_state(prm, phi0, p0, ux0, uy0, sigma, M):
 def step(prm, s, sigma, M):
     """One time step in the order of lbm_oracle.c: fields at t^n, collision,
     streaming, moments, TVD-RK3 correction, Picard sweeps, filter."""
+    set_axes(prm)
     kappa, beta, stau = coefficients(prm, sigma, M)
     F = u_independent_forces(prm, s["phi"], s["p"], kappa, beta, M)
     fx, fy, (dxux, dyux, dxuy, dyuy) = total_force(prm, F, s["p"], s["ux"], s["uy"])
@@ -258,7 +304,7 @@ def step(prm, s, sigma, M):
     # selective filter, Sec. III.B Eq. (filter)
     fo, fa = prm["filter_order"], prm["filter_a"]
     return dict(f=f, g=g, phi=phin, p=selective_filter(phat, fo, fa),
-                ux=selective_filter(ukx, fo, fa), uy=selective_filter(uky, fo, fa),
+                ux=selective_filter(ukx, fo, fa, ODD), uy=selective_filter(uky, fo, fa, ODD),
                 uhx=ukx, uhy=uky, upx=ux, upy=uy)
 
 

@@ -876,41 +876,60 @@ template <typename T> struct Engine {
 
     // Forward level kernel gi: the records of fgroups[gi] in order, a
     // thread per node of a batch of steps; slot q is the variable fq.
+    // Global loads of a generated kernel, each (plane, tap) read once: the
+    // first use declares a variable in the node loop's scope.
+    struct Loads {
+        std::map<std::pair<const void *, int>, std::string> at;
+        std::string decl;   // declarations to emit before the current operation
+        std::string get(ArgPack &A, const void *p, int dx, int dy, bool tap, const char *off)
+        {
+            const int key = tap ? (dx + 64) * 256 + (dy + 64) : -1;
+            auto it = at.find({p, key});
+            if (it != at.end()) return it->second;
+            const std::string v = "g" + S((int)at.size());
+            decl += "        const T " + v + " = __ldg(" + A.p(p) + " + " + off +
+                    (tap ? " + nbi(x, y, " + S(dx) + ", " + S(dy) + ", nx, ny)" : std::string(" + k")) + ");\n";
+            at.emplace(std::make_pair(p, key), v);
+            return v;
+        }
+    };
+
     std::string gen_fwd(int gi, ArgPack &A)
     {
         const Group &G = fgroups[gi];
         std::string b;
+        Loads ld;
         for (int j = 0; j < G.n; ++j) {
             const VOp<T> &d = hfwd[G.off + j];
-            b += "        {\n";
+            std::string o = "        {\n";
             if (d.k == OP_STENCIL) {
                 const Stencil &St = stencils[d.st];
-                const std::string src = A.p(d.in[0]);
-                b += "            T r = T(0);\n";
+                o += "            T r = T(0);\n";
                 for (int i = 0; i < St.n; ++i)
-                    b += "            r += " + A.c(St.w[i]) + " * __ldg(" + src + " + voff + base + nbi(x, y, " + S(St.dx[i]) +
-                         ", " + S(St.dy[i]) + ", nx, ny));\n";
+                    o += "            r += " + A.c(St.w[i]) + " * " + ld.get(A, d.in[0], St.dx[i], St.dy[i], true, "voff + base") +
+                         ";\n";
             } else {
                 for (int i = 0; i < d.nin; ++i)
-                    b += "            const T v" + S(i) + " = " +
-                         (((d.fint >> i) & 1u) ? "f" + S(d.fslot[i]) : "__ldg(" + A.p(d.in[i]) + " + voff + k)") + ";\n";
+                    o += "            const T v" + S(i) + " = " +
+                         (((d.fint >> i) & 1u) ? "f" + S(d.fslot[i]) : ld.get(A, d.in[i], 0, 0, false, "voff")) + ";\n";
                 switch (d.k) {
                 case OP_LIN:
-                    b += "            T r = " + A.c((double)d.c0) + ";\n";
-                    for (int i = 0; i < d.nin; ++i) b += "            r += " + A.c((double)d.c[i]) + " * v" + S(i) + ";\n";
+                    o += "            T r = " + A.c((double)d.c0) + ";\n";
+                    for (int i = 0; i < d.nin; ++i) o += "            r += " + A.c((double)d.c[i]) + " * v" + S(i) + ";\n";
                     break;
-                case OP_SCALEP: b += "            const T r = " + A.c((double)d.c0) + " * v0;\n"; break;
-                case OP_MUL: b += "            const T r = v0 * v1;\n"; break;
-                case OP_DIV: b += "            const T r = v0 / v1;\n"; break;
-                case OP_POW3: b += "            const T r = v0 * v0 * v0;\n"; break;
-                case OP_SQRT: b += "            const T r = sqrt(v0);\n"; break;
-                case OP_CLAMP1: b += "            const T r = v0 < T(-1) ? T(-1) : (v0 > T(1) ? T(1) : v0);\n"; break;
-                default: b += "            const T r = T(1) / v0;\n"; break;   // OP_RECIP
+                case OP_SCALEP: o += "            const T r = " + A.c((double)d.c0) + " * v0;\n"; break;
+                case OP_MUL: o += "            const T r = v0 * v1;\n"; break;
+                case OP_DIV: o += "            const T r = v0 / v1;\n"; break;
+                case OP_POW3: o += "            const T r = v0 * v0 * v0;\n"; break;
+                case OP_SQRT: o += "            const T r = sqrt(v0);\n"; break;
+                case OP_CLAMP1: o += "            const T r = v0 < T(-1) ? T(-1) : (v0 > T(1) ? T(1) : v0);\n"; break;
+                default: o += "            const T r = T(1) / v0;\n"; break;   // OP_RECIP
                 }
             }
-            if (d.fout >= 0) b += "            f" + S(d.fout) + " = r;\n";
-            if (d.out) b += "            " + A.p(d.out) + "[voff + k] = r;\n";
-            b += "        }\n";
+            if (d.fout >= 0) o += "            f" + S(d.fout) + " = r;\n";
+            if (d.out) o += "            " + A.p(d.out) + "[voff + k] = r;\n";
+            b += ld.decl + o + "        }\n";
+            ld.decl.clear();
         }
         std::string f = A.decl("KF" + S(gi));
         f += "extern \"C\" __global__ void " + bounds() + " f" + S(gi) +
@@ -933,24 +952,25 @@ template <typename T> struct Engine {
         const RGroup &G = rgroups[gi];
         std::string b;
         bool pgr = false;
+        Loads ld;   // value planes (voff + k) and output adjoints (k, or taps around it)
         for (int t : ex) {
             const Op &o = tape[t];
             const VOp<T> &d = rec[t];
             const int nc = ncontrib(o);
+            const size_t at = b.size();   // where this operation's new loads are declared
             b += "        {\n";
             if (o.k == OP_STENCIL) {   // transpose: gathered from the output adjoint around the node
                 const Stencil &St = stencils[o.st];
-                const std::string src = A.p(d.aout);
                 b += "            T c0 = T(0);\n";
                 for (int i = 0; i < St.n; ++i)
-                    b += "            c0 += " + A.c(St.w[i]) + " * __ldg(" + src + " + nbi(x, y, " + S(-St.dx[i]) + ", " +
-                         S(-St.dy[i]) + ", nx, ny));\n";
+                    b += "            c0 += " + A.c(St.w[i]) + " * " + ld.get(A, d.aout, -St.dx[i], -St.dy[i], true, "0") +
+                         ";\n";
             } else {
-                b += "            T g = " + (d.aout ? "__ldg(" + A.p(d.aout) + " + k)" : std::string("T(0)")) +
+                b += "            T g = " + (d.aout ? ld.get(A, d.aout, 0, 0, false, "0") : std::string("T(0)")) +
                      (d.rout >= 0 ? " + s" + S(d.rout) : std::string("")) + ";\n";
-                if (o.k != OP_LIN && o.k != OP_SQRT) b += "            const T a = __ldg(" + A.p(d.in[0]) + " + voff + k);\n";
-                if (o.k == OP_MUL || o.k == OP_DIV) b += "            const T bb = __ldg(" + A.p(d.in[1]) + " + voff + k);\n";
-                if (o.k == OP_SQRT) b += "            const T z = __ldg(" + A.p(d.out) + " + voff + k);\n";
+                if (o.k != OP_LIN && o.k != OP_SQRT) b += "            const T a = " + ld.get(A, d.in[0], 0, 0, false, "voff") + ";\n";
+                if (o.k == OP_MUL || o.k == OP_DIV) b += "            const T bb = " + ld.get(A, d.in[1], 0, 0, false, "voff") + ";\n";
+                if (o.k == OP_SQRT) b += "            const T z = " + ld.get(A, d.out, 0, 0, false, "voff") + ";\n";
                 switch (o.k) {
                 case OP_LIN:
                     for (int i = 0; i < nc; ++i) b += "            const T c" + S(i) + " = " + A.c((double)d.c[i]) + " * g;\n";
@@ -973,6 +993,8 @@ template <typename T> struct Engine {
                 b += "            " + q + " = " + (((d.rassign >> i) & 1u) ? "c" + S(i) : q + " + c" + S(i)) + ";\n";
             }
             b += "        }\n";
+            b.insert(at, ld.decl);
+            ld.decl.clear();
         }
         for (int i = 0; i < G.nfl; ++i) {
             const VFlush<T> &F = hfl[G.fl0 + i];

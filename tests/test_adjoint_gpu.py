@@ -203,3 +203,61 @@ def test_adjoint_translating_drop_256():
     assert dm32 == pytest.approx(dm64, rel=1e-2)
     assert abs(ds32 - ds64) <= 1e-2 * (abs(ds64) + abs(dm64))
     assert np.abs(g32 - g64).max() <= 1e-2 * np.abs(g64).max()
+
+
+def test_adjoint_fp32_against_finite_differences_256():
+    """FP32 adjoint on the 256^2 translating drop (rho ratio 100, 500 steps,
+    checkpoint every 22) against central differences of the FP64 forward
+    (h = 1e-4 relative; the FP64 adjoint meets them to 1e-6).  The FP32
+    reverse sweep is seeded with the FP64 residual phi_T - target: it then
+    differentiates the FP64 loss, linearised about the FP32 trajectory.
+    Measured: dL/dM and dL/dphi0 . v within 2e-5 of the differences, dL/dsigma
+    within 1e-4 of |dL/dsigma| + |dL/dM| (dL/dsigma is a small difference of
+    large surface-tension terms, each rounded in FP32).  Seeded with its own
+    residual instead, the FP32 gradient differs by the FP32 trajectory's
+    departure from the FP64 one relative to the residual (here 1.8e-5 against
+    2.8e-4 after 500 steps: a few per cent), a floor of the FP32 forward, not
+    of the reverse sweep."""
+    n, steps = 256, 500
+    prm, fields = inputs.translating_drop(n=n, R=n / 8.0, U0=0.01)
+    rng = np.random.default_rng(0)
+    xi = rng.standard_normal(2)
+    tp = dict(prm, sigma=prm["sigma"] * (1 + 0.05 * xi[0]), M=prm["M"] * (1 + 0.05 * xi[1]))
+    s = lbm.Sim(tp, *fields, precision="fp64")
+    s.step(steps)
+    target = s.fields()[0]
+    s.close()
+    hs, hm, he = 1e-4 * prm["sigma"], 1e-4 * prm["M"], 1e-5
+    fd_s = (gpu_loss(dict(prm, sigma=prm["sigma"] + hs), fields, target, steps)
+            - gpu_loss(dict(prm, sigma=prm["sigma"] - hs), fields, target, steps)) / (2 * hs)
+    fd_m = (gpu_loss(dict(prm, M=prm["M"] + hm), fields, target, steps)
+            - gpu_loss(dict(prm, M=prm["M"] - hm), fields, target, steps)) / (2 * hm)
+    v = rng.standard_normal(fields[0].shape) * (np.abs(fields[0]) < 0.95)
+    fp = list(fields); fm = list(fields)
+    fp[0] = fields[0] + he * v
+    fm[0] = fields[0] - he * v
+    fd_v = (gpu_loss(prm, fp, target, steps) - gpu_loss(prm, fm, target, steps)) / (2 * he)
+    seed = None
+    res = {}
+    for precision in ("fp64", "fp32"):
+        s = lbm.Sim(prm, *fields, precision=precision)
+        s.adjoint_begin(steps, 22)
+        phiT = s.fields()[0]
+        if seed is None:
+            seed, phi64 = phiT - target, phiT
+        res[precision] = s.adjoint_end(seed)
+        if precision == "fp32":
+            drift = float(np.abs(phiT - phi64).max())
+        s.close()
+    g, ds, dm = res["fp32"]
+    gv = float((g * v).sum())
+    scale = abs(fd_s) + abs(fd_m)
+    print("fp32 adjoint vs fd: dsigma", abs(ds - fd_s) / abs(fd_s), "of scale", abs(ds - fd_s) / scale,
+          "dM", abs(dm - fd_m) / abs(fd_m), "dphi0.v", abs(gv - fd_v) / abs(fd_v),
+          "trajectory drift", drift, "residual", float(np.abs(seed).max()))
+    g64, ds64, dm64 = res["fp64"]
+    assert ds64 == pytest.approx(fd_s, rel=1e-5)
+    assert dm64 == pytest.approx(fd_m, rel=1e-5)
+    assert abs(ds - fd_s) <= 1e-4 * scale
+    assert dm == pytest.approx(fd_m, rel=1e-4)
+    assert gv == pytest.approx(fd_v, rel=1e-4)

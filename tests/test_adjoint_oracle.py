@@ -100,3 +100,37 @@ def test_torch_adjoint_every_component_on_a_small_grid():
                         - c_loss(prm, fields, steps, target, phi0=phi - e)) / (2 * he)
     assert np.abs(fd - g).max() <= 1e-6 * np.abs(g).max()
     assert np.abs(g).max() > 0
+
+
+@pytest.mark.parametrize("px,py", [(1, 0), (0, 0)])
+def test_torch_walls_forward_and_adjoint_match_c_oracle(px, py):
+    """Walls on one or both axes (halfway bounce-back, mirrored ghosts with
+    each field's parity): the torch restatement's forward equals the C oracle
+    to round-off, and its gradients equal central differences of the C oracle."""
+    prm, fields, steps, target, rng = drop_case(n=20, steps=5)
+    prm = dict(prm, periodic_x=px, periodic_y=py, gy=-1e-5)
+    # the drop straddles the wall y = -1/2 (and x = -1/2): every stencil
+    # reads interface values through the mirrored ghosts
+    fields = (inputs.drop(20, 20, 6.0, 5.0, 3.0, prm["W"]),) + tuple(fields[1:])
+    s = oracle.Sim(prm, *fields)
+    s.step(steps)
+    r = tr.run(prm, *(T(a) for a in fields), T(prm["sigma"]), T(prm["M"]), steps)
+    for a, b in zip(s.fields(), (r["phi"], r["p"], r["ux"], r["uy"])):
+        assert np.abs(a - b.numpy()).max() <= 1e-12 * max(np.abs(a).max(), 1e-30)
+    phi0 = T(fields[0]).requires_grad_(True)
+    sig = T(prm["sigma"]).requires_grad_(True)
+    M = T(prm["M"]).requires_grad_(True)
+    r = tr.run(prm, phi0, T(fields[1]), T(fields[2]), T(fields[3]), sig, M, steps)
+    loss = 0.5 * ((r["phi"] - T(target)) ** 2).sum()
+    gphi, gs, gm = torch.autograd.grad(loss, [phi0, sig, M])
+    hs, hm, he = 1e-4 * prm["sigma"], 1e-4 * prm["M"], 1e-5
+    fd_s = (c_loss(prm, fields, steps, target, sigma=prm["sigma"] + hs)
+            - c_loss(prm, fields, steps, target, sigma=prm["sigma"] - hs)) / (2 * hs)
+    fd_m = (c_loss(prm, fields, steps, target, M=prm["M"] + hm)
+            - c_loss(prm, fields, steps, target, M=prm["M"] - hm)) / (2 * hm)
+    v = rng.standard_normal(fields[0].shape) * (np.abs(fields[0]) < 0.95)
+    fd_v = (c_loss(prm, fields, steps, target, phi0=fields[0] + he * v)
+            - c_loss(prm, fields, steps, target, phi0=fields[0] - he * v)) / (2 * he)
+    assert gs.item() == pytest.approx(fd_s, rel=1e-6)
+    assert gm.item() == pytest.approx(fd_m, rel=1e-6)
+    assert float((gphi.numpy() * v).sum()) == pytest.approx(fd_v, rel=1e-6)
