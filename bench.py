@@ -70,6 +70,8 @@ def parse_args():
     ap.add_argument("--n", type=int, default=4096, help="grid is n x n")
     ap.add_argument("--adjoint-n", type=int, default=256, help="side of the adjoint side measurement's grid")
     ap.add_argument("--adjoint-steps", type=int, default=200, help="steps of the adjoint side measurement")
+    ap.add_argument("--adjoint-sweep", type=int, nargs="*", default=[512, 1024, 2048, 4096],
+                    help="grid sides of the adjoint/forward time sweep on the capillary wave")
     ap.add_argument("--precision", default="fp32", choices=("fp32", "fp64"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -417,9 +419,8 @@ def run_ours(args):
                                                 "b_min_frac": round(B_MIN["mixed"] * N / (ms_v / 1e3) / 1e9 / peak, 4)}}
             v.close()
         an, asteps, aevery = args.adjoint_n, args.adjoint_steps, 22
-        aprm, afields = inputs.translating_drop(n=an, R=an / 8.0, U0=0.01)
 
-        def adjoint_run(nsteps):
+        def adjoint_run(aprm, afields, nsteps):
             a = lbm.Sim(aprm, *afields, precision="fp32", stream=stream.cuda_stream)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
@@ -431,23 +432,38 @@ def run_ours(args):
             eng = a.adjoint_engine()
             a.close()
             return t1 - t0, t2 - t1, eng
+        engines = {1: "compiled level kernels", 0: "tape interpreter"}
+        aprm, afields = inputs.translating_drop(n=an, R=an / 8.0, U0=0.01)
         # the first reverse sweep of a tape structure compiles its level
         # kernels (once per process): a short untimed run does that
-        _, c_rev, _ = adjoint_run(2)
-        fw, rv, eng = adjoint_run(asteps)
+        _, c_rev, _ = adjoint_run(aprm, afields, 2)
+        fw, rv, eng = adjoint_run(aprm, afields, asteps)
         os.environ["LBM_ADJOINT_COMPILED"] = "0"
         try:
-            fwi, rvi, engi = adjoint_run(asteps)
+            fwi, rvi, engi = adjoint_run(aprm, afields, asteps)
         finally:
             del os.environ["LBM_ADJOINT_COMPILED"]
         variants["adjoint"] = {"workload": f"translating drop {an}x{an}, rho ratio 100, {asteps} steps, "
                                            f"checkpoint every {aevery}, FP32 forward and reverse sweep",
-                               "engine": {1: "compiled level kernels", 0: "tape interpreter"}.get(eng, "none"),
+                               "engine": engines.get(eng, "none"),
                                "forward_s": round(fw, 4), "reverse_s": round(rv, 4),
                                "adjoint_over_forward": round(rv / fw, 2),
                                "first_sweep_with_compile_s": round(c_rev, 3),
-                               "interpreter": {"engine": {1: "compiled level kernels", 0: "tape interpreter"}.get(engi),
+                               "interpreter": {"engine": engines.get(engi),
                                                "reverse_s": round(rvi, 4), "adjoint_over_forward": round(rvi / fwi, 2)}}
+        # the reverse/forward ratio per grid on the capillary wave (walls in
+        # y, density ratio 1000), 44 steps in two checkpoint segments
+        sweep = []
+        for gn in args.adjoint_sweep:
+            cprm, cfields = inputs.capillary_wave(n=gn)
+            if not sweep:
+                adjoint_run(cprm, cfields, 2)   # compiles the walled tape's kernels
+            cfw, crv, ceng = adjoint_run(cprm, cfields, 44)
+            sweep.append({"n": gn, "forward_s": round(cfw, 4), "reverse_s": round(crv, 4),
+                          "adjoint_over_forward": round(crv / cfw, 2), "engine": engines.get(ceng, "none")})
+        variants["adjoint_sweep"] = {"workload": "capillary wave n x n, walls in y, rho ratio 1000, 44 steps, "
+                                                 f"checkpoint every {aevery}, FP32 forward and reverse sweep",
+                                     "grids": sweep}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

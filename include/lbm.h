@@ -267,8 +267,10 @@ const char *lbm_kernel_variant(const lbm_handle *h, int kind);
  * final order parameter with respect to the initial order parameter, the
  * surface tension sigma and the mobility M.
  *   lbm_adjoint_begin(h, nsteps, k): the handle must hold a state freshly set
- *     from fields (lbm_create or lbm_set_fields, no step since), periodic
- *     axes, and FP64 or FP32 populations.  Advances nsteps steps, keeping
+ *     from fields (lbm_create or lbm_set_fields, no step since) and FP64 or
+ *     FP32 populations; axes periodic or walled as in lbm_step (the walls'
+ *     bounce-back and mirrored stencil ghosts have their own
+ *     vector-Jacobian products).  Advances nsteps steps, keeping
  *     every k-th state as a checkpoint on the device; the handle then holds
  *     the state after nsteps steps.  Errors: LBM_ERR_ARG, LBM_ERR_STATE,
  *     LBM_ERR_OOM, LBM_ERR_CUDA.
@@ -281,8 +283,8 @@ const char *lbm_kernel_variant(const lbm_handle *h, int kind);
  *     summed in FP64) -- and writes dL/dphi0 (host [ny][nx], may be NULL),
  *     dL/dsigma and dL/dM (may be NULL).  The handle is left at the state
  *     after nsteps steps.
- *     Synchronises the stream.  Errors: LBM_ERR_STATE (no begin), LBM_ERR_ARG,
- *     LBM_ERR_CUDA.
+ *     Synchronises the stream.  Errors: LBM_ERR_STATE (no begin), LBM_ERR_ARG
+ *     (also: walls without the compiled level kernels below), LBM_ERR_CUDA.
  * sigma enters through kappa = 3 sigma W/8 and beta = 3 sigma/(4W)
  * (Sec. II.A); M through tau_f (Eq. mobility), the flux q and J (Sec. II).
  */

@@ -3,10 +3,10 @@
 // The reverse sweep works on a tape of plane operations.  To differentiate
 // one step, the step is re-expressed as a sequence of whole-plane
 // operations -- linear combinations, products, quotients, cubes, square
-// roots, the clamp of rho(phi), periodic stencils (isotropic gradient and
-// Laplacian, fourth-order differences, the selective filter, the streaming
-// shifts) and scalings by the differentiable parameters kappa, beta, M and
-// 1/tau_f -- and recorded.  Each operation has a hand-written
+// roots, the clamp of rho(phi), stencils (isotropic gradient and Laplacian,
+// fourth-order differences, the selective filter, the streaming shifts and
+// bounce-back masks) and scalings by the differentiable parameters kappa,
+// beta, M and 1/tau_f -- and recorded.  Each operation has a hand-written
 // vector-Jacobian product; the reverse sweep applies them in reverse order.
 // The operations run a level at a time: the stencils and pointwise
 // operations between two layers of stencils form one kernel that applies
@@ -17,9 +17,14 @@
 // the fallback.  Across steps, sqrt(N)-style checkpointing keeps every k-th
 // state, regenerates a segment with the fused forward kernels and reverses
 // it step by step, the tape's forward passes of a segment batched and
-// overlapped with the reverse passes on a second stream.  Periodic axes,
-// FP64 or FP32 populations; the reverse sweep runs in the handle's arithmetic
-// type, with the parameter gradients summed in FP64.
+// overlapped with the reverse passes on a second stream.  FP64 or FP32
+// populations; the reverse sweep runs in the handle's arithmetic type, with
+// the parameter gradients summed in FP64.  Walls (axes that are not
+// periodic) as in the forward step: each stencil records the parity of its
+// input along each axis, and across a wall it reads the mirror image about
+// the halfway wall times that parity; streaming pulls from across a wall
+// through a bounce-back mask stencil.  Walled tapes run on the compiled level
+// kernels only (the interpreter's stencils are periodic).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,6 +55,10 @@ struct Stencil {
     int n = 0;
     int dx[MAXST]{}, dy[MAXST]{};
     double w[MAXST]{};
+    // a mask stencil passes its one tap (0, 0) only where (x + mx, y + my)
+    // lies across a wall (the bounce-back part of streaming)
+    bool mask = false;
+    int mx = 0, my = 0;
 };
 
 struct Op {
@@ -61,6 +70,9 @@ struct Op {
     double c0 = 0.0;
     int param = -1;
     int st = -1;
+    // a stencil's ghost signs across a wall along x and y: the input's parity
+    // (+1 even, -1 odd) in that direction, or 0 for a ghost that is zero
+    signed char sgx = 1, sgy = 1;
 };
 
 
@@ -85,6 +97,7 @@ int blocks_for(long long N) { return (int)std::min<long long>((N + NTH - 1) / NT
 
 template <typename T> struct VOp {   // one operation as the level kernels run it
     int k, nin, param, live, st;
+    int sgx, sgy;           // a stencil's ghost signs across walls (Op::sgx, Op::sgy)
     unsigned fint;          // bit i: input i is read from forward slot fslot[i]
     unsigned rassign;       // bit i: the contribution to reverse slot rslot[i] stores instead of adding
     short fslot[MAXIN], rslot[MAXIN];
@@ -437,6 +450,8 @@ __global__ void __launch_bounds__(NTV) kk_vm_rev(RevArgs<T> A, double *pgrad, in
 // ---------------------------------------------------------------------------
 template <typename T> struct Engine {
     int nx = 0, ny = 0;
+    int perx = 1, pery = 1;           // periodic axes; a wall stands halfway beyond the edge of the others
+    bool walls() const { return !perx || !pery; }
     long long N = 0;
     cudaStream_t st = nullptr;        // forward passes
     cudaStream_t rst = nullptr;       // reverse passes and collection (st when null)
@@ -603,7 +618,19 @@ template <typename T> struct Engine {
     int binary(OpKind k, int a, int b) { Op o; o.k = k; o.in[0] = a; o.in[1] = b; o.nin = 2; return emit(o); }
     int mul(int a, int b) { return binary(OP_MUL, a, b); }
     int div(int a, int b) { return binary(OP_DIV, a, b); }
-    int sten(int a, int s) { Op o; o.k = OP_STENCIL; o.in[0] = a; o.nin = 1; o.st = s; return emit(o); }
+    // a stencil on plane a; across a wall the ghosts are the mirror images
+    // about the halfway wall times sgx (x) and sgy (y)
+    int sten(int a, int s, int sgx = 1, int sgy = 1)
+    {
+        Op o;
+        o.k = OP_STENCIL;
+        o.in[0] = a;
+        o.nin = 1;
+        o.st = s;
+        o.sgx = (signed char)sgx;
+        o.sgy = (signed char)sgy;
+        return emit(o);
+    }
     int scalep(int a, int p) { Op o; o.k = OP_SCALEP; o.in[0] = a; o.nin = 1; o.param = p; return emit(o); }
     int emit(Op o)
     {
@@ -618,7 +645,8 @@ template <typename T> struct Engine {
         if (a.size() != b.size()) return false;
         for (size_t i = 0; i < a.size(); ++i) {
             const Op &x = a[i], &y = b[i];
-            if (x.k != y.k || x.out != y.out || x.nin != y.nin || x.c0 != y.c0 || x.param != y.param || x.st != y.st)
+            if (x.k != y.k || x.out != y.out || x.nin != y.nin || x.c0 != y.c0 || x.param != y.param || x.st != y.st ||
+                x.sgx != y.sgx || x.sgy != y.sgy)
                 return false;
             for (int j = 0; j < x.nin; ++j)
                 if (x.in[j] != y.in[j] || x.c[j] != y.c[j]) return false;
@@ -771,6 +799,8 @@ template <typename T> struct Engine {
                 d.nin = o.nin;
                 d.param = o.param;
                 d.st = o.st;
+                d.sgx = o.sgx;
+                d.sgy = o.sgy;
                 for (int i = 0; i < o.nin; ++i) {
                     const int p = o.in[i];
                     d.in[i] = val[p];
@@ -902,11 +932,18 @@ template <typename T> struct Engine {
         for (int j = 0; j < G.n; ++j) {
             const VOp<T> &d = hfwd[G.off + j];
             std::string o = "        {\n";
-            if (d.k == OP_STENCIL) {
+            if (d.k == OP_STENCIL && stencils[d.st].mask) {
+                const Stencil &St = stencils[d.st];
+                o += "            const T r = wout(x + " + S(St.mx) + ", y + " + S(St.my) + ", nx, ny) ? " +
+                     ld.get(A, d.in[0], 0, 0, true, "voff + base") + " : T(0);\n";
+            } else if (d.k == OP_STENCIL) {
                 const Stencil &St = stencils[d.st];
                 o += "            T r = T(0);\n";
                 for (int i = 0; i < St.n; ++i)
-                    o += "            r += " + A.c(St.w[i]) + " * " + ld.get(A, d.in[0], St.dx[i], St.dy[i], true, "voff + base") +
+                    o += "            r += " + A.c(St.w[i]) + " * " +
+                         (walls() ? "wtap(" + A.p(d.in[0]) + " + voff + base, x, y, " + S(St.dx[i]) + ", " + S(St.dy[i]) +
+                                        ", nx, ny, T(" + S(d.sgx) + "), T(" + S(d.sgy) + "))"
+                                  : ld.get(A, d.in[0], St.dx[i], St.dy[i], true, "voff + base")) +
                          ";\n";
             } else {
                 for (int i = 0; i < d.nin; ++i)
@@ -959,11 +996,18 @@ template <typename T> struct Engine {
             const int nc = ncontrib(o);
             const size_t at = b.size();   // where this operation's new loads are declared
             b += "        {\n";
-            if (o.k == OP_STENCIL) {   // transpose: gathered from the output adjoint around the node
+            if (o.k == OP_STENCIL && stencils[o.st].mask) {   // a mask is its own transpose
+                const Stencil &St = stencils[o.st];
+                b += "            const T c0 = wout(x + " + S(St.mx) + ", y + " + S(St.my) + ", nx, ny) ? " +
+                     ld.get(A, d.aout, 0, 0, true, "0") + " : T(0);\n";
+            } else if (o.k == OP_STENCIL) {   // transpose: gathered from the output adjoint around the node
                 const Stencil &St = stencils[o.st];
                 b += "            T c0 = T(0);\n";
                 for (int i = 0; i < St.n; ++i)
-                    b += "            c0 += " + A.c(St.w[i]) + " * " + ld.get(A, d.aout, -St.dx[i], -St.dy[i], true, "0") +
+                    b += "            c0 += " + A.c(St.w[i]) + " * " +
+                         (walls() ? "wadj(" + A.p(d.aout) + ", x, y, " + S(-St.dx[i]) + ", " + S(-St.dy[i]) +
+                                        ", nx, ny, T(" + S(o.sgx) + "), T(" + S(o.sgy) + "))"
+                                  : ld.get(A, d.aout, -St.dx[i], -St.dy[i], true, "0")) +
                          ";\n";
             } else {
                 b += "            T g = " + (d.aout ? ld.get(A, d.aout, 0, 0, false, "0") : std::string("T(0)")) +
@@ -1016,6 +1060,47 @@ template <typename T> struct Engine {
         return f + "}\n";
     }
 
+    // Source of the wall helpers of a walled tape's kernels (empty when every
+    // axis is periodic).  A wall stands halfway beyond the last node: across
+    // it a stencil reads the mirror image times the ghost sign, and the
+    // transpose of a tap gathers the output adjoint at the tap's offset from
+    // the node and from each of its mirror images across the walls (times the
+    // same signs), zero wherever that lands outside the domain.
+    std::string wall_helpers() const
+    {
+        if (!walls()) return "";
+        return "constexpr int WX = " + S(!perx) + ", WY = " + S(!pery) + ";   // walled axes\n"
+            "__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }\n"
+            "// (xx, yy) lies across a wall\n"
+            "__device__ __forceinline__ bool wout(int xx, int yy, int nx, int ny)\n{\n"
+            "    return (WX && (xx < 0 || xx >= nx)) || (WY && (yy < 0 || yy >= ny));\n}\n"
+            "// p at (x + dx, y + dy), mirrored across walls with signs sx, sy\n"
+            "__device__ __forceinline__ T wtap(const T *p, int x, int y, int dx, int dy, int nx, int ny, T sx, T sy)\n{\n"
+            "    int xx = x + dx, yy = y + dy;\n"
+            "    T f = T(1);\n"
+            "    if (WX) { if (xx < 0) { xx = -1 - xx; f = sx; } else if (xx >= nx) { xx = 2 * nx - 1 - xx; f = sx; } }\n"
+            "    else xx = wrapi(xx, nx);\n"
+            "    if (WY) { if (yy < 0) { yy = -1 - yy; f *= sy; } else if (yy >= ny) { yy = 2 * ny - 1 - yy; f *= sy; } }\n"
+            "    else yy = wrapi(yy, ny);\n"
+            "    return f == T(0) ? T(0) : f * __ldg(p + (long long)yy * nx + xx);\n}\n"
+            "// p at (xx, yy), zero across a wall\n"
+            "__device__ __forceinline__ T wext(const T *p, int xx, int yy, int nx, int ny)\n{\n"
+            "    if (wout(xx, yy, nx, ny)) return T(0);\n"
+            "    return __ldg(p + (long long)wrapi(yy, ny) * nx + wrapi(xx, nx));\n}\n"
+            "// transpose of a tap at (dx, dy) = minus the stencil's offset\n"
+            "__device__ __forceinline__ T wadj(const T *p, int x, int y, int dx, int dy, int nx, int ny, T sx, T sy)\n{\n"
+            "    T acc = wext(p, x + dx, y + dy, nx, ny);\n"
+            "    const int xl = -1 - x + dx, xh = 2 * nx - 1 - x + dx, yl = -1 - y + dy, yh = 2 * ny - 1 - y + dy;\n"
+            "    if (WY && sy != T(0)) acc += sy * (wext(p, x + dx, yl, nx, ny) + wext(p, x + dx, yh, nx, ny));\n"
+            "    if (WX && sx != T(0)) {\n"
+            "        acc += sx * (wext(p, xl, y + dy, nx, ny) + wext(p, xh, y + dy, nx, ny));\n"
+            "        if (WY && sy != T(0))\n"
+            "            acc += sx * sy * (wext(p, xl, yl, nx, ny) + wext(p, xl, yh, nx, ny) + wext(p, xh, yl, nx, ny) +\n"
+            "                              wext(p, xh, yh, nx, ny));\n"
+            "    }\n"
+            "    return acc;\n}\n";
+    }
+
     // Write the schedule out as compiled level kernels (unless switched off
     // by LBM_ADJOINT_COMPILED=0); jit says whether they run this tape.
     void compile_levels(const std::vector<VOp<T>> &rec, const std::vector<std::vector<int>> &rex)
@@ -1033,7 +1118,7 @@ template <typename T> struct Engine {
             "    int xx = x + dx, yy = y + dy;\n"
             "    xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);\n"
             "    yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);\n"
-            "    return (long long)yy * nx + xx;\n}\n"
+            "    return (long long)yy * nx + xx;\n}\n" + wall_helpers() +
             "// Node of this thread in tile t of a batch: tiles of 32 x JTY nodes (a warp per\n"
             "// row, so vertical stencil taps are mostly shared through L1), tiles_x per\n"
             "// row of tiles, tpp per step; false outside the grid.\n"
@@ -1338,7 +1423,7 @@ template <typename T> struct Engine {
 };
 
 // Stencil table indices.
-enum { S_GX, S_GY, S_LAP, S_D1X, S_D1Y, S_D2X, S_D2Y, S_FILTER, S_SHIFT0 };
+enum { S_GX, S_GY, S_LAP, S_D1X, S_D1Y, S_D2X, S_D2Y, S_FILTER, S_SHIFT0, S_BB0 = S_SHIFT0 + 9 };
 const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 const double WQ[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
@@ -1366,7 +1451,7 @@ void filter_coeffs(int order, double d[6])
 
 std::vector<Stencil> make_stencils(const lbm_params &p)
 {
-    std::vector<Stencil> S(S_SHIFT0 + 9);
+    std::vector<Stencil> S(S_BB0 + 9);
     auto add = [](Stencil &s, int dx, int dy, double w) { s.dx[s.n] = dx; s.dy[s.n] = dy; s.w[s.n] = w; ++s.n; };
     for (int q = 1; q < 9; ++q) {   // isotropic stencils, Sec. III.B Eq. (dicretized)
         if (CX[q]) add(S[S_GX], CX[q], CY[q], 3.0 * WQ[q] * CX[q]);
@@ -1396,6 +1481,12 @@ std::vector<Stencil> make_stencils(const lbm_params &p)
         add(S[S_FILTER], 0, -m, -a * d[m]);
     }
     for (int q = 0; q < 9; ++q) add(S[S_SHIFT0 + q], -CX[q], -CY[q], 1.0);   // f_q(x) = f*_q(x - c_q)
+    for (int q = 0; q < 9; ++q) {   // halfway bounce-back: f_q(x) = f*_opp(q)(x) where x - c_q is across a wall
+        add(S[S_BB0 + q], 0, 0, 1.0);
+        S[S_BB0 + q].mask = true;
+        S[S_BB0 + q].mx = -CX[q];
+        S[S_BB0 + q].my = -CY[q];
+    }
     return S;
 }
 
@@ -1417,8 +1508,9 @@ template <typename T> struct Recorder {
     const lbm_params &P;
     Recorder(Engine<T> &e, const lbm_params &p) : E(e), P(p) {}
 
-    int gx(int a) { return E.sten(a, S_GX); }
-    int gy(int a) { return E.sten(a, S_GY); }
+    // isotropic gradient of a plane whose parities across walls are (sx, sy)
+    int gx(int a, int sx = 1, int sy = 1) { return E.sten(a, S_GX, sx, sy); }
+    int gy(int a, int sx = 1, int sy = 1) { return E.sten(a, S_GY, sx, sy); }
 
     struct Fields { int rho, ir, nu, mu, grx, gry, Jx, Jy, Fsx, Fsy, gpx, gpy; };
 
@@ -1437,9 +1529,10 @@ template <typename T> struct Recorder {
         F.mu = chem_iso(phi);
         int gphx = gx(phi), gphy = gy(phi);
         int gx2 = E.mul(gphx, gphx), gy2 = E.mul(gphy, gphy), gxy = E.mul(gphx, gphy);
-        // F_s = kappa div(|grad phi|^2 I - grad phi grad phi)
-        F.Fsx = E.scalep(E.lin({{gx(gy2), 1.0}, {gy(gxy), -1.0}}), P_KAPPA);
-        F.Fsy = E.scalep(E.lin({{gx(gxy), -1.0}, {gy(gx2), 1.0}}), P_KAPPA);
+        // F_s = kappa div(|grad phi|^2 I - grad phi grad phi); the product of the
+        // components of grad phi is odd across walls on either axis
+        F.Fsx = E.scalep(E.lin({{gx(gy2), 1.0}, {gy(gxy, -1, -1), -1.0}}), P_KAPPA);
+        F.Fsy = E.scalep(E.lin({{gx(gxy, -1, -1), -1.0}, {gy(gx2), 1.0}}), P_KAPPA);
         F.Jx = E.scalep(E.lin({{gx(F.mu), dr}}), P_M);
         F.Jy = E.scalep(E.lin({{gy(F.mu), dr}}), P_M);
         F.grx = E.lin({{gphx, dr}});
@@ -1456,7 +1549,7 @@ template <typename T> struct Recorder {
     // F = F_p + F_s + F_nu + F_m + F_g (Sec. II.B Eq. reformNS)
     void force(const Fields &F, int p, int ux, int uy, int &Fx, int &Fy, int du[4])
     {
-        du[0] = gx(ux); du[1] = gy(ux); du[2] = gx(uy); du[3] = gy(uy);
+        du[0] = gx(ux, -1, -1); du[1] = gy(ux, -1, -1); du[2] = gx(uy, -1, -1); du[3] = gy(uy, -1, -1);   // no slip
         int Sxx = E.lin({{du[0], 2.0}}), Sxy = E.lin({{du[1], 1.0}, {du[2], 1.0}}), Syy = E.lin({{du[3], 2.0}});
         int nvx = E.mul(F.nu, E.lin({{E.mul(Sxx, F.grx), 1.0}, {E.mul(Sxy, F.gry), 1.0}}));
         int nvy = E.mul(F.nu, E.lin({{E.mul(Sxy, F.grx), 1.0}, {E.mul(Syy, F.gry), 1.0}}));
@@ -1520,7 +1613,8 @@ template <typename T> struct Recorder {
             jx = E.lin({{jx, 1.0}, {E.mul(qn, nxp), -1.0}});
             jy = E.lin({{jy, 1.0}, {E.mul(qn, nyp), -1.0}});
         }
-        return E.lin({{E.sten(jx, S_D1X), 1.0}, {E.sten(jy, S_D1Y), 1.0}});
+        // J_x is odd across an x wall and even across a y wall, J_y the reverse
+        return E.lin({{E.sten(jx, S_D1X, -1, 1), 1.0}, {E.sten(jy, S_D1Y, 1, -1), 1.0}});
     }
 
     StateIds step(StateIds s)
@@ -1579,8 +1673,15 @@ template <typename T> struct Recorder {
         unmoments(mgs, gs);
         // streaming and post-stream moments
         for (int q = 0; q < 9; ++q) {
-            o.f[q] = E.sten(fs[q], S_SHIFT0 + q);
-            o.g[q] = E.sten(gs[q], S_SHIFT0 + q);
+            if (E.walls()) {   // pulls from across a wall take the node's opposite population
+                int qo = 0;
+                while (CX[qo] != -CX[q] || CY[qo] != -CY[q]) ++qo;
+                o.f[q] = E.lin({{E.sten(fs[q], S_SHIFT0 + q, 0, 0), 1.0}, {E.sten(fs[qo], S_BB0 + q), 1.0}});
+                o.g[q] = E.lin({{E.sten(gs[q], S_SHIFT0 + q, 0, 0), 1.0}, {E.sten(gs[qo], S_BB0 + q), 1.0}});
+            } else {
+                o.f[q] = E.sten(fs[q], S_SHIFT0 + q);
+                o.g[q] = E.sten(gs[q], S_SHIFT0 + q);
+            }
         }
         double one[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1}, third[9], cxd[9], cyd[9];
         for (int q = 0; q < 9; ++q) { third[q] = 1.0 / 3.0; cxd[q] = CX[q]; cyd[q] = CY[q]; }
@@ -1605,8 +1706,8 @@ template <typename T> struct Recorder {
         }
         // selective filter, Eq. (filter)
         o.p = E.sten(phat, S_FILTER);
-        o.ux = E.sten(ukx, S_FILTER);
-        o.uy = E.sten(uky, S_FILTER);
+        o.ux = E.sten(ukx, S_FILTER, -1, -1);
+        o.uy = E.sten(uky, S_FILTER, -1, -1);
         o.uhx = ukx; o.uhy = uky;
         o.upx = E.lin({{s.ux, 1.0}});   // u^{n-1} of the next step, a plane of its own
         o.upy = E.lin({{s.uy, 1.0}});
@@ -1723,6 +1824,8 @@ template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, 
         A->eng64 = sizeof(D) == sizeof(double);
     }
     E->nx = h->grid.nx; E->ny = h->grid.ny; E->N = h->N; E->st = h->stream; E->nb = blocks_for(h->N);
+    E->perx = h->grid.periodic_x ? 1 : 0;
+    E->pery = h->grid.periodic_y ? 1 : 0;
     E->err = cudaSuccess;
     E->stencils = make_stencils(h->prm);
     const lbm_params &P = h->prm;
@@ -1758,6 +1861,9 @@ template <typename T> lbm_status run_reverse(lbm_handle *h, const double *seed, 
     E->leaf_stride = (long long)NSTATE * (long long)n;
     E->prepare();
     if (E->err != cudaSuccess) return afail(h, LBM_ERR_CUDA, std::string("adjoint: ") + cudaGetErrorString(E->err));
+    if (E->walls() && !E->jit)   // the tape interpreter's stencils are periodic only
+        return afail(h, LBM_ERR_ARG, "adjoint: walls need the compiled level kernels" +
+                                         (lbm_jit::reason().empty() ? std::string() : " (" + lbm_jit::reason() + ")"));
     const int Bc = std::max(1, std::min(E->Bcap, E->Bwant)), nvb = E->nvbuf;
     int ids[NSTATE], ido[NSTATE];
     D *dst[NSTATE];
@@ -1923,7 +2029,6 @@ lbm_status lbm_adjoint_begin(lbm_handle *h, int nsteps, int checkpoint_every)
 {
     if (!h) return LBM_ERR_ARG;
     if (nsteps < 1 || checkpoint_every < 1) return afail(h, LBM_ERR_ARG, "nsteps and checkpoint_every must be >= 1");
-    if (!h->grid.periodic_x || !h->grid.periodic_y) return afail(h, LBM_ERR_ARG, "the adjoint needs periodic axes");
     if (h->grid.precision != LBM_FP64 && h->grid.precision != LBM_FP32)
         return afail(h, LBM_ERR_ARG, "the adjoint needs FP64 or FP32 populations");
     if (!h->fresh_init) return afail(h, LBM_ERR_STATE, "lbm_adjoint_begin needs a state freshly set from fields");
