@@ -1121,6 +1121,24 @@ __device__ __forceinline__ float2 add_hi_lo(float2 h, float2 r, float *lo)
 }
 __device__ __forceinline__ void sts2(float *s, int i, float2 v) { *reinterpret_cast<float2 *>(s + i) = v; }
 
+// Item it of a region of NP column pairs by NB bands of rows, numbered so
+// that the lanes of a warp share a band: the first 32 pairs of every band
+// come first, a band per 32 items, then the remaining NP - 32 pairs of every
+// band.  (Numbered row-major instead, a warp whose items straddle two bands
+// reads shared-memory rows that fall on the same banks.)
+template <int NP, int NB> __device__ __forceinline__ void band_item(int it, int &pair, int &band)
+{
+    constexpr int MAIN = NP < 32 ? NP : 32, REST = NP - MAIN;
+    if (REST == 0 || it < MAIN * NB) {
+        band = it / MAIN;
+        pair = it - band * MAIN;
+    } else {
+        const int j = it - MAIN * NB;
+        band = j / (REST > 0 ? REST : 1);
+        pair = MAIN + j - band * REST;
+    }
+}
+
 // Pass 2 for FP32 on grids of even width, same tile and result as
 // k_rk_stage: each thread covers a column pair over VR1 / VR2 / VR3 rows of
 // the mu / J / divergence regions, holding the y-neighbours in registers.
@@ -1137,10 +1155,12 @@ __device__ __forceinline__ void rk_strips_body(const KP<float> &P, const float *
                   "strips must tile the regions");
 
     if (P.flux_corr) {   // mu on the (TX+8) x (TY+8) region, psi offset 2
-        constexpr int NP = W4 / 2, NI = NP * (H4 / VR1);
+        constexpr int NP = W4 / 2, NB = H4 / VR1, NI = NP * NB;
         const float2 fb = f2(4.0f * P.beta), nk = f2(-P.kappa);
         for (int it = threadIdx.x; it < NI; it += NT) {
-            const int lx = 2 * (it % NP), r0 = (it / NP) * VR1;
+            int pr, bd;
+            band_item<NP, NB>(it, pr, bd);
+            const int lx = 2 * pr, r0 = bd * VR1;
             const int xc = lx + 2;
             float2 w[VR1 + 4];
 #pragma unroll
@@ -1159,10 +1179,12 @@ __device__ __forceinline__ void rk_strips_body(const KP<float> &P, const float *
     }
 
     {   // J = lambda J_phi n + q on the (TX+4) x (TY+4) region, psi offset 4, mu offset 2
-        constexpr int NP = W2 / 2, NI = NP * (H2 / VR2);
+        constexpr int NP = W2 / 2, NB = H2 / VR2, NI = NP * NB;
         const float2 lam = f2(P.lambda), tw = f2(P.two_over_W), e2 = f2(P.eps2), nm = f2(-P.M);
         for (int it = threadIdx.x; it < NI; it += NT) {
-            const int lx = 2 * (it % NP), r0 = (it / NP) * VR2;
+            int pr, bd;
+            band_item<NP, NB>(it, pr, bd);
+            const int lx = 2 * pr, r0 = bd * VR2;
             const int xc = lx + 4;
             float2 w[VR2 + 4];
 #pragma unroll
@@ -1299,10 +1321,12 @@ __device__ __forceinline__ void picard_strips_body(const KP<float> &P, const flo
     static_assert(TX % 2 == 0 && SP % 2 == 0 && SA % 2 == 0 && HA % VR1 == 0 && TY % VR2 == 0,
                   "strips must tile the regions");
     {   // mu and grad phi on the (TX+4) x (TY+2) region
-        constexpr int NP = WA / 2, NI = NP * (HA / VR1);
+        constexpr int NP = WA / 2, NB = HA / VR1, NI = NP * NB;
         const float2 fb = f2(4.0f * P.beta), nk = f2(-P.kappa);
         for (int it = threadIdx.x; it < NI; it += NT) {
-            const int lx = 2 * (it % NP), r0 = (it / NP) * VR1;
+            int pr, bd;
+            band_item<NP, NB>(it, pr, bd);
+            const int lx = 2 * pr, r0 = bd * VR1;
             float2 C[VR1 + 2], D[VR1 + 2], S[VR1 + 2];
 #pragma unroll
             for (int k = 0; k < VR1 + 2; ++k) {
@@ -1892,10 +1916,12 @@ k_collide_pairs(const __grid_constant__ TmaMaps tm, KP<float> P, const S *__rest
     if (!tile.wait(by_tma, err)) return;
 
     {   // mu and grad phi on (x0 - 4 .. x0 + TX + 3) x (y0 - 2 .. y0 + TY + 1)
-        constexpr int NP = W2 / 2, NI = NP * (H2 / VR1);
+        constexpr int NP = W2 / 2, NB = H2 / VR1, NI = NP * NB;
         const float2 fb = f2(4.0f * P.beta), nk = f2(-P.kappa);
         for (int it = threadIdx.x; it < NI; it += G::NT) {
-            const int lx = 2 * (it % NP), r0 = (it / NP) * VR1;
+            int pr, bd;
+            band_item<NP, NB>(it, pr, bd);
+            const int lx = 2 * pr, r0 = bd * VR1;
             float2 C[VR1 + 2], D[VR1 + 2], Sm[VR1 + 2];
 #pragma unroll
             for (int k = 0; k < VR1 + 2; ++k) {
