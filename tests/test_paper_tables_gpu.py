@@ -76,8 +76,8 @@ def test_table3_volume_errors(R, printed):
     """Table 3 after 2 x 10^5 steps: the original CH method loses 3.9344 %
     (R = 10) and 0.6426 % (R = 20) of the drop's volume, the present method
     none.  The volume is a count of nodes, so the printed percentages are
-    node counts (48 of 1220 nodes at R = 10): the reproduction must land on
-    the same count, within one node."""
+    node counts (12 of 305 nodes at R = 10, 8 of 1245 at R = 20): the
+    reproduction must land on the same count, within one node."""
     err_orig, v0 = _table3_volume_error(R, True)
     err_present, _ = _table3_volume_error(R, False)
     print("table 3", R, err_orig, err_present, v0)
