@@ -255,6 +255,27 @@ def oracle_mlups(n, steps, warmup=1):
     return n * n * steps / dt / 1e6, dt
 
 
+def _oracle_worker(job):
+    n, steps = job
+    v, dt = oracle_mlups(n, steps)
+    return n * n * steps, dt
+
+
+def oracle_mlups_all_cores(n, steps):
+    """The same oracle in one process per host core, each on its own copy of
+    the sample (processes started by spawn, so none inherits a CUDA context):
+    node updates of all processes over the wall time of the slowest."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_worker, [(64, 1)] * cores)   # workers up, oracle loaded
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, [(n, steps)] * cores)
+        wall = time.perf_counter() - t0
+    return sum(r[0] for r in res) / wall / 1e6, wall, cores
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the oracle as it stands, on the host cores
 # ---------------------------------------------------------------------------
@@ -472,6 +493,10 @@ def run_ours(args):
         cpu = {"value": round(v, 3), "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                "sample": f"capillary wave {cn}x{cn}, same parameters, {cs} steps ({dt:.1f} s), FP64 oracle, "
                          f"single thread on {cpu_model()} ({os.cpu_count()} cores on the host)"}
+        va, wall, ncores = oracle_mlups_all_cores(cn, cs)
+        cpu["all_cores"] = {"value": round(va, 3), "unit": UNIT, "cores": ncores, "kind": "oracle",
+                            "sample": f"the same sample in {ncores} processes at once, one per core "
+                                      f"({wall:.1f} s wall): throughput of the whole host, not a parallel oracle"}
 
     diag = sim.diagnostics()
     ok = diag[10] == 0

@@ -2,8 +2,9 @@
 
 Error measure: max |gpu - oracle| / max |oracle| per field.
 FP64: at most 1e-12 for every field after the stated number of steps.
-FP32: every field at most 1e-5 at density ratios up to 100 (phi, p, u after
-200 steps measure <= 8e-9, 4e-6, 8e-6 on the 64^2 static drop).  The FP32
+FP32: every field at most 1e-5 at density ratios up to 100, after 200 steps
+in every FP32 case (phi, p, u measure <= 8e-9, 4e-6, 8e-6 on the 64^2 static
+drop; the largest over the cases are 1.8e-6, 7.7e-6, 9.5e-6).  The FP32
 path carries phi as a pair of floats (phi_hi + phi_lo) and the step's change
 of phi as increments (the post-stream sum and the RK3 stages, Sec. III.A
 Eq. TVD-3order), so phi is not rounded to 24 bits near +-1, where rho(phi)
@@ -99,7 +100,7 @@ def test_even_width_fp32(nx, ny, px, py):
     R = max(min(nx, ny) / 4.0, 3.0)
     phi = inputs.drop(nx, ny, R, nx / 2 + 0.3, ny / 2 - 0.2, prm["W"])
     z = np.zeros_like(phi)
-    o, g = run_both(prm, (phi, z, z, z), 60, "fp32")
+    o, g = run_both(prm, (phi, z, z, z), 200, "fp32")
     assert_parity(o, g, TOL["fp32"])
 
 
@@ -127,7 +128,7 @@ def test_translating_drop_fp32(n):
     column-pair kernels, odd widths the one-node-per-thread kernels)."""
     U0 = 0.02
     prm, fields = inputs.translating_drop(n=n, R=10.0, U0=U0)
-    o, g = run_both(prm, fields, 100, "fp32")
+    o, g = run_both(prm, fields, 200, "fp32")
     of, gf = o.fields(), g.fields()
     assert rel_err(gf[0], of[0]) <= TOL["fp32"]
     assert np.abs(gf[1] - of[1]).max() / (prm["rho_H"] * U0 ** 2) <= 1e-5
@@ -245,30 +246,32 @@ def test_zero_steps_and_conservation_fp32():
 def test_rising_bubble_256x512_fp32():
     """The rising-bubble workload (rho ratio 1000, walls) at its full size."""
     prm, fields = inputs.rising_bubble()
-    o, g = run_both(prm, fields, 40, "fp32")
+    o, g = run_both(prm, fields, 200, "fp32")
     assert_parity(o, g, TOL["fp32"], tol_pu=TOL_FP32_PU_R1000)
 
 
 def test_full_size_capillary_wave_sampled_fp32():
-    """4096^2 capillary wave (the throughput workload), one step in the launch
+    """4096^2 capillary wave (the throughput workload), five steps in the launch
     configuration the benchmark times, checked on sampled patches: the oracle
-    advances each 128^2 patch of the initial state on its own (periodic in x,
+    advances each 512^2 patch of the initial state on its own (periodic in x,
     the real wall where the patch touches one) and the central nodes, which no
-    patch edge reaches within one step, must match."""
-    n = 4096
+    patch edge reaches within five steps (a step's stencils reach about 32
+    nodes: collision and streaming, three RK3 stages of radius 6, two Picard
+    sweeps, the radius-5 filter), must match."""
+    n, steps = 4096, 5
     prm, fields = inputs.capillary_wave(n=n)
     g = lbm.Sim(prm, *fields, precision="fp32")
-    g.step(1)
+    g.step(steps)
     gf = g.fields()
     g.close()
-    P, m = 128, 40
-    for (x0, y0, wall) in [(1000, 1980, False), (4096 - 128, 2000, False), (200, 0, True)]:
+    P, m = 512, 180
+    for (x0, y0, wall) in [(1000, 1800, False), (4096 - 512, 1900, False), (200, 0, True)]:
         sub = [a[y0:y0 + P, x0:x0 + P] for a in fields]
         pp = dict(prm)
         pp["periodic_x"] = 1
         pp["periodic_y"] = 0 if wall else 1
         o = oracle.Sim(pp, *sub)
-        o.step(1)
+        o.step(steps)
         of = o.fields()
         ys = slice(0, P - m) if wall else slice(m, P - m)
         for name, a, b in zip(("phi", "p", "ux", "uy"), gf, of):
@@ -289,7 +292,7 @@ def test_general_relaxation_rates(precision):
     prm["s_g"] = [1.0, 1.1, 1.2, 0.95, 1.6, 1.05, 1.5, 1.0, 1.0]
     phi = inputs.drop(nx, ny, 8.0, 20.0, 14.0, prm["W"])
     z = np.zeros_like(phi)
-    o, g = run_both(prm, (phi, z, z, z), 60, precision)
+    o, g = run_both(prm, (phi, z, z, z), 200, precision)
     assert_parity(o, g, TOL[precision], tol_pu=pu_tol(precision))
 
 
@@ -308,7 +311,7 @@ def test_srt_equal_rates(precision):
     prm["s_g"] = [1.0 / tau_g] * 9
     phi = inputs.drop(nx, ny, 8.0, 20.0, 14.0, prm["W"])
     z = np.zeros_like(phi)
-    o, g = run_both(prm, (phi, z, z, z), 60, precision)
+    o, g = run_both(prm, (phi, z, z, z), 200, precision)
     assert g.kernel_variants()["k_collide_stream"] == "k_collide_stream"
     assert_parity(o, g, TOL[precision], tol_pu=pu_tol(precision))
 
@@ -323,12 +326,12 @@ def test_strain_rate_from_moments(precision, nx):
     ny = 37
     phi, p, ux, uy = inputs.random_fields(nx, ny, seed=3, u_amp=5e-3)
     prm = inputs.base_params(rho_H=20.0, nu_H=0.05, nu_L=0.01, sigma=5e-3, gy=-2e-6, periodic_y=0, flags=1)
-    o, g = run_both(prm, (phi, p, ux, uy), 60, precision)
+    o, g = run_both(prm, (phi, p, ux, uy), 200, precision)
     assert g.kernel_variants()["k_picard"] == "k_picard"
     assert_parity(o, g, TOL[precision], tol_pu=pu_tol(precision))
     prm0 = dict(prm, flags=0)
     o0 = oracle.Sim(prm0, phi, p, ux, uy)
-    o0.step(60)
+    o0.step(200)
     d = max(rel_err(a, b) for a, b in zip(o.fields()[1:], o0.fields()[1:]))
     print("moments vs stencils", d)
     assert d > 100 * TOL[precision]
