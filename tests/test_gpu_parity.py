@@ -15,7 +15,8 @@ ratio across the interface, where F_p = -p grad rho and grad p nearly cancel
 in the NS source (Eq. Gi), and the FP32 rounding of grad phi and of the
 surface-tension tensor kappa(|grad phi|^2 I - grad phi grad phi) enters that
 residual amplified by the jump: p measures 2.4e-5 .. 2.7e-5 (64^2, 66^2
-capillary waves, 200 steps) and 1.4e-5 (256x512 bubble), u <= 5.2e-5.
+capillary waves, 200 steps) and 5.8e-5 (256x512 bubble, 200 steps, its heavy
+phase nearly inviscid), u <= 4e-5.
 """
 import math
 
