@@ -2229,7 +2229,22 @@ __device__ __forceinline__ double warp_min(double v)
     return v;
 }
 
-constexpr int DSEG = 8;   // nodes a thread sums in T before adding to the FP64 sums
+constexpr int DSEG = 8;   // nodes a thread sums before adding to the FP64 sums
+
+// A float accumulator carried as an unevaluated sum hi + lo (Knuth's TwoSum
+// after every addition): a segment of FP32 terms is summed without rounding
+// error beyond the order of the square of the unit roundoff, and enters the
+// FP64 sums as (double)hi + (double)lo.
+struct FFAcc {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float s = hi + x;
+        lo += two_sum_err(hi, x, s);
+        hi = s;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -2237,7 +2252,12 @@ k_diag_partial(int nx, int ny, const T *__restrict__ phi, const T *__restrict__ 
                const T *__restrict__ uy, double *__restrict__ part)
 {
     // block b takes rows b, b + gridDim.x, ...; each thread accumulates at
-    // most DSEG nodes of a row in T before adding the segment to FP64 sums
+    // most DSEG nodes of a row before adding the segment to the FP64 sums.
+    // FP64 handles add in FP64 throughout.  FP32 handles form every term
+    // exactly as a float pair -- w = (1 - phi)/2 by TwoSum (the halving is
+    // exact), w uy by an FMA for the product's error -- and sum the segment
+    // in FFAcc, so the sums match FP64 sums of the same FP32 fields to the
+    // order of the FP64 rounding.
     double s_ph = 0.0, s_v = 0.0, s_w = 0.0, s_wy = 0.0, s_wv = 0.0;
     long long n_pos = 0, n_neg = 0, s_y = 0, n_bad = 0;
     T mx = T(-INFINITY), mn = T(INFINITY);
@@ -2246,7 +2266,6 @@ k_diag_partial(int nx, int ny, const T *__restrict__ phi, const T *__restrict__ 
         int npos = 0, nneg = 0;
         // segments of DSEG nodes per thread, their loads all issued first
         for (int xs = threadIdx.x; xs < nx; xs += DSEG * blockDim.x) {
-            T a_ph = T(0), a_v = T(0), a_w = T(0), a_wv = T(0);
             T ph[DSEG], v[DSEG], pp[DSEG], uu[DSEG];
 #pragma unroll
             for (int u = 0; u < DSEG; ++u) {
@@ -2257,27 +2276,57 @@ k_diag_partial(int nx, int ny, const T *__restrict__ phi, const T *__restrict__ 
                 pp[u] = in ? p[r + x] : T(0);
                 uu[u] = in ? ux[r + x] : T(0);
             }
+            if constexpr (std::is_same<T, float>::value) {
+                FFAcc a_ph, a_v, a_w, a_wv;
 #pragma unroll
-            for (int u = 0; u < DSEG; ++u) {
-                if (xs + u * blockDim.x >= nx) break;
-                const T w = (T(1) - ph[u]) * T(0.5);
-                a_ph += ph[u];
-                a_w += w;
-                a_wv += w * v[u];
-                if (ph[u] > T(0)) ++npos;
-                if (ph[u] < T(0)) {
-                    ++nneg;
-                    a_v += v[u];
+                for (int u = 0; u < DSEG; ++u) {
+                    if (xs + u * blockDim.x >= nx) break;
+                    const float om = 1.0f - ph[u];
+                    const float w = 0.5f * om, wl = 0.5f * two_sum_err(1.0f, -ph[u], om);   // w + wl = (1 - phi)/2
+                    const float wv = w * v[u];
+                    a_ph.add(ph[u]);
+                    a_w.add(w);
+                    a_w.lo += wl;
+                    a_wv.add(wv);
+                    a_wv.lo += fmaf(w, v[u], -wv) + wl * v[u];
+                    if (ph[u] > 0.0f) ++npos;
+                    if (ph[u] < 0.0f) {
+                        ++nneg;
+                        a_v.add(v[u]);
+                    }
+                    mx = fmax(mx, ph[u]);
+                    mn = fmin(mn, ph[u]);
+                    n_bad += (int)!isfinite(ph[u]) + (int)!isfinite(pp[u]) + (int)!isfinite(uu[u]) + (int)!isfinite(v[u]);
                 }
-                mx = fmax(mx, ph[u]);
-                mn = fmin(mn, ph[u]);
-                n_bad += (int)!isfinite(ph[u]) + (int)!isfinite(pp[u]) + (int)!isfinite(uu[u]) + (int)!isfinite(v[u]);
+                s_ph += a_ph.value();
+                s_v += a_v.value();
+                s_w += a_w.value();
+                s_wy += (double)y * a_w.value();
+                s_wv += a_wv.value();
+            } else {
+                T a_ph = T(0), a_v = T(0), a_w = T(0), a_wv = T(0);
+#pragma unroll
+                for (int u = 0; u < DSEG; ++u) {
+                    if (xs + u * blockDim.x >= nx) break;
+                    const T w = (T(1) - ph[u]) * T(0.5);
+                    a_ph += ph[u];
+                    a_w += w;
+                    a_wv += w * v[u];
+                    if (ph[u] > T(0)) ++npos;
+                    if (ph[u] < T(0)) {
+                        ++nneg;
+                        a_v += v[u];
+                    }
+                    mx = fmax(mx, ph[u]);
+                    mn = fmin(mn, ph[u]);
+                    n_bad += (int)!isfinite(ph[u]) + (int)!isfinite(pp[u]) + (int)!isfinite(uu[u]) + (int)!isfinite(v[u]);
+                }
+                s_ph += (double)a_ph;
+                s_v += (double)a_v;
+                s_w += (double)a_w;
+                s_wy += (double)y * (double)a_w;
+                s_wv += (double)a_wv;
             }
-            s_ph += (double)a_ph;
-            s_v += (double)a_v;
-            s_w += (double)a_w;
-            s_wy += (double)y * (double)a_w;
-            s_wv += (double)a_wv;
         }
         n_pos += npos;
         n_neg += nneg;

@@ -36,10 +36,10 @@ def test_noalloc_sums_match_diagnostics_twice(precision, nx, ny):
         lbm.field_sums_noalloc(*bufs, out)
         got = out.cpu().numpy()
         n = shp[0] * shp[1]
-        # FP64 sums of n terms agree to 1e-12 of n + |sum|; an FP32 handle's
-        # diagnostics add row segments of at most 8 terms in FP32 first,
-        # which is off by at most 7 roundings (2^-24) of each |term| <= 1
-        rel = 1e-12 if precision == "fp64" else 7 * 2.0 ** -24
+        # FP64 sums of n terms agree to 1e-12 of n + |sum|, for FP32 handles
+        # too: their diagnostics form each term exactly as a float pair and
+        # sum the row segments with TwoSum before the FP64 sums
+        rel = 1e-12
         for k in (0, 3, 4, 5, 6, 7):
             assert abs(got[k] - ref[k]) <= rel * (n + abs(ref[k])), (k, got[k], ref[k])
         for k in (1, 2, 8, 9, 10):             # counts and extrema are exact
