@@ -427,17 +427,23 @@ def run_ours(args):
             k = max(10, args.steps // 2)
             a0 = torch.cuda.Event(enable_timing=True)
             a1 = torch.cuda.Event(enable_timing=True)
+            v.profile(True)
             a0.record(stream)
             v.step(k)
             a1.record(stream)
             torch.cuda.synchronize(dev)
+            vprof = v.profile_read()
+            v.profile(False)
+            vvar = v.kernel_variants()
             ms_v = a0.elapsed_time(a1) / k
             variants[prec] = {"MLUPS": round(N / ms_v / 1e3, 1), "ms_per_step": round(ms_v, 4), "steps": k,
                               "vs_fp32": round((N / ms_v / 1e3) / (N / (ms_max / args.steps) / 1e3), 4),
                               "step_roofline": {"algorithmic_bytes_per_node": MIXED_STEP_BYTES,
                                                 "frac": round(MIXED_STEP_BYTES * N / (ms_v / 1e3) / 1e9 / peak, 4),
                                                 "b_min_bytes_per_node": B_MIN["mixed"],
-                                                "b_min_frac": round(B_MIN["mixed"] * N / (ms_v / 1e3) / 1e9 / peak, 4)}}
+                                                "b_min_frac": round(B_MIN["mixed"] * N / (ms_v / 1e3) / 1e9 / peak, 4)},
+                              "kernels": {kk: {"kernel": vvar[kk], "ms_per_launch": round(x[0] / max(x[1], 1), 4)}
+                                          for kk, x in vprof.items()}}
             v.close()
         an, asteps, aevery = args.adjoint_n, args.adjoint_steps, 22
 
