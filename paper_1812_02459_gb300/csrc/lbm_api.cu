@@ -40,7 +40,7 @@ constexpr int PT_TX = 64, PT_TY = 16, PT_NT = 128, PT_VR1 = 6, PT_VR2 = 4, PT_MI
 constexpr int FT_TX = 64, FT_TY = 32, FT_VR = 4, FT_MINB = 4;
 constexpr int CP_TX = 60, CP_TY = 14, CP_VR1 = 2;   // collide+stream on node pairs
 constexpr int DIAG_THREADS = 256;
-constexpr int DIAG_MAX_BLOCKS = 1216;    // 8 x 152 SMs
+constexpr int DIAG_MAX_BLOCKS = 608;     // 4 x 152 SMs (the diagnostics kernel's resident blocks)
 
 thread_local std::string g_create_error;
 
@@ -937,7 +937,7 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params, const doub
     const size_t plane = round_up((size_t)h->N * h->elem, 256);
     const size_t pplane = round_up((size_t)h->N * 9 * h->pop_elem, 256);
     const int nscalar = 23;   // phi[2], philo, pf, ux[2], uy[2], uhx, uhy, dbar[2], phat[2], jx, jy, s1, s2, tk[2][2], 1 spare
-    h->diag_blocks = std::min(grid->ny, DIAG_MAX_BLOCKS);   // rows per block: ny / blocks
+    h->diag_blocks = std::min(grid->ny, DIAG_MAX_BLOCKS);   // blocks of the diagnostics sums; the partials they write
     const size_t diag_bytes = round_up(sizeof(double) * (size_t)(h->diag_blocks + 1) * NDIAG, 256);
     h->arena_bytes = 4 * pplane + nscalar * plane + diag_bytes + 256;   // + the device error word
     cudaError_t e = cudaMalloc((void **)&h->arena, h->arena_bytes);

@@ -2243,29 +2243,56 @@ struct FFAcc {
         lo += two_sum_err(hi, x, s);
         hi = s;
     }
+    // this += b: TwoSum of the high parts, the low parts and that error
+    // added, then renormalised; the error is of the order of the square of
+    // the unit roundoff times |this + b|
+    __device__ __forceinline__ void add(const FFAcc &b)
+    {
+        const float s = hi + b.hi;
+        const float e = two_sum_err(hi, b.hi, s) + (lo + b.lo);
+        hi = s + e;
+        lo = two_sum_err(s, e, hi);
+    }
+    // this += b * y for an integer y exactly representable as a float
+    __device__ __forceinline__ void add_scaled(const FFAcc &b, float y)
+    {
+        FFAcc t;
+        t.hi = b.hi * y;
+        t.lo = fmaf(b.hi, y, -t.hi) + b.lo * y;
+        add(t);
+    }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_diag_partial(int nx, int ny, const T *__restrict__ phi, const T *__restrict__ p, const T *__restrict__ ux,
                const T *__restrict__ uy, double *__restrict__ part)
 {
-    // block b takes rows b, b + gridDim.x, ...; each thread accumulates at
-    // most DSEG nodes of a row before adding the segment to the FP64 sums.
+    // each thread accumulates at most DSEG nodes of a row (a segment) before
+    // adding the segment to its sums.
     // FP64 handles add in FP64 throughout.  FP32 handles form every term
     // exactly as a float pair -- w = (1 - phi)/2 by TwoSum (the halving is
-    // exact), w uy by an FMA for the product's error -- and sum the segment
-    // in FFAcc, so the sums match FP64 sums of the same FP32 fields to the
-    // order of the FP64 rounding.
+    // exact), w uy by an FMA for the product's error -- sum the segment in
+    // FFAcc and the segments in float-pair sums, which go to FP64 once per
+    // thread: the sums match FP64 sums of the same FP32 fields to the order
+    // of the FP64 rounding (each segment is off by at most (7u)^2 of the sum
+    // of its |terms|, u = 2^-24, each float-pair addition by about u^2).
     double s_ph = 0.0, s_v = 0.0, s_w = 0.0, s_wy = 0.0, s_wv = 0.0;
+    FFAcc f_ph, f_v, f_w, f_wy, f_wv;   // FP32 handles: the segments' sums, as float pairs
     long long n_pos = 0, n_neg = 0, s_y = 0, n_bad = 0;
     T mx = T(-INFINITY), mn = T(INFINITY);
-    for (int y = blockIdx.x; y < ny; y += gridDim.x) {
+    // work items: a row cut into chunks of DSEG * blockDim.x nodes (one
+    // segment per thread), dealt to the blocks in turn, so that the blocks
+    // finish together
+    const int chunk = DSEG * (int)blockDim.x, cpr = (nx + chunk - 1) / chunk;
+    for (long long item = blockIdx.x; item < (long long)ny * cpr; item += gridDim.x) {
+        const int y = (int)(item / cpr), xc = (int)(item - (long long)y * cpr) * chunk;
         const long long r = (long long)y * nx;
         int npos = 0, nneg = 0;
-        // segments of DSEG nodes per thread, their loads all issued first
-        for (int xs = threadIdx.x; xs < nx; xs += DSEG * blockDim.x) {
+        // one segment of DSEG nodes per thread, its loads all issued first
+        {
+            const int xs = xc + (int)threadIdx.x;
             T ph[DSEG], v[DSEG], pp[DSEG], uu[DSEG];
 #pragma unroll
             for (int u = 0; u < DSEG; ++u) {
@@ -2298,11 +2325,13 @@ k_diag_partial(int nx, int ny, const T *__restrict__ phi, const T *__restrict__ 
                     mn = fmin(mn, ph[u]);
                     n_bad += (int)!isfinite(ph[u]) + (int)!isfinite(pp[u]) + (int)!isfinite(uu[u]) + (int)!isfinite(v[u]);
                 }
-                s_ph += a_ph.value();
-                s_v += a_v.value();
-                s_w += a_w.value();
-                s_wy += (double)y * a_w.value();
-                s_wv += a_wv.value();
+                // the segment into the thread's float-pair sums (FP32 arithmetic:
+                // FP64 is a small fraction of the FP32 rate on this GPU)
+                f_ph.add(a_ph);
+                f_v.add(a_v);
+                f_w.add(a_w);
+                f_wy.add_scaled(a_w, (float)y);
+                f_wv.add(a_wv);
             } else {
                 T a_ph = T(0), a_v = T(0), a_w = T(0), a_wv = T(0);
 #pragma unroll
@@ -2331,6 +2360,13 @@ k_diag_partial(int nx, int ny, const T *__restrict__ phi, const T *__restrict__ 
         n_pos += npos;
         n_neg += nneg;
         s_y += (long long)y * nneg;
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        s_ph = f_ph.value();
+        s_v = f_v.value();
+        s_w = f_w.value();
+        s_wy = f_wy.value();
+        s_wv = f_wv.value();
     }
     // a non-finite phi poisons fmax/fmin only through NaN, which fmax skips:
     // the count in slot 10 reports it
