@@ -936,7 +936,7 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params, const doub
     // one arena: 2x9 f planes, 2x9 g planes, then the scalar planes, 256-byte aligned each
     const size_t plane = round_up((size_t)h->N * h->elem, 256);
     const size_t pplane = round_up((size_t)h->N * 9 * h->pop_elem, 256);
-    const int nscalar = 23;   // phi[2], philo, pf, ux[2], uy[2], uhx, uhy, dbar[2], phat[2], jx, jy, s1, s2, tk[2][2], 1 spare
+    const int nscalar = 22;   // phi[2], philo, pf, ux[2], uy[2], uhx, uhy, dbar[2], phat[2], jx, jy, s1, s2, tk[2][2]
     h->diag_blocks = std::min(grid->ny, DIAG_MAX_BLOCKS);   // blocks of the diagnostics sums; the partials they write
     const size_t diag_bytes = round_up(sizeof(double) * (size_t)(h->diag_blocks + 1) * NDIAG, 256);
     h->arena_bytes = 4 * pplane + nscalar * plane + diag_bytes + 256;   // + the device error word
@@ -955,8 +955,8 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_params *params, const doub
     void **sc[] = {&h->phi[0], &h->phi[1], &h->philo, &h->pf, &h->ux[0], &h->ux[1], &h->uy[0], &h->uy[1], &h->uhx, &h->uhy,
                    &h->dbar[0], &h->dbar[1], &h->phat[0], &h->phat[1], &h->jx, &h->jy, &h->s1, &h->s2,
                    &h->tk[0][0], &h->tk[0][1], &h->tk[1][0], &h->tk[1][1]};
+    static_assert(sizeof(sc) / sizeof(sc[0]) == 22, "one plane per scalar field of the arena");
     for (void **pp : sc) { *pp = a; a += plane; }
-    a += 1 * plane;
     h->diag_part = (double *)a;
     h->diag_out = h->diag_part + (size_t)h->diag_blocks * NDIAG;
     h->dev_err = (unsigned *)(h->arena + h->arena_bytes - 256);

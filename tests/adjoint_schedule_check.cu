@@ -87,11 +87,12 @@ lbm_params params(int flux, int picard, int filter)
     return P;
 }
 
-template <typename T> void check_case(int flux, int picard, int filter, bool nvrtc)
+template <typename T> void check_case(int flux, int picard, int filter, bool nvrtc, int perx = 1, int pery = 1)
 {
     const lbm_params P = params(flux, picard, filter);
     Engine<T> E;
     E.nx = 40; E.ny = 24; E.N = 40 * 24; E.nb = 1;
+    E.perx = perx; E.pery = pery;
     E.stencils = make_stencils(P);
     Recorder<T> R(E, P);
     static T src[1], lam[1];
@@ -149,6 +150,17 @@ template <typename T> void check_case(int flux, int picard, int filter, bool nvr
         }
     }
     for (auto &l : E.leaves) EXPECT(E.val[l.first] != nullptr, "leaf stored");
+    // walls: every stencil's ghost signs are parities or zero, the bounce-back
+    // masks appear exactly when an axis is walled (two per direction of f and g)
+    int masks = 0, zero_ghost = 0;
+    for (const Op &o : E.tape) {
+        if (o.k != OP_STENCIL) continue;
+        EXPECT(o.sgx >= -1 && o.sgx <= 1 && o.sgy >= -1 && o.sgy <= 1, "ghost signs");
+        if (E.stencils[o.st].mask) ++masks;
+        if (o.sgx == 0 && o.sgy == 0) ++zero_ghost;
+    }
+    EXPECT(masks == (E.walls() ? 18 : 0), "bounce-back masks");
+    EXPECT(zero_ghost == (E.walls() ? 18 : 0), "streaming shifts with zero ghosts");
     int ids[NSTATE], ido[NSTATE];
     for (int i = 0; i < NSTATE; ++i) {
         ids[i] = *slot(in, i);
@@ -160,9 +172,10 @@ template <typename T> void check_case(int flux, int picard, int filter, bool nvr
         EXPECT(E.enable_pingpong(ids, ido, NSTATE), "argument packs can be exchanged");
         for (auto &J : E.jrev) EXPECT(J.pack_sw.size() == J.pack.size(), "exchanged pack");
     }
-    printf("%s flux %d picard %d filter %2d: %zu ops, %zu forward + %zu reverse kernels, compiled %d, failures %d\n",
-           sizeof(T) == 8 ? "fp64" : "fp32", flux, picard, filter, E.tape.size(), E.fgroups.size(), E.rgroups.size(),
-           (int)E.jit, failures);
+    printf("%s flux %d picard %d filter %2d walls %d%d: %zu ops, %zu forward + %zu reverse kernels, compiled %d, "
+           "failures %d\n",
+           sizeof(T) == 8 ? "fp64" : "fp32", flux, picard, filter, !perx, !pery, E.tape.size(), E.fgroups.size(),
+           E.rgroups.size(), (int)E.jit, failures);
 }
 
 }  // namespace
@@ -176,5 +189,9 @@ int main(int argc, char **argv)
         if (failures) return 1;
     }
     check_case<double>(1, 2, 11, nvrtc);
+    // walls in y, in x and y (FP32), in y (FP64)
+    check_case<float>(1, 2, 11, nvrtc, 1, 0);
+    check_case<float>(1, 2, 11, nvrtc, 0, 0);
+    check_case<double>(1, 2, 11, nvrtc, 1, 0);
     return failures ? 1 : 0;
 }

@@ -1,9 +1,11 @@
 """The adjoint engine's schedule, checked on the host (no GPU): builds
 tests/adjoint_schedule_check.cu with nvcc (lbm_adjoint.cu with its few
 runtime calls replaced by stand-ins) and runs it over five tape structures in
-FP32 and one in FP64.  It checks slot bounds, storage of every plane read,
-the staging of every operand and stencil tap in its phase, flushes, and, when
-NVRTC is available, that the generated level kernels compile and that the
+FP32 and one in FP64 on periodic axes, and over walled axes (y; x and y) in
+FP32 and FP64.  It checks slot bounds, storage of every plane read, the
+staging of every operand and stencil tap in its phase, flushes, the walls'
+ghost signs and bounce-back masks, and, when NVRTC is available, that the
+generated level kernels (with the wall helpers) compile and that the
 argument packs can be exchanged between reverse passes."""
 import os
 import shutil
@@ -28,4 +30,4 @@ def test_adjoint_schedule_on_host(tmp_path):
     print(r.stdout)
     assert r.returncode == 0, r.stdout + r.stderr
     lines = [l for l in r.stdout.splitlines() if "failures" in l]
-    assert len(lines) == 6 and all(l.endswith("failures 0") for l in lines)
+    assert len(lines) == 9 and all(l.endswith("failures 0") for l in lines)
