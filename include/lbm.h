@@ -174,7 +174,7 @@ lbm_status lbm_set_fields(lbm_handle *h, const double *phi0, const double *p0,
 /*
  * lbm_diagnostics -- sums over the nodes (Sec. IV.C volume error,
  * Sec. IV.E Eqs. quantify-yc, quantify-uc), into host out[LBM_NDIAG]; the
- * sums are FP64 over row segments of at most 8 nodes (FP64 handles sum the
+ * sums are FP64 over row segments of at most 16 nodes (FP64 handles sum the
  * segments in FP64; FP32 handles form each term exactly as a pair of floats
  * and sum the segment with TwoSum, which matches FP64 sums of the same
  * fields to the order of FP64 rounding; exact counts in [1], [2], [3], [10]):

@@ -40,7 +40,7 @@ constexpr int PT_TX = 64, PT_TY = 16, PT_NT = 128, PT_VR1 = 6, PT_VR2 = 4, PT_MI
 constexpr int FT_TX = 64, FT_TY = 32, FT_VR = 4, FT_MINB = 4;
 constexpr int CP_TX = 60, CP_TY = 14, CP_VR1 = 2;   // collide+stream on node pairs
 constexpr int DIAG_THREADS = 256;
-constexpr int DIAG_MAX_BLOCKS = 608;     // 4 x 152 SMs (the diagnostics kernel's resident blocks)
+constexpr int DIAG_MAX_BLOCKS = 304;     // 2 x 152 SMs (the diagnostics kernel's resident blocks)
 
 thread_local std::string g_create_error;
 

@@ -2229,7 +2229,7 @@ __device__ __forceinline__ double warp_min(double v)
     return v;
 }
 
-constexpr int DSEG = 8;   // nodes a thread sums before adding to the FP64 sums
+constexpr int DSEG = 16;  // nodes a thread sums before adding to its sums
 
 // A float accumulator carried as an unevaluated sum hi + lo (Knuth's TwoSum
 // after every addition): a segment of FP32 terms is summed without rounding
@@ -2265,7 +2265,7 @@ struct FFAcc {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 2)
 k_diag_partial(int nx, int ny, const T *__restrict__ phi, const T *__restrict__ p, const T *__restrict__ ux,
                const T *__restrict__ uy, double *__restrict__ part)
 {
@@ -2276,7 +2276,7 @@ k_diag_partial(int nx, int ny, const T *__restrict__ phi, const T *__restrict__ 
     // exact), w uy by an FMA for the product's error -- sum the segment in
     // FFAcc and the segments in float-pair sums, which go to FP64 once per
     // thread: the sums match FP64 sums of the same FP32 fields to the order
-    // of the FP64 rounding (each segment is off by at most (7u)^2 of the sum
+    // of the FP64 rounding (each segment is off by at most (15u)^2 of the sum
     // of its |terms|, u = 2^-24, each float-pair addition by about u^2).
     double s_ph = 0.0, s_v = 0.0, s_w = 0.0, s_wy = 0.0, s_wv = 0.0;
     FFAcc f_ph, f_v, f_w, f_wy, f_wv;   // FP32 handles: the segments' sums, as float pairs
