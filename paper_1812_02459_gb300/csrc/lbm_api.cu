@@ -7,6 +7,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <mutex>
@@ -322,12 +323,16 @@ cudaEvent_t take_event(lbm_handle *h)
 }
 
 // Brackets one kernel launch with events when per-kernel timing is on.
+// Every pass of a step is launched inside a Timed: an NVTX range named for
+// the pass's kind (seen by a profiler that records NVTX; free otherwise)
+// and, while lbm_profile is on, CUDA events around the launch.
 struct Timed {
     lbm_handle *h;
     int kind;
     cudaEvent_t a = nullptr;
     Timed(lbm_handle *h_, int k) : h(h_), kind(k)
     {
+        nvtxRangePushA(lbm_kernel_name(k));
         if (h->prof) {
             a = take_event(h);
             cudaEventRecord(a, h->stream);
@@ -340,6 +345,7 @@ struct Timed {
             cudaEventRecord(b, h->stream);
             h->marks.push_back({kind, a, b});
         }
+        nvtxRangePop();
     }
 };
 
