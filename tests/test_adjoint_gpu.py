@@ -384,3 +384,21 @@ def test_adjoint_walls_refused_by_the_interpreter(monkeypatch):
         s.adjoint_end(s.fields()[0] - target)
     assert e.value.status == 1 and "walls" in str(e.value)
     s.close()
+
+
+@pytest.mark.parametrize("steps,every", [(1, 1), (3, 1), (2, 5)])
+def test_adjoint_degenerate_segments(steps, every):
+    """One step, a checkpoint at every step, and a segment longer than the
+    run: the FP64 sweep against the oracle adjoint."""
+    prm, fields, target = case()
+    loss, g, ds, dm = gpu_grad(prm, fields, target, steps, every, "fp64")
+    phi0 = T(fields[0]).requires_grad_(True)
+    sig = T(prm["sigma"]).requires_grad_(True)
+    M = T(prm["M"]).requires_grad_(True)
+    r = tr.run(prm, phi0, T(fields[1]), T(fields[2]), T(fields[3]), sig, M, steps)
+    lt = 0.5 * ((r["phi"] - T(target)) ** 2).sum()
+    gphi, gs, gm = torch.autograd.grad(lt, [phi0, sig, M])
+    assert loss == pytest.approx(lt.item(), rel=1e-12)
+    assert np.abs(g - gphi.numpy()).max() <= 1e-10 * np.abs(gphi.numpy()).max()
+    assert ds == pytest.approx(gs.item(), rel=1e-10)
+    assert dm == pytest.approx(gm.item(), rel=1e-10)
