@@ -255,6 +255,18 @@ lbm_status lbm_profile_read(lbm_handle *h, double *ms, long long *launches);
 const char *lbm_kernel_name(int kind);
 
 /*
+ * lbm_debug_violations -- in a library built with LBM_DEBUG (liblbm_debug.so,
+ * the debug build beside liblbm.so), every paired shared-memory access of the
+ * FP32 kernels is checked against the launch's dynamic shared memory; an
+ * access outside it is skipped and the first one recorded.  Synchronises
+ * the device and returns that record (block index in the high 32 bits,
+ * 1 + byte offset in the low ones), or 0 when every access was in bounds,
+ * and clears it.  ~0 if the device could not be read.  Always 0 in a
+ * release build, which checks nothing.
+ */
+unsigned long long lbm_debug_violations(void);
+
+/*
  * lbm_kernel_variant -- name of the kernel that lbm_step launches on this
  * handle for kernel kind `kind` (a static string; "none" for a filter of
  * order 0, "unknown" for a NULL handle or a kind outside 0..LBM_NKERNELS-1).

@@ -1163,6 +1163,19 @@ lbm_status lbm_profile_read(lbm_handle *h, double *ms, long long *launches)
     return LBM_OK;
 }
 
+unsigned long long lbm_debug_violations(void)
+{
+#ifdef LBM_DEBUG
+    unsigned long long v = 0, z = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return ~0ull;
+    if (cudaMemcpyFromSymbol(&v, g_lbm_debug, sizeof v) != cudaSuccess) return ~0ull;
+    cudaMemcpyToSymbol(g_lbm_debug, &z, sizeof z);
+    return v;
+#else
+    return 0;
+#endif
+}
+
 const char *lbm_kernel_name(int kind)
 {
     static const char *names[LBM_NKERNELS] = {"k_collide_stream", "k_rk_stage", "k_picard", "k_filter"};

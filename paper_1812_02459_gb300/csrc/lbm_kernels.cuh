@@ -1110,7 +1110,34 @@ __device__ __forceinline__ float2 pd2x(float2 l, float2 c, float2 r)
     return fma2(f2(4.0f / 3.0f), make_float2(l.y + c.y, c.x + r.x),
                 fma2(f2(-2.5f), c, mul2(f2(-1.0f / 12.0f), add2(l, r))));
 }
+#ifdef LBM_DEBUG
+// Debug builds (LBM_DEBUG) check every paired shared-memory access of the
+// FP32 kernels (lds2/sts2 on a pointer into shared memory; sts2 also
+// stores to global planes, which are not checked) against the launch's
+// dynamic shared memory.  An access outside it is not made (a load returns
+// zero) and the first one is recorded in g_lbm_debug: the block index in
+// the high 32 bits, 1 + the byte offset from the start of the dynamic
+// shared memory (two's complement, low 31 bits) in the low ones.
+static __device__ unsigned long long g_lbm_debug;
+extern __shared__ __align__(16) unsigned char lbm_dyn_smem[];
+__device__ __forceinline__ bool smem_in(const float *s, int i)
+{
+    if (!__isShared(s)) return true;   // a global plane
+    unsigned dyn;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    const long long off = (long long)(reinterpret_cast<const unsigned char *>(s + i) - lbm_dyn_smem);
+    if (off >= 0 && off + 8 <= (long long)dyn) return true;
+    const unsigned long long blk = blockIdx.x + (unsigned long long)gridDim.x * blockIdx.y;
+    atomicCAS(&g_lbm_debug, 0ull, (blk << 32) | (((unsigned long long)off & 0x7fffffffull) + 1ull));
+    return false;
+}
+__device__ __forceinline__ float2 lds2(const float *s, int i)
+{
+    return smem_in(s, i) ? *reinterpret_cast<const float2 *>(s + i) : make_float2(0.0f, 0.0f);
+}
+#else
 __device__ __forceinline__ float2 lds2(const float *s, int i) { return *reinterpret_cast<const float2 *>(s + i); }
+#endif
 // phi^{n+1} = phi_hi + r for the pair: returns the new phi_hi and writes the
 // new phi_lo to *lo.
 __device__ __forceinline__ float2 add_hi_lo(float2 h, float2 r, float *lo)
@@ -1119,7 +1146,14 @@ __device__ __forceinline__ float2 add_hi_lo(float2 h, float2 r, float *lo)
     *reinterpret_cast<float2 *>(lo) = make_float2(two_sum_err(h.x, r.x, s.x), two_sum_err(h.y, r.y, s.y));
     return s;
 }
+#ifdef LBM_DEBUG
+__device__ __forceinline__ void sts2(float *s, int i, float2 v)
+{
+    if (smem_in(s, i)) *reinterpret_cast<float2 *>(s + i) = v;
+}
+#else
 __device__ __forceinline__ void sts2(float *s, int i, float2 v) { *reinterpret_cast<float2 *>(s + i) = v; }
+#endif
 
 // Item it of a region of NP column pairs by NB bands of rows, numbered so
 // that the lanes of a warp share a band: the first 32 pairs of every band

@@ -49,7 +49,7 @@ EXPORTS = ("lbm_create", "lbm_step", "lbm_step_ch", "lbm_fields", "lbm_fields_de
            "lbm_profile", "lbm_profile_read", "lbm_kernel_name", "lbm_kernel_variant",
            "lbm_field_sums_noalloc", "lbm_noalloc_last_error",
            "lbm_adjoint_begin", "lbm_adjoint_end", "lbm_adjoint_engine",
-           "lbm_device_bytes", "lbm_destroy", "lbm_last_error")
+           "lbm_device_bytes", "lbm_destroy", "lbm_last_error", "lbm_debug_violations")
 LBM_NKERNELS = 4
 
 _lib = None
@@ -114,6 +114,8 @@ def load(path=None):
     L.lbm_destroy.argtypes = [vp]
     L.lbm_last_error.restype = C.c_char_p
     L.lbm_last_error.argtypes = [vp]
+    L.lbm_debug_violations.restype = C.c_ulonglong
+    L.lbm_debug_violations.argtypes = []
     if path is None:
         _lib = L
     return L
@@ -173,8 +175,8 @@ def field_sums_noalloc(phi, p, ux, uy, out, stream=None):
 class Sim:
     """A simulation on the GPU; host fields are float64 numpy arrays shaped [ny, nx]."""
 
-    def __init__(self, prm, phi0, p0, ux0, uy0, precision="fp32", stream=None):
-        self._lib = load()
+    def __init__(self, prm, phi0, p0, ux0, uy0, precision="fp32", stream=None, lib=None):
+        self._lib = lib if lib is not None else load()
         phi0, p0, ux0, uy0 = (_f64(a) for a in (phi0, p0, ux0, uy0))
         self.ny, self.nx = phi0.shape
         self.precision = precision

@@ -114,6 +114,7 @@ def test_null_handle_rejected_without_cuda():
     assert L.lbm_adjoint_end(None, pd, pd, pd, pd) == ARG
     assert L.lbm_adjoint_engine(None) == -1
     assert L.lbm_profile(None, 1) == ARG
+    assert L.lbm_debug_violations() == 0   # release build: nothing is checked
     L.lbm_destroy(None)
     assert L.lbm_diagnostics_async(None, pd) == ARG
     assert L.lbm_last_error(None) == b"NULL handle"
