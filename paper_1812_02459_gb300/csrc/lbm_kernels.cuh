@@ -1339,6 +1339,118 @@ struct PicardRow {
     float2 Dux, Uux, Duy, Uuy;  // u^k
 };
 
+// mu and grad phi of Sec. III.B Eq. dicretized over a region of NPA column
+// pairs x NRA rows (strips of VR1 rows).  s_phi points at the region's origin
+// less two columns and one row, with row stride SP; the outputs have row
+// stride WA from the region's origin.
+template <int NPA, int NRA, int VR1, int NT, int SP, int WA>
+__device__ __forceinline__ void picard_mu_grad(const KP<float> &P, const float *s_phi, float *s_mu, float *s_gx,
+                                               float *s_gy)
+{
+    static_assert(NRA % VR1 == 0 && SP % 2 == 0 && WA % 2 == 0, "strips must tile the region");
+    constexpr int NB = NRA / VR1, NI = NPA * NB;
+    const float2 fb = f2(4.0f * P.beta), nk = f2(-P.kappa);
+    for (int it = threadIdx.x; it < NI; it += NT) {
+        int pr, bd;
+        band_item<NPA, NB>(it, pr, bd);
+        const int lx = 2 * pr, r0 = bd * VR1;
+        float2 C[VR1 + 2], D[VR1 + 2], S[VR1 + 2];
+#pragma unroll
+        for (int k = 0; k < VR1 + 2; ++k) {
+            const int row = (r0 + k) * SP + lx + 2;
+            const float2 l = lds2(s_phi, row - 2), c = lds2(s_phi, row), r = lds2(s_phi, row + 2);
+            C[k] = c;
+            D[k] = make_float2(c.y - l.y, r.x - c.x);
+            S[k] = make_float2(c.y + l.y, r.x + c.x);
+        }
+#pragma unroll
+        for (int i = 0; i < VR1; ++i) {
+            const float2 gx = iso_dx(D[i], D[i + 1], D[i + 2]);
+            const float2 gy = fma2(f2(1.0f / 3.0f), sub2(C[i + 2], C[i]), mul2(f2(1.0f / 12.0f), sub2(S[i + 2], S[i])));
+            const float2 lap = fma2(f2(2.0f / 3.0f), add2(S[i + 1], add2(C[i + 2], C[i])),
+                                    fma2(f2(1.0f / 6.0f), add2(S[i + 2], S[i]), mul2(f2(-10.0f / 3.0f), C[i + 1])));
+            const float2 ph = C[i + 1];
+            const float2 mu = fma2(fb, sub2(mul2(mul2(ph, ph), ph), ph), mul2(nk, lap));
+            const int o = (r0 + i) * WA + lx;
+            sts2(s_mu, o, mu);
+            sts2(s_gx, o, gx);
+            sts2(s_gy, o, gy);
+        }
+    }
+}
+
+// One Picard sweep, u^{k+1} = j + F(u^k) / (2 rho) (Sec. III.B), over a
+// region of NP column pairs x NR rows with global origin (X0, Y0), in strips
+// of VR2 rows.  s_mu, s_gx, s_gy (row stride WA) and s_p, s_ux, s_uy (row
+// stride SA) point at the region's origin less two columns and one row;
+// s_phi (row stride SP) at the origin less four columns and two rows.  With
+// CLIP, pairs and rows outside the domain are skipped (an output region);
+// without, every node of the region is computed (a ring around a tile,
+// whose inputs were staged through the wrap/mirror map).
+// jf(i, ly, lx, X, Y, jx, jy) returns j at row i of the thread's strip
+// (region row ly, column lx, global X, Y); out(i, ly, lx, X, Y, ux, uy)
+// receives u^{k+1} there.
+template <int NP, int NR, int VR2, int NT, int WA, int SA, int SP, bool CLIP, typename JF, typename OUT>
+__device__ __forceinline__ void picard_sweep(const KP<float> &P, const float *s_mu, const float *s_gx,
+                                             const float *s_gy, const float *s_p, const float *s_ux,
+                                             const float *s_uy, const float *s_phi, int X0, int Y0, JF &&jf,
+                                             OUT &&out)
+{
+    static_assert(NR % VR2 == 0 && WA % 2 == 0 && SA % 2 == 0 && SP % 2 == 0, "strips must tile the region");
+    constexpr int NI = NP * (NR / VR2);
+    const float2 dr = f2(P.drho), drm = f2(P.drho * P.M), kap = f2(P.kappa);
+    for (int it = threadIdx.x; it < NI; it += NT) {
+        const int lx = 2 * (it % NP), r0 = (it / NP) * VR2;
+        const int X = X0 + lx;
+        if (CLIP && X >= P.nx) continue;
+        PicardRow rw[VR2 + 2];
+#pragma unroll
+        for (int k = 0; k < VR2 + 2; ++k) {
+            const int a = (r0 + k) * WA + lx + 2, au = (r0 + k) * SA + lx + 2;
+            iso_row(lds2(s_mu, a - 2), lds2(s_mu, a), lds2(s_mu, a + 2), rw[k].Dm, rw[k].Um);
+            const float2 gxl = lds2(s_gx, a - 2), gxc = lds2(s_gx, a), gxr = lds2(s_gx, a + 2);
+            const float2 gyl = lds2(s_gy, a - 2), gyc = lds2(s_gy, a), gyr = lds2(s_gy, a + 2);
+            float2 dummy;
+            iso_row(mul2(gyl, gyl), mul2(gyc, gyc), mul2(gyr, gyr), rw[k].Dxx, dummy);
+            const float2 m1 = f2(-1.0f);
+            iso_row(mul2(m1, mul2(gxl, gyl)), mul2(m1, mul2(gxc, gyc)), mul2(m1, mul2(gxr, gyr)), rw[k].Dxy,
+                    rw[k].Uxy);
+            iso_row(mul2(gxl, gxl), mul2(gxc, gxc), mul2(gxr, gxr), dummy, rw[k].Uyy);
+            iso_row(lds2(s_ux, au - 2), lds2(s_ux, au), lds2(s_ux, au + 2), rw[k].Dux, rw[k].Uux);
+            iso_row(lds2(s_uy, au - 2), lds2(s_uy, au), lds2(s_uy, au + 2), rw[k].Duy, rw[k].Uuy);
+            if (k < 2) continue;
+            // output row i = k - 2 from rows k - 2 (south), k - 1 (centre), k (north)
+            const int i = k - 2;
+            const int Y = Y0 + r0 + i;
+            if (CLIP && Y >= P.ny) break;
+            const PicardRow &sR = rw[k - 2], &cR = rw[k - 1], &nR = rw[k];
+            const float2 dmx = iso_dx(sR.Dm, cR.Dm, nR.Dm), dmy = sub2(nR.Um, sR.Um);
+            const float2 Fsx = mul2(kap, add2(iso_dx(sR.Dxx, cR.Dxx, nR.Dxx), sub2(nR.Uxy, sR.Uxy)));
+            const float2 Fsy = mul2(kap, add2(iso_dx(sR.Dxy, cR.Dxy, nR.Dxy), sub2(nR.Uyy, sR.Uyy)));
+            const float2 dxux = iso_dx(sR.Dux, cR.Dux, nR.Dux), dyux = sub2(nR.Uux, sR.Uux);
+            const float2 dxuy = iso_dx(sR.Duy, cR.Duy, nR.Duy), dyuy = sub2(nR.Uuy, sR.Uuy);
+            const int ac = (r0 + i + 1) * WA + lx + 2;
+            const float2 grx = mul2(dr, lds2(s_gx, ac)), gry = mul2(dr, lds2(s_gy, ac));
+            const float2 Jx = mul2(drm, dmx), Jy = mul2(drm, dmy);
+            const float2 pc = lds2(s_p, (r0 + i + 1) * SA + lx + 2);
+            const float2 ph = lds2(s_phi, (r0 + i + 2) * SP + lx + 4);
+            float2 rho, ir, nu;
+            rho_nu(P, ph.x, rho.x, ir.x, nu.x);
+            rho_nu(P, ph.y, rho.y, ir.y, nu.y);
+            const float2 Sxx = add2(dxux, dxux), Sxy = add2(dyux, dxuy), Syy = add2(dyuy, dyuy);
+            const float2 rg = sub2(rho, f2(P.g_rho_ref));
+            float2 Fx = fma2(rg, f2(P.gx), fma2(Jx, dxux, mul2(Jy, dyux)));
+            float2 Fy = fma2(rg, f2(P.gy), fma2(Jx, dxuy, mul2(Jy, dyuy)));
+            Fx = fma2(nu, fma2(Sxx, grx, mul2(Sxy, gry)), add2(Fx, fma2(mul2(m1, pc), grx, Fsx)));
+            Fy = fma2(nu, fma2(Sxy, grx, mul2(Syy, gry)), add2(Fy, fma2(mul2(m1, pc), gry, Fsy)));
+            const float2 hh = mul2(f2(0.5f), ir);
+            float2 jxv, jyv;
+            jf(i, r0 + i, lx, X, Y, jxv, jyv);
+            out(i, r0 + i, lx, X, Y, fma2(Fx, hh, jxv), fma2(Fy, hh, jyv));
+        }
+    }
+}
+
 // s_phi holds phi from (x0 - 4, y0 - 2) with row stride SP; s_p, s_ux, s_uy
 // hold p_hat, u^k from (x0 - 2, y0 - 1) with row stride SA; s_mu, s_gx, s_gy
 // are (TX + 4) x (TY + 2) work arrays.
@@ -1354,95 +1466,20 @@ __device__ __forceinline__ void picard_strips_body(const KP<float> &P, const flo
     constexpr int WA = G::WA, HA = G::HA;
     static_assert(TX % 2 == 0 && SP % 2 == 0 && SA % 2 == 0 && HA % VR1 == 0 && TY % VR2 == 0,
                   "strips must tile the regions");
-    {   // mu and grad phi on the (TX+4) x (TY+2) region
-        constexpr int NP = WA / 2, NB = HA / VR1, NI = NP * NB;
-        const float2 fb = f2(4.0f * P.beta), nk = f2(-P.kappa);
-        for (int it = threadIdx.x; it < NI; it += NT) {
-            int pr, bd;
-            band_item<NP, NB>(it, pr, bd);
-            const int lx = 2 * pr, r0 = bd * VR1;
-            float2 C[VR1 + 2], D[VR1 + 2], S[VR1 + 2];
-#pragma unroll
-            for (int k = 0; k < VR1 + 2; ++k) {
-                const int row = (r0 + k) * SP + lx + 2;
-                const float2 l = lds2(s_phi, row - 2), c = lds2(s_phi, row), r = lds2(s_phi, row + 2);
-                C[k] = c;
-                D[k] = make_float2(c.y - l.y, r.x - c.x);
-                S[k] = make_float2(c.y + l.y, r.x + c.x);
-            }
-#pragma unroll
-            for (int i = 0; i < VR1; ++i) {
-                const float2 gx = iso_dx(D[i], D[i + 1], D[i + 2]);
-                const float2 gy = fma2(f2(1.0f / 3.0f), sub2(C[i + 2], C[i]), mul2(f2(1.0f / 12.0f), sub2(S[i + 2], S[i])));
-                const float2 lap = fma2(f2(2.0f / 3.0f), add2(S[i + 1], add2(C[i + 2], C[i])),
-                                        fma2(f2(1.0f / 6.0f), add2(S[i + 2], S[i]), mul2(f2(-10.0f / 3.0f), C[i + 1])));
-                const float2 ph = C[i + 1];
-                const float2 mu = fma2(fb, sub2(mul2(mul2(ph, ph), ph), ph), mul2(nk, lap));
-                const int o = (r0 + i) * WA + lx;
-                sts2(s_mu, o, mu);
-                sts2(s_gx, o, gx);
-                sts2(s_gy, o, gy);
-            }
-        }
-    }
+    // mu and grad phi on the (TX+4) x (TY+2) region
+    picard_mu_grad<WA / 2, HA, VR1, NT, SP, WA>(P, s_phi, s_mu, s_gx, s_gy);
     __syncthreads();
-
-    {   // u^{k+1} = j + F(u^k) / (2 rho) on the tile
-        constexpr int NP = TX / 2, NI = NP * (TY / VR2);
-        const float2 dr = f2(P.drho), drm = f2(P.drho * P.M), kap = f2(P.kappa);
-        for (int it = threadIdx.x; it < NI; it += NT) {
-            const int lx = 2 * (it % NP), r0 = (it / NP) * VR2;
-            const int X = x0 + lx;
-            if (X >= P.nx) continue;
-            PicardRow rw[VR2 + 2];
-#pragma unroll
-            for (int k = 0; k < VR2 + 2; ++k) {
-                const int a = (r0 + k) * WA + lx + 2, au = (r0 + k) * SA + lx + 2;
-                iso_row(lds2(s_mu, a - 2), lds2(s_mu, a), lds2(s_mu, a + 2), rw[k].Dm, rw[k].Um);
-                const float2 gxl = lds2(s_gx, a - 2), gxc = lds2(s_gx, a), gxr = lds2(s_gx, a + 2);
-                const float2 gyl = lds2(s_gy, a - 2), gyc = lds2(s_gy, a), gyr = lds2(s_gy, a + 2);
-                float2 dummy;
-                iso_row(mul2(gyl, gyl), mul2(gyc, gyc), mul2(gyr, gyr), rw[k].Dxx, dummy);
-                const float2 m1 = f2(-1.0f);
-                iso_row(mul2(m1, mul2(gxl, gyl)), mul2(m1, mul2(gxc, gyc)), mul2(m1, mul2(gxr, gyr)), rw[k].Dxy,
-                        rw[k].Uxy);
-                iso_row(mul2(gxl, gxl), mul2(gxc, gxc), mul2(gxr, gxr), dummy, rw[k].Uyy);
-                iso_row(lds2(s_ux, au - 2), lds2(s_ux, au), lds2(s_ux, au + 2), rw[k].Dux, rw[k].Uux);
-                iso_row(lds2(s_uy, au - 2), lds2(s_uy, au), lds2(s_uy, au + 2), rw[k].Duy, rw[k].Uuy);
-                if (k < 2) continue;
-                // output row i = k - 2 from rows k - 2 (south), k - 1 (centre), k (north)
-                const int i = k - 2;
-                const int Y = y0 + r0 + i;
-                if (Y >= P.ny) break;
-                const PicardRow &sR = rw[k - 2], &cR = rw[k - 1], &nR = rw[k];
-                const float2 dmx = iso_dx(sR.Dm, cR.Dm, nR.Dm), dmy = sub2(nR.Um, sR.Um);
-                const float2 Fsx = mul2(kap, add2(iso_dx(sR.Dxx, cR.Dxx, nR.Dxx), sub2(nR.Uxy, sR.Uxy)));
-                const float2 Fsy = mul2(kap, add2(iso_dx(sR.Dxy, cR.Dxy, nR.Dxy), sub2(nR.Uyy, sR.Uyy)));
-                const float2 dxux = iso_dx(sR.Dux, cR.Dux, nR.Dux), dyux = sub2(nR.Uux, sR.Uux);
-                const float2 dxuy = iso_dx(sR.Duy, cR.Duy, nR.Duy), dyuy = sub2(nR.Uuy, sR.Uuy);
-                const int ac = (r0 + i + 1) * WA + lx + 2;
-                const float2 grx = mul2(dr, lds2(s_gx, ac)), gry = mul2(dr, lds2(s_gy, ac));
-                const float2 Jx = mul2(drm, dmx), Jy = mul2(drm, dmy);
-                const float2 pc = lds2(s_p, (r0 + i + 1) * SA + lx + 2);
-                const float2 ph = lds2(s_phi, (r0 + i + 2) * SP + lx + 4);
-                float2 rho, ir, nu;
-                rho_nu(P, ph.x, rho.x, ir.x, nu.x);
-                rho_nu(P, ph.y, rho.y, ir.y, nu.y);
-                const float2 Sxx = add2(dxux, dxux), Sxy = add2(dyux, dxuy), Syy = add2(dyuy, dyuy);
-                const float2 rg = sub2(rho, f2(P.g_rho_ref));
-                float2 Fx = fma2(rg, f2(P.gx), fma2(Jx, dxux, mul2(Jy, dyux)));
-                float2 Fy = fma2(rg, f2(P.gy), fma2(Jx, dxuy, mul2(Jy, dyuy)));
-                Fx = fma2(nu, fma2(Sxx, grx, mul2(Sxy, gry)), add2(Fx, fma2(mul2(m1, pc), grx, Fsx)));
-                Fy = fma2(nu, fma2(Sxy, grx, mul2(Syy, gry)), add2(Fy, fma2(mul2(m1, pc), gry, Fsy)));
-                const float2 hh = mul2(f2(0.5f), ir);
-                const long long gidx = (long long)Y * P.nx + X;
-                float2 jxv, jyv;
-                jf(i, r0 + i, lx, gidx, jxv, jyv);
-                *reinterpret_cast<float2 *>(&uox[gidx]) = fma2(Fx, hh, jxv);
-                *reinterpret_cast<float2 *>(&uoy[gidx]) = fma2(Fy, hh, jyv);
-            }
-        }
-    }
+    // u^{k+1} = j + F(u^k) / (2 rho) on the tile
+    picard_sweep<TX / 2, TY, VR2, NT, WA, SA, SP, true>(
+        P, s_mu, s_gx, s_gy, s_p, s_ux, s_uy, s_phi, x0, y0,
+        [&](int i, int ly, int lx, int X, int Y, float2 &a, float2 &b) {
+            jf(i, ly, lx, (long long)Y * P.nx + X, a, b);
+        },
+        [&](int, int, int, int X, int Y, float2 vx, float2 vy) {
+            const long long gidx = (long long)Y * P.nx + X;
+            *reinterpret_cast<float2 *>(&uox[gidx]) = vx;
+            *reinterpret_cast<float2 *>(&uoy[gidx]) = vy;
+        });
 }
 
 template <int TX, int TY, int NT, int VR1, int VR2>

@@ -105,6 +105,21 @@ def test_even_width_fp32(nx, ny, px, py):
     assert_parity(o, g, TOL["fp32"])
 
 
+@pytest.mark.parametrize("picard", [1, 2, 3, 4])
+def test_tma_picard_sweeps_walls_fp32(picard):
+    """One to four Picard sweeps through the TMA kernels: walls on both axes,
+    tiles ragged in both axes, tiles whose windows lie inside the grid beside
+    edge tiles, flow at the walls."""
+    nx, ny = 200, 37
+    prm = inputs.base_params(rho_H=20.0, sigma=5e-3, gx=1e-6, gy=-2e-6, picard_iters=picard, periodic_x=0,
+                             periodic_y=0)
+    phi = inputs.drop(nx, ny, 9.0, 12.3, 11.6, prm["W"])
+    z = np.zeros_like(phi)
+    o, g = run_both(prm, (phi, z, z, z), 200, "fp32")
+    assert g.kernel_variants()["k_picard"] == "k_picard_tma"
+    assert_parity(o, g, TOL["fp32"])
+
+
 @pytest.mark.parametrize("order,picard,flux", [(0, 2, 1), (5, 1, 1), (7, 3, 1), (9, 2, 1), (11, 2, 0)])
 def test_even_width_filter_orders_sweeps_fp32(order, picard, flux):
     """Every filter radius, Picard sweep count and the variant without the
