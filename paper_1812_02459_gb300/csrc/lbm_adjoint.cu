@@ -939,12 +939,19 @@ template <typename T> struct Engine {
             } else if (d.k == OP_STENCIL) {
                 const Stencil &St = stencils[d.st];
                 o += "            T r = T(0);\n";
+                std::string plain;
                 for (int i = 0; i < St.n; ++i)
-                    o += "            r += " + A.c(St.w[i]) + " * " +
-                         (walls() ? "wtap(" + A.p(d.in[0]) + " + voff + base, x, y, " + S(St.dx[i]) + ", " + S(St.dy[i]) +
-                                        ", nx, ny, T(" + S(d.sgx) + "), T(" + S(d.sgy) + "))"
-                                  : ld.get(A, d.in[0], St.dx[i], St.dy[i], true, "voff + base")) +
-                         ";\n";
+                    plain += "            r += " + A.c(St.w[i]) + " * " +
+                             ld.get(A, d.in[0], St.dx[i], St.dy[i], true, "voff + base") + ";\n";
+                if (walls()) {   // interior nodes: every tap inside, no mirror
+                    o += "            if (inner) {\n" + plain + "            } else {\n";
+                    for (int i = 0; i < St.n; ++i)
+                        o += "            r += " + A.c(St.w[i]) + " * wtap(" + A.p(d.in[0]) + " + voff + base, x, y, " +
+                             S(St.dx[i]) + ", " + S(St.dy[i]) + ", nx, ny, T(" + S(d.sgx) + "), T(" + S(d.sgy) + "));\n";
+                    o += "            }\n";
+                } else {
+                    o += plain;
+                }
             } else {
                 for (int i = 0; i < d.nin; ++i)
                     o += "            const T v" + S(i) + " = " +
@@ -976,7 +983,7 @@ template <typename T> struct Engine {
              "        int x, y;\n"
              "        long long k;\n"
              "        if (!tile_node(t, tiles_x, tpp, nx, ny, N, x, y, k)) continue;\n"
-             "        const long long base = k - ((long long)y * nx + x);\n";
+             "        const long long base = k - ((long long)y * nx + x);\n" + inner_flag();
         for (int q = 0; q < G.slots; ++q) f += "        T f" + S(q) + " = T(0);\n";
         return f + b + "    }\n}\n";
     }
@@ -1003,12 +1010,19 @@ template <typename T> struct Engine {
             } else if (o.k == OP_STENCIL) {   // transpose: gathered from the output adjoint around the node
                 const Stencil &St = stencils[o.st];
                 b += "            T c0 = T(0);\n";
+                std::string plain;
                 for (int i = 0; i < St.n; ++i)
-                    b += "            c0 += " + A.c(St.w[i]) + " * " +
-                         (walls() ? "wadj(" + A.p(d.aout) + ", x, y, " + S(-St.dx[i]) + ", " + S(-St.dy[i]) +
-                                        ", nx, ny, T(" + S(o.sgx) + "), T(" + S(o.sgy) + "))"
-                                  : ld.get(A, d.aout, -St.dx[i], -St.dy[i], true, "0")) +
-                         ";\n";
+                    plain += "            c0 += " + A.c(St.w[i]) + " * " + ld.get(A, d.aout, -St.dx[i], -St.dy[i], true, "0") +
+                             ";\n";
+                if (walls()) {   // interior nodes: no mirror image lies in the domain
+                    b += "            if (inner) {\n" + plain + "            } else {\n";
+                    for (int i = 0; i < St.n; ++i)
+                        b += "            c0 += " + A.c(St.w[i]) + " * wadj(" + A.p(d.aout) + ", x, y, " + S(-St.dx[i]) +
+                             ", " + S(-St.dy[i]) + ", nx, ny, T(" + S(o.sgx) + "), T(" + S(o.sgy) + "));\n";
+                    b += "            }\n";
+                } else {
+                    b += plain;
+                }
             } else {
                 b += "            T g = " + (d.aout ? ld.get(A, d.aout, 0, 0, false, "0") : std::string("T(0)")) +
                      (d.rout >= 0 ? " + s" + S(d.rout) : std::string("")) + ";\n";
@@ -1053,7 +1067,7 @@ template <typename T> struct Engine {
              "    for (long long t = blockIdx.x; t < tpp; t += gridDim.x) {\n"
              "        int x, y;\n"
              "        long long k;\n"
-             "        if (!tile_node(t, tiles_x, tpp, nx, ny, N, x, y, k)) continue;\n";
+             "        if (!tile_node(t, tiles_x, tpp, nx, ny, N, x, y, k)) continue;\n" + inner_flag();
         for (int q = 0; q < nslots; ++q) f += "        T s" + S(q) + " = T(0);\n";
         f += b + "    }\n";
         if (pgr) f += "    pgrad_add(q0, q1, q2, q3, pgrad);\n";
@@ -1099,6 +1113,23 @@ template <typename T> struct Engine {
             "                              wext(p, xh, yh, nx, ny));\n"
             "    }\n"
             "    return acc;\n}\n";
+    }
+
+    // Declaration of `inner` in a walled tape's kernels: the node lies at
+    // least the stencils' reach from every wall, so every tap of a stencil
+    // lands inside the domain and no mirror image of a transposed tap does
+    // (wtap and wadj reduce there to the plain tap, bit for bit).
+    std::string inner_flag() const
+    {
+        if (!walls()) return "";
+        int rx = 0, ry = 0;
+        for (const Stencil &St : stencils)
+            for (int i = 0; i < St.n; ++i) {
+                rx = std::max(rx, std::abs(St.dx[i]));
+                ry = std::max(ry, std::abs(St.dy[i]));
+            }
+        return "        const bool inner = (!WX || (x >= " + S(rx) + " && x < nx - " + S(rx) + ")) && (!WY || (y >= " +
+               S(ry) + " && y < ny - " + S(ry) + "));\n";
     }
 
     // Write the schedule out as compiled level kernels (unless switched off
