@@ -242,9 +242,12 @@ lbm_status lbm_set_state(lbm_handle *h, const double *f, const double *g, const 
 
 /*
  * Per-kernel device timing (a tracing aid, not part of the method).
- * lbm_profile(h, 1) clears the totals and starts recording a pair of CUDA
- * events around every kernel launch that lbm_step issues; lbm_profile(h, 0)
- * stops.  lbm_profile_read fills ms[k] (total device milliseconds) and
+ * lbm_profile(h, 1) clears the totals and starts recording CUDA events
+ * around every kernel launch that lbm_step issues: within one lbm_step call
+ * a launch that directly follows another starts at that one's end event, so
+ * a step records one event per launch boundary (a launch's time then
+ * includes the gap before it); lbm_profile(h, 0) stops.  lbm_profile_read
+ * fills ms[k] (total device milliseconds) and
  * launches[k] for each kernel kind k < LBM_NKERNELS, summed since recording
  * started; it synchronises the stream.  Kinds: 0 collide+stream,
  * 1 RK3 stage, 2 Picard sweep, 3 filter.

@@ -330,12 +330,18 @@ struct Timed {
     lbm_handle *h;
     int kind;
     cudaEvent_t a = nullptr;
+    bool own = true;
     Timed(lbm_handle *h_, int k) : h(h_), kind(k)
     {
         nvtxRangePushA(lbm_kernel_name(k));
         if (h->prof) {
-            a = take_event(h);
-            cudaEventRecord(a, h->stream);
+            if (h->chain_ok && h->chain) {
+                a = h->chain;
+                own = false;
+            } else {
+                a = take_event(h);
+                cudaEventRecord(a, h->stream);
+            }
         }
     }
     ~Timed()
@@ -343,7 +349,8 @@ struct Timed {
         if (h->prof && a) {
             cudaEvent_t b = take_event(h);
             cudaEventRecord(b, h->stream);
-            h->marks.push_back({kind, a, b});
+            h->marks.push_back({kind, a, b, own});
+            h->chain = b;
         }
         nvtxRangePop();
     }
@@ -535,6 +542,7 @@ lbm_status step_impl(lbm_handle *h)
         CK(h, cudaMemcpyAsync(pf, phat, b, cudaMemcpyDeviceToDevice, st), "copy p");
         CK(h, cudaMemcpyAsync(uxp, uhx, b, cudaMemcpyDeviceToDevice, st), "copy ux");
         CK(h, cudaMemcpyAsync(uyp, uhy, b, cudaMemcpyDeviceToDevice, st), "copy uy");
+        h->chain = nullptr;   // the next launch does not directly follow a timed one
     }
     }
     CK(h, cudaGetLastError(), "kernel launch");
@@ -1004,6 +1012,11 @@ lbm_status lbm_step(lbm_handle *h, int n)
     if (h->chk_status == LBM_ERR_NONFINITE) return fail(h, h->chk_status, "periodic check: non-finite field value");
     if (h->chk_status == LBM_ERR_RANGE) return fail(h, h->chk_status, "periodic check: phi outside [-1-delta, 1+delta]");
     if (n > 0) h->fresh_init = false;
+    struct Chain {   // timed launches share boundary events only inside this call
+        lbm_handle *h;
+        explicit Chain(lbm_handle *h_) : h(h_) { h->chain = nullptr; h->chain_ok = true; }
+        ~Chain() { h->chain = nullptr; h->chain_ok = false; }
+    } chain(h);
     return dispatch(h->grid.precision, [&](auto tp, auto sp) {
         TS_TYPES(tp, sp);
         for (int t = 0; t < n; ++t) {
@@ -1014,6 +1027,7 @@ lbm_status lbm_step(lbm_handle *h, int n)
                 if (st) return st;
                 CK(h, cudaEventRecord(h->chk_ev, h->stream), "check event");
                 h->chk_pending = true;
+                h->chain = nullptr;
             }
         }
         return LBM_OK;
@@ -1135,8 +1149,12 @@ lbm_status lbm_profile(lbm_handle *h, int on)
     if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
     if (on) {
         CK(h, cudaStreamSynchronize(h->stream), "profile sync");
-        for (auto &m : h->marks) { h->pool.push_back(m.a); h->pool.push_back(m.b); }
+        for (auto &m : h->marks) {
+            if (m.own_a) h->pool.push_back(m.a);
+            h->pool.push_back(m.b);
+        }
         h->marks.clear();
+        h->chain = nullptr;
         for (int k = 0; k < LBM_NKERNELS; ++k) { h->prof_ms[k] = 0.0; h->prof_n[k] = 0; }
     }
     h->prof = on != 0;
@@ -1152,10 +1170,11 @@ lbm_status lbm_profile_read(lbm_handle *h, double *ms, long long *launches)
         CK(h, cudaEventElapsedTime(&t, m.a, m.b), "cudaEventElapsedTime");
         h->prof_ms[m.kind] += t;
         h->prof_n[m.kind] += 1;
-        h->pool.push_back(m.a);
+        if (m.own_a) h->pool.push_back(m.a);
         h->pool.push_back(m.b);
     }
     h->marks.clear();
+    h->chain = nullptr;
     for (int k = 0; k < LBM_NKERNELS; ++k) {
         if (ms) ms[k] = h->prof_ms[k];
         if (launches) launches[k] = h->prof_n[k];
@@ -1205,7 +1224,10 @@ void lbm_destroy(lbm_handle *h)
 {
     if (!h) return;
     lbm_internal_adjoint_free(h);
-    for (auto &m : h->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+    for (auto &m : h->marks) {
+        if (m.own_a) cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
     for (auto e : h->pool) cudaEventDestroy(e);
     if (h->chk_ev) cudaEventDestroy(h->chk_ev);
     if (h->chk_host) cudaFreeHost(h->chk_host);

@@ -37,9 +37,13 @@ struct lbm_handle {
     int diag_blocks = 1;
     lbm::KP<double> kpd{};
     lbm::KP<float> kpf{};
-    // per-kernel timing
+    // per-kernel timing; inside lbm_step a launch that directly follows
+    // another timed launch starts at that one's end event (chain), so a
+    // step records one event per launch boundary
     bool prof = false;
-    struct Mark { int kind; cudaEvent_t a, b; };
+    bool chain_ok = false;
+    cudaEvent_t chain = nullptr;
+    struct Mark { int kind; cudaEvent_t a, b; bool own_a; };
     std::vector<Mark> marks;
     std::vector<cudaEvent_t> pool;
     double prof_ms[LBM_NKERNELS]{};
