@@ -2301,6 +2301,7 @@ __device__ __forceinline__ double warp_min(double v)
 }
 
 constexpr int DSEG = 16;  // nodes a thread sums before adding to its sums
+static_assert(DSEG % 2 == 0, "whole segments are summed as node pairs");
 
 // A float accumulator carried as an unevaluated sum hi + lo (Knuth's TwoSum
 // after every addition): a segment of FP32 terms is summed without rounding
@@ -2333,6 +2334,29 @@ struct FFAcc {
         add(t);
     }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Two FFAcc side by side in paired FP32 (one lane per node of a pair).
+struct FFAcc2 {
+    float2 hi = make_float2(0.0f, 0.0f), lo = make_float2(0.0f, 0.0f);
+    __device__ __forceinline__ void add(float2 x)
+    {
+        const float2 s = add2(hi, x);
+        const float2 bp = sub2(s, hi), ap = sub2(s, bp);
+        lo = add2(lo, add2(sub2(hi, ap), sub2(x, bp)));   // TwoSum error, lane by lane
+        hi = s;
+    }
+    // the two lanes' sums, as one float pair
+    __device__ __forceinline__ FFAcc merged() const
+    {
+        FFAcc a, b;
+        a.hi = hi.x;
+        a.lo = lo.x;
+        b.hi = hi.y;
+        b.lo = lo.y;
+        a.add(b);
+        return a;
+    }
 };
 
 template <typename T>
@@ -2376,6 +2400,47 @@ k_diag_partial(int nx, int ny, const T *__restrict__ phi, const T *__restrict__ 
             }
             if constexpr (std::is_same<T, float>::value) {
                 FFAcc a_ph, a_v, a_w, a_wv;
+                if (xs + (DSEG - 1) * (int)blockDim.x < nx) {
+                    // a whole segment: nodes u and u + 1 as the two lanes of
+                    // paired FP32, the same terms as below; the finiteness of
+                    // every value is tested at once by a running sum of x - x
+                    // (0 for every finite x), counted one by one only when
+                    // that sum is NaN
+                    FFAcc2 b_ph, b_v, b_w, b_wv;
+                    float2 nan_acc = f2(0.0f);
+                    const float2 one = f2(1.0f), half = f2(0.5f), m1 = f2(-1.0f);
+#pragma unroll
+                    for (int u = 0; u < DSEG; u += 2) {
+                        const float2 P = make_float2(ph[u], ph[u + 1]), V = make_float2(v[u], v[u + 1]);
+                        const float2 Q = make_float2(pp[u], pp[u + 1]), U = make_float2(uu[u], uu[u + 1]);
+                        const float2 om = sub2(one, P), mP = mul2(m1, P);
+                        const float2 bp = sub2(om, one), ap = sub2(om, bp);
+                        const float2 w = mul2(half, om);
+                        const float2 wl = mul2(half, add2(sub2(one, ap), sub2(mP, bp)));   // w + wl = (1 - phi)/2
+                        const float2 wv = mul2(w, V);
+                        b_ph.add(P);
+                        b_w.add(w);
+                        b_w.lo = add2(b_w.lo, wl);
+                        b_wv.add(wv);
+                        b_wv.lo = add2(b_wv.lo, add2(fma2(w, V, mul2(m1, wv)), mul2(wl, V)));
+                        b_v.add(make_float2(P.x < 0.0f ? V.x : 0.0f, P.y < 0.0f ? V.y : 0.0f));
+                        npos += (int)(P.x > 0.0f) + (int)(P.y > 0.0f);
+                        nneg += (int)(P.x < 0.0f) + (int)(P.y < 0.0f);
+                        mx = fmax(mx, fmax(P.x, P.y));
+                        mn = fmin(mn, fmin(P.x, P.y));
+                        nan_acc = add2(nan_acc, add2(add2(sub2(P, P), sub2(V, V)), add2(sub2(Q, Q), sub2(U, U))));
+                    }
+                    if (isnan(nan_acc.x) || isnan(nan_acc.y)) {
+#pragma unroll
+                        for (int u = 0; u < DSEG; ++u)
+                            n_bad += (int)!isfinite(ph[u]) + (int)!isfinite(pp[u]) + (int)!isfinite(uu[u]) +
+                                     (int)!isfinite(v[u]);
+                    }
+                    a_ph = b_ph.merged();
+                    a_v = b_v.merged();
+                    a_w = b_w.merged();
+                    a_wv = b_wv.merged();
+                } else {   // the last, partial segment of a row
 #pragma unroll
                 for (int u = 0; u < DSEG; ++u) {
                     if (xs + u * blockDim.x >= nx) break;
@@ -2395,6 +2460,7 @@ k_diag_partial(int nx, int ny, const T *__restrict__ phi, const T *__restrict__ 
                     mx = fmax(mx, ph[u]);
                     mn = fmin(mn, ph[u]);
                     n_bad += (int)!isfinite(ph[u]) + (int)!isfinite(pp[u]) + (int)!isfinite(uu[u]) + (int)!isfinite(v[u]);
+                }
                 }
                 // the segment into the thread's float-pair sums (FP32 arithmetic:
                 // FP64 is a small fraction of the FP32 rate on this GPU)

@@ -245,6 +245,49 @@ def test_diagnostics_async_matches_sync():
         a.fields(out=[np.empty((48, 96))] * 4)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "mix_bf16"])
+def test_diagnostics_wide_rows_against_fp64_sums(precision):
+    """Rows wider than a diagnostics block's piece of 4096 nodes: whole
+    16-node segments are summed as node pairs, the last piece of a row node by
+    node.  Against FP64 sums (torch) of the same FP32 values read back with
+    lbm_fields_device: sums to 1e-12 of n + |sum|, counts and extrema exact,
+    with a NaN and an Inf planted in whole segments and one NaN in a partial
+    one (in p and u_x, which enter only the count), then again after 3 steps
+    on finite fields."""
+    import torch
+    nx, ny = 8200, 24
+    phi, p, ux, uy = inputs.random_fields(nx, ny, seed=11, u_amp=1e-2, p_amp=1e-3)
+    prm = inputs.base_params(rho_H=10.0, sigma=1e-3)
+    for case in range(2):
+        if case == 0:
+            p, ux, uy = p.copy(), ux.copy(), uy.copy()
+            p[3, 5000] = np.nan
+            ux[10, 100] = np.inf
+            p[20, 8195] = np.nan   # p and u_x enter only the count
+            g = lbm.Sim(prm, phi, p, ux, uy, precision=precision)
+        else:
+            g = lbm.Sim(prm, *inputs.random_fields(nx, ny, seed=11, u_amp=1e-2, p_amp=1e-3), precision=precision)
+            g.step(3)
+        got = g.diagnostics()
+        t = [torch.empty((ny, nx), dtype=torch.float32, device="cuda") for _ in range(4)]
+        g.fields_device(*t)
+        torch.cuda.synchronize()
+        ph, v = t[0].double(), t[3].double()
+        yy = torch.arange(ny, device="cuda", dtype=torch.float64).view(ny, 1).expand(ny, nx)
+        w = (1.0 - ph) * 0.5
+        neg = ph < 0
+        ref = [ph.sum(), (ph > 0).sum(), neg.sum(), yy[neg].sum(), v[neg].sum(), w.sum(), (w * yy).sum(),
+               (w * v).sum(), ph.max(), ph.min(), sum((~torch.isfinite(a)).sum() for a in t)]
+        ref = [float(a) for a in ref]
+        n = nx * ny
+        for k in (0, 3, 4, 5, 6, 7):
+            assert abs(got[k] - ref[k]) <= 1e-12 * (n + abs(ref[k])), (case, k, got[k], ref[k])
+        for k in (1, 2, 8, 9, 10):
+            assert got[k] == ref[k], (case, k, got[k], ref[k])
+        assert got[10] == (3 if case == 0 else 0)
+        g.close()
+
+
 def test_zero_steps_and_conservation_fp32():
     prm, fields = inputs.static_drop(n=40, R=10.0)
     g = lbm.Sim(prm, *fields, precision="fp32")
