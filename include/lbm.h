@@ -60,6 +60,11 @@ typedef enum {
     LBM_MIX_BF16 = 2,       /* populations stored as bf16, arithmetic in float */
     LBM_MIX_FP16 = 3        /* populations stored as fp16, arithmetic in float */
 } lbm_precision;
+/* The 16-bit words hold f_1..f_8 and g_q - w_q (3 p_hat + s_q(u^n)), the NS
+ * populations less their equilibrium (Sec. III.B Eq. geq) at the node's
+ * post-stream p_hat and the velocity u^n they were collided with; the rest
+ * populations come from the FP32 moments (phi_bar, p_hat).  lbm_get_state /
+ * lbm_set_state decode and encode this form. */
 
 typedef struct {
     int nx, ny;             /* nodes per axis, each >= LBM_MIN_EXTENT */

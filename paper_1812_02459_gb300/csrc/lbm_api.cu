@@ -774,14 +774,17 @@ template <typename S> S host_store(float v) { return S(v); }
 template <> __half host_store<__half>(float v) { return __float2half_rn(v * 16384.0f); }
 
 // Rebuild full population sets on the host from reduced-precision storage:
-// f_q, g_q - 3 w_q p_hat stored for q = 1..8; f_0, g_0 from the moments
-// (phi_bar = phi of the previous step + dbar).
+// f_q and g_q - w_q (3 p_hat + s_q(u^n)) stored for q = 1..8, u^n in the
+// u^{n-1} slot; f_0, g_0 from the moments (phi_bar = phi of the previous
+// step + dbar).
 template <typename T, typename S>
 lbm_status decode_mixed(lbm_handle *h, double *f, double *g)
 {
     const size_t n = (size_t)h->N;
     std::vector<S> fs(9 * n), gs(9 * n);
-    std::vector<T> pb(n), db(n), ph(n);
+    std::vector<T> pb(n), db(n), ph(n), u0(n), u1(n);
+    CK(h, cudaMemcpyAsync(u0.data(), h->ux[1 - h->ucur], n * sizeof(T), cudaMemcpyDeviceToHost, h->stream), "state");
+    CK(h, cudaMemcpyAsync(u1.data(), h->uy[1 - h->ucur], n * sizeof(T), cudaMemcpyDeviceToHost, h->stream), "state");
     CK(h, cudaMemcpyAsync(fs.data(), h->f[h->cur], 9 * n * sizeof(S), cudaMemcpyDeviceToHost, h->stream), "state");
     CK(h, cudaMemcpyAsync(gs.data(), h->g[h->cur], 9 * n * sizeof(S), cudaMemcpyDeviceToHost, h->stream), "state");
     CK(h, cudaMemcpyAsync(pb.data(), h->phi[1 - h->pcur], n * sizeof(T), cudaMemcpyDeviceToHost, h->stream), "state");
@@ -793,7 +796,7 @@ lbm_status decode_mixed(lbm_handle *h, double *f, double *g)
         T sf = T(0), sg = T(0);
         for (int q = 1; q < 9; ++q) {
             const T fq = (T)host_load<S>(fs[q * n + k]);
-            const T gq = (T)host_load<S>(gs[q * n + k]) + T(3) * (T)(float)kW[q] * ph[k];
+            const T gq = (T)host_load<S>(gs[q * n + k]) + (T)(float)kW[q] * (T(3) * ph[k] + s_eq(q, u0[k], u1[k]));
             if (f) f[q * n + k] = fq;
             if (g) g[q * n + k] = gq;
             sf += fq;
@@ -806,9 +809,12 @@ lbm_status decode_mixed(lbm_handle *h, double *f, double *g)
 }
 
 // The stored populations are collided next against phi (given to both phi
-// slots), so their sum enters as dbar = sum f - phi.
+// slots), so their sum enters as dbar = sum f - phi; g is stored less its
+// equilibrium at (p_hat, u^{n-1} of the state), the velocity the next step
+// adds back.
 template <typename T, typename S>
-lbm_status encode_mixed(lbm_handle *h, const double *f, const double *g, const double *phi)
+lbm_status encode_mixed(lbm_handle *h, const double *f, const double *g, const double *phi, const double *upx,
+                        const double *upy)
 {
     const size_t n = (size_t)h->N;
     std::vector<S> fs(9 * n), gs(9 * n);
@@ -825,7 +831,8 @@ lbm_status encode_mixed(lbm_handle *h, const double *f, const double *g, const d
         gs[k] = host_store<S>(0.0f);
         for (int q = 1; q < 9; ++q) {
             fs[q * n + k] = host_store<S>((float)f[q * n + k]);
-            gs[q * n + k] = host_store<S>((float)((T)g[q * n + k] - T(3) * (T)(float)kW[q] * ph[k]));
+            gs[q * n + k] = host_store<S>(
+                (float)((T)g[q * n + k] - (T)(float)kW[q] * (T(3) * ph[k] + s_eq(q, (T)upx[k], (T)upy[k]))));
         }
     }
     CK(h, cudaMemcpyAsync(h->f[0], fs.data(), 9 * n * sizeof(S), cudaMemcpyHostToDevice, h->stream), "state");
@@ -867,7 +874,7 @@ lbm_status set_state_impl(lbm_handle *h, const double *f, const double *g, const
     h->ucur = 0;
     h->acur = 0;
     if (Mixed<T, S>::on) {
-        if ((st = encode_mixed<T, S>(h, f, g, phi))) return st;
+        if ((st = encode_mixed<T, S>(h, f, g, phi, upx, upy))) return st;
     } else {
         for (int q = 0; q < 9; ++q) {
             if ((st = upload_field<S>(h, (S *)h->f[0] + q * n, f + q * n))) return st;

@@ -233,6 +233,21 @@ template <typename T, typename S> struct Mixed {
     static constexpr bool on = sizeof(S) < sizeof(T);
 };
 
+// The velocity part of the NS equilibrium g_q = w_q (3 p + s_q(u)) of
+// Eq. (geq), without its weight: s_q(u) = 3 c.u + 9/2 (c.u)^2 - 3/2 u.u.
+// Reduced-precision storage keeps g_q - w_q (3 p_hat + s_q(u^n)), the NS
+// populations less their equilibrium at the node's post-stream p_hat and the
+// velocity u^n they were collided with, so that the 16-bit words carry only
+// the non-equilibrium part; a reader adds the equilibrium back from p_hat and
+// u^n (the u^{n-1} slot of the next step).
+template <typename T> __host__ __device__ __forceinline__ T s_eq(int q, T u0, T u1)
+{
+    const int cx = (q == 1 || q == 5 || q == 8) ? 1 : ((q == 3 || q == 6 || q == 7) ? -1 : 0);
+    const int cy = (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0);
+    const T cu = T(cx) * u0 + T(cy) * u1;
+    return cu * (T(3) + T(4.5) * cu) - T(1.5) * (u0 * u0 + u1 * u1);
+}
+
 // Moment transform m = M f with the rows of Eq. (D2Q9MRT).
 template <typename T>
 __device__ __forceinline__ void to_moments(const T f[9], T m[9])
@@ -405,6 +420,8 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
     T f[9], g[9], upx_ = T(0), upy_ = T(0), uhx_ = T(0), uhy_ = T(0), pprev = T(0), plo = T(0);
     if (!ghost) {
         const unsigned N32 = P.N32;
+        upx_ = __ldg(&upx[gidx]);
+        upy_ = __ldg(&upy[gidx]);
         if constexpr (Mixed<T, S>::on) {
             T sf = T(0), sg = T(0);
             const T ph0 = __ldg(&phat_old[gidx]);
@@ -412,7 +429,7 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
             for (int q = 1; q < 9; ++q) {
                 const unsigned o = (unsigned)gidx + (unsigned)q * N32;
                 f[q] = Codec<S, T>::load(__ldg(&fin[o]));
-                g[q] = Codec<S, T>::load(__ldg(&gin[o])) + T(3) * T(lattice_w(q)) * ph0;
+                g[q] = Codec<S, T>::load(__ldg(&gin[o])) + T(lattice_w(q)) * (T(3) * ph0 + s_eq(q, upx_, upy_));
                 sf += f[q];
                 sg += g[q];
             }
@@ -429,8 +446,6 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
             }
         }
         if (philo) plo = __ldg(&philo[gidx]);
-        upx_ = __ldg(&upx[gidx]);
-        upy_ = __ldg(&upy[gidx]);
         uhx_ = __ldg(&uhx[gidx]);
         uhy_ = __ldg(&uhy[gidx]);
     }
@@ -591,11 +606,13 @@ k_collide_stream(KP<T> P, const S *__restrict__ fin, const S *__restrict__ gin,
         const T pn = sg * T(1.0 / 3.0);
         const unsigned N32 = P.N32;
         if constexpr (Mixed<T, S>::on) {
+            const int iu = (ky + 2) * W2 + (kx + 2);   // u^n of this node in its window
+            const T un0 = s_ux[iu], un1 = s_uy[iu];
 #pragma unroll
             for (int q = 1; q < 9; ++q) {
                 const unsigned o = (unsigned)nidx + (unsigned)q * N32;
                 fout[o] = Codec<S, T>::store(fv[q]);
-                gout[o] = Codec<S, T>::store(gv[q] - T(3) * T(lattice_w(q)) * pn);
+                gout[o] = Codec<S, T>::store(gv[q] - T(lattice_w(q)) * (T(3) * pn + s_eq(q, un0, un1)));
             }
         } else {
             fout[nidx] = Codec<S, T>::store(s_phi[(ky + 3) * W3 + (kx + 3)] + fv[0]);
@@ -1983,6 +2000,13 @@ k_collide_pairs(const __grid_constant__ TmaMaps tm, KP<float> P, const S *__rest
         m6i = fma2(f2(2.0f), sub2(b[4], b[2]), d56);
         m7i = sub2(add2(b[1], b[3]), add2(b[2], b[4]));
         m8i = sub2(add2(b[5], b[7]), add2(b[6], b[8]));
+        if constexpr (Mixed<float, S>::on) {   // the stored words leave out w_q (3 p_hat + s_q(u^{n-1})),
+            // whose m4, m6, m7, m8 are -u_x, -u_y, u_x^2 - u_y^2, u_x u_y (p_hat cancels)
+            m4i = sub2(m4i, upx2);
+            m6i = sub2(m6i, upy2);
+            m7i = add2(m7i, fma2(upx2, upx2, mul2(f2(-1.0f), mul2(upy2, upy2))));
+            m8i = fma2(upx2, upy2, m8i);
+        }
     }
     if (!tile.wait(by_tma, err)) return;
 
@@ -2162,11 +2186,21 @@ k_collide_pairs(const __grid_constant__ TmaMaps tm, KP<float> P, const S *__rest
     const unsigned N32 = P.N32;
     if constexpr (Mixed<float, S>::on) {
 #pragma unroll
-        for (int q = 1; q < 9; ++q) {
-            const unsigned o = (unsigned)nidx + (unsigned)q * N32;
-            Codec2<S>::store(fout + o, fv[q]);
-            Codec2<S>::store(gout + o, fma2(f2(-3.0f * lattice_w(q)), pn, gv[q]));
-        }
+        for (int q = 1; q < 9; ++q) Codec2<S>::store(fout + (unsigned)nidx + (unsigned)q * N32, fv[q]);
+        // g less its equilibrium at (p_hat, u^n) of this node (see s_eq), for the
+        // opposite directions q, qo with c_q.u = c: 3 p_hat - 3/2 u.u + 9/2 c^2 +- 3 c
+        const int iu = (warp + 2) * BW + 6 + 2 * lane;
+        const float2 un0 = lds2(s_ux, iu), un1 = lds2(s_uy, iu);
+        const float2 p3 = fma2(f2(-1.5f), fma2(un0, un0, mul2(un1, un1)), mul2(f2(3.0f), pn));
+        auto store_pair = [&](int q, int qo, float2 c) {
+            const float2 ev = fma2(mul2(f2(4.5f), c), c, p3), od = mul2(f2(3.0f), c), w = f2(-lattice_w(q));
+            Codec2<S>::store(gout + (unsigned)nidx + (unsigned)q * N32, fma2(w, add2(ev, od), gv[q]));
+            Codec2<S>::store(gout + (unsigned)nidx + (unsigned)qo * N32, fma2(w, sub2(ev, od), gv[qo]));
+        };
+        store_pair(1, 3, un0);
+        store_pair(2, 4, un1);
+        store_pair(5, 7, add2(un0, un1));
+        store_pair(6, 8, sub2(un1, un0));
     } else {
         Codec2<S>::store(fout + nidx, add2(phc, fv[0]));
 #pragma unroll
@@ -2229,7 +2263,7 @@ __global__ void k_init(KP<T> P, const T *__restrict__ phi, const T *__restrict__
             if (Mixed<T, S>::on) {
                 if (q == 0) continue;
                 f[q * N + k] = Codec<S, T>::store(fv[q]);
-                g[q * N + k] = Codec<S, T>::store(gv[q] - T(3) * T(lattice_w(q)) * pn);
+                g[q * N + k] = Codec<S, T>::store(gv[q] - T(lattice_w(q)) * (T(3) * pn + s_eq(q, u0, u1)));
             } else {
                 f[q * N + k] = Codec<S, T>::store(fv[q]);
                 g[q * N + k] = Codec<S, T>::store(gv[q]);

@@ -1,13 +1,13 @@
 """Reduced-precision population storage (bf16 / fp16 words, FP32 arithmetic).
 
-Only the deviations from the rest equilibria are stored in 16 bits; the
-post-stream moments phi_bar = sum f and p_hat = cs^2 sum g stay in FP32, so
-the volume is conserved exactly as in the FP32 path.  The errors against the
-FP64 oracle are reported, and bounded with margin above their measured
-values: phi as FP32 (1e-5 after 200 steps at density ratios 10 and 1000),
-p and u 2e-3 of their maxima at ratio 10 (at ratio 1000 see the
-capillary-wave test).  The rising-bubble centroid must
-stay within 0.5 % of the bubble diameter of the FP32 run.
+The 16-bit words hold f_1..f_8 and the NS populations less their
+equilibrium at (p_hat, u^n) (Sec. III.B Eq. geq), so that they carry only the
+non-equilibrium part; the post-stream moments phi_bar = sum f and
+p_hat = cs^2 sum g stay in FP32, so the volume is conserved exactly as in the
+FP32 path.  The errors against the FP64 oracle after 200 steps are printed
+and bounded about 2.5x above their measured values (in each test's
+docstring).  The rising-bubble centroid must stay within 0.5 % of the bubble
+diameter of the FP32 run.
 """
 import numpy as np
 import pytest
@@ -26,6 +26,8 @@ def rel_err(a, b):
 
 @pytest.mark.parametrize("precision", MIXED)
 def test_static_drop_against_oracle(precision):
+    """Density ratio 10, 200 steps: phi 3.7e-7 (bf16) and 2.8e-8 (fp16) of
+    its maximum; p, u at most 7.2e-5 (bf16) and 1.3e-5 (fp16)."""
     prm, fields = inputs.static_drop(n=64, R=16.0)
     o = oracle.Sim(prm, *fields)
     g = lbm.Sim(prm, *fields, precision=precision)
@@ -35,7 +37,7 @@ def test_static_drop_against_oracle(precision):
     errs = {n: rel_err(a, b) for n, a, b in zip(("phi", "p", "ux", "uy"), g.fields(), o.fields())}
     print(precision, errs)
     assert errs["phi"] <= 1e-5
-    assert max(errs["p"], errs["ux"], errs["uy"]) <= 2e-3
+    assert max(errs["p"], errs["ux"], errs["uy"]) <= (2e-4 if precision == "mix_bf16" else 4e-5)
     # the FP32 moments carry the volume: drift as in FP32 storage of phi
     assert abs(g.diagnostics()[0] - d0) <= 200 * fields[0].size * 2.0 ** -24
 
@@ -43,21 +45,21 @@ def test_static_drop_against_oracle(precision):
 @pytest.mark.parametrize("precision", MIXED)
 @pytest.mark.parametrize("n", [64, 66])
 def test_capillary_wave_walls_against_oracle(precision, n):
-    """Walls in y and density ratio 1000 (the benchmark workload, small).
-    Here p is a residual of the large density contrast: after 100 steps its
-    error is 7.4e-3 of max|p| with bf16 storage (8-bit significand), 1.2e-3
-    with fp16 and 0.6e-3 .. 0.9e-3 in FP32, the same whether the grid width
-    takes the node-pair kernels (64) or not (66); u stays within 1.4e-3."""
+    """Walls in y and density ratio 1000 (the benchmark workload, small),
+    200 steps, through the node-pair kernels (64) and the one-node ones (66).
+    Here p is a residual of the large density contrast: 5.6e-4 .. 7.3e-4 of
+    max|p| with bf16 words (8-bit significand), 7.4e-5 .. 9.3e-5 with fp16
+    (2.4e-5 .. 2.7e-5 in FP32); u at most 1.3e-4 (bf16) and 1.8e-5 (fp16)."""
     prm, fields = inputs.capillary_wave(n=n)
     o = oracle.Sim(prm, *fields)
     g = lbm.Sim(prm, *fields, precision=precision)
-    o.step(100)
-    g.step(100)
+    o.step(200)
+    g.step(200)
     errs = {k: rel_err(a, b) for k, a, b in zip(("phi", "p", "ux", "uy"), g.fields(), o.fields())}
     print(precision, n, errs)
     assert errs["phi"] <= 1e-5
-    assert errs["p"] <= (1.5e-2 if precision == "mix_bf16" else 3e-3)
-    assert max(errs["ux"], errs["uy"]) <= 3e-3
+    assert errs["p"] <= (2e-3 if precision == "mix_bf16" else 2.5e-4)
+    assert max(errs["ux"], errs["uy"]) <= (3e-4 if precision == "mix_bf16" else 5e-5)
 
 
 @pytest.mark.parametrize("precision", MIXED)
