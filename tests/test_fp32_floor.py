@@ -1,0 +1,108 @@
+"""How much FP32 rounding of the state moves the exact (FP64 oracle) trajectory.
+
+These tests measure the problem, not an implementation. They give the reading
+behind the FP32 tolerances of the GPU parity tests at density ratio 1000.
+
+At that ratio the kinematic pressure p = p'/rho (Sec. II.B, below Eq. reformNS)
+jumps by the ratio across the interface. The NS source F/rho - grad p (Sec.
+III.B Eq. Gi), with F_p = -p grad rho and rho(phi) of Eq. (rho), is then a
+small difference of large terms in the light phase, where p'/rho is largest.
+So the order parameter phi is the sensitive input. Near phi = -1 a single
+float resolves phi to 6e-8, and d rho / d phi = (rho_H - rho_L)/2 multiplies
+that by about 500.
+
+Three measurements on the oracle, 200 steps:
+- The state rounded to FP32 after every step, phi kept in FP64: populations
+  f and g, p, u, u_hat and u^{n-1}. p and u move by at most a few 1e-6 of
+  their maxima, so FP32 storage of these leaves the 1e-5 target reachable.
+- The same with phi rounded too. At ratio 1000, p moves by about 3.5e-4;
+  at ratio 10, by about 1e-6. This is why the FP32 GPU path carries phi as a
+  pair of floats.
+- A single relative perturbation of phi^0 by 2^-24 (one FP32 unit roundoff),
+  all arithmetic FP64 afterwards. At ratio 1000 this moves u by more than
+  1e-5 of its maximum. So FP32 arithmetic on phi-derived quantities, such as
+  grad phi and mu, which rounds at that size every step, has a floor near the
+  1e-5 target. The response is linear: a 2^-30 perturbation moves the fields
+  64 times less.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_02459_gb300 import inputs
+
+KEYS = ("f", "g", "phi", "p", "ux", "uy", "uhx", "uhy", "upx", "upy")
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def spread(ref, other):
+    return {n: rel(b, a) for n, a, b in zip(("phi", "p", "ux", "uy"), ref.fields(), other.fields())}
+
+
+def run_rounded(prm, fields, steps, keys):
+    """Oracle steps, with the state's planes in `keys` rounded to FP32 after each step."""
+    o = oracle.Sim(prm, *fields)
+    for _ in range(steps):
+        o.step(1)
+        st = o.state()
+        st.update(zip(("phi", "p", "ux", "uy"), o.fields()))
+        for k in keys:
+            st[k] = st[k].astype(np.float32).astype(np.float64)
+        o.set_state(*[st[k] for k in KEYS])
+    return o
+
+
+def perturbed(fields, eps, seed=7):
+    r = np.random.default_rng(seed).uniform(-1.0, 1.0, fields[0].shape)
+    return (fields[0] * (1.0 + eps * r),) + tuple(fields[1:])
+
+
+@pytest.fixture(scope="module")
+def capillary_1000():
+    prm, fields = inputs.capillary_wave(n=64)
+    ref = oracle.Sim(prm, *fields)
+    ref.step(200)
+    return prm, fields, ref
+
+
+def test_fp32_storage_except_phi_is_not_the_floor(capillary_1000):
+    prm, fields, ref = capillary_1000
+    o = run_rounded(prm, fields, 200, [k for k in KEYS if k != "phi"])
+    s = spread(ref, o)
+    print("state in FP32, phi kept:", s)          # p 1.2e-6, u 1.4e-7
+    assert max(s["p"], s["ux"], s["uy"]) <= 5e-6
+
+
+def test_single_float_phi_at_density_ratio_1000(capillary_1000):
+    prm, fields, ref = capillary_1000
+    s = spread(ref, run_rounded(prm, fields, 200, KEYS))
+    print("state and phi in FP32, ratio 1000:", s)   # p 3.5e-4, u 1e-4
+    assert s["p"] >= 1e-4
+    prm10, fields10 = inputs.static_drop(n=64, R=16.0)
+    ref10 = oracle.Sim(prm10, *fields10)
+    ref10.step(200)
+    s10 = spread(ref10, run_rounded(prm10, fields10, 200, KEYS))
+    print("state and phi in FP32, ratio 10:", s10)   # p 1.4e-6, u 6.8e-6
+    assert s10["p"] <= 5e-6 and max(s10["ux"], s10["uy"]) <= 2e-5
+
+
+def test_unit_roundoff_of_phi0_moves_u_past_1e5_at_ratio_1000():
+    prm, fields = inputs.capillary_wave(n=64)
+    sims = [oracle.Sim(prm, *f) for f in (fields, perturbed(fields, 2.0 ** -24), perturbed(fields, 2.0 ** -30))]
+    for o in sims:
+        o.step(25)
+    s24, s30 = spread(sims[0], sims[1]), spread(sims[0], sims[2])
+    print("2^-24:", s24, "2^-30:", s30)              # u 4.3e-5 / 3.8e-5, p 9.3e-6
+    assert max(s24["ux"], s24["uy"]) >= 2e-5
+    for n in ("p", "ux", "uy"):                       # linear response
+        assert 0.8 * 64 <= s24[n] / s30[n] <= 1.2 * 64, n
+    prm10, fields10 = inputs.static_drop(n=64, R=16.0)
+    a, b = oracle.Sim(prm10, *fields10), oracle.Sim(prm10, *perturbed(fields10, 2.0 ** -24))
+    a.step(25)
+    b.step(25)
+    s10 = spread(a, b)
+    print("ratio 10, 2^-24:", s10)                    # u 1.3e-6
+    assert max(s10["p"], s10["ux"], s10["uy"]) <= 4e-6

@@ -15,8 +15,11 @@ ratio across the interface, where F_p = -p grad rho and grad p nearly cancel
 in the NS source (Eq. Gi), and the FP32 rounding of grad phi and of the
 surface-tension tensor kappa(|grad phi|^2 I - grad phi grad phi) enters that
 residual amplified by the jump: p measures 2.4e-5 .. 2.7e-5 (64^2, 66^2
-capillary waves, 200 steps) and 5.8e-5 (256x512 bubble, 200 steps, its heavy
-phase nearly inviscid), u <= 4e-5.
+capillary waves, 200 steps) and 5.8e-5 (256x512 bubble, 200 steps), u <= 4e-5.
+These sit at the problem's own floor: a single relative change of phi^0 by
+2^-24, followed by exact arithmetic, moves u by 1.3e-5 (66^2 wave) and p by
+4.6e-4 (256x512 bubble) after 200 steps, while FP32 storage of every plane
+but phi moves p and u by at most 2e-6 (tests/test_fp32_floor.py).
 """
 import math
 
