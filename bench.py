@@ -488,7 +488,10 @@ def run_ours(args):
                 adjoint_run(cprm, cfields, 2)   # compiles the walled tape's kernels
             cfw, crv, ceng = adjoint_run(cprm, cfields, 44)
             sweep.append({"n": gn, "forward_s": round(cfw, 4), "reverse_s": round(crv, 4),
-                          "adjoint_over_forward": round(crv / cfw, 2), "engine": engines.get(ceng, "none")})
+                          "adjoint_over_forward": round(crv / cfw, 2), "engine": engines.get(ceng, "none"),
+                          # node updates per second of the reverse sweep, and of forward + reverse
+                          "reverse_MLUPS": round(gn * gn * 44 / crv / 1e6, 1),
+                          "gradient_MLUPS": round(gn * gn * 44 / (cfw + crv) / 1e6, 1)})
         variants["adjoint_sweep"] = {"workload": "capillary wave n x n, walls in y, rho ratio 1000, 44 steps, "
                                                  f"checkpoint every {aevery}, FP32 forward and reverse sweep",
                                      "grids": sweep}

@@ -1,5 +1,5 @@
-"""Failure detection on host-injected faults (SURVEY-planned checks of the
-step's state; the paper has no counterpart).
+"""Failure detection on host-injected faults (checks of the step's state; the
+paper has no counterpart).
 
 Faults are planted from the host as field values -- a NaN or an Inf in p or
 u, phi outside [-1, 1] -- through lbm_set_fields; nothing here faults, traps
