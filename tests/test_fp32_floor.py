@@ -106,3 +106,16 @@ def test_unit_roundoff_of_phi0_moves_u_past_1e5_at_ratio_1000():
     s10 = spread(a, b)
     print("ratio 10, 2^-24:", s10)                    # u 1.3e-6
     assert max(s10["p"], s10["ux"], s10["uy"]) <= 4e-6
+
+
+def test_unit_roundoff_of_phi0_after_200_steps_on_the_66_wave():
+    """After the 200 steps of the parity tests, one FP32 unit roundoff of
+    phi^0 moves u on the 66^2 capillary wave (ratio 1000) by more than 1e-5
+    of its maximum (measured 1.22e-5 and 1.26e-5), with exact arithmetic."""
+    prm, fields = inputs.capillary_wave(n=66)
+    a, b = oracle.Sim(prm, *fields), oracle.Sim(prm, *perturbed(fields, 2.0 ** -24))
+    a.step(200)
+    b.step(200)
+    s = spread(a, b)
+    print(s)
+    assert min(s["ux"], s["uy"]) > 1e-5
