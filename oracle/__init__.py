@@ -51,6 +51,7 @@ def lib():
         L.orc_step_ch.restype = C.c_int
         L.orc_fields.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
         L.orc_state.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.orc_dynamic_pressure.argtypes = [C.c_void_p, _dp]
         L.orc_set_state.argtypes = [C.c_void_p] + [_dp] * 10
         L.orc_diagnostics.argtypes = [C.c_void_p, _dp]
         L.orc_last_picard_sweeps.restype = C.c_int
@@ -270,6 +271,12 @@ class Sim:
         phi, p, ux, uy = (np.empty(shp) for _ in range(4))
         lib().orc_fields(self._h, _ptr(phi), _ptr(p), _ptr(ux), _ptr(uy))
         return phi, p, ux, uy
+
+    def dynamic_pressure(self):
+        """p' = rho(phi) p, Sec. II.B (p = p'/rho), as a [ny, nx] array."""
+        out = np.empty((self.ny, self.nx))
+        lib().orc_dynamic_pressure(self._h, _ptr(out))
+        return out
 
     def state(self):
         shp = (self.ny, self.nx)

@@ -934,6 +934,15 @@ void orc_fields(const orc_sim *s, double *phi, double *p, double *ux, double *uy
     if (uy) memcpy(uy, s->uyf, N * sizeof(double));
 }
 
+/* Dynamic pressure p' = rho(phi) p at every node: the kinematic pressure of
+   the state is p = p'/rho (Sec. II.B, below Eq. reformNS), with rho(phi) of
+   Eq. (rho) as the step uses it (phi clamped to [-1,1]). */
+void orc_dynamic_pressure(const orc_sim *s, double *out)
+{
+    size_t N = (size_t)s->p.nx * s->p.ny;
+    for (size_t k = 0; k < N; ++k) out[k] = rho_of(&s->p, s->phi[k]) * s->pf_[k];
+}
+
 void orc_state(const orc_sim *s, double *f, double *g, double *uhx, double *uhy,
                double *upx, double *upy)
 {

@@ -88,6 +88,8 @@ int  orc_step(orc_sim *s, int n);
    TVD-RK3.  Returns 2 on a non-finite phi. */
 int  orc_step_ch(orc_sim *s, int n, const double *ux, const double *uy);
 void orc_fields(const orc_sim *s, double *phi, double *p, double *ux, double *uy);
+/* p' = rho(phi) p (the dynamic pressure) into out[ny][nx]. */
+void orc_dynamic_pressure(const orc_sim *s, double *out);
 void orc_state(const orc_sim *s, double *f, double *g, double *uhx, double *uhy,
                double *upx, double *upy);
 void orc_set_state(orc_sim *s, const double *f, const double *g, const double *phi,

@@ -418,7 +418,11 @@ def test_galilean_drop_translation():
 
 @pytest.mark.slow
 def test_laplace_law():
-    """Static drop: pressure jump (rho p) across the interface equals sigma/R (Sec. IV.C)."""
+    """Static drop: the jump of the dynamic pressure p' = rho p across the
+    interface equals sigma/R (Sec. IV.C). p' is the oracle's
+    orc_dynamic_pressure, so this also pins it: with rho_H and rho_L
+    swapped, or rho taken as 1, the heavy drop's jump would be off by the
+    density ratio."""
     n, R, sigma = 48, 12.0, 2e-3
     prm = inputs.base_params(rho_H=10.0, sigma=sigma)
     phi0 = inputs.drop(n, n, R, n / 2, n / 2, prm["W"])
@@ -430,11 +434,18 @@ def test_laplace_law():
     jumps = []
     for _ in range(8):
         s.step(50)
-        phi, p, _, _ = s.fields()
-        rho = 1 + 9 * (1 + np.clip(phi, -1, 1)) / 2
-        pp = rho * p
+        pp = s.dynamic_pressure()
         jumps.append(pp[r < R - 4].mean() - pp[r > R + 6].mean())
     assert abs(np.mean(jumps) / (sigma / R) - 1) < 0.08
+
+
+def test_dynamic_pressure_at_equal_densities_is_p():
+    """With rho_H = rho_L = 1, rho(phi) = 1 everywhere, so p' = p exactly."""
+    prm, fields = inputs.static_drop(n=24, R=6.0)
+    prm.update(rho_H=1.0, rho_L=1.0)
+    s = oracle.Sim(prm, *fields)
+    s.step(10)
+    assert np.array_equal(s.dynamic_pressure(), s.fields()[1])
 
 
 @pytest.mark.slow
