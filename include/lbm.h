@@ -164,6 +164,17 @@ lbm_status lbm_step_ch(lbm_handle *h, int n, const double *ux, const double *uy,
 lbm_status lbm_fields(lbm_handle *h, double *phi, double *p, double *ux, double *uy);
 
 /*
+ * lbm_dynamic_pressure -- the dynamic pressure p' = rho(phi) p into the host
+ * [ny][nx] double array pd (caller-owned).  The state's p is the kinematic
+ * pressure p'/rho (Sec. II.B, below Eq. reformNS); rho(phi) is Eq. (rho)
+ * with phi clamped to [-1, 1], as in the step.  The product is formed on the
+ * device in FP64 from phi (both floats of an FP32 handle's phi) and the
+ * filtered p.  LBM_ERR_ARG for a NULL handle or pd.  Synchronises the
+ * stream; like lbm_fields it reports a recorded device error.
+ */
+lbm_status lbm_dynamic_pressure(lbm_handle *h, double *pd);
+
+/*
  * lbm_fields_device -- same fields into caller-owned device buffers of
  * nx*ny elements; dtype 0 = double, 1 = float.  Asynchronous.
  */

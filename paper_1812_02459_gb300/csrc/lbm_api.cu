@@ -674,6 +674,36 @@ lbm_status download_phi(lbm_handle *h, double *dst)
     }
 }
 
+// Dynamic pressure p' = rho(phi) p at every node (Sec. II.B: the state's p is
+// the kinematic pressure p'/rho), with rho(phi) of Eq. (rho) and phi clamped
+// to [-1, 1] as in the step.  The reconstruction runs in FP64 from phi (the
+// float pair phi_hi + phi_lo of FP32 handles, lo NULL otherwise) and p.
+template <typename T>
+static __global__ void k_dynamic_pressure(const T *__restrict__ phi, const float *__restrict__ lo,
+                                          const T *__restrict__ p, double rhoH, double rhoL,
+                                          double *__restrict__ out, long long n)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        double c = (double)phi[k] + (lo ? (double)lo[k] : 0.0);
+        c = c < -1.0 ? -1.0 : (c > 1.0 ? 1.0 : c);
+        out[k] = (rhoH * (1.0 + c) * 0.5 + rhoL * (1.0 - c) * 0.5) * (double)p[k];
+    }
+}
+
+template <typename T>
+lbm_status dynamic_pressure_impl(lbm_handle *h, double *dst)
+{
+    const size_t n = (size_t)h->N;
+    const float *lo = sizeof(T) == sizeof(float) ? (const float *)h->philo : nullptr;
+    k_dynamic_pressure<T><<<(int)std::min<long long>((h->N + 255) / 256, 4096), 256, 0, h->stream>>>(
+        (const T *)phi_cur(h), lo, (const T *)h->pf, h->prm.rho_H, h->prm.rho_L, staging(h), h->N);
+    CK(h, cudaGetLastError(), "dynamic pressure");
+    CK(h, cudaMemcpyAsync(dst, staging(h), n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "download");
+    CK(h, cudaStreamSynchronize(h->stream), "download sync");
+    return LBM_OK;
+}
+
 template <typename T>
 lbm_status upload_field(lbm_handle *h, void *dst, const double *src)
 {
@@ -1073,6 +1103,15 @@ lbm_status lbm_fields(lbm_handle *h, double *phi, double *p, double *ux, double 
     if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
     lbm_status st =
         h->grid.precision == LBM_FP64 ? fields_impl<double>(h, phi, p, ux, uy) : fields_impl<float>(h, phi, p, ux, uy);
+    return st ? st : lbm_internal_poll_device_error(h);
+}
+
+lbm_status lbm_dynamic_pressure(lbm_handle *h, double *pd)
+{
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "NULL handle");
+    if (!pd) return fail(h, LBM_ERR_ARG, "pd must be non-NULL");
+    lbm_status st = h->grid.precision == LBM_FP64 ? dynamic_pressure_impl<double>(h, pd)
+                                                  : dynamic_pressure_impl<float>(h, pd);
     return st ? st : lbm_internal_poll_device_error(h);
 }
 

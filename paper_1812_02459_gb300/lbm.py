@@ -44,7 +44,8 @@ class LbmError(RuntimeError):
         self.status = status
 
 
-EXPORTS = ("lbm_create", "lbm_step", "lbm_step_ch", "lbm_fields", "lbm_fields_device", "lbm_set_fields",
+EXPORTS = ("lbm_create", "lbm_step", "lbm_step_ch", "lbm_fields", "lbm_dynamic_pressure", "lbm_fields_device",
+           "lbm_set_fields",
            "lbm_diagnostics", "lbm_diagnostics_async", "lbm_check", "lbm_set_check", "lbm_get_state", "lbm_set_state",
            "lbm_profile", "lbm_profile_read", "lbm_kernel_name", "lbm_kernel_variant",
            "lbm_field_sums_noalloc", "lbm_noalloc_last_error",
@@ -74,6 +75,8 @@ def load(path=None):
     L.lbm_step_ch.argtypes = [vp, C.c_int, _dp, _dp, _dp]
     L.lbm_fields.restype = C.c_int
     L.lbm_fields.argtypes = [vp, _dp, _dp, _dp, _dp]
+    L.lbm_dynamic_pressure.restype = C.c_int
+    L.lbm_dynamic_pressure.argtypes = [vp, _dp]
     L.lbm_fields_device.restype = C.c_int
     L.lbm_fields_device.argtypes = [vp, vp, vp, vp, vp, C.c_int]
     L.lbm_set_fields.restype = C.c_int
@@ -217,6 +220,17 @@ class Sim:
             raise ValueError("out must be four contiguous float64 arrays of shape (ny, nx)")
         self._ck(self._lib.lbm_fields(self._h, *[_ptr(a) for a in out]))
         return tuple(out)
+
+    def dynamic_pressure(self, out=None):
+        """p' = rho(phi) p as a host float64 [ny, nx] array (out: a caller-owned
+        contiguous float64 array to fill)."""
+        shp = (self.ny, self.nx)
+        if out is None:
+            out = np.empty(shp)
+        elif out.dtype != np.float64 or out.shape != shp or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous float64 array of shape (ny, nx)")
+        self._ck(self._lib.lbm_dynamic_pressure(self._h, _ptr(out)))
+        return out
 
     def fields_device(self, phi, p, ux, uy):
         """Copy into caller-owned device tensors (dtype of the handle's arithmetic)."""

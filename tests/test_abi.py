@@ -109,6 +109,7 @@ def test_null_handle_rejected_without_cuda():
     assert L.lbm_diagnostics_async(None, pd) == ARG
     assert L.lbm_check(None, C.c_double(0.01)) == ARG
     assert L.lbm_fields(None, pd, pd, pd, pd) == ARG
+    assert L.lbm_dynamic_pressure(None, pd) == ARG
     assert L.lbm_set_fields(None, pd, pd, pd, pd) == ARG
     assert L.lbm_adjoint_begin(None, 4, 2) == ARG
     assert L.lbm_adjoint_end(None, pd, pd, pd, pd) == ARG
