@@ -9,7 +9,9 @@ path carries phi as a pair of floats (phi_hi + phi_lo) and the step's change
 of phi as increments (the post-stream sum and the RK3 stages, Sec. III.A
 Eq. TVD-3order), so phi is not rounded to 24 bits near +-1, where rho(phi)
 of Sec. II.B Eq. (rho) would multiply the rounding by rho_H/rho_L.
-At density ratio 1000, p and u stay at most 1e-4 (phi at 1e-5): the kinematic
+At density ratio 1000, phi, u and the dynamic pressure p' = rho p stay within
+1e-5 on the capillary waves (test_capillary_wave_ratio_1000), and p and u
+stay at most 1e-4 everywhere: the kinematic
 pressure p = p'/rho (Sec. II.B, below Eq. reformNS) jumps by the density
 ratio across the interface, where F_p = -p grad rho and grad p nearly cancel
 in the NS source (Eq. Gi), and the FP32 rounding of grad phi and of the
