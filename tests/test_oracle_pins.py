@@ -305,18 +305,23 @@ def test_fd_rhs_vanishes_on_tanh_profile_at_fourth_order():
     assert errs[1] < errs[0] / 8.0         # fourth-order truncation (ideal 16x)
 
 
-def test_flux_correction_removes_normal_diffusion():
+@pytest.mark.parametrize("axis", ["y", "x"])
+def test_flux_correction_removes_normal_diffusion(axis):
     """q = -M (grad mu . n) n cancels the normal part of the CH diffusion flux
     (Sec. II.A): a 1-D non-equilibrium profile then barely evolves, unlike the
-    original CH equation (q off) which diffuses it toward equilibrium."""
+    original CH equation (q off) which diffuses it toward equilibrium. Run
+    along y and along x, so that each component of q is checked."""
     ny, nx = 48, 4
     y = np.arange(ny, dtype=float)
     phi0 = np.repeat(np.tanh(2 * (y - 24) / 8.0)[:, None], nx, 1)   # wider than W = 4
-    z = np.zeros((ny, nx))
+    if axis == "x":
+        phi0 = np.ascontiguousarray(phi0.T)
+    z = np.zeros_like(phi0)
     change = {}
     for fc in (1, 0):
+        walls = dict(periodic_y=0) if axis == "y" else dict(periodic_x=0)
         prm = inputs.base_params(lam=0.0, flux_correction=fc, sigma=1e-2, rho_H=1.0,
-                                 rho_L=1.0, periodic_y=0)
+                                 rho_L=1.0, **walls)
         s = oracle.Sim(prm, phi0, z, z, z)
         s.step(200)
         change[fc] = np.abs(s.fields()[0] - phi0).max()
@@ -384,18 +389,20 @@ def test_shear_wave_viscous_decay(order):
     assert abs(rate / expect - 1) < 6e-3
 
 
-def test_hydrostatic_pressure_gradient():
-    """Single fluid between walls under gravity: grad p = g (kinematic pressure)."""
+@pytest.mark.parametrize("rho_ref", [0.0, 2.5])
+def test_hydrostatic_pressure_gradient(rho_ref):
+    """Single fluid (rho = 5) between walls under gravity: the kinematic
+    pressure balances F_g = (rho - rho_ref) g, so grad p = (1 - rho_ref/rho) g."""
     nx, ny = 4, 24
     g = -1e-5
-    prm = inputs.base_params(rho_H=5.0, nu_H=0.1, nu_L=0.1, gy=g, periodic_y=0)
+    prm = inputs.base_params(rho_H=5.0, nu_H=0.1, nu_L=0.1, gy=g, g_rho_ref=rho_ref, periodic_y=0)
     phi0 = np.ones((ny, nx))
     z = np.zeros((ny, nx))
     s = oracle.Sim(prm, phi0, z, z, z)
     s.step(3000)
     _, p, ux, uy = s.fields()
     slope = np.polyfit(np.arange(4, ny - 4), p[4:ny - 4, 0], 1)[0]
-    assert abs(slope / g - 1) < 1e-2
+    assert abs(slope / ((1 - rho_ref / 5.0) * g) - 1) < 1e-2
     assert np.abs(uy).max() < 1e-3 * abs(g) * ny * ny
 
 
