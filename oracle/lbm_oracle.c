@@ -38,8 +38,15 @@
  * against its 1-D steady solution; removal of normal diffusion by q; the
  * azimuthal acceleration Omega J_r that F_m = J.grad u alone gives a
  * non-equilibrium drop in rigid rotation.
+ * The dynamic pressure p' = rho p is pinned by the Laplace law, which takes
+ * its jump across a static drop.
  * The choice of u_hat inside the filtered-equilibrium reading above is a
  * reading, not a law, and has no pin beyond GPU-oracle parity.
+ * Parity unpinned by a law: the index order of u.grad u in the CH source's
+ * acceleration, and the odd mirror of u at walls in the velocity gradients
+ * and in the filter.  Slips planted there survive the pins
+ * (oracle/planted_mistakes.py); the comparison with the independent
+ * restatement in oracle/torch_ref.py catches them.
  */
 #include "lbm_oracle.h"
 
