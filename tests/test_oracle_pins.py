@@ -614,3 +614,18 @@ def test_layered_channel_with_moment_strain():
         test_layered_channel_viscous_stress(0.0)
     finally:
         inputs.base_params = orig
+
+
+def test_planted_mistake_anchors_present():
+    """Every slip of oracle/planted_mistakes.py still names text that occurs
+    exactly once in the oracle, so the campaign follows the source."""
+    import importlib.util
+    here = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("planted_mistakes",
+                                                  os.path.join(here, "oracle", "planted_mistakes.py"))
+    pm = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(pm)
+    src = open(os.path.join(here, "oracle", "lbm_oracle.c")).read()
+    assert len(pm.MISTAKES) >= 30
+    for name, old, new in pm.MISTAKES:
+        assert src.count(old) == 1 and old != new, name
