@@ -42,9 +42,10 @@
  * its jump across a static drop.
  * The choice of u_hat inside the filtered-equilibrium reading above is a
  * reading, not a law, and has no pin beyond GPU-oracle parity.
- * Parity unpinned by a law: the index order of u.grad u in the CH source's
- * acceleration, and the odd mirror of u at walls in the velocity gradients
- * and in the filter.  Slips planted there survive the pins
+ * A uniform phi in a steady rotation staying uniform pins the acceleration
+ * of the CH source.
+ * Parity unpinned by a law: the odd mirror of u at walls in the velocity
+ * gradients and in the filter.  Slips planted there survive the pins
  * (oracle/planted_mistakes.py); the comparison with the independent
  * restatement in oracle/torch_ref.py catches them.
  */

@@ -59,6 +59,7 @@ MISTAKES = [
  ("Picard: F/rho for F/(2 rho)", "unx[k] = jx[k] + Fx / (2.0 * F.rho[k]);", "unx[k] = jx[k] + Fx / (F.rho[k]);"),
  ("p_hat without cs2", "phibar[k] = sp; phat[k] = CS2 * sgv;", "phibar[k] = sp; phat[k] = sgv;"),
  ("a: u.grad u transposed", "double ax = (ux - s->upx[k]) + ux * dxux[k] + uy * dyux[k];", "double ax = (ux - s->upx[k]) + ux * dxux[k] + uy * dxuy[k];"),
+ ("a: u.grad u dropped", "double ay = (uy - s->upy[k]) + ux * dxuy[k] + uy * dyuy[k];", "double ay = (uy - s->upy[k]);"),
  ("rho(phi): densities swapped", "return p->rho_H * (1.0 + c) / 2.0 + p->rho_L * (1.0 - c) / 2.0;", "return p->rho_L * (1.0 + c) / 2.0 + p->rho_H * (1.0 - c) / 2.0;"),
  ("viscosity: nu_H and nu_L swapped", "return p->rho_H * p->nu_H * (1.0 + c) / 2.0 + p->rho_L * p->nu_L * (1.0 - c) / 2.0;", "return p->rho_H * p->nu_L * (1.0 + c) / 2.0 + p->rho_L * p->nu_H * (1.0 - c) / 2.0;"),
  ("u gradients even at walls", "orc_grad_iso(q->nx, q->ny, q->periodic_x, q->periodic_y, -1, ux, dxux, dyux);", "orc_grad_iso(q->nx, q->ny, q->periodic_x, q->periodic_y, +1, ux, dxux, dyux);"),
@@ -82,7 +83,9 @@ def _try(d, mistake, original):
     with open(os.path.join(d, "oracle", "lbm_oracle.c"), "w") as f:
         f.write(original.replace(old, new))
     subprocess.run([sys.executable, "oracle/build.py", "--force"], cwd=d, check=True, capture_output=True)
-    r = subprocess.run([sys.executable, "-m", "pytest", *PINS, "-m", "not gpu", "-x", "-q", "-p", "no:cacheprovider"],
+    # the anchor check of this list fails on any planted copy by construction
+    r = subprocess.run([sys.executable, "-m", "pytest", *PINS, "-m", "not gpu", "-x", "-q", "-p", "no:cacheprovider",
+                        "--deselect", "tests/test_oracle_pins.py::test_planted_mistake_anchors_present"],
                        cwd=d, capture_output=True, text=True)
     failed = [l for l in r.stdout.splitlines() if l.startswith("FAILED")]
     return name, r.returncode != 0, failed[0] if failed else ""

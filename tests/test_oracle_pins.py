@@ -629,3 +629,43 @@ def test_planted_mistake_anchors_present():
     assert len(pm.MISTAKES) >= 30
     for name, old, new in pm.MISTAKES:
         assert src.count(old) == 1 and old != new, name
+
+
+def test_ch_source_keeps_uniform_phi_in_rotation():
+    """The CH source F_i (Sec. III.A Eq. Fi) carries a = d_t u + u.grad u.
+    In the LBE's first-order error, (tau_f - 1/2) div(phi (d_t u + u.grad u)
+    - phi a), it cancels the acceleration term. So a uniform phi in a steady,
+    divergence-free rotation stays uniform, as the CH equation requires:
+    d_t phi = -phi div u = 0. The flow is a rigid rotation with a smooth
+    envelope, started with the kinematic pressure in centripetal balance,
+    dp/dr = u_theta^2 / r, so that no transient compresses it; lambda = 0 and
+    q off, so the FD step leaves a uniform phi alone. A wrong a (for instance
+    u.grad u with its indices transposed, which turns the centripetal
+    acceleration outward) leaves a source of order
+    4 (tau_f - 1/2) phi Omega^2 per step; the range of phi must stay below
+    that term's accumulation over the run."""
+    n, Om, T, phi_u = 64, 5e-3, 200, 0.5
+    prm = inputs.base_params(rho_H=1.0, rho_L=1.0, nu_H=0.01, nu_L=0.01, sigma=0.01, M=0.1, lam=0.0,
+                             flux_correction=0, filter_order=0)
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    X, Y = x - n / 2, y - n / 2
+    r = np.hypot(X, Y)
+
+    def envelope(s):
+        e = np.clip((26 - s) / 8.0, 0, 1)
+        return e * e * (3 - 2 * e)
+
+    env = envelope(r)
+    ux0, uy0 = -Om * Y * env, Om * X * env
+    sg = np.linspace(0, 50, 20001)
+    ut = Om * sg * envelope(sg)
+    dpdr = np.where(sg > 0, ut * ut / np.maximum(sg, 1e-12), 0.0)
+    P = np.concatenate([[0.0], np.cumsum(0.5 * (dpdr[1:] + dpdr[:-1]) * (sg[1] - sg[0]))])
+    p0 = np.interp(r, sg, P)
+    s = oracle.Sim(prm, np.full((n, n), phi_u), p0 - p0.mean(), ux0, uy0)
+    s.step(T)
+    phi = s.fields()[0]
+    tau_f = 0.5 + prm["M"] / (prm["eta"] * CS2)
+    slip = 4 * (tau_f - 0.5) * phi_u * Om * Om * T       # 1.5e-3
+    print("range of phi", phi.max() - phi.min(), "slip scale", slip)   # 9.3e-4
+    assert phi.max() - phi.min() < slip
